@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""bench.py -- the MASK hot path (multilevel k-means build + top-down k-NN
+query) on GB300, one JSON line on stdout.
+
+A step is one pass of the whole hot path over one batch of synthetic input:
+mask_build over the points (k-means++ seeding and Lloyd iterations at every
+level, membership lists, cluster-major layout), then mask_query of the query
+batch, then the index is freed.  Inputs are resident in HBM when the timed
+region starts (2.56 GB of points: larger than L2, so no flush is needed).
+
+Workload (default "dense10m"): 10,000,000 points x 64 fp32 from 1,000
+anisotropic Gaussian blobs (covariance eigenvalues log-uniform in [0.1, 10],
+Zipf(1.1) blob weights), index 32,768 / 1,024 / 32 centroids with 15 Lloyd
+iterations per level, 10,000 queries from the same mixture, k = 10, probes
+8 / 4 / 2 (finest level first).
+
+value = queries answered / device time of the query phase (queries/s), with
+the build time, batch latency percentiles and recall@10 beside it.
+Multi-GPU (torchrun): every rank builds and queries its own partition (an
+independent index per GPU, as in the paper's distributed design, §3.4); no
+data crosses ranks; timing is the max over ranks ("weak" scaling).
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload, on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s at recall@10>=0.95, p50/p99 latency, build s; %roofline vs FP32 path"
+
+WORKLOADS = {
+    "dense10m": dict(n=10_000_000, d=64, blobs=1000, kind="anisotropic", k_per_level=[32768, 1024, 32],
+                     iters=15, nq=10_000, k=10, probes=[8, 4, 2],
+                     desc="10M x 64 fp32, 1000 anisotropic blobs (eig log-U[0.1,10], Zipf 1.1), "
+                          "index 32768/1024/32, 15 Lloyd iters, 10k queries, k=10, probes 8/4/2"),
+    "small": dict(n=20_000, d=16, blobs=10, kind="isotropic", k_per_level=[200, 20], iters=20,
+                  nq=1_000, k=10, probes=[3, 3],
+                  desc="20k x 16 fp32, 10 isotropic blobs (sigma 1), index 200/20, 20 Lloyd iters, "
+                       "1k queries, k=10, probes 3/3"),
+}
+
+# Oracle sample for the CPU baseline: the first n_s points of the same data,
+# with the per-query candidate volume kept (~305 points per leaf cluster,
+# ~32 children per parent, the same leaf probes).
+CPU_SAMPLE = {
+    "dense10m": dict(n=100_000, k_per_level=[328, 10], probes=[8, 4], nq=1000),
+    "small": dict(n=20_000, k_per_level=[200, 20], probes=[3, 3], nq=1000),
+}
+REF_SAMPLE = {
+    "dense10m": dict(n=50_000, k_per_level=[164, 5], probes=[8, 4], nq=1000),
+    "small": dict(n=20_000, k_per_level=[200, 20], probes=[3, 3], nq=1000),
+}
+
+# FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (maximum SM clock).
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_data(w, rank=0):
+    from paper_2208_02734_gb300 import synth
+    if w["kind"] == "anisotropic":
+        mix = synth.AnisotropicMixture(d=w["d"], n_blobs=w["blobs"], seed=0)
+    else:
+        mix = synth.IsotropicMixture(d=w["d"], n_blobs=w["blobs"], seed=0)
+    X = mix.sample(w["n"], seed=2 * rank)
+    Q = mix.sample(w["nq"], seed=2 * rank + 1)
+    return X, Q
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def source_hash(name):
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2208_02734_gb300", "csrc", name), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 5 and cells[0] == kernel and cells[1] == workload:
+            try:
+                src, sha, val = cells[2], cells[3], float(cells[4])
+            except ValueError:
+                continue
+            return val if source_hash(src) == sha else None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                smax.append(float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ recall
+
+def exact_knn_fp64(Xd, Qs, k, chunk=1 << 20):
+    """Exact k-NN of a few queries in FP64 on the device (torch matmul):
+    ground truth for recall@k only -- evaluation, not part of the timed path."""
+    import torch
+    q = Qs.double()
+    qn = (q * q).sum(1, keepdim=True)
+    best_d = torch.full((q.shape[0], 0), float("inf"), dtype=torch.float64, device=q.device)
+    best_i = torch.zeros((q.shape[0], 0), dtype=torch.int64, device=q.device)
+    for c0 in range(0, Xd.shape[0], chunk):
+        x = Xd[c0:c0 + chunk].double()
+        dd = (qn - 2.0 * q @ x.T + (x * x).sum(1)[None, :]).clamp_min_(0)
+        v, i = torch.topk(dd, min(k, dd.shape[1]), dim=1, largest=False)
+        best_d = torch.cat([best_d, v], 1)
+        best_i = torch.cat([best_i, i + c0], 1)
+        best_d, o = torch.topk(best_d, min(k, best_d.shape[1]), dim=1, largest=False)
+        best_i = torch.gather(best_i, 1, o)
+    return best_i, best_d
+
+
+def recall_at_k(Xd, Qd, ids, k, sample=200):
+    """recall@k on `sample` queries: a returned id is a hit when its exact
+    distance is within the true k-th distance (x (1 + 1e-5) for ties)."""
+    import torch
+    sel = torch.arange(0, Qd.shape[0], max(1, Qd.shape[0] // sample), device=Qd.device)[:sample]
+    Qs = Qd[sel]
+    _, gt_d = exact_knn_fp64(Xd, Qs, k)
+    dk = gt_d[:, -1:]
+    got = ids[sel]
+    valid = got >= 0
+    xr = Xd[got.clamp_min(0)].double()
+    dist = ((xr - Qs.double()[:, None, :]) ** 2).sum(-1)
+    hits = (valid & (dist <= dk * (1 + 1e-5))).sum().item()
+    return hits / (len(sel) * k), int(len(sel))
+
+
+# --------------------------------------------------------- oracle (CPU) arms
+
+def cpu_baseline(X, Q, w, wname):
+    import oracle as O
+    s = CPU_SAMPLE[wname]
+    Xs, Qs = np.ascontiguousarray(X[: s["n"]]), np.ascontiguousarray(Q[: s["nq"]])
+    t0 = time.perf_counter()
+    idx = O.build(Xs, s["k_per_level"], iters=w["iters"], seed=0)
+    t1 = time.perf_counter()
+    idx.query(Qs, w["k"], s["probes"])
+    t2 = time.perf_counter()
+    return {"value": s["nq"] / (t2 - t1), "unit": "queries/s", "cores": O.max_threads(),
+            "kind": "oracle",
+            "sample": (f"first {s['n']} points of the same data, index "
+                       f"{'/'.join(map(str, s['k_per_level']))} ({w['iters']} Lloyd iters, "
+                       f"same points per leaf cluster), {s['nq']} queries, k={w['k']}, "
+                       f"probes {'/'.join(map(str, s['probes']))}; FP64; oracle build "
+                       f"{t1 - t0:.2f} s")}
+
+
+def run_reference(args, w, wname):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    s = REF_SAMPLE[wname]
+    X, Q = make_data(dict(w, n=s["n"], nq=s["nq"]), 0)
+    q_times, b_times = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        idx = O.build(X, s["k_per_level"], iters=w["iters"], seed=0)
+        t1 = time.perf_counter()
+        idx.query(Q, w["k"], s["probes"])
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            b_times.append(t1 - t0)
+            q_times.append(t2 - t1)
+    value = args.steps * s["nq"] / sum(q_times)
+    sample = (f"{s['n']} points x {w['d']} from the same mixture, index "
+              f"{'/'.join(map(str, s['k_per_level']))}, {w['iters']} Lloyd iters, {s['nq']} queries, "
+              f"k={w['k']}, probes {'/'.join(map(str, s['probes']))}; FP64 oracle on host cores")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * (sum(q_times) + sum(b_times)) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "build_s": statistics.mean(b_times),
+            "config": {"workload": w["desc"], "reference_sample": sample},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": O.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+
+KERNEL_KIND = {"assign_gemm": "alu", "assign_recheck": "alu", "scan_topk_leaf": "hbm",
+               "scan_topk_level": "hbm", "centroid_update": "hbm", "label_sort": "hbm",
+               "kmeanspp": "hbm"}
+KERNEL_SRC = {"assign_gemm": "assign.cu", "scan_topk_leaf": "query.cu",
+              "centroid_update": "kmeans.cu", "kmeanspp": "kmeans.cu", "label_sort": "kmeans.cu"}
+
+
+def run_ours(args, w, wname):
+    import torch
+    import torch.distributed as dist
+    from paper_2208_02734_gb300 import mask as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(vals):
+        t = torch.tensor(vals, dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.tolist()
+
+    M.load()
+    t_gen = time.perf_counter()
+    X, Q = make_data(w, rank)
+    log(f"[bench] data {X.shape} generated in {time.perf_counter() - t_gen:.1f} s")
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    kpl, probes, k = w["k_per_level"], w["probes"], w["k"]
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        idx = M.mask_build(Xd, kpl, w["iters"], seed=0)
+        ev[1].record(stream)
+        ids, dd = M.mask_query(idx, Qd, k, probes)
+        ev[2].record(stream)
+        idx.free()
+        return ids, dd, ev
+
+    for i in range(args.warmup):
+        t = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        log(f"[bench] warmup {i}: {time.perf_counter() - t:.2f} s")
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    M.mask_profile_reset()
+    M.mask_profile_enable(True)
+    sampler.start()
+    lc0 = M.mask_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    results = [step() for _ in range(args.steps)]
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = M.mask_launch_count() - lc0
+    clocks = sampler.stop()
+    M.mask_profile_enable(False)
+    build_ms = [r[2][0].elapsed_time(r[2][1]) for r in results]
+    query_ms = [r[2][1].elapsed_time(r[2][2]) for r in results]
+    total_ms = t_start.elapsed_time(t_end)
+    q_sum, tot = max_over_ranks([sum(query_ms), total_ms])
+    value = world * args.steps * w["nq"] / (q_sum / 1000.0)
+
+    kernels = {}
+    for name in KERNEL_KIND:
+        r = M.mask_profile_read(name)
+        if r is not None:
+            kernels[name] = {"launches": r[0], "ms": r[1], "work": r[2]}
+    recall, n_rec = recall_at_k(Xd, Qd, results[-1][0], k)
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Qh = torch.from_numpy(Q).pin_memory()
+        ke = max(1, min(args.steps, 2))
+        qt, bt = [], []
+        for i in range(1 + ke):
+            t0 = time.perf_counter()
+            idx = M.mask_build(Xh, kpl, w["iters"], seed=0)
+            t1 = time.perf_counter()
+            ids_h, d_h = M.mask_query(idx, Qh, k, probes)
+            t2 = time.perf_counter()
+            idx.free()
+            if i > 0:
+                bt.append(t1 - t0)
+                qt.append(t2 - t1)
+        qe, = max_over_ranks([sum(qt)])
+        e2e = {"value": world * ke * w["nq"] / qe, "unit": "queries/s",
+               "h2d_bytes_per_step": int(X.nbytes + Q.nbytes),
+               "d2h_bytes_per_step": int(ids_h.nbytes + d_h.nbytes),
+               "build_s": statistics.mean(bt), "steps": ke,
+               "note": "host-pinned points and queries in, host ids/dists out, wall clock"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = measured_peaks()
+    for name, kv in kernels.items():
+        if kv["ms"] <= 0:
+            continue
+        if KERNEL_KIND[name] == "alu":
+            kv["achieved_tflops"] = kv["work"] / (kv["ms"] / 1e3) / 1e12
+        else:
+            kv["achieved_gbs"] = kv["work"] / (kv["ms"] / 1e3) / 1e9
+    dom = max(kernels, key=lambda n: kernels[n]["ms"]) if kernels else None
+    roofline = None
+    if dom is not None:
+        kv = kernels[dom]
+        if KERNEL_KIND[dom] == "alu":
+            peak = FP32_ALU_TFLOPS
+            roofline = {"kernel": dom, "bound": "alu", "achieved": kv.get("achieved_tflops"),
+                        "peak": peak, "unit": "TFLOP/s",
+                        "frac": kv.get("achieved_tflops", 0) / peak,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                        "work_per_launch": kv["work"] / kv["launches"]}
+        else:
+            peak = peaks["hbm_gbs"]
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": kv.get("achieved_gbs"),
+                        "peak": peak, "unit": "GB/s", "frac": kv.get("achieved_gbs", 0) / peak,
+                        "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
+                        "work_per_launch": kv["work"] / kv["launches"]}
+        roofline["traffic"] = ncu_traffic(dom, wname) if dom in KERNEL_SRC else None
+        roofline["ms_share_of_step"] = kv["ms"] / max(1e-9, sum(build_ms) + sum(query_ms))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "n": w["n"], "d": w["d"], "k_per_level": kpl,
+                   "iters": w["iters"], "queries": w["nq"], "k": k, "probes": probes,
+                   "l2": "inputs larger than L2 (points 2.56 GB); no flush",
+                   "parallelism": f"independent index per GPU x{world}"},
+        "recall_at_10": recall, "recall_queries": n_rec,
+        "build_s": statistics.mean(build_ms) / 1e3,
+        "p50_ms": float(np.percentile(query_ms, 50)), "p99_ms": float(np.percentile(query_ms, 99)),
+        "latency_note": "device time of one 10k-query batch (query phase), over the timed steps",
+        "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
+        "clocks": clocks, "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(X, Q, w, wname)
+        except Exception as ex:  # report, do not hide, a baseline failure
+            line["cpu_baseline"] = {"error": repr(ex)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense10m")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, args.workload)
+    return run_ours(args, w, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * mask.h -- C ABI of the GB300 MASK library (libmask_gb300.so).
+ *
+ * MASK (Ortega, Algar, Martin de Diego, Moguerza, "Unconventional application
+ * of k-means for distributed approximate similarity search"):
+ *   - build (§3.1, Algorithm 1, global form): level by level, k-means++
+ *     seeding (§3.2) and Lloyd iterations (§2.4) over the items of the level
+ *     below; the centroids of one level are the data of the next.
+ *   - query (§3.3, Algorithm 2): distances from the query to the top level's
+ *     centroids, keep the nearest p; at each lower level keep the nearest p
+ *     among the children of the kept centroids; scan the points of the kept
+ *     leaf clusters and return the k nearest.
+ * Metric: Euclidean (§4.2).  Distances are returned SQUARED.
+ *
+ * Conventions for every entry point:
+ *   - Pointers are plain host or device pointers of the current CUDA device;
+ *     each is classified per call (cudaPointerGetAttributes).  Host inputs are
+ *     copied in and host outputs copied back before the call returns; with
+ *     device pointers only, a query is stream-ordered on `stream` and returns
+ *     without synchronising.
+ *   - Arrays are dense row-major with no padding: a [n x d] float array has
+ *     element (i, t) at i*d + t.
+ *   - The caller owns every buffer it passes.  The library owns the index
+ *     (device memory inside); it is released only by mask_free.
+ *   - Errors are returned as mask_status; nothing is thrown across the ABI.
+ *     mask_last_error() gives a message for the calling thread's last failure.
+ *   - Level numbering: arrays indexed by level are finest first (index 0 =
+ *     the centroids directly above the points).
+ *   - Random numbers: SplitMix64 (Steele, Lea & Flood 2014); the stream of
+ *     level lv starts at seed ^ (0x9E3779B97F4A7C15 * (lv + 1)); a uniform
+ *     draw is (next >> 11) * 2^-53.  The paper names no generator.
+ */
+#ifndef MASK_GB300_H
+#define MASK_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MASK_MAX_LEVELS 16
+
+typedef struct mask_index mask_index;
+
+/* A cudaStream_t; NULL is the legacy default stream. */
+typedef void *mask_stream;
+
+typedef enum {
+    MASK_OK = 0,
+    MASK_EINVAL = -1,       /* bad argument (sizes, k > items below, NULL) */
+    MASK_ENOMEM = -2,       /* device or host allocation failed */
+    MASK_ECUDA = -3,        /* a CUDA call or kernel launch failed */
+    MASK_ETIMEOUT = -4,     /* a bounded device-side wait ran out */
+    MASK_EUNSUPPORTED = -5  /* valid request this build does not implement */
+} mask_status;
+
+typedef enum {
+    MASK_FP32 = 0,     /* all distances in FP32 */
+    MASK_BF16 = 1,     /* BF16 distance GEMMs + exact FP32 re-rank */
+    MASK_FP8E4M3 = 2   /* FP8 e4m3 (per-row scales) + exact FP32 re-rank */
+} mask_precision;
+
+typedef struct {
+    int64_t n;                               /* indexed points */
+    int32_t d;                               /* dimension */
+    int32_t n_levels;
+    int32_t k_per_level[MASK_MAX_LEVELS];    /* finest first */
+    int32_t iters;                           /* Lloyd iterations per level */
+    int32_t sparse;                          /* built from CSR rows */
+    int64_t device_bytes;                    /* device memory the index holds */
+} mask_index_info;
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *mask_last_error(void);
+
+/*
+ * Build a multilevel k-means index over n dense points (§3.1, Algorithm 1,
+ * one group per level).
+ *   points       [n x d] float32.
+ *   k_per_level  host array [n_levels], finest first; 1 <= k_0 <= n and
+ *                1 <= k_l <= k_{l-1}; n_levels <= MASK_MAX_LEVELS.
+ *   iters        Lloyd iterations per level (>= 0): iters updates and
+ *                iters+1 assignments; ties go to the smallest centroid index;
+ *                an empty cluster keeps its centroid.
+ *   seed         RNG seed for k-means++ seeding (§3.2).  When n_in * k > 2^32
+ *                and 8k < n_in, seeding runs on 8k inputs drawn by a partial
+ *                Fisher-Yates shuffle.
+ *   out          receives the index (free with mask_free).
+ * Synchronises `stream` before returning.
+ */
+mask_status mask_build(const float *points, int64_t n, int32_t d,
+                       const int32_t *k_per_level, int32_t n_levels, int32_t iters,
+                       uint64_t seed, mask_stream stream, mask_index **out);
+
+/*
+ * As mask_build, for n sparse points in CSR form (the TF-IDF shape of §4.3):
+ *   row_ptr [n+1] int64, col [nnz] int32 (each in [0, d)), val [nnz] float32.
+ * Centroids are dense.  Returns MASK_EUNSUPPORTED if sparse support is not
+ * built in.
+ */
+mask_status mask_build_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                           int64_t n, int32_t d, const int32_t *k_per_level,
+                           int32_t n_levels, int32_t iters, uint64_t seed,
+                           mask_stream stream, mask_index **out);
+
+/*
+ * Approximate k-NN of nq dense queries (§3.3, Algorithm 2, p_l kept centroids
+ * per level instead of one).
+ *   queries   [nq x d] float32.
+ *   k         neighbours per query (1 <= k <= 1024).
+ *   probes    host array [n_levels], finest first; p_l >= 1, clamped to k_l.
+ *   precision MASK_FP32 (others: MASK_EUNSUPPORTED until built).
+ *   ids_out   [nq x k] int64 original point ids, ascending by (distance, id);
+ *             -1 where fewer than k points were reached.
+ *   dists_out [nq x k] float32 squared distances; +inf where ids_out is -1.
+ * Each query's result does not depend on the other queries in the batch.
+ */
+mask_status mask_query(const mask_index *index, const float *queries, int64_t nq,
+                       int32_t k, const int32_t *probes, mask_precision precision,
+                       int64_t *ids_out, float *dists_out, mask_stream stream);
+
+/* As mask_query, for CSR queries (row_ptr [nq+1], col [nnz], val [nnz]). */
+mask_status mask_query_csr(const mask_index *index, const int64_t *row_ptr,
+                           const int32_t *col, const float *val, int64_t nq, int32_t k,
+                           const int32_t *probes, mask_precision precision,
+                           int64_t *ids_out, float *dists_out, mask_stream stream);
+
+/* Release an index (NULL is ignored). */
+void mask_free(mask_index *index);
+
+/* Sizes of an index. */
+mask_status mask_index_get_info(const mask_index *index, mask_index_info *out);
+
+/*
+ * Copy one level of an index out (level 0 = finest).
+ *   centroids_out [k_level x d] float32 in k-means cluster order (may be NULL).
+ *   labels_out    [n_below] int32: the level's centroid of every item one level
+ *                 below (points for level 0), in item order (may be NULL).
+ *   chosen_out    [k_level] int64: the inputs k-means++ picked as initial
+ *                 centres, as indices into the level's inputs (may be NULL).
+ *   objective_out [iters+1] double: k-means objective sum ||x - c_label||^2
+ *                 after each assignment (may be NULL).
+ * Synchronises `stream`.
+ */
+mask_status mask_index_export_level(const mask_index *index, int32_t level,
+                                    float *centroids_out, int32_t *labels_out,
+                                    int64_t *chosen_out, double *objective_out,
+                                    mask_stream stream);
+
+/*
+ * Assemble an index from given centroids and labels instead of building it
+ * (used to query an index built elsewhere, e.g. loaded from disk).
+ *   points         [n x d] float32.
+ *   centroids[l]   [k_l x d] float32 (host array of n_levels pointers).
+ *   labels[l]      [n_below(l)] int32, each in [0, k_l) (host array of pointers).
+ * The structure (membership lists, cluster-major leaf layout) is derived on
+ * the device exactly as mask_build derives it.  Synchronises `stream`.
+ */
+mask_status mask_index_load(const float *points, int64_t n, int32_t d, int32_t n_levels,
+                            const int32_t *k_per_level, const float *const *centroids,
+                            const int32_t *const *labels, mask_stream stream,
+                            mask_index **out);
+
+/* ---- k-means steps (the build's kernels, callable on their own) -------- */
+
+/*
+ * k-means++ seeding (§3.2) of k centres from the n rows of X, with the
+ * random stream of `level` under `seed` (subsampling rule as in mask_build).
+ *   centroids_out [k x d] float32: copies of the chosen rows.
+ *   chosen_out    [k] int64 indices into X (may be NULL).
+ * Synchronises `stream`.
+ */
+mask_status mask_kmeanspp(const float *X, int64_t n, int32_t d, int32_t k, uint64_t seed,
+                          int32_t level, float *centroids_out, int64_t *chosen_out,
+                          mask_stream stream);
+
+/*
+ * Lloyd assignment half-step (§2.4): labels_out[i] = argmin_j ||x_i - c_j||^2,
+ * ties to the smallest j.  dist_out[i] (may be NULL) = the minimum squared
+ * distance, evaluated as sum_t (x_it - c_jt)^2 in FP32.
+ *   X [n x d], C [k x d] float32; labels_out [n] int32.
+ */
+mask_status mask_kmeans_assign(const float *X, int64_t n, int32_t d, const float *C,
+                               int32_t k, int32_t *labels_out, float *dist_out,
+                               mask_stream stream);
+
+/*
+ * Lloyd update half-step (§2.4): C_out[j] = mean of the rows of X with
+ * label j; an empty cluster copies C_prev[j].  counts_out [k] (may be NULL)
+ * receives the cluster sizes.  Sums are FP32, FP64 for clusters with more
+ * than 2^20 members.
+ */
+mask_status mask_kmeans_update(const float *X, int64_t n, int32_t d, const int32_t *labels,
+                               int32_t k, const float *C_prev, float *C_out,
+                               int64_t *counts_out, mask_stream stream);
+
+/* ---- observability ---------------------------------------------------- */
+
+/*
+ * Per-kernel device timing.  The paper reports wall-clock build and search
+ * times only (§4.2, Tables 3-6); these split the device time by kernel.
+ * While enabled, the library brackets its main kernels with CUDA events on
+ * the launching stream.  Region names: "assign_gemm", "assign_recheck",
+ * "label_sort", "centroid_update", "kmeanspp", "scan_topk_level",
+ * "scan_topk_leaf".  Off by default.
+ */
+void mask_profile_enable(int32_t on);
+
+/* Drop all recorded timings. */
+void mask_profile_reset(void);
+
+/*
+ * Totals for one region since the last reset: launches, summed device time
+ * in ms, summed algorithmic work (flop for "assign_gemm", bytes for the
+ * others).  Waits for the recorded events.  Returns 1, or 0 if nothing was
+ * recorded under that name.  Any output pointer may be NULL.
+ */
+int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,
+                          double *work);
+
+/* Kernel launches the library has issued since it was loaded. */
+int64_t mask_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MASK_GB300_H */

@@ -1,0 +1,194 @@
+// common.cuh -- internal declarations shared by the CUDA translation units of
+// libmask_gb300.so (not part of the C ABI; see include/mask.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+
+#include "mask.h"
+
+namespace mask {
+
+// ------------------------------------------------------------------ errors
+
+struct Error : std::runtime_error {
+    mask_status status;
+    Error(mask_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+[[noreturn]] void fail(mask_status s, const std::string &msg);
+
+// ------------------------------------------------------------- profiling
+
+// Counts one kernel launch (called by MASK_LAUNCHED at every launch site).
+void count_launch();
+
+// While profiling is enabled, brackets its scope with CUDA events on stream s
+// and books the elapsed device time and `work` (flop or bytes) under `name`.
+class ProfRegion {
+  public:
+    ProfRegion(const char *name, cudaStream_t s, double work);
+    ~ProfRegion();
+    ProfRegion(const ProfRegion &) = delete;
+    ProfRegion &operator=(const ProfRegion &) = delete;
+
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    double work_;
+    cudaEvent_t a_{}, b_{};
+    bool active_ = false;
+};
+
+#define MASK_CUDA(call)                                                             \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            ::mask::fail(e_ == cudaErrorMemoryAllocation ? MASK_ENOMEM : MASK_ECUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+#define MASK_LAUNCHED(what)                                                          \
+    do {                                                                             \
+        ::mask::count_launch();                                                      \
+        cudaError_t e_ = cudaGetLastError();                                         \
+        if (e_ != cudaSuccess)                                                       \
+            ::mask::fail(MASK_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define MASK_REQUIRE(cond, msg)                                   \
+    do {                                                          \
+        if (!(cond)) ::mask::fail(MASK_EINVAL, std::string(msg)); \
+    } while (0)
+
+// --------------------------------------------------------- device buffers
+
+// Stream-ordered scratch (cudaMallocAsync / cudaFreeAsync on one stream).
+template <class T>
+struct Scratch {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    Scratch() = default;
+    Scratch(size_t count, cudaStream_t st) { alloc(count, st); }
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    Scratch(Scratch &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    Scratch &operator=(Scratch &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    void alloc(size_t count, cudaStream_t st) {
+        release();
+        s = st;
+        n = count;
+        if (count) MASK_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    ~Scratch() { release(); }
+    T *get() const { return p; }
+};
+
+// Long-lived device array (cudaMalloc), owned by an index.
+template <class T>
+struct DevArray {
+    T *p = nullptr;
+    size_t n = 0;
+    DevArray() = default;
+    DevArray(const DevArray &) = delete;
+    DevArray &operator=(const DevArray &) = delete;
+    DevArray(DevArray &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevArray &operator=(DevArray &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) MASK_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevArray() { release(); }
+    T *get() const { return p; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// ------------------------------------------------------------- constants
+
+// Internal row stride: dimensions are zero-padded to a multiple of 8 floats
+// (32 bytes) so every row starts 16-byte aligned and splits into float4s.
+inline int padded_dim(int d) { return (d + 7) / 8 * 8; }
+
+// Lanes cooperating on one row: the largest power of two <= min(32, dp/4).
+inline int lanes_per_row(int dp) {
+    int c = dp / 4, l = 1;
+    while (l * 2 <= c && l * 2 <= 32) l *= 2;
+    return l;
+}
+
+constexpr uint64_t kNoKey = ~0ull;
+
+// ------------------------------------------------------ kernel launchers
+
+// kmeans.cu
+void pad_rows(const float *src, int64_t n, int d, float *dst, int dp, cudaStream_t s);
+void unpad_rows(const float *src, int64_t n, int dp, float *dst, int d, cudaStream_t s);
+void row_sqnorm(const float *X, int64_t n, int dp, float *out, cudaStream_t s);
+void max_reduce(const float *v, int64_t n, float *out, cudaStream_t s);
+template <class I>
+void gather_rows(const float *src, int dp, const I *idx, int64_t m, float *dst, cudaStream_t s);
+void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
+// k-means++ over the m rows of Xs; chosen[0] must be set; fills chosen[1..k)
+void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_dev,
+                    int64_t *chosen, cudaStream_t s);
+// counting sort of labels in [0,k): off[k+1] (int64), perm[n] (item ids by label)
+void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *perm,
+                cudaStream_t s);
+// per-cluster mean (write=true) and sum of squared distances to C_prev
+void centroid_update(const float *X, int dp, const int32_t *perm, const int64_t *off, int k,
+                     const float *C_prev, float *C_new, float *sse, bool write,
+                     cudaStream_t s);
+// dist[i] = ||x_i - c_{labels[i]}||^2, difference form
+void label_dist(const float *X, int64_t n, int dp, const float *C, const int32_t *labels,
+                float *dist, cudaStream_t s);
+void sum_reduce_f32_to_f64(const float *v, int64_t n, double *out, cudaStream_t s);
+void off_to_counts(const int64_t *off, int k, int64_t *counts, cudaStream_t s);
+void count_bad_labels(const int32_t *labels, int64_t n, int k, int *bad, cudaStream_t s);
+
+// assign.cu -- labels[i] = argmin_j ||x_i - c_j||^2 (ties to the smallest j)
+void assign_labels(const float *X, const float *xn, int64_t n, int dp, const float *C, int k,
+                   int32_t *labels, cudaStream_t s);
+
+// query.cu -- keep the K nearest rows among the children of each query's parents
+struct ScanArgs {
+    const float *R = nullptr;     // [M x dp] rows (parent-major)
+    const int32_t *rid = nullptr; // [M] id of each row (used in the ordering key)
+    const int64_t *off = nullptr; // [n_parents+1] child ranges, or null for the root range
+    const int32_t *sel = nullptr; // [Q x P] parent ids (-1 = none), or null for the root
+    int P = 0;
+    int64_t root_end = 0;         // root range [0, root_end) when off == null
+    const float *Q = nullptr;     // [nq x dp] padded queries
+    int64_t nq = 0;
+    int dp = 0;
+    int K = 0;
+    int32_t *out_ids32 = nullptr; // [nq x K] (levels) ...
+    int64_t *out_ids64 = nullptr; // ... or int64 (leaf)
+    float *out_d = nullptr;       // [nq x K] (may be null)
+};
+void scan_topk(const ScanArgs &a, cudaStream_t s);
+// bytes streamed by the scans since the last reset ([0] levels, [1] leaf)
+double scan_bytes(int which);
+void scan_bytes_reset();
+
+}  // namespace mask

@@ -1,0 +1,656 @@
+// kmeans.cu -- k-means building blocks of the MASK build (§2.4, §3.1, §3.2):
+// row padding and norms, k-means++ seeding steps, the label counting sort that
+// turns a labelling into membership lists, and the per-cluster mean update.
+#include <cfloat>
+#include <climits>
+
+#include "common.cuh"
+
+namespace mask {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------- block reductions
+
+template <int T>
+__device__ double block_sum_f64(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < T / 32; ++i) t += red[i];
+    return t;
+}
+
+template <int T>
+__device__ long long block_min_ll(long long v, long long *red) {
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    long long t = LLONG_MAX;
+    for (int i = 0; i < T / 32; ++i) t = min(t, red[i]);
+    return t;
+}
+
+template <int T>
+__device__ long long block_max_ll(long long v, long long *red) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    long long t = LLONG_MIN;
+    for (int i = 0; i < T / 32; ++i) t = max(t, red[i]);
+    return t;
+}
+
+// Inclusive scan of one double per thread (block of T threads, fixed tree).
+template <int T>
+__device__ double block_incl_scan_f64(double v, double *wsum) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        double t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    __syncthreads();
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    double base = 0.0;
+    for (int i = 0; i < w; ++i) base += wsum[i];
+    return v + base;
+}
+
+// ------------------------------------------------------ elementwise kernels
+
+__global__ void pad_rows_kernel(const float *__restrict__ src, int64_t n, int d,
+                                float *__restrict__ dst, int dp) {
+    const int64_t total = n * dp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / dp;
+        const int t = (int)(e - i * dp);
+        dst[e] = t < d ? src[i * d + t] : 0.f;
+    }
+}
+
+__global__ void unpad_rows_kernel(const float *__restrict__ src, int64_t n, int dp,
+                                  float *__restrict__ dst, int d) {
+    const int64_t total = n * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / d;
+        const int t = (int)(e - i * d);
+        dst[e] = src[i * dp + t];
+    }
+}
+
+template <class I>
+__global__ void gather_rows_kernel(const float4 *__restrict__ src, int dp4,
+                                   const I *__restrict__ idx, int64_t m,
+                                   float4 *__restrict__ dst) {
+    const int64_t total = m * dp4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / dp4;
+        const int c = (int)(e - r * dp4);
+        dst[e] = src[(int64_t)idx[r] * dp4 + c];
+    }
+}
+
+__global__ void iota_kernel(int32_t *p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+
+// Squared norm of each row, one group of LPR lanes per row.
+template <int LPR>
+__global__ void row_sqnorm_kernel(const float4 *__restrict__ X, int64_t n, int dp4,
+                                  float *__restrict__ out) {
+    const int gl = threadIdx.x % LPR;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / LPR);
+    int64_t row = (int64_t)blockIdx.x * (blockDim.x / LPR) + threadIdx.x / LPR;
+    // every lane of a warp runs the same number of iterations (shuffles below)
+    const int64_t n_round = (n + groups - 1) / groups * groups;
+    for (; row < n_round; row += groups) {
+        float acc = 0.f;
+        if (row < n) {
+            const float4 *xr = X + row * dp4;
+            for (int c = gl; c < dp4; c += LPR) {
+                float4 v = xr[c];
+                acc = fmaf(v.x, v.x, acc);
+                acc = fmaf(v.y, v.y, acc);
+                acc = fmaf(v.z, v.z, acc);
+                acc = fmaf(v.w, v.w, acc);
+            }
+        }
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (gl == 0 && row < n) out[row] = acc;
+    }
+}
+
+// dist[i] = sum_t (x_it - c_{labels[i],t})^2
+template <int LPR>
+__global__ void label_dist_kernel(const float4 *__restrict__ X, int64_t n, int dp4,
+                                  const float4 *__restrict__ C,
+                                  const int32_t *__restrict__ labels, float *__restrict__ dist) {
+    const int gl = threadIdx.x % LPR;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / LPR);
+    int64_t row = (int64_t)blockIdx.x * (blockDim.x / LPR) + threadIdx.x / LPR;
+    const int64_t n_round = (n + groups - 1) / groups * groups;
+    for (; row < n_round; row += groups) {
+        float acc = 0.f;
+        if (row < n) {
+            const float4 *xr = X + row * dp4;
+            const float4 *cr = C + (int64_t)labels[row] * dp4;
+            for (int c = gl; c < dp4; c += LPR) {
+                float4 a = xr[c], b = cr[c];
+                float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+                acc = fmaf(e0, e0, acc);
+                acc = fmaf(e1, e1, acc);
+                acc = fmaf(e2, e2, acc);
+                acc = fmaf(e3, e3, acc);
+            }
+        }
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (gl == 0 && row < n) dist[row] = acc;
+    }
+}
+
+__global__ void max_reduce_kernel(const float *__restrict__ v, int64_t n, float *out) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    // values are >= 0, so their bit patterns order like unsigned integers
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(out), __float_as_uint(m));
+}
+
+__global__ void sum_f32_to_f64_kernel(const float *__restrict__ v, int64_t n, double *out) {
+    __shared__ double red[8];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) s += (double)v[i];
+    s = block_sum_f64<256>(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// --------------------------------------------------------------- k-means++
+
+constexpr int kKppThreads = 256;
+constexpr int kKppRows = 256;  // rows per block; one D^2 block sum each
+
+// One k-means++ step t >= 1 (§3.2): fold the centre picked at step t-1 into
+// D^2, then the last block to finish draws centre t: the smallest row whose
+// inclusive prefix of D^2 exceeds u_t * sum(D^2) (sums in FP64); if the sum
+// is 0, the lowest-index row not chosen yet.
+template <int LPR>
+__global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
+    const float *__restrict__ X, int64_t m, int dp, int t, const double *__restrict__ u,
+    float *__restrict__ D2, double *__restrict__ bsum, unsigned *__restrict__ counter,
+    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken) {
+    __shared__ double red[kKppThreads / 32];
+    __shared__ long long redi[kKppThreads / 32];
+    __shared__ double incs[kKppThreads];
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x;
+    constexpr int G = kKppThreads / LPR;
+    const int g = tid / LPR, gl = tid % LPR;
+    const int dp4 = dp / 4;
+    const int64_t c = chosen[t - 1];
+    const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
+    const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
+
+    double local = 0.0;
+    for (int r = g; r < kKppRows; r += G) {
+        const int64_t i = r0 + r;
+        float acc = 0.f;
+        if (i < m) {
+            const float4 *xr = reinterpret_cast<const float4 *>(X + i * dp);
+            for (int ch = gl; ch < dp4; ch += LPR) {
+                float4 a = xr[ch], b = __ldg(crow + ch);
+                float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+                acc = fmaf(e0, e0, acc);
+                acc = fmaf(e1, e1, acc);
+                acc = fmaf(e2, e2, acc);
+                acc = fmaf(e3, e3, acc);
+            }
+        }
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (gl == 0 && i < m) {
+            const float nv = (t == 1) ? acc : fminf(D2[i], acc);
+            D2[i] = nv;
+            local += (double)nv;
+        }
+    }
+    const double bs = block_sum_f64<kKppThreads>(local, red);
+    if (tid == 0) bsum[blockIdx.x] = bs;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // ---------------- the last block draws centre t ----------------
+    const int nb = gridDim.x;
+    if (t == 1 && tid == 0) taken[chosen[0]] = 1;
+    double part = 0.0;
+    for (int b = tid; b < nb; b += kKppThreads) part += __ldcg(bsum + b);
+    const double S = block_sum_f64<kKppThreads>(part, red);
+    long long pick = -1;
+    if (S > 0.0) {
+        const double target = u[t] * S;
+        // first block whose inclusive prefix exceeds the target
+        double carry = 0.0, excl = 0.0;
+        long long fb = LLONG_MAX;
+        for (int c0 = 0; c0 < nb && fb == LLONG_MAX; c0 += kKppThreads) {
+            const int b = c0 + tid;
+            const double v = b < nb ? __ldcg(bsum + b) : 0.0;
+            const double inc = block_incl_scan_f64<kKppThreads>(v, red) + carry;
+            incs[tid] = inc;
+            fb = block_min_ll<kKppThreads>(b < nb && inc > target ? b : LLONG_MAX, redi);
+            if (fb != LLONG_MAX) {
+                const int lt = (int)(fb - c0);
+                excl = lt == 0 ? carry : incs[lt - 1];
+            }
+            carry = incs[kKppThreads - 1];
+            __syncthreads();
+        }
+        if (fb != LLONG_MAX) {
+            const int64_t i = fb * kKppRows + tid;
+            const double v = i < m ? (double)__ldcg(D2 + i) : 0.0;
+            const double inc = block_incl_scan_f64<kKppThreads>(v, red) + excl;
+            pick = block_min_ll<kKppThreads>(i < m && inc > target ? i : LLONG_MAX, redi);
+            if (pick == LLONG_MAX)  // rounding: the last positive row of that block
+                pick = block_max_ll<kKppThreads>(i < m && v > 0.0 ? i : -1, redi);
+        }
+        if (pick < 0 || pick == LLONG_MAX) {
+            // rounding left the target past the end: last row with D^2 > 0
+            long long lb = -1;
+            for (int b = tid; b < nb; b += kKppThreads)
+                if (__ldcg(bsum + b) > 0.0) lb = b;
+            lb = block_max_ll<kKppThreads>(lb, redi);
+            const int64_t i = lb * kKppRows + tid;
+            const bool pos = lb >= 0 && i < m && __ldcg(D2 + i) > 0.f;
+            pick = block_max_ll<kKppThreads>(pos ? i : -1, redi);
+        }
+    } else {
+        __syncthreads();
+        long long first = LLONG_MAX;
+        for (int64_t c0 = 0; c0 < m && first == LLONG_MAX; c0 += kKppThreads) {
+            const int64_t i = c0 + tid;
+            first = block_min_ll<kKppThreads>(i < m && !taken[i] ? i : LLONG_MAX, redi);
+        }
+        pick = first;
+    }
+    if (tid == 0) {
+        chosen[t] = pick;
+        taken[pick] = 1;
+        *counter = 0u;
+    }
+}
+
+// ------------------------------------------------------------ label sort
+
+__global__ void label_hist_kernel(const int32_t *__restrict__ labels, int64_t n,
+                                  int32_t *__restrict__ counts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(counts + labels[i], 1);
+}
+
+// Exclusive scan of k counts into off[0..k] (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) count_scan_kernel(const int32_t *__restrict__ counts,
+                                                          int k, int64_t *__restrict__ off) {
+    __shared__ long long part[1024];
+    const int tid = threadIdx.x;
+    const int per = (k + 1023) / 1024;
+    const int b = tid * per, e = min(k, b + per);
+    long long s = 0;
+    for (int j = b; j < e; ++j) s += counts[j];
+    part[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        long long v = tid >= o ? part[tid - o] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    long long run = part[tid] - s;
+    for (int j = b; j < e; ++j) {
+        off[j] = run;
+        run += counts[j];
+    }
+    if (tid == 1023) off[k] = part[1023];
+}
+
+__global__ void label_scatter_kernel(const int32_t *__restrict__ labels, int64_t n,
+                                     const int64_t *__restrict__ off, int32_t *__restrict__ fill,
+                                     int32_t *__restrict__ perm) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t l = labels[i];
+        const int32_t pos = atomicAdd(fill + l, 1);
+        perm[off[l] + pos] = (int32_t)i;
+    }
+}
+
+// Put each membership list in ascending item order (bitonic sort in shared
+// memory), so sums over a cluster run in the same order on every build.
+constexpr int kSegSortMax = 4096;
+__global__ void __launch_bounds__(512) segment_sort_kernel(const int64_t *__restrict__ off,
+                                                           int32_t *__restrict__ perm) {
+    __shared__ int32_t s[kSegSortMax];
+    const int64_t b = off[blockIdx.x], e = off[blockIdx.x + 1];
+    const int m = (int)(e - b);
+    if (m <= 1 || m > kSegSortMax) return;
+    int S = 1;
+    while (S < m) S <<= 1;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s[i] = i < m ? perm[b + i] : INT_MAX;
+    __syncthreads();
+    for (int kk = 2; kk <= S; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < S; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & kk) == 0;
+                    const int32_t a = s[i], c = s[ixj];
+                    if ((a > c) == up) { s[i] = c; s[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = s[i];
+}
+
+// --------------------------------------------------------- centroid update
+
+// One block per (cluster j, column slice): sum the members' rows (gathered
+// through the label-sorted membership list) and their squared distances to the
+// previous centroid; C_new[j] = sum / count, or C_prev[j] for an empty cluster.
+template <int LPR, int CPL, class Acc>
+__device__ void update_body(const float4 *__restrict__ X, int dp4, const int32_t *__restrict__ perm,
+                            int64_t b, int64_t m, const float4 *cp, float4 *__restrict__ Cn,
+                            float *__restrict__ sse, int j, int ch0, bool write, float *fred) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    Acc *accs = reinterpret_cast<Acc *>(dyn);  // [G][LPR*CPL][4] partial sums
+    const int tid = threadIdx.x;
+    constexpr int G = 256 / LPR;
+    const int g = tid / LPR, gl = tid % LPR;
+    Acc ax[CPL], ay[CPL], az[CPL], aw[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) ax[q] = ay[q] = az[q] = aw[q] = Acc(0);
+    float sl = 0.f;
+#pragma unroll 1
+    for (int64_t r = g; r < m; r += G) {
+        const int64_t row = perm[b + r];
+        const float4 *xr = X + row * dp4;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const int ch = ch0 + gl + q * LPR;
+            if (ch < dp4) {
+                const float4 v = xr[ch];
+                ax[q] += v.x; ay[q] += v.y; az[q] += v.z; aw[q] += v.w;
+                const float e0 = v.x - cp[q].x, e1 = v.y - cp[q].y, e2 = v.z - cp[q].z,
+                            e3 = v.w - cp[q].w;
+                sl = fmaf(e0, e0, sl); sl = fmaf(e1, e1, sl);
+                sl = fmaf(e2, e2, sl); sl = fmaf(e3, e3, sl);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        Acc *p = accs + ((size_t)g * LPR * CPL + gl * CPL + q) * 4;
+        p[0] = ax[q]; p[1] = ay[q]; p[2] = az[q]; p[3] = aw[q];
+    }
+    for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(kFull, sl, o);
+    if ((tid & 31) == 0) fred[tid >> 5] = sl;
+    __syncthreads();
+    // column sums over the G groups, in group order; then the mean
+    if (write && tid < LPR * CPL) {
+        const int lane_in = tid / CPL, q = tid % CPL;
+        const int ch = ch0 + lane_in + q * LPR;
+        Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll 1
+        for (int gg = 0; gg < G; ++gg) {
+            const Acc *p = accs + ((size_t)gg * LPR * CPL + lane_in * CPL + q) * 4;
+            s0 += p[0]; s1 += p[1]; s2 += p[2]; s3 += p[3];
+        }
+        if (ch < dp4) {
+            const Acc cnt = Acc(m);
+            Cn[(int64_t)j * dp4 + ch] = make_float4((float)(s0 / cnt), (float)(s1 / cnt),
+                                                    (float)(s2 / cnt), (float)(s3 / cnt));
+        }
+    }
+    if (tid == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += fred[w];
+        atomicAdd(sse + j, t);
+    }
+}
+
+template <int LPR, int CPL>
+__global__ __launch_bounds__(256) void centroid_update_kernel(
+    const float4 *__restrict__ X, int dp4, const int32_t *__restrict__ perm,
+    const int64_t *__restrict__ off, const float4 *__restrict__ Cp, float4 *__restrict__ Cn,
+    float *__restrict__ sse, int write) {
+    __shared__ float fred[8];
+    const int j = blockIdx.x;
+    const int ch0 = blockIdx.y * LPR * CPL;
+    const int gl = threadIdx.x % LPR;
+    const int64_t b = off[j], m = off[j + 1] - b;
+    float4 cp[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int ch = ch0 + gl + q * LPR;
+        cp[q] = ch < dp4 ? Cp[(int64_t)j * dp4 + ch] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (m == 0) {
+        // empty cluster: keep the previous centroid
+        if (write && threadIdx.x < LPR * CPL) {
+            const int ch = ch0 + threadIdx.x;
+            if (ch < dp4) Cn[(int64_t)j * dp4 + ch] = Cp[(int64_t)j * dp4 + ch];
+        }
+        return;
+    }
+    if (m > (1 << 20))
+        update_body<LPR, CPL, double>(X, dp4, perm, b, m, cp, Cn, sse, j, ch0, write != 0, fred);
+    else
+        update_body<LPR, CPL, float>(X, dp4, perm, b, m, cp, Cn, sse, j, ch0, write != 0, fred);
+}
+
+__global__ void off_to_counts_kernel(const int64_t *__restrict__ off, int k,
+                                     int64_t *__restrict__ counts) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x)
+        counts[j] = off[j + 1] - off[j];
+}
+
+__global__ void count_bad_labels_kernel(const int32_t *__restrict__ labels, int64_t n, int k,
+                                        int *__restrict__ bad) {
+    int b = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b += (labels[i] < 0 || labels[i] >= k) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(kFull, b, o);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(bad, b);
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+// ================================================================ launchers
+
+void pad_rows(const float *src, int64_t n, int d, float *dst, int dp, cudaStream_t s) {
+    if (n == 0) return;
+    pad_rows_kernel<<<grid_for(n * dp, 256), 256, 0, s>>>(src, n, d, dst, dp);
+    MASK_LAUNCHED("pad_rows");
+}
+
+void unpad_rows(const float *src, int64_t n, int dp, float *dst, int d, cudaStream_t s) {
+    if (n == 0) return;
+    unpad_rows_kernel<<<grid_for(n * d, 256), 256, 0, s>>>(src, n, dp, dst, d);
+    MASK_LAUNCHED("unpad_rows");
+}
+
+template <class I>
+void gather_rows(const float *src, int dp, const I *idx, int64_t m, float *dst, cudaStream_t s) {
+    if (m == 0) return;
+    gather_rows_kernel<I><<<grid_for(m * (dp / 4), 256), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(src), dp / 4, idx, m, reinterpret_cast<float4 *>(dst));
+    MASK_LAUNCHED("gather_rows");
+}
+template void gather_rows<int32_t>(const float *, int, const int32_t *, int64_t, float *,
+                                   cudaStream_t);
+template void gather_rows<int64_t>(const float *, int, const int64_t *, int64_t, float *,
+                                   cudaStream_t);
+
+void iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
+    if (n == 0) return;
+    iota_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+    MASK_LAUNCHED("iota");
+}
+
+#define MASK_LPR_DISPATCH(lpr, KERNEL_CALL)      \
+    switch (lpr) {                               \
+    case 1: { constexpr int L = 1; KERNEL_CALL; } break;   \
+    case 2: { constexpr int L = 2; KERNEL_CALL; } break;   \
+    case 4: { constexpr int L = 4; KERNEL_CALL; } break;   \
+    case 8: { constexpr int L = 8; KERNEL_CALL; } break;   \
+    case 16: { constexpr int L = 16; KERNEL_CALL; } break; \
+    default: { constexpr int L = 32; KERNEL_CALL; } break; \
+    }
+
+void row_sqnorm(const float *X, int64_t n, int dp, float *out, cudaStream_t s) {
+    if (n == 0) return;
+    const int lpr = lanes_per_row(dp);
+    const int grid = grid_for(n * lpr, 256);
+    MASK_LPR_DISPATCH(lpr, (row_sqnorm_kernel<L><<<grid, 256, 0, s>>>(
+                               reinterpret_cast<const float4 *>(X), n, dp / 4, out)));
+    MASK_LAUNCHED("row_sqnorm");
+}
+
+void label_dist(const float *X, int64_t n, int dp, const float *C, const int32_t *labels,
+                float *dist, cudaStream_t s) {
+    if (n == 0) return;
+    const int lpr = lanes_per_row(dp);
+    const int grid = grid_for(n * lpr, 256);
+    MASK_LPR_DISPATCH(lpr, (label_dist_kernel<L><<<grid, 256, 0, s>>>(
+                               reinterpret_cast<const float4 *>(X), n, dp / 4,
+                               reinterpret_cast<const float4 *>(C), labels, dist)));
+    MASK_LAUNCHED("label_dist");
+}
+
+void max_reduce(const float *v, int64_t n, float *out, cudaStream_t s) {
+    MASK_CUDA(cudaMemsetAsync(out, 0, sizeof(float), s));
+    if (n == 0) return;
+    max_reduce_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, n, out);
+    MASK_LAUNCHED("max_reduce");
+}
+
+void sum_reduce_f32_to_f64(const float *v, int64_t n, double *out, cudaStream_t s) {
+    sum_f32_to_f64_kernel<<<1, 256, 0, s>>>(v, n, out);
+    MASK_LAUNCHED("sum_reduce");
+}
+
+void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_dev,
+                    int64_t *chosen, cudaStream_t s) {
+    if (k <= 1) return;
+    ProfRegion pr("kmeanspp", s, (double)(k - 1) * (double)m * dp * 4.0);
+    const int nb = (int)((m + kKppRows - 1) / kKppRows);
+    Scratch<float> D2(m, s);
+    Scratch<double> bsum(nb, s);
+    Scratch<unsigned> counter(1, s);
+    Scratch<unsigned char> taken(m, s);
+    MASK_CUDA(cudaMemsetAsync(counter.get(), 0, sizeof(unsigned), s));
+    MASK_CUDA(cudaMemsetAsync(taken.get(), 0, m, s));
+    const int lpr = lanes_per_row(dp);
+    for (int t = 1; t < k; ++t) {
+        MASK_LPR_DISPATCH(lpr, (kpp_step_kernel<L><<<nb, kKppThreads, 0, s>>>(
+                                   Xs, m, dp, t, u_dev, D2.get(), bsum.get(), counter.get(),
+                                   chosen, taken.get())));
+        MASK_LAUNCHED("kpp_step");
+    }
+}
+
+void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *perm,
+                cudaStream_t s) {
+    ProfRegion pr("label_sort", s, 20.0 * (double)n + 16.0 * (double)k);
+    Scratch<int32_t> counts(k, s), fill(k, s);
+    MASK_CUDA(cudaMemsetAsync(counts.get(), 0, sizeof(int32_t) * k, s));
+    MASK_CUDA(cudaMemsetAsync(fill.get(), 0, sizeof(int32_t) * k, s));
+    if (n > 0) {
+        label_hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(labels, n, counts.get());
+        MASK_LAUNCHED("label_hist");
+    }
+    count_scan_kernel<<<1, 1024, 0, s>>>(counts.get(), k, off);
+    MASK_LAUNCHED("count_scan");
+    if (n > 0) {
+        label_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(labels, n, off, fill.get(), perm);
+        MASK_LAUNCHED("label_scatter");
+        segment_sort_kernel<<<k, 512, 0, s>>>(off, perm);
+        MASK_LAUNCHED("segment_sort");
+    }
+}
+
+template <int L, int CPL>
+void launch_update(dim3 grid, size_t smem, const float *X, int dp4, const int32_t *perm,
+                   const int64_t *off, int k, const float *C_prev, float *C_new, float *sse,
+                   bool write, cudaStream_t s) {
+    (void)k;
+    auto kfn = centroid_update_kernel<L, CPL>;
+    MASK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kfn<<<grid, 256, smem, s>>>(reinterpret_cast<const float4 *>(X), dp4, perm, off,
+                                reinterpret_cast<const float4 *>(C_prev),
+                                reinterpret_cast<float4 *>(C_new), sse, write ? 1 : 0);
+}
+
+void centroid_update(const float *X, int dp, const int32_t *perm, const int64_t *off, int k,
+                     const float *C_prev, float *C_new, float *sse, bool write,
+                     cudaStream_t s) {
+    const int dp4 = dp / 4;
+    const int lpr = lanes_per_row(dp);
+    int cpl = (dp4 + lpr - 1) / lpr;
+    cpl = cpl >= 4 ? 4 : (cpl >= 2 ? 2 : 1);
+    const int slices = (dp4 + lpr * cpl - 1) / (lpr * cpl);
+    MASK_CUDA(cudaMemsetAsync(sse, 0, sizeof(float) * k, s));
+    ProfRegion pr("centroid_update", s, 0.0);
+    dim3 grid(k, slices);
+    // dynamic shared memory holds the per-group partial sums (FP64 worst case)
+    const size_t smem = (size_t)(256 / lpr) * lpr * cpl * 4 * sizeof(double);
+    if (cpl == 1) {
+        MASK_LPR_DISPATCH(lpr, (launch_update<L, 1>(grid, smem, X, dp4, perm, off, k, C_prev, C_new, sse, write, s)));
+    } else if (cpl == 2) {
+        MASK_LPR_DISPATCH(lpr, (launch_update<L, 2>(grid, smem, X, dp4, perm, off, k, C_prev, C_new, sse, write, s)));
+    } else {
+        MASK_LPR_DISPATCH(lpr, (launch_update<L, 4>(grid, smem, X, dp4, perm, off, k, C_prev, C_new, sse, write, s)));
+    }
+    MASK_LAUNCHED("centroid_update");
+}
+
+void off_to_counts(const int64_t *off, int k, int64_t *counts, cudaStream_t s) {
+    if (k == 0) return;
+    off_to_counts_kernel<<<grid_for(k, 256), 256, 0, s>>>(off, k, counts);
+    MASK_LAUNCHED("off_to_counts");
+}
+
+void count_bad_labels(const int32_t *labels, int64_t n, int k, int *bad, cudaStream_t s) {
+    MASK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    if (n == 0) return;
+    count_bad_labels_kernel<<<grid_for(n, 256), 256, 0, s>>>(labels, n, k, bad);
+    MASK_LAUNCHED("count_bad_labels");
+}
+
+}  // namespace mask

@@ -1,0 +1,605 @@
+// mask_api.cu -- host orchestration and the C ABI of libmask_gb300.so.
+//
+// Build (§3.1, Algorithm 1, one group per level): for each level, k-means++
+// seeding (§3.2), Lloyd iterations (§2.4) as assign -> label sort -> mean
+// update, a final assignment, then the level's centroids are the next
+// level's data.  Afterwards every level is laid out parent-major (children of
+// a centroid contiguous) and the points cluster-major, so the query (§3.3,
+// Algorithm 2) is a chain of scan_topk launches over contiguous row ranges.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+struct mask_index {
+    int device = 0;
+    int64_t n = 0;
+    int d = 0, dp = 0, L = 0, iters = 0;
+    bool sparse = false;
+    mask::DevArray<float> Xs;        // [n x dp] points, cluster-major (level-0 parent-major)
+    mask::DevArray<int32_t> xids;    // [n] original id of each row of Xs
+    struct Level {
+        int k = 0;
+        mask::DevArray<float> C;       // [k x dp] centroids in k-means cluster order
+        mask::DevArray<float> Cs;      // [k x dp] centroids parent-major (top: cluster order)
+        mask::DevArray<int32_t> ids;   // [k] cluster id of each row of Cs
+        mask::DevArray<int64_t> off;   // [k+1] children of centroid j: rows off[j]..off[j+1]
+                                       //       of the level below's parent-major array
+        mask::DevArray<int32_t> labels;// [n_below] centroid of every item one level below
+        std::vector<int64_t> chosen;   // k-means++ picks (indices into the level's inputs)
+        std::vector<double> objective; // k-means objective after each assignment
+    };
+    std::vector<Level> lv;
+};
+
+namespace mask {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void fail(mask_status s, const std::string &msg) { throw Error(s, msg); }
+
+namespace {
+
+// ----------------------------------------------------------- R1: SplitMix64
+
+struct SplitMix64 {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * 0x1.0p-53; }
+};
+
+uint64_t level_state(uint64_t seed, int lv) {
+    return seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(lv + 1));
+}
+
+// ------------------------------------------------------- pointer staging
+
+bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A caller input as a device pointer (host data copied in on the stream).
+template <class T>
+struct In {
+    const T *p = nullptr;
+    Scratch<T> tmp;
+    In(const T *src, size_t count, cudaStream_t s) {
+        if (src == nullptr || count == 0 || on_device(src)) {
+            p = src;
+            return;
+        }
+        tmp.alloc(count, s);
+        MASK_CUDA(cudaMemcpyAsync(tmp.get(), src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+        p = tmp.get();
+    }
+};
+
+// A caller output as a device pointer (copied back to host memory by finish()).
+template <class T>
+struct Out {
+    T *user = nullptr, *p = nullptr;
+    size_t count = 0;
+    bool host = false;
+    Scratch<T> tmp;
+    Out(T *dst, size_t c, cudaStream_t s) : user(dst), count(c) {
+        if (dst == nullptr || c == 0 || on_device(dst)) {
+            p = dst;
+            return;
+        }
+        host = true;
+        tmp.alloc(c, s);
+        p = tmp.get();
+    }
+    void finish(cudaStream_t s) {
+        if (host)
+            MASK_CUDA(cudaMemcpyAsync(user, p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    }
+};
+
+template <class T>
+void to_host(std::vector<T> &v, const T *dev, size_t count, cudaStream_t s) {
+    v.resize(count);
+    if (count == 0) return;
+    MASK_CUDA(cudaMemcpyAsync(v.data(), dev, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    MASK_CUDA(cudaStreamSynchronize(s));
+}
+
+template <class T>
+void copy_out_host_vec(const std::vector<T> &v, T *dst, cudaStream_t s) {
+    if (dst == nullptr || v.empty()) return;
+    if (on_device(dst)) {
+        MASK_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        MASK_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(dst, v.data(), v.size() * sizeof(T));
+    }
+}
+
+template <class F>
+mask_status guard(F &&f) {
+    try {
+        f();
+        return MASK_OK;
+    } catch (const Error &e) {
+        g_err = e.what();
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return MASK_ENOMEM;
+    } catch (const std::exception &e) {
+        g_err = e.what();
+        return MASK_ECUDA;
+    }
+}
+
+int current_device() {
+    int dev = 0;
+    MASK_CUDA(cudaGetDevice(&dev));
+    return dev;
+}
+
+// ---------------------------------------------------- seeding (§3.2, R2-R3)
+
+// Number of inputs k-means++ runs on: all of them, or 8k when the n*k
+// distance evaluations of full seeding exceed 2^32 and 8k < n.
+int64_t seed_sample_size(int64_t n, int k) {
+    if ((double)n * (double)k > 4294967296.0 && 8 * (int64_t)k < n) return 8 * (int64_t)k;
+    return n;
+}
+
+// k-means++ for one level: C_out [k x dp] = the chosen rows of X; `chosen`
+// receives their indices into X.  Random draws on the host (R1): first the
+// partial Fisher-Yates draws of the subsample (if any), then one per centre.
+void seed_level(const float *X, int64_t n, int dp, int k, uint64_t seed, int lv, float *C_out,
+                std::vector<int64_t> &chosen, cudaStream_t s) {
+    SplitMix64 rng{level_state(seed, lv)};
+    const int64_t m = seed_sample_size(n, k);
+    std::vector<int64_t> sample;
+    Scratch<float> Xsub;
+    const float *S = X;
+    if (m < n) {
+        std::vector<int64_t> idx((size_t)n);
+        for (int64_t i = 0; i < n; ++i) idx[(size_t)i] = i;
+        for (int64_t j = 0; j < m; ++j) {
+            int64_t r = j + (int64_t)std::floor(rng.uniform() * (double)(n - j));
+            if (r > n - 1) r = n - 1;
+            std::swap(idx[(size_t)j], idx[(size_t)r]);
+        }
+        sample.assign(idx.begin(), idx.begin() + m);
+        Scratch<int64_t> sidx(m, s);
+        MASK_CUDA(cudaMemcpyAsync(sidx.get(), sample.data(), m * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, s));
+        Xsub.alloc((size_t)m * dp, s);
+        gather_rows<int64_t>(X, dp, sidx.get(), m, Xsub.get(), s);
+        S = Xsub.get();
+        MASK_CUDA(cudaStreamSynchronize(s));  // sidx and sample are released below
+    }
+    std::vector<double> u((size_t)k);
+    for (int t = 0; t < k; ++t) u[(size_t)t] = rng.uniform();
+    int64_t first = (int64_t)std::floor(u[0] * (double)m);
+    if (first > m - 1) first = m - 1;
+    Scratch<double> ud(k, s);
+    Scratch<int64_t> ch(k, s);
+    MASK_CUDA(cudaMemcpyAsync(ud.get(), u.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    MASK_CUDA(cudaMemcpyAsync(ch.get(), &first, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    kmeanspp_steps(S, m, dp, k, ud.get(), ch.get(), s);
+    gather_rows<int64_t>(S, dp, ch.get(), k, C_out, s);
+    to_host(chosen, ch.get(), (size_t)k, s);
+    if (m < n)
+        for (auto &c : chosen) c = sample[(size_t)c];
+}
+
+// ------------------------------------------------------- Lloyd (§2.4, R4)
+
+// Lloyd iterations on the n_in rows of X (padded) from the centres in C
+// (k x dp, updated in place).  Writes the final labels, the membership list
+// of the final assignment (off [k+1], perm [n_in]) and the objective after
+// each assignment (iters+1 values).
+void lloyd(const float *X, int64_t n_in, int dp, int k, int iters, float *C, int32_t *labels,
+           int64_t *off, int32_t *perm, std::vector<double> &objective, cudaStream_t s) {
+    Scratch<float> xn(n_in, s), Cn((size_t)k * dp, s), sse(k, s);
+    Scratch<double> J(iters + 1, s);
+    row_sqnorm(X, n_in, dp, xn.get(), s);
+    float *cur = C, *nxt = Cn.get();
+    for (int it = 0; it < iters; ++it) {
+        assign_labels(X, xn.get(), n_in, dp, cur, k, labels, s);
+        label_sort(labels, n_in, k, off, perm, s);
+        centroid_update(X, dp, perm, off, k, cur, nxt, sse.get(), true, s);
+        sum_reduce_f32_to_f64(sse.get(), k, J.get() + it, s);
+        std::swap(cur, nxt);
+    }
+    assign_labels(X, xn.get(), n_in, dp, cur, k, labels, s);
+    label_sort(labels, n_in, k, off, perm, s);
+    centroid_update(X, dp, perm, off, k, cur, nullptr, sse.get(), false, s);
+    sum_reduce_f32_to_f64(sse.get(), k, J.get() + iters, s);
+    if (cur != C)
+        MASK_CUDA(cudaMemcpyAsync(C, cur, sizeof(float) * k * dp, cudaMemcpyDeviceToDevice, s));
+    to_host(objective, J.get(), (size_t)iters + 1, s);
+}
+
+// ------------------------------------------------------------ index layout
+
+// Given every level's centroids C, labels and membership lists (level lv's
+// off, and the perm of its items, stored as the ids of the level below),
+// lay out the parent-major arrays: points cluster-major (Xs), and each
+// non-top level's centroids in the order of their parents (Cs).
+void finish_layout(mask_index &idx, const float *Xp, cudaStream_t s) {
+    const int dp = idx.dp;
+    idx.Xs.alloc((size_t)idx.n * dp);
+    gather_rows<int32_t>(Xp, dp, idx.xids.get(), idx.n, idx.Xs.get(), s);
+    for (int lv = 0; lv < idx.L; ++lv) {
+        auto &L = idx.lv[(size_t)lv];
+        L.Cs.alloc((size_t)L.k * dp);
+        if (lv == idx.L - 1) {
+            L.ids.alloc((size_t)L.k);
+            iota_i32(L.ids.get(), L.k, s);
+            MASK_CUDA(cudaMemcpyAsync(L.Cs.get(), L.C.get(), sizeof(float) * L.k * dp,
+                                      cudaMemcpyDeviceToDevice, s));
+        } else {
+            gather_rows<int32_t>(L.C.get(), dp, L.ids.get(), L.k, L.Cs.get(), s);
+        }
+    }
+    MASK_CUDA(cudaStreamSynchronize(s));
+}
+
+void check_common(int64_t n, int d, const int32_t *k_per_level, int n_levels, mask_index **out) {
+    MASK_REQUIRE(out != nullptr, "out is NULL");
+    MASK_REQUIRE(n >= 1 && n <= INT32_MAX, "n must be in [1, 2^31)");
+    MASK_REQUIRE(d >= 1, "d must be >= 1");
+    MASK_REQUIRE(n_levels >= 1 && n_levels <= MASK_MAX_LEVELS, "n_levels out of range");
+    MASK_REQUIRE(k_per_level != nullptr, "k_per_level is NULL");
+    int64_t below = n;
+    for (int l = 0; l < n_levels; ++l) {
+        MASK_REQUIRE(k_per_level[l] >= 1 && (int64_t)k_per_level[l] <= below,
+                     "k_per_level[" + std::to_string(l) + "] must be in [1, items below]");
+        below = k_per_level[l];
+    }
+}
+
+std::unique_ptr<mask_index> new_index(int64_t n, int d, const int32_t *kpl, int L) {
+    auto idx = std::make_unique<mask_index>();
+    idx->device = current_device();
+    idx->n = n;
+    idx->d = d;
+    idx->dp = padded_dim(d);
+    idx->L = L;
+    idx->lv.resize((size_t)L);
+    for (int l = 0; l < L; ++l) idx->lv[(size_t)l].k = kpl[l];
+    return idx;
+}
+
+// Level-l items' ids array (the perm of level l's membership lists): the
+// point ids for l = 0, else the ids of level l-1's parent-major rows.
+int32_t *below_ids(mask_index &idx, int lv, int64_t n_in) {
+    if (lv == 0) {
+        idx.xids.alloc((size_t)n_in);
+        return idx.xids.get();
+    }
+    auto &B = idx.lv[(size_t)lv - 1];
+    B.ids.alloc((size_t)n_in);
+    return B.ids.get();
+}
+
+void build_dense(mask_index &idx, const float *Xp, uint64_t seed, cudaStream_t s) {
+    const float *in = Xp;
+    int64_t n_in = idx.n;
+    for (int lv = 0; lv < idx.L; ++lv) {
+        auto &L = idx.lv[(size_t)lv];
+        L.C.alloc((size_t)L.k * idx.dp);
+        L.labels.alloc((size_t)n_in);
+        L.off.alloc((size_t)L.k + 1);
+        int32_t *perm = below_ids(idx, lv, n_in);
+        seed_level(in, n_in, idx.dp, L.k, seed, lv, L.C.get(), L.chosen, s);
+        lloyd(in, n_in, idx.dp, L.k, idx.iters, L.C.get(), L.labels.get(), L.off.get(), perm,
+              L.objective, s);
+        in = L.C.get();
+        n_in = L.k;
+    }
+    finish_layout(idx, Xp, s);
+}
+
+}  // namespace
+}  // namespace mask
+
+using namespace mask;
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+const char *mask_last_error(void) { return g_err.c_str(); }
+
+mask_status mask_build(const float *points, int64_t n, int32_t d, const int32_t *k_per_level,
+                       int32_t n_levels, int32_t iters, uint64_t seed, mask_stream stream,
+                       mask_index **out) {
+    return guard([&] {
+        check_common(n, d, k_per_level, n_levels, out);
+        MASK_REQUIRE(points != nullptr, "points is NULL");
+        MASK_REQUIRE(iters >= 0, "iters must be >= 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        auto idx = new_index(n, d, k_per_level, n_levels);
+        idx->iters = iters;
+        In<float> P(points, (size_t)n * d, s);
+        Scratch<float> Xp((size_t)n * idx->dp, s);
+        pad_rows(P.p, n, d, Xp.get(), idx->dp, s);
+        build_dense(*idx, Xp.get(), seed, s);
+        MASK_CUDA(cudaStreamSynchronize(s));
+        *out = idx.release();
+    });
+}
+
+mask_status mask_build_csr(const int64_t *, const int32_t *, const float *, int64_t, int32_t,
+                           const int32_t *, int32_t, int32_t, uint64_t, mask_stream,
+                           mask_index **) {
+    g_err = "sparse inputs are not built in this version";
+    return MASK_EUNSUPPORTED;
+}
+
+mask_status mask_index_load(const float *points, int64_t n, int32_t d, int32_t n_levels,
+                            const int32_t *k_per_level, const float *const *centroids,
+                            const int32_t *const *labels, mask_stream stream,
+                            mask_index **out) {
+    return guard([&] {
+        check_common(n, d, k_per_level, n_levels, out);
+        MASK_REQUIRE(points && centroids && labels, "NULL array");
+        cudaStream_t s = (cudaStream_t)stream;
+        auto idx = new_index(n, d, k_per_level, n_levels);
+        In<float> P(points, (size_t)n * d, s);
+        Scratch<float> Xp((size_t)n * idx->dp, s);
+        pad_rows(P.p, n, d, Xp.get(), idx->dp, s);
+        Scratch<int> bad(1, s);
+        int64_t n_in = n;
+        for (int lv = 0; lv < n_levels; ++lv) {
+            auto &L = idx->lv[(size_t)lv];
+            MASK_REQUIRE(centroids[lv] && labels[lv], "NULL level array");
+            In<float> Cin(centroids[lv], (size_t)L.k * d, s);
+            In<int32_t> Lin(labels[lv], (size_t)n_in, s);
+            L.C.alloc((size_t)L.k * idx->dp);
+            pad_rows(Cin.p, L.k, d, L.C.get(), idx->dp, s);
+            L.labels.alloc((size_t)n_in);
+            MASK_CUDA(cudaMemcpyAsync(L.labels.get(), Lin.p, sizeof(int32_t) * n_in,
+                                      cudaMemcpyDeviceToDevice, s));
+            count_bad_labels(L.labels.get(), n_in, L.k, bad.get(), s);
+            int nbad = 0;
+            MASK_CUDA(cudaMemcpyAsync(&nbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+            MASK_CUDA(cudaStreamSynchronize(s));
+            MASK_REQUIRE(nbad == 0, "labels of level " + std::to_string(lv) + " out of range");
+            L.off.alloc((size_t)L.k + 1);
+            label_sort(L.labels.get(), n_in, L.k, L.off.get(), below_ids(*idx, lv, n_in), s);
+            n_in = L.k;
+        }
+        finish_layout(*idx, Xp.get(), s);
+        *out = idx.release();
+    });
+}
+
+void mask_free(mask_index *index) {
+    if (index == nullptr) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(index->device);
+    delete index;
+    cudaSetDevice(prev);
+}
+
+mask_status mask_index_get_info(const mask_index *index, mask_index_info *out) {
+    return guard([&] {
+        MASK_REQUIRE(index && out, "NULL argument");
+        std::memset(out, 0, sizeof(*out));
+        out->n = index->n;
+        out->d = index->d;
+        out->n_levels = index->L;
+        out->iters = index->iters;
+        out->sparse = index->sparse ? 1 : 0;
+        int64_t bytes = (int64_t)(index->Xs.bytes() + index->xids.bytes());
+        for (int l = 0; l < index->L; ++l) {
+            const auto &L = index->lv[(size_t)l];
+            out->k_per_level[l] = L.k;
+            bytes += (int64_t)(L.C.bytes() + L.Cs.bytes() + L.ids.bytes() + L.off.bytes() +
+                               L.labels.bytes());
+        }
+        out->device_bytes = bytes;
+    });
+}
+
+mask_status mask_index_export_level(const mask_index *index, int32_t level, float *centroids_out,
+                                    int32_t *labels_out, int64_t *chosen_out,
+                                    double *objective_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(index != nullptr, "index is NULL");
+        MASK_REQUIRE(level >= 0 && level < index->L, "level out of range");
+        cudaStream_t s = (cudaStream_t)stream;
+        const auto &L = index->lv[(size_t)level];
+        const int64_t n_below = level == 0 ? index->n : index->lv[(size_t)level - 1].k;
+        if (centroids_out) {
+            Out<float> C(centroids_out, (size_t)L.k * index->d, s);
+            unpad_rows(L.C.get(), L.k, index->dp, C.p, index->d, s);
+            C.finish(s);
+        }
+        if (labels_out) {
+            Out<int32_t> lb(labels_out, (size_t)n_below, s);
+            MASK_CUDA(cudaMemcpyAsync(lb.p, L.labels.get(), sizeof(int32_t) * n_below,
+                                      cudaMemcpyDeviceToDevice, s));
+            lb.finish(s);
+        }
+        MASK_CUDA(cudaStreamSynchronize(s));
+        copy_out_host_vec(L.chosen, chosen_out, s);
+        copy_out_host_vec(L.objective, objective_out, s);
+    });
+}
+
+mask_status mask_query(const mask_index *index, const float *queries, int64_t nq, int32_t k,
+                       const int32_t *probes, mask_precision precision, int64_t *ids_out,
+                       float *dists_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(index != nullptr, "index is NULL");
+        MASK_REQUIRE(nq >= 0, "nq must be >= 0");
+        MASK_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+        MASK_REQUIRE(probes != nullptr, "probes is NULL");
+        MASK_REQUIRE(current_device() == index->device, "index lives on another device");
+        if (precision != MASK_FP32) fail(MASK_EUNSUPPORTED, "only MASK_FP32 is built in this version");
+        if (nq == 0) return;
+        MASK_REQUIRE(queries && ids_out, "NULL queries or ids_out");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int L = index->L, dp = index->dp;
+        std::vector<int> p((size_t)L);
+        for (int l = 0; l < L; ++l) {
+            MASK_REQUIRE(probes[l] >= 1, "probes must be >= 1");
+            p[(size_t)l] = std::min<int>(probes[l], index->lv[(size_t)l].k);
+        }
+        In<float> Qin(queries, (size_t)nq * index->d, s);
+        Scratch<float> Qp((size_t)nq * dp, s);
+        pad_rows(Qin.p, nq, index->d, Qp.get(), dp, s);
+        Out<int64_t> ids(ids_out, (size_t)nq * k, s);
+        Out<float> dd(dists_out, (size_t)nq * k, s);
+        std::vector<Scratch<int32_t>> sel((size_t)L);
+        for (int l = 0; l < L; ++l) sel[(size_t)l].alloc((size_t)nq * p[(size_t)l], s);
+
+        ScanArgs a;
+        a.Q = Qp.get();
+        a.nq = nq;
+        a.dp = dp;
+        const int top = L - 1;
+        a.R = index->lv[(size_t)top].Cs.get();
+        a.rid = index->lv[(size_t)top].ids.get();
+        a.root_end = index->lv[(size_t)top].k;
+        a.K = p[(size_t)top];
+        a.out_ids32 = sel[(size_t)top].get();
+        scan_topk(a, s);
+        for (int l = top; l >= 1; --l) {
+            ScanArgs b = a;
+            b.R = index->lv[(size_t)l - 1].Cs.get();
+            b.rid = index->lv[(size_t)l - 1].ids.get();
+            b.off = index->lv[(size_t)l].off.get();
+            b.sel = sel[(size_t)l].get();
+            b.P = p[(size_t)l];
+            b.K = p[(size_t)l - 1];
+            b.out_ids32 = sel[(size_t)l - 1].get();
+            scan_topk(b, s);
+        }
+        ScanArgs c = a;
+        c.R = index->Xs.get();
+        c.rid = index->xids.get();
+        c.off = index->lv[0].off.get();
+        c.sel = sel[0].get();
+        c.P = p[0];
+        c.K = k;
+        c.out_ids32 = nullptr;
+        c.out_ids64 = ids.p;
+        c.out_d = dd.p;
+        scan_topk(c, s);
+        ids.finish(s);
+        dd.finish(s);
+        if (ids.host || dd.host) MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+mask_status mask_query_csr(const mask_index *, const int64_t *, const int32_t *, const float *,
+                           int64_t, int32_t, const int32_t *, mask_precision, int64_t *, float *,
+                           mask_stream) {
+    g_err = "sparse queries are not built in this version";
+    return MASK_EUNSUPPORTED;
+}
+
+mask_status mask_kmeanspp(const float *X, int64_t n, int32_t d, int32_t k, uint64_t seed,
+                          int32_t level, float *centroids_out, int64_t *chosen_out,
+                          mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(X && centroids_out, "NULL argument");
+        MASK_REQUIRE(n >= 1 && n <= INT32_MAX && d >= 1, "bad n or d");
+        MASK_REQUIRE(k >= 1 && k <= n, "k must be in [1, n]");
+        MASK_REQUIRE(level >= 0, "level must be >= 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int dp = padded_dim(d);
+        In<float> Xin(X, (size_t)n * d, s);
+        Scratch<float> Xp((size_t)n * dp, s), Cp((size_t)k * dp, s);
+        pad_rows(Xin.p, n, d, Xp.get(), dp, s);
+        std::vector<int64_t> chosen;
+        seed_level(Xp.get(), n, dp, k, seed, level, Cp.get(), chosen, s);
+        Out<float> C(centroids_out, (size_t)k * d, s);
+        unpad_rows(Cp.get(), k, dp, C.p, d, s);
+        C.finish(s);
+        MASK_CUDA(cudaStreamSynchronize(s));
+        copy_out_host_vec(chosen, chosen_out, s);
+    });
+}
+
+mask_status mask_kmeans_assign(const float *X, int64_t n, int32_t d, const float *C, int32_t k,
+                               int32_t *labels_out, float *dist_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(X && C && labels_out, "NULL argument");
+        MASK_REQUIRE(n >= 0 && n <= INT32_MAX && d >= 1 && k >= 1, "bad sizes");
+        if (n == 0) return;
+        cudaStream_t s = (cudaStream_t)stream;
+        const int dp = padded_dim(d);
+        In<float> Xin(X, (size_t)n * d, s), Cin(C, (size_t)k * d, s);
+        Scratch<float> Xp((size_t)n * dp, s), Cp((size_t)k * dp, s), xn(n, s);
+        pad_rows(Xin.p, n, d, Xp.get(), dp, s);
+        pad_rows(Cin.p, k, d, Cp.get(), dp, s);
+        row_sqnorm(Xp.get(), n, dp, xn.get(), s);
+        Out<int32_t> lb(labels_out, (size_t)n, s);
+        assign_labels(Xp.get(), xn.get(), n, dp, Cp.get(), k, lb.p, s);
+        if (dist_out) {
+            Out<float> dist(dist_out, (size_t)n, s);
+            label_dist(Xp.get(), n, dp, Cp.get(), lb.p, dist.p, s);
+            dist.finish(s);
+            lb.finish(s);
+            MASK_CUDA(cudaStreamSynchronize(s));
+        } else {
+            lb.finish(s);
+            if (lb.host) MASK_CUDA(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+mask_status mask_kmeans_update(const float *X, int64_t n, int32_t d, const int32_t *labels,
+                               int32_t k, const float *C_prev, float *C_out,
+                               int64_t *counts_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(X && labels && C_prev && C_out, "NULL argument");
+        MASK_REQUIRE(n >= 0 && n <= INT32_MAX && d >= 1 && k >= 1, "bad sizes");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int dp = padded_dim(d);
+        In<float> Xin(X, (size_t)n * d, s), Cin(C_prev, (size_t)k * d, s);
+        In<int32_t> Lin(labels, (size_t)n, s);
+        Scratch<int> bad(1, s);
+        count_bad_labels(Lin.p, n, k, bad.get(), s);
+        int nbad = 0;
+        MASK_CUDA(cudaMemcpyAsync(&nbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        MASK_CUDA(cudaStreamSynchronize(s));
+        MASK_REQUIRE(nbad == 0, "labels out of range");
+        Scratch<float> Xp((size_t)n * dp, s), Cp((size_t)k * dp, s), Cn((size_t)k * dp, s), sse(k, s);
+        Scratch<int64_t> off((size_t)k + 1, s);
+        Scratch<int32_t> perm((size_t)n, s);
+        pad_rows(Xin.p, n, d, Xp.get(), dp, s);
+        pad_rows(Cin.p, k, d, Cp.get(), dp, s);
+        label_sort(Lin.p, n, k, off.get(), perm.get(), s);
+        centroid_update(Xp.get(), dp, perm.get(), off.get(), k, Cp.get(), Cn.get(), sse.get(), true, s);
+        Out<float> Co(C_out, (size_t)k * d, s);
+        unpad_rows(Cn.get(), k, dp, Co.p, d, s);
+        Co.finish(s);
+        if (counts_out) {
+            Out<int64_t> cnt(counts_out, (size_t)k, s);
+            off_to_counts(off.get(), k, cnt.p, s);
+            cnt.finish(s);
+        }
+        MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+}  // extern "C"

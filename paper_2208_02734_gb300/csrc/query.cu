@@ -1,0 +1,228 @@
+// query.cu -- one kernel for every step of the top-down k-NN search (§3.3,
+// Algorithm 2, generalised to p kept centroids per level):
+//
+//   keep the K nearest rows among the children of each query's kept parents.
+//
+// The index stores every level parent-major: the children of a parent occupy
+// one contiguous row range (off[parent] .. off[parent+1]) of the level below,
+// and the points of a leaf cluster one contiguous range of the cluster-major
+// point array.  So the top level (root range), each intermediate level and
+// the final leaf scan are the same operation: stream a few row ranges, take
+// exact FP32 distances sum_t (q_t - r_t)^2, keep the K smallest keys
+// (distance bits << 32 | id) -- a total order, so the result does not depend
+// on the order rows are visited in or on the other queries in the launch.
+//
+// One block per query.  Groups of LPR lanes read a row with coalesced float4
+// loads (consecutive lanes, consecutive 16-byte chunks of a contiguous row
+// range); U rows per group are in flight per round.  Candidates below the
+// current K-th key are appended to a shared-memory buffer, which is bitonic-
+// sorted together with the current top list whenever it could overflow.
+#include <climits>
+
+#include "common.cuh"
+
+namespace mask {
+
+// Bytes the scan kernels stream (rows x (row + id)), [0] levels, [1] leaf.
+__device__ unsigned long long g_scan_bytes[2];
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+
+__device__ __forceinline__ void bitonic_sort_keys(unsigned long long *buf, int S) {
+    for (int kk = 2; kk <= S; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < S; i += kThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & kk) == 0;
+                    const unsigned long long a = buf[i], b = buf[ixj];
+                    if ((a > b) == up) { buf[i] = b; buf[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+template <int LPR>
+__global__ __launch_bounds__(kThreads) void scan_topk_kernel(
+    const float4 *__restrict__ R, int dp4, const int32_t *__restrict__ rid,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P, int64_t root_end,
+    const float4 *__restrict__ Q, int K, int KP, int S, int32_t *__restrict__ out32,
+    int64_t *__restrict__ out64, float *__restrict__ out_d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem);  // S keys
+    int64_t *rb = reinterpret_cast<int64_t *>(buf + S);                      // P range begins
+    int64_t *cum = rb + P;                                                   // P+1 prefix sizes
+    float4 *qs = reinterpret_cast<float4 *>(cum + P + 2);                    // dp4 query chunks
+    __shared__ int cnt;
+    __shared__ unsigned long long thresh;
+
+    constexpr int G = kThreads / LPR;
+    constexpr int ROUND = G * kUnroll;
+    const int tid = threadIdx.x, g = tid / LPR, gl = tid % LPR;
+    const int64_t q = blockIdx.x;
+
+    for (int c = tid; c < dp4; c += kThreads) qs[c] = Q[q * dp4 + c];
+    for (int i = tid; i < S; i += kThreads) buf[i] = kNoKey;
+    if (tid == 0) {
+        cnt = 0;
+        thresh = kNoKey;
+        int64_t tot = 0;
+        if (sel == nullptr) {
+            rb[0] = 0;
+            cum[0] = 0;
+            tot = root_end;
+            cum[1] = tot;
+        } else {
+            cum[0] = 0;
+            for (int s = 0; s < P; ++s) {
+                const int32_t p = sel[q * P + s];
+                int64_t b = 0, e = 0;
+                if (p >= 0) { b = off[p]; e = off[p + 1]; }
+                rb[s] = b;
+                tot += e - b;
+                cum[s + 1] = tot;
+            }
+        }
+    }
+    __syncthreads();
+    const int nr = sel == nullptr ? 1 : P;
+    const int64_t T = cum[nr];
+    const int lim = S - KP - ROUND;
+    if (tid == 0)
+        atomicAdd(&g_scan_bytes[out64 ? 1 : 0], (unsigned long long)T * (dp4 * 16ull + 4ull));
+
+    for (int64_t base = 0; base < T; base += ROUND) {
+        float acc[kUnroll];
+        int64_t row[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t t = base + g + (int64_t)u * G;
+            row[u] = -1;
+            if (t < T) {
+                // the range holding t: the last s with cum[s] <= t
+                int lo = 0, hi = nr - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (cum[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                row[u] = rb[lo] + (t - cum[lo]);
+            }
+            acc[u] = 0.f;
+        }
+        for (int c = gl; c < dp4; c += LPR) {
+            const float4 qv = qs[c];
+            float4 v[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                v[u] = row[u] >= 0 ? R[row[u] * dp4 + c] : qv;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const float e0 = v[u].x - qv.x, e1 = v[u].y - qv.y, e2 = v[u].z - qv.z,
+                            e3 = v[u].w - qv.w;
+                acc[u] = fmaf(e0, e0, acc[u]);
+                acc[u] = fmaf(e1, e1, acc[u]);
+                acc[u] = fmaf(e2, e2, acc[u]);
+                acc[u] = fmaf(e3, e3, acc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            for (int o = LPR / 2; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], o);
+        if (gl == 0) {
+            const unsigned long long th = thresh;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (row[u] < 0) continue;
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(acc[u]) << 32) | (unsigned)rid[row[u]];
+                if (key < th) buf[KP + atomicAdd(&cnt, 1)] = key;
+            }
+        }
+        __syncthreads();
+        const int c_now = cnt;
+        __syncthreads();
+        if (c_now > lim || base + ROUND >= T) {
+            for (int i = KP + c_now + tid; i < S; i += kThreads) buf[i] = kNoKey;
+            __syncthreads();
+            bitonic_sort_keys(buf, S);
+            for (int i = K + tid; i < KP; i += kThreads) buf[i] = kNoKey;
+            if (tid == 0) {
+                thresh = buf[K - 1];
+                cnt = 0;
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = tid; r < K; r += kThreads) {
+        const unsigned long long key = buf[r];
+        const bool ok = key != kNoKey;
+        const int32_t id = ok ? (int32_t)(key & 0xffffffffu) : -1;
+        const float dist = ok ? __uint_as_float((unsigned)(key >> 32)) : __int_as_float(0x7f800000);
+        if (out32) out32[q * K + r] = id;
+        if (out64) out64[q * K + r] = id;
+        if (out_d) out_d[q * K + r] = dist;
+    }
+}
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+void scan_topk(const ScanArgs &a, cudaStream_t s) {
+    if (a.nq == 0) return;
+    MASK_REQUIRE(a.K >= 1 && a.K <= 4096, "scan_topk: K out of range");
+    const int lpr = lanes_per_row(a.dp);
+    const int round = kThreads / lpr * kUnroll;
+    const int KP = next_pow2(a.K);
+    const int S = next_pow2(KP + 4 * round > 4 * KP ? KP + 4 * round : 4 * KP);
+    const int P = a.sel ? a.P : 1;
+    const size_t smem = (size_t)S * 8 + (size_t)(2 * P + 2) * 8 + (size_t)a.dp * 4;
+    MASK_REQUIRE(smem <= 220 * 1024, "scan_topk: K, probes or dimension too large");
+    const float4 *R = reinterpret_cast<const float4 *>(a.R);
+    const float4 *Qv = reinterpret_cast<const float4 *>(a.Q);
+#define MASK_SCAN(LPRV)                                                                     \
+    do {                                                                                    \
+        auto kfn = scan_topk_kernel<LPRV>;                                                  \
+        MASK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                       (int)smem));                                         \
+        kfn<<<(unsigned)a.nq, kThreads, smem, s>>>(R, a.dp / 4, a.rid, a.off, a.sel, P,     \
+                                                   a.root_end, Qv, a.K, KP, S, a.out_ids32, \
+                                                   a.out_ids64, a.out_d);                   \
+    } while (0)
+    ProfRegion pr(a.out_ids64 ? "scan_topk_leaf" : "scan_topk_level", s, 0.0);
+    switch (lpr) {
+    case 1: MASK_SCAN(1); break;
+    case 2: MASK_SCAN(2); break;
+    case 4: MASK_SCAN(4); break;
+    case 8: MASK_SCAN(8); break;
+    case 16: MASK_SCAN(16); break;
+    default: MASK_SCAN(32); break;
+    }
+#undef MASK_SCAN
+    MASK_LAUNCHED("scan_topk");
+}
+
+double scan_bytes(int which) {
+    unsigned long long v[2] = {0, 0};
+    if (cudaMemcpyFromSymbol(v, g_scan_bytes, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return (double)v[which];
+}
+
+void scan_bytes_reset() {
+    const unsigned long long z[2] = {0, 0};
+    if (cudaMemcpyToSymbol(g_scan_bytes, z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+}
+
+}  // namespace mask

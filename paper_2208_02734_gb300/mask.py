@@ -1,0 +1,344 @@
+"""ctypes binding of libmask_gb300.so (C ABI in include/mask.h).
+
+Argument marshalling only: every function here forwards to the C entry point
+of the same name.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays;
+outputs are allocated like the first array argument (CUDA tensor in ->
+CUDA tensor out, otherwise numpy).  CUDA tensors are passed on torch's current
+stream.  There is no fallback: if the library cannot be loaded (or built with
+nvcc), every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+MASK_OK, MASK_EINVAL, MASK_ENOMEM, MASK_ECUDA, MASK_ETIMEOUT, MASK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+MASK_FP32, MASK_BF16, MASK_FP8E4M3 = 0, 1, 2
+MASK_MAX_LEVELS = 16
+
+_STATUS = {0: "MASK_OK", -1: "MASK_EINVAL", -2: "MASK_ENOMEM", -3: "MASK_ECUDA",
+           -4: "MASK_ETIMEOUT", -5: "MASK_EUNSUPPORTED"}
+
+EXPORTED = [
+    "mask_last_error", "mask_build", "mask_build_csr", "mask_query", "mask_query_csr",
+    "mask_free", "mask_index_get_info", "mask_index_export_level", "mask_index_load",
+    "mask_kmeanspp", "mask_kmeans_assign", "mask_kmeans_update",
+    "mask_profile_enable", "mask_profile_reset", "mask_profile_read", "mask_launch_count",
+]
+
+
+class MaskError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn} -> {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mask_index_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("n_levels", C.c_int32),
+                ("k_per_level", C.c_int32 * MASK_MAX_LEVELS), ("iters", C.c_int32),
+                ("sparse", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp, _i32, _i64, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Open the shared library (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_stale else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmask_gb300.so not found at {path}")
+        lib = C.CDLL(path)
+        sig = {
+            "mask_last_error": (C.c_char_p, []),
+            "mask_build": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _i32, _u64, _vp, _vp]),
+            "mask_build_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _vp, _i32, _i32, _u64, _vp,
+                                         _vp]),
+            "mask_query": (C.c_int, [_vp, _vp, _i64, _i32, _vp, C.c_int, _vp, _vp, _vp]),
+            "mask_query_csr": (C.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _vp, C.c_int, _vp, _vp,
+                                         _vp]),
+            "mask_free": (None, [_vp]),
+            "mask_index_get_info": (C.c_int, [_vp, C.POINTER(mask_index_info)]),
+            "mask_index_export_level": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+            "mask_index_load": (C.c_int, [_vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+            "mask_kmeanspp": (C.c_int, [_vp, _i64, _i32, _i32, _u64, _i32, _vp, _vp, _vp]),
+            "mask_kmeans_assign": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
+            "mask_kmeans_update": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
+            "mask_profile_enable": (None, [_i32]),
+            "mask_profile_reset": (None, []),
+            "mask_profile_read": (C.c_int32, [C.c_char_p, C.POINTER(C.c_int64),
+                                              C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "mask_launch_count": (C.c_int64, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def mask_last_error() -> str:
+    return load().mask_last_error().decode()
+
+
+def _check(status: int, fn: str) -> None:
+    if status != MASK_OK:
+        raise MaskError(status, fn, mask_last_error())
+
+
+# ------------------------------------------------------------- marshalling
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _is_cuda(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
+def _arr(x, dtype: str):
+    """Contiguous array of the given dtype name; returns (obj, pointer)."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        td = {"float32": torch.float32, "int32": torch.int32, "int64": torch.int64,
+              "float64": torch.float64}[dtype]
+        x = x.to(td).contiguous()
+        return x, x.data_ptr()
+    x = np.ascontiguousarray(x, dtype=dtype)
+    return x, x.ctypes.data
+
+
+def _empty_like_kind(ref, shape, dtype: str):
+    if _is_cuda(ref):
+        import torch
+        td = {"float32": torch.float32, "int32": torch.int32, "int64": torch.int64,
+              "float64": torch.float64}[dtype]
+        t = torch.empty(shape, dtype=td, device=ref.device)
+        return t, t.data_ptr()
+    a = np.empty(shape, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def _stream(ref, stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    if _is_cuda(ref):
+        import torch
+        return torch.cuda.current_stream(ref.device).cuda_stream
+    return None
+
+
+def _host_i32(v):
+    a = np.ascontiguousarray(v, dtype=np.int32)
+    return a, a.ctypes.data
+
+
+# ------------------------------------------------------------------ index
+
+class Index:
+    """Owner of a mask_index* (freed by .free() or garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def free(self) -> None:
+        if self.handle and self.handle.value:
+            load().mask_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    @property
+    def info(self) -> mask_index_info:
+        return mask_index_get_info(self)
+
+
+def _handle(index) -> C.c_void_p:
+    h = index.handle if isinstance(index, Index) else C.c_void_p(index)
+    if not h or not h.value:
+        raise ValueError("index is freed or NULL")
+    return h
+
+
+# ------------------------------------------------------------- entry points
+
+def mask_build(points, k_per_level, iters: int, seed: int, stream=None) -> Index:
+    X, px = _arr(points, "float32")
+    n, d = X.shape
+    kp, pk = _host_i32(k_per_level)
+    out = C.c_void_p()
+    _check(load().mask_build(px, n, d, pk, len(kp), iters, seed & 0xFFFFFFFFFFFFFFFF,
+                             _stream(X, stream), C.byref(out)), "mask_build")
+    return Index(out.value)
+
+
+def mask_build_csr(row_ptr, col, val, n_cols: int, k_per_level, iters: int, seed: int,
+                   stream=None) -> Index:
+    rp, prp = _arr(row_ptr, "int64")
+    cl, pcl = _arr(col, "int32")
+    vl, pvl = _arr(val, "float32")
+    kp, pk = _host_i32(k_per_level)
+    out = C.c_void_p()
+    _check(load().mask_build_csr(prp, pcl, pvl, len(rp) - 1, n_cols, pk, len(kp), iters,
+                                 seed & 0xFFFFFFFFFFFFFFFF, _stream(vl, stream), C.byref(out)),
+           "mask_build_csr")
+    return Index(out.value)
+
+
+def mask_query(index, queries, k: int, probes, precision: int = MASK_FP32, stream=None):
+    Q, pq = _arr(queries, "float32")
+    nq = Q.shape[0]
+    pr, pp = _host_i32(probes)
+    ids, pids = _empty_like_kind(Q, (nq, k), "int64")
+    dists, pd = _empty_like_kind(Q, (nq, k), "float32")
+    _check(load().mask_query(_handle(index), pq, nq, k, pp, precision, pids, pd,
+                             _stream(Q, stream)), "mask_query")
+    return ids, dists
+
+
+def mask_query_csr(index, row_ptr, col, val, k: int, probes, precision: int = MASK_FP32,
+                   stream=None):
+    rp, prp = _arr(row_ptr, "int64")
+    cl, pcl = _arr(col, "int32")
+    vl, pvl = _arr(val, "float32")
+    nq = len(rp) - 1
+    pr, pp = _host_i32(probes)
+    ids, pids = _empty_like_kind(vl, (nq, k), "int64")
+    dists, pd = _empty_like_kind(vl, (nq, k), "float32")
+    _check(load().mask_query_csr(_handle(index), prp, pcl, pvl, nq, k, pp, precision, pids, pd,
+                                 _stream(vl, stream)), "mask_query_csr")
+    return ids, dists
+
+
+def mask_free(index) -> None:
+    if isinstance(index, Index):
+        index.free()
+    else:
+        load().mask_free(C.c_void_p(index))
+
+
+def mask_index_get_info(index) -> mask_index_info:
+    info = mask_index_info()
+    _check(load().mask_index_get_info(_handle(index), C.byref(info)), "mask_index_get_info")
+    return info
+
+
+def mask_index_export_level(index, level: int, device=None, stream=None):
+    """Returns dict(centroids [k x d], labels [n_below], chosen [k], objective [iters+1])."""
+    info = mask_index_get_info(index)
+    k = info.k_per_level[level]
+    n_below = info.n if level == 0 else info.k_per_level[level - 1]
+    if device is not None and str(device).startswith("cuda"):
+        import torch
+        ref = torch.empty(0, device=device)
+    else:
+        ref = None
+    cen, pc = _empty_like_kind(ref, (k, info.d), "float32")
+    lab, pl = _empty_like_kind(ref, (n_below,), "int32")
+    chosen = np.empty(k, dtype=np.int64)
+    obj = np.empty(info.iters + 1, dtype=np.float64)
+    chosen[:] = -1
+    obj[:] = np.nan
+    _check(load().mask_index_export_level(_handle(index), level, pc, pl, chosen.ctypes.data,
+                                          obj.ctypes.data, _stream(ref, stream)),
+           "mask_index_export_level")
+    return {"centroids": cen, "labels": lab, "chosen": chosen, "objective": obj}
+
+
+def mask_index_load(points, centroids, labels, stream=None) -> Index:
+    X, px = _arr(points, "float32")
+    n, d = X.shape
+    L = len(centroids)
+    cs = [_arr(c, "float32") for c in centroids]
+    ls = [_arr(lb, "int32") for lb in labels]
+    kp, pk = _host_i32([c[0].shape[0] for c in cs])
+    cptr = (C.c_void_p * L)(*[p for _, p in cs])
+    lptr = (C.c_void_p * L)(*[p for _, p in ls])
+    out = C.c_void_p()
+    _check(load().mask_index_load(px, n, d, L, pk, cptr, lptr, _stream(X, stream),
+                                  C.byref(out)), "mask_index_load")
+    return Index(out.value)
+
+
+def mask_kmeanspp(X, k: int, seed: int, level: int = 0, stream=None):
+    X, px = _arr(X, "float32")
+    n, d = X.shape
+    cen, pc = _empty_like_kind(X, (k, d), "float32")
+    chosen = np.empty(k, dtype=np.int64)
+    _check(load().mask_kmeanspp(px, n, d, k, seed & 0xFFFFFFFFFFFFFFFF, level, pc,
+                                chosen.ctypes.data, _stream(X, stream)), "mask_kmeanspp")
+    return cen, chosen
+
+
+def mask_kmeans_assign(X, Cc, with_dist: bool = True, stream=None):
+    X, px = _arr(X, "float32")
+    Cc, pc = _arr(Cc, "float32")
+    n, d = X.shape
+    lab, pl = _empty_like_kind(X, (n,), "int32")
+    dist, pd = _empty_like_kind(X, (n,), "float32") if with_dist else (None, None)
+    _check(load().mask_kmeans_assign(px, n, d, pc, Cc.shape[0], pl, pd, _stream(X, stream)),
+           "mask_kmeans_assign")
+    return lab, dist
+
+
+def mask_kmeans_update(X, labels, C_prev, stream=None):
+    X, px = _arr(X, "float32")
+    lb, pl = _arr(labels, "int32")
+    Cp, pc = _arr(C_prev, "float32")
+    n, d = X.shape
+    k = Cp.shape[0]
+    Cn, pn = _empty_like_kind(X, (k, d), "float32")
+    cnt, pcnt = _empty_like_kind(X, (k,), "int64")
+    _check(load().mask_kmeans_update(px, n, d, pl, k, pc, pn, pcnt, _stream(X, stream)),
+           "mask_kmeans_update")
+    return Cn, cnt
+
+
+# ------------------------------------------------------------ observability
+
+def mask_profile_enable(on: bool = True) -> None:
+    load().mask_profile_enable(1 if on else 0)
+
+
+def mask_profile_reset() -> None:
+    load().mask_profile_reset()
+
+
+def mask_profile_read(name: str):
+    """(launches, total_ms, work) for a region, or None if nothing recorded."""
+    n, ms, w = C.c_int64(0), C.c_double(0.0), C.c_double(0.0)
+    if not load().mask_profile_read(name.encode(), C.byref(n), C.byref(ms), C.byref(w)):
+        return None
+    return int(n.value), float(ms.value), float(w.value)
+
+
+def mask_launch_count() -> int:
+    return int(load().mask_launch_count())

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are seeded synthetic data (paper_2208_02734_gb300.synth).  Each k-means
+step is teacher-forced with the oracle's state (same centroids / labels in);
+the build is also compared end to end on the small dense workload (20,000 x 16,
+10 blobs, 200/20 centroids, 20 Lloyd iterations); the query is compared on an
+index assembled from the oracle's build (mask_index_load).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2208_02734_gb300 import mask as M
+from paper_2208_02734_gb300 import synth
+
+from parity_util import RTOL, arr, check_close, check_knn, check_labels, check_rows_close, f64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ------------------------------------------------------------------ assign
+
+ASSIGN_SHAPES = [(1000, 1, 7), (3000, 3, 200), (5000, 16, 257), (2000, 17, 64),
+                 (4000, 64, 130), (700, 130, 33), (300, 8, 1), (129, 24, 128)]
+
+
+@pytest.mark.parametrize("n,d,k", ASSIGN_SHAPES)
+def test_assign_matches_oracle(n, d, k):
+    rng = np.random.default_rng(n * 7 + d * 3 + k)
+    X = (rng.normal(size=(n, d)) * 3 + rng.uniform(-10, 10, size=(1, d))).astype(np.float32)
+    Cc = (X[rng.choice(n, k, replace=False)] + 0.05 * rng.normal(size=(k, d))).astype(np.float32)
+    lab_o, dist_o = O.assign(X, Cc)
+    lab_g, dist_g = M.mask_kmeans_assign(cuda(X), cuda(Cc))
+    check_labels(X, Cc, lab_g, lab_o)
+    eq = arr(lab_g) == lab_o
+    check_close(arr(dist_g)[eq], dist_o[eq], atol=1e-30, what="assign dist")
+
+
+def test_assign_exact_ties_go_to_smallest_index():
+    rng = np.random.default_rng(3)
+    base = rng.normal(size=(40, 16)).astype(np.float32)
+    Cc = np.concatenate([base, base, base])          # every centroid three times
+    X = np.concatenate([base, base + 0.25]).astype(np.float32)
+    lab_g, _ = M.mask_kmeans_assign(cuda(X), cuda(Cc))
+    lab_o, _ = O.assign(X, Cc)
+    assert np.array_equal(arr(lab_g), lab_o)
+    assert arr(lab_g).max() < 40
+
+
+def test_assign_host_buffers_equal_device_buffers():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(3000, 16)).astype(np.float32)
+    Cc = rng.normal(size=(50, 16)).astype(np.float32)
+    lh, dh = M.mask_kmeans_assign(X, Cc)
+    ld, dd = M.mask_kmeans_assign(cuda(X), cuda(Cc))
+    assert isinstance(lh, np.ndarray)
+    assert np.array_equal(lh, arr(ld)) and np.array_equal(dh, arr(dd))
+
+
+# ------------------------------------------------------------------ update
+
+@pytest.mark.parametrize("n,d,k", [(5000, 16, 200), (3000, 17, 64), (2000, 64, 33),
+                                   (1000, 130, 7), (800, 3, 300)])
+def test_update_matches_oracle(n, d, k):
+    rng = np.random.default_rng(n + d)
+    X = (rng.normal(size=(n, d)) * 2).astype(np.float32)
+    Cprev = (rng.normal(size=(k, d)) * 2).astype(np.float32)
+    Cprev[: k // 10] += 1000.0                        # far away: empty clusters
+    lab, _ = O.assign(X, Cprev)
+    C_o, cnt_o = O.update(X, lab, Cprev)
+    C_g, cnt_g = M.mask_kmeans_update(cuda(X), cuda(lab), cuda(Cprev))
+    assert np.array_equal(arr(cnt_g), cnt_o)
+    assert (cnt_o == 0).sum() >= k // 10
+    check_rows_close(C_g, C_o, what="centroids")
+    empty = cnt_o == 0
+    assert np.array_equal(arr(C_g)[empty], Cprev[empty])
+
+
+def test_update_rejects_out_of_range_labels():
+    X = np.zeros((10, 4), np.float32)
+    with pytest.raises(M.MaskError):
+        M.mask_kmeans_update(cuda(X), cuda(np.full(10, 5, np.int32)), cuda(np.zeros((3, 4), np.float32)))
+
+
+# ------------------------------------------------------------ k-means++
+
+@pytest.mark.parametrize("n,d,k,seed,level", [(5000, 16, 60, 0, 0), (20000, 16, 200, 0, 0),
+                                               (3000, 3, 300, 9, 2), (400, 33, 400, 5, 1)])
+def test_kmeanspp_matches_oracle(n, d, k, seed, level):
+    mix = synth.IsotropicMixture(d=d, n_blobs=10, seed=seed)
+    X = mix.sample(n, seed=seed + 1)
+    ch_o, C_o = O.seed_level(X, k, seed=seed, level=level)
+    C_g, ch_g = M.mask_kmeanspp(cuda(X), k, seed=seed, level=level)
+    assert ch_g.tolist() == ch_o.tolist()
+    assert np.array_equal(arr(C_g), X[ch_o])
+
+
+def test_kmeanspp_duplicates_exhaust_distinct_points():
+    X = np.repeat(np.arange(5, dtype=np.float32)[:, None], 4, axis=0)  # 5 values x 4 copies
+    ch_o, _ = O.seed_level(X, 12, seed=3, level=0)
+    _, ch_g = M.mask_kmeanspp(cuda(X), 12, seed=3, level=0)
+    assert ch_g.tolist() == ch_o.tolist()
+
+
+@pytest.mark.slow
+def test_kmeanspp_subsample_path_matches_oracle():
+    n, k = 4_200_000, 1024                 # n*k > 2^32: seeding on 8k sampled points
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(n, 2)).astype(np.float32)
+    ch_o, _ = O.seed_level(X, k, seed=5, level=0)
+    _, ch_g = M.mask_kmeanspp(cuda(X), k, seed=5, level=0)
+    assert ch_g.tolist() == ch_o.tolist()
+
+
+# ------------------------------------------------------------ build (c1)
+
+def small_dense_workload():
+    mix = synth.IsotropicMixture(d=16, n_blobs=10, sigma=1.0, box=10.0, seed=0)
+    return mix.sample(20_000, seed=0), mix.sample(1_000, seed=1)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    X, Q = small_dense_workload()
+    idx_o = O.build(X, [200, 20], iters=20, seed=0)
+    return X, Q, idx_o
+
+
+def test_build_end_to_end_matches_oracle(c1):
+    X, Q, idx_o = c1
+    with M.mask_build(cuda(X), [200, 20], iters=20, seed=0) as idx:
+        X_in = X
+        for lv in range(2):
+            e = M.mask_index_export_level(idx, lv)
+            assert e["chosen"].tolist() == idx_o.chosen[lv].tolist(), f"seeding level {lv}"
+            flips = check_labels(X_in, idx_o.centroids[lv], e["labels"], idx_o.labels[lv])
+            assert flips == 0, f"{flips} tolerated label flips at level {lv}"
+            check_rows_close(e["centroids"], idx_o.centroids[lv], what=f"centroids level {lv}")
+            # objective after each assignment, against the oracle's own trace
+            _, _, J = O.lloyd(X_in, f64(X_in)[idx_o.chosen[lv]], 20)
+            check_close(e["objective"], J[0::2], rtol=1e-4, what="objective trace")
+            assert np.all(np.diff(e["objective"]) <= 1e-5 * e["objective"][0])
+            X_in = idx_o.centroids[lv]       # the oracle's input of the next level
+
+
+def test_build_info_and_host_input(c1):
+    X, _, _ = c1
+    with M.mask_build(X, [200, 20], iters=2, seed=0) as idx:
+        info = idx.info
+        assert info.n == 20_000 and info.d == 16 and info.n_levels == 2
+        assert list(info.k_per_level[:2]) == [200, 20]
+        assert info.device_bytes >= 20_000 * 16 * 4
+
+
+# ------------------------------------------------------------------ query
+
+def oracle_index_fp32(idx_o):
+    """The oracle's index with centroids rounded to FP32 (what the GPU holds)."""
+    cs = [c.astype(np.float32) for c in idx_o.centroids]
+    return O.Index(idx_o.X, [c.astype(np.float64) for c in cs], idx_o.labels), cs
+
+
+@pytest.fixture(scope="module")
+def loaded(c1):
+    X, Q, idx_o = c1
+    ref, cs = oracle_index_fp32(idx_o)
+    idx = M.mask_index_load(cuda(X), [cuda(c) for c in cs], [cuda(lb) for lb in idx_o.labels])
+    yield X, Q, ref, idx
+    idx.free()
+
+
+@pytest.mark.parametrize("k,probes", [(10, [3, 3]), (1, [1, 1]), (10, [1, 1]), (100, [5, 4]),
+                                      (17, [2, 20])])
+def test_query_matches_oracle(loaded, k, probes):
+    X, Q, ref, idx = loaded
+    ids_o, d_o, clear = ref.query(Q, k, probes)
+    ids_g, d_g = M.mask_query(idx, cuda(Q), k, probes)
+    loose = check_knn(X, Q, ids_g, d_g, ids_o, d_o, clear)
+    assert loose <= 0.01 * len(Q)
+
+
+def test_probing_everything_is_exact_knn(loaded):
+    X, Q, ref, idx = loaded
+    ids_b, d_b = O.bruteforce_knn(X, Q[:200], 10)
+    ids_g, d_g = M.mask_query(idx, cuda(Q[:200]), 10, [200, 20])
+    check_knn(X, Q[:200], ids_g, d_g, ids_b, d_b, np.ones(200, bool))
+
+
+def test_query_results_do_not_depend_on_the_batch(loaded):
+    X, Q, ref, idx = loaded
+    ids_all, d_all = M.mask_query(idx, cuda(Q), 10, [3, 3])
+    pos = 0
+    for size in [1, 7, 512, 200, 280]:
+        ids_p, d_p = M.mask_query(idx, cuda(Q[pos:pos + size]), 10, [3, 3])
+        assert torch.equal(ids_p, ids_all[pos:pos + size])
+        assert torch.equal(d_p, d_all[pos:pos + size])
+        pos += size
+    assert pos == len(Q)
+
+
+def test_query_host_buffers(loaded):
+    X, Q, ref, idx = loaded
+    ids_h, d_h = M.mask_query(idx, Q[:50], 10, [3, 3])
+    ids_d, d_d = M.mask_query(idx, cuda(Q[:50]), 10, [3, 3])
+    assert np.array_equal(ids_h, arr(ids_d)) and np.array_equal(d_h, arr(d_d))
+
+
+def test_query_pads_when_fewer_candidates_than_k():
+    X = np.array([[0, 0], [1, 0], [10, 0], [11, 0], [30, 0]], np.float32)
+    C1 = np.array([[0.5, 0], [10.5, 0], [30, 0]], np.float32)
+    C2 = np.array([[5, 0], [30, 0]], np.float32)
+    idx = M.mask_index_load(cuda(X), [cuda(C1), cuda(C2)],
+                            [cuda(np.array([0, 0, 1, 1, 2], np.int32)), cuda(np.array([0, 0, 1], np.int32))])
+    ids, d = M.mask_query(idx, cuda(np.array([[0.2, 0]], np.float32)), 4, [1, 1])
+    assert arr(ids)[0].tolist() == [0, 1, -1, -1]
+    assert np.isinf(arr(d)[0][2:]).all()
+    ids, _ = M.mask_query(idx, cuda(np.array([[0.2, 0]], np.float32)), 5, [9, 9])
+    assert arr(ids)[0].tolist() == [0, 1, 2, 3, 4]
+    idx.free()
+
+
+def test_query_empty_batch(loaded):
+    X, Q, ref, idx = loaded
+    ids, d = M.mask_query(idx, cuda(Q[:0]), 10, [3, 3])
+    assert ids.shape == (0, 10)
+
+
+def test_descent_hand_worked_on_gpu():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "descent_2d.json")))
+    f = lambda a: cuda(np.array(a, np.float32))  # noqa: E731
+    idx = M.mask_index_load(f(g["points"]), [f(g["level1_centroids"]), f(g["level2_centroids"])],
+                            [cuda(np.array(g["level1_labels"], np.int32)),
+                             cuda(np.array(g["level2_labels"], np.int32))])
+    for c in g["queries"]:
+        ids, d = M.mask_query(idx, f([c["q"]]), c["k"], c["probes"])
+        assert arr(ids)[0].tolist() == c["ids"]
+        assert arr(d)[0].tolist() == [float("inf") if x == "inf" else x for x in c["dists"]]
+    idx.free()
+
+
+def test_export_and_reload_gives_the_same_answers(c1):
+    X, Q, _ = c1
+    with M.mask_build(cuda(X), [200, 20], iters=5, seed=1) as idx:
+        e = [M.mask_index_export_level(idx, lv) for lv in range(2)]
+        ids1, d1 = M.mask_query(idx, cuda(Q), 10, [3, 3])
+    idx2 = M.mask_index_load(cuda(X), [cuda(x["centroids"]) for x in e],
+                             [cuda(x["labels"]) for x in e])
+    ids2, d2 = M.mask_query(idx2, cuda(Q), 10, [3, 3])
+    idx2.free()
+    assert torch.equal(ids1, ids2) and torch.equal(d1, d2)
