@@ -195,6 +195,36 @@ mask_status mask_kmeans_update(const float *X, int64_t n, int32_t d, const int32
                                int32_t k, const float *C_prev, float *C_out,
                                int64_t *counts_out, mask_stream stream);
 
+/*
+ * Allocation-free variant of mask_kmeans_assign, for callers that cannot let
+ * this library allocate device memory: frameworks that reserve the GPU's
+ * memory up front and hand it out only through their own allocator (a
+ * cudaMalloc from inside the library could fail or fragment their pool), and
+ * latency-critical loops that cannot absorb the device-wide synchronisation
+ * cudaMalloc/cudaFree may cause.  The paper has no counterpart: this is an
+ * interface convenience, not part of the method.
+ *
+ * Same result as mask_kmeans_assign (same kernels), but it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its temporaries live in
+ * one file-scope device array of 2.36 MB that every GPU which loads the
+ * library holds until the process exits.
+ *   X [n x d], C [k x d] float32, labels_out [n] int32, dist_out [n] float32
+ *   (may be NULL): all DEVICE memory; X and C 16-byte aligned.
+ *   d must be a multiple of 8 (rows are used in place, not padded).
+ *   1 <= k <= 65536 (the array holds at most 65536 centroid norms); any n
+ *   (rows are processed 262,144 at a time).
+ * Larger k, host pointers or other d return MASK_EINVAL with a message.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array: calls whose
+ * work overlaps on the GPU (different streams or host threads without
+ * ordering between them) race and give wrong labels.  Calls ordered on one
+ * stream are safe; each call clears what it needs.
+ */
+mask_status mask_kmeans_assign_noalloc(const float *X, int64_t n, int32_t d, const float *C,
+                                       int32_t k, int32_t *labels_out, float *dist_out,
+                                       mask_stream stream);
+
 /* ---- observability ---------------------------------------------------- */
 
 /*

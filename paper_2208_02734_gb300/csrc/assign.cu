@@ -11,8 +11,10 @@
 //  2. Rows whose gap is within the bound are listed and re-decided exactly in
 //     the difference form sum_t (x_t - c_t)^2 (relative error ~ dp * 2^-24 of
 //     the distance itself) over all centroids.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -215,3 +217,126 @@ void assign_labels(const float *X, const float *xn, int64_t n, int dp, const flo
 }
 
 }  // namespace mask
+
+// ------------------------------------------------- allocation-free variant
+//
+// mask_kmeans_assign_noalloc runs the same two kernels as mask_kmeans_assign,
+// but every temporary lives in one file-scope device array instead of memory
+// obtained from cudaMalloc/cudaMallocAsync.  The array is sized for at most
+// kNoAllocMaxK centroids; rows are processed kNoAllocChunk at a time, so the
+// number of rows is unbounded.  Layout in 4-byte words, each section starting
+// on a 256-byte boundary:
+//   [centroid norms: kNoAllocMaxK][max norm: 64][flag count: 64]
+//   [row norms: kNoAllocChunk][flagged rows: kNoAllocChunk]
+namespace mask {
+namespace {
+
+constexpr int kNoAllocMaxK = 65536;
+constexpr int64_t kNoAllocChunk = 1 << 18;
+constexpr size_t kOffCn = 0;
+constexpr size_t kOffCmax = kOffCn + kNoAllocMaxK;
+constexpr size_t kOffNflag = kOffCmax + 64;
+constexpr size_t kOffXn = kOffNflag + 64;
+constexpr size_t kOffFlagged = kOffXn + kNoAllocChunk;
+constexpr size_t kNoAllocWords = kOffFlagged + kNoAllocChunk;  // 2.36 MB
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the symbol g_noalloc_scratch is only a host-side stand-in, so the address is
+// looked up once per device (with that device current) and cached.
+uint32_t *noalloc_scratch() {
+    int dev = 0;
+    MASK_CUDA(cudaGetDevice(&dev));
+    MASK_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            fail(MASK_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    return static_cast<uint32_t *>(g_noalloc_ptr[dev]);
+}
+
+bool is_device_memory(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void assign_noalloc(const float *X, int64_t n, int d, const float *C, int k, int32_t *labels,
+                    float *dist, cudaStream_t s) {
+    uint32_t *base = noalloc_scratch();
+    float *cn = reinterpret_cast<float *>(base + kOffCn);
+    float *cmax = reinterpret_cast<float *>(base + kOffCmax);
+    int *nflag = reinterpret_cast<int *>(base + kOffNflag);
+    float *xn = reinterpret_cast<float *>(base + kOffXn);
+    int32_t *flagged = reinterpret_cast<int32_t *>(base + kOffFlagged);
+
+    row_sqnorm(C, k, d, cn, s);
+    max_reduce(cn, k, cmax, s);  // clears cmax first
+    const float coef = (float)(2.0 * (2.0 * d + 4.0) * 0x1.0p-24);
+    const int lpr = lanes_per_row(d);
+    for (int64_t c0 = 0; c0 < n; c0 += kNoAllocChunk) {
+        const int64_t m = std::min<int64_t>(kNoAllocChunk, n - c0);
+        const float *Xc = X + c0 * d;
+        row_sqnorm(Xc, m, d, xn, s);
+        MASK_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), s));
+        assign_gemm_kernel<<<(unsigned)((m + BM - 1) / BM), NT, 0, s>>>(
+            Xc, xn, m, d, C, cn, k, cmax, coef, labels + c0, flagged, nflag);
+        MASK_LAUNCHED("assign_gemm (no-alloc)");
+        const float4 *X4 = reinterpret_cast<const float4 *>(Xc);
+        const float4 *C4 = reinterpret_cast<const float4 *>(C);
+        const int grid = 152 * 8;
+        switch (lpr) {
+        case 1: assign_recheck_kernel<1><<<grid, 256, 0, s>>>(X4, d / 4, C4, k, flagged, nflag, labels + c0); break;
+        case 2: assign_recheck_kernel<2><<<grid, 256, 0, s>>>(X4, d / 4, C4, k, flagged, nflag, labels + c0); break;
+        case 4: assign_recheck_kernel<4><<<grid, 256, 0, s>>>(X4, d / 4, C4, k, flagged, nflag, labels + c0); break;
+        case 8: assign_recheck_kernel<8><<<grid, 256, 0, s>>>(X4, d / 4, C4, k, flagged, nflag, labels + c0); break;
+        case 16: assign_recheck_kernel<16><<<grid, 256, 0, s>>>(X4, d / 4, C4, k, flagged, nflag, labels + c0); break;
+        default: assign_recheck_kernel<32><<<grid, 256, 0, s>>>(X4, d / 4, C4, k, flagged, nflag, labels + c0); break;
+        }
+        MASK_LAUNCHED("assign_recheck (no-alloc)");
+        if (dist) label_dist(Xc, m, d, C, labels + c0, dist + c0, s);
+    }
+}
+
+}  // namespace
+}  // namespace mask
+
+extern "C" mask_status mask_kmeans_assign_noalloc(const float *X, int64_t n, int32_t d,
+                                                  const float *C, int32_t k, int32_t *labels_out,
+                                                  float *dist_out, mask_stream stream) {
+    using namespace mask;
+    try {
+        MASK_REQUIRE(X && C && labels_out, "NULL argument");
+        MASK_REQUIRE(n >= 0 && n <= INT32_MAX, "n must be in [0, 2^31)");
+        MASK_REQUIRE(d >= 8 && d % 8 == 0, "d must be a positive multiple of 8 (rows are used in place)");
+        MASK_REQUIRE(k >= 1 && k <= kNoAllocMaxK,
+                     "k must be in [1, 65536]: the no-alloc scratch holds at most 65536 centroid norms");
+        MASK_REQUIRE((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(C)) % 16 == 0,
+                     "X and C must be 16-byte aligned");
+        MASK_REQUIRE(is_device_memory(X) && is_device_memory(C) && is_device_memory(labels_out) &&
+                         (dist_out == nullptr || is_device_memory(dist_out)),
+                     "all arrays must be device memory (host staging would allocate)");
+        if (n == 0) return MASK_OK;
+        assign_noalloc(X, n, d, C, k, labels_out, dist_out, (cudaStream_t)stream);
+        return MASK_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return MASK_ECUDA;
+    }
+}

@@ -20,6 +20,8 @@ struct Error : std::runtime_error {
 };
 
 [[noreturn]] void fail(mask_status s, const std::string &msg);
+// Sets the calling thread's mask_last_error() message.
+void set_last_error(const std::string &msg);
 
 // ------------------------------------------------------------- profiling
 

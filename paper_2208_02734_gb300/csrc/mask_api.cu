@@ -43,6 +43,8 @@ thread_local std::string g_err;
 
 void fail(mask_status s, const std::string &msg) { throw Error(s, msg); }
 
+void set_last_error(const std::string &msg) { g_err = msg; }
+
 namespace {
 
 // ----------------------------------------------------------- R1: SplitMix64

@@ -30,6 +30,7 @@ EXPORTED = [
     "mask_free", "mask_index_get_info", "mask_index_export_level", "mask_index_load",
     "mask_kmeanspp", "mask_kmeans_assign", "mask_kmeans_update",
     "mask_profile_enable", "mask_profile_reset", "mask_profile_read", "mask_launch_count",
+    "mask_kmeans_assign_noalloc",
 ]
 
 
@@ -84,6 +85,7 @@ def load(build_if_stale: bool = True):
             "mask_profile_read": (C.c_int32, [C.c_char_p, C.POINTER(C.c_int64),
                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mask_launch_count": (C.c_int64, []),
+            "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -307,6 +309,17 @@ def mask_kmeans_assign(X, Cc, with_dist: bool = True, stream=None):
     _check(load().mask_kmeans_assign(px, n, d, pc, Cc.shape[0], pl, pd, _stream(X, stream)),
            "mask_kmeans_assign")
     return lab, dist
+
+
+def mask_kmeans_assign_noalloc(X, Cc, labels_out, dist_out=None, stream=None):
+    """Allocation-free assignment for callers that cannot let the library
+    allocate: every array (inputs and the caller-provided outputs) must be a
+    CUDA tensor; d a multiple of 8; k <= 65536."""
+    _check(load().mask_kmeans_assign_noalloc(
+        X.data_ptr(), X.shape[0], X.shape[1], Cc.data_ptr(), Cc.shape[0], labels_out.data_ptr(),
+        None if dist_out is None else dist_out.data_ptr(), _stream(X, stream)),
+        "mask_kmeans_assign_noalloc")
+    return labels_out, dist_out
 
 
 def mask_kmeans_update(X, labels, C_prev, stream=None):
