@@ -182,23 +182,30 @@ __global__ void sum_f32_to_f64_kernel(const float *__restrict__ v, int64_t n, do
 
 // --------------------------------------------------------------- k-means++
 
-constexpr int kKppThreads = 256;
-constexpr int kKppRows = 256;  // rows per block; one D^2 block sum each
+constexpr int kKppThreads = 512;
+constexpr int kKppRows = 1024;   // rows per block; one D^2 block sum each
+constexpr int kKppPer = kKppRows / kKppThreads;  // rows per thread in the block search
+constexpr int kKppUnroll = 8;    // rows in flight per lane group
 
-// One k-means++ step t >= 1 (§3.2): fold the centre picked at step t-1 into
-// D^2, then the last block to finish draws centre t: the smallest row whose
-// inclusive prefix of D^2 exceeds u_t * sum(D^2) (sums in FP64); if the sum
-// is 0, the lowest-index row not chosen yet.
+// One k-means++ step (§3.2).  The step number t >= 1 is read from *t_dev.
+// Fold the centre picked at step t-1 into D^2 (FP32 difference form), then
+// the last block to finish draws centre t: the smallest row whose inclusive
+// prefix of D^2 exceeds u_t * sum(D^2) (all sums FP64); if that sum is 0, the
+// lowest-index row not chosen yet.  The last block then advances *t_dev, so
+// identical launches can be replayed step after step.
 template <int LPR>
 __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
-    const float *__restrict__ X, int64_t m, int dp, int t, const double *__restrict__ u,
-    float *__restrict__ D2, double *__restrict__ bsum, unsigned *__restrict__ counter,
-    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken) {
+    const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
+    const double *__restrict__ u, float *__restrict__ D2, double *__restrict__ bsum,
+    unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
+    unsigned char *__restrict__ taken) {
     __shared__ double red[kKppThreads / 32];
     __shared__ long long redi[kKppThreads / 32];
     __shared__ double incs[kKppThreads];
     __shared__ int s_last;
+    __shared__ long long s_pick;
 
+    const int t = *t_dev;
     const int tid = threadIdx.x;
     constexpr int G = kKppThreads / LPR;
     const int g = tid / LPR, gl = tid % LPR;
@@ -208,25 +215,39 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
     const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
 
     double local = 0.0;
-    for (int r = g; r < kKppRows; r += G) {
-        const int64_t i = r0 + r;
-        float acc = 0.f;
-        if (i < m) {
-            const float4 *xr = reinterpret_cast<const float4 *>(X + i * dp);
-            for (int ch = gl; ch < dp4; ch += LPR) {
-                float4 a = xr[ch], b = __ldg(crow + ch);
-                float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
-                acc = fmaf(e0, e0, acc);
-                acc = fmaf(e1, e1, acc);
-                acc = fmaf(e2, e2, acc);
-                acc = fmaf(e3, e3, acc);
+    for (int rb = 0; rb < kKppRows; rb += G * kKppUnroll) {
+        float acc[kKppUnroll];
+#pragma unroll
+        for (int q = 0; q < kKppUnroll; ++q) acc[q] = 0.f;
+        for (int ch = gl; ch < dp4; ch += LPR) {
+            const float4 b = __ldg(crow + ch);
+            float4 a[kKppUnroll];
+#pragma unroll
+            for (int q = 0; q < kKppUnroll; ++q) {
+                const int r = rb + q * G + g;  // row within this block
+                const int64_t i = r0 + r;
+                a[q] = (r < kKppRows && i < m) ? reinterpret_cast<const float4 *>(X + i * dp)[ch] : b;
+            }
+#pragma unroll
+            for (int q = 0; q < kKppUnroll; ++q) {
+                const float e0 = a[q].x - b.x, e1 = a[q].y - b.y, e2 = a[q].z - b.z,
+                            e3 = a[q].w - b.w;
+                acc[q] = fmaf(e0, e0, acc[q]);
+                acc[q] = fmaf(e1, e1, acc[q]);
+                acc[q] = fmaf(e2, e2, acc[q]);
+                acc[q] = fmaf(e3, e3, acc[q]);
             }
         }
-        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (gl == 0 && i < m) {
-            const float nv = (t == 1) ? acc : fminf(D2[i], acc);
-            D2[i] = nv;
-            local += (double)nv;
+#pragma unroll
+        for (int q = 0; q < kKppUnroll; ++q) {
+            for (int o = LPR / 2; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], o);
+            const int r = rb + q * G + g;
+            const int64_t i = r0 + r;
+            if (gl == 0 && r < kKppRows && i < m) {
+                const float nv = (t == 1) ? acc[q] : fminf(D2[i], acc[q]);
+                D2[i] = nv;
+                local += (double)nv;
+            }
         }
     }
     const double bs = block_sum_f64<kKppThreads>(local, red);
@@ -264,22 +285,50 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
             __syncthreads();
         }
         if (fb != LLONG_MAX) {
-            const int64_t i = fb * kKppRows + tid;
-            const double v = i < m ? (double)__ldcg(D2 + i) : 0.0;
-            const double inc = block_incl_scan_f64<kKppThreads>(v, red) + excl;
-            pick = block_min_ll<kKppThreads>(i < m && inc > target ? i : LLONG_MAX, redi);
-            if (pick == LLONG_MAX)  // rounding: the last positive row of that block
-                pick = block_max_ll<kKppThreads>(i < m && v > 0.0 ? i : -1, redi);
+            // within the block: each thread owns kKppPer consecutive rows
+            const int64_t i0 = fb * kKppRows + (int64_t)tid * kKppPer;
+            double v[kKppPer], vs = 0.0;
+#pragma unroll
+            for (int q = 0; q < kKppPer; ++q) {
+                v[q] = i0 + q < m ? (double)__ldcg(D2 + i0 + q) : 0.0;
+                vs += v[q];
+            }
+            const double inc = block_incl_scan_f64<kKppThreads>(vs, red) + excl;
+            const long long owner =
+                block_min_ll<kKppThreads>(inc > target && vs > 0.0 ? tid : LLONG_MAX, redi);
+            if (tid == 0) s_pick = -1;
+            __syncthreads();
+            if (owner != LLONG_MAX && tid == owner) {
+                double run = inc - vs;
+                long long p = -1;
+#pragma unroll
+                for (int q = 0; q < kKppPer; ++q) {
+                    if (v[q] > 0.0) p = i0 + q;
+                    run += v[q];
+                    if (run > target && v[q] > 0.0) { p = i0 + q; break; }
+                }
+                s_pick = p;
+            }
+            long long lastpos = -1;
+#pragma unroll
+            for (int q = 0; q < kKppPer; ++q)
+                if (v[q] > 0.0) lastpos = i0 + q;
+            __syncthreads();
+            const long long op = s_pick;
+            pick = op >= 0 ? op : block_max_ll<kKppThreads>(lastpos, redi);
         }
-        if (pick < 0 || pick == LLONG_MAX) {
+        if (pick < 0) {
             // rounding left the target past the end: last row with D^2 > 0
             long long lb = -1;
             for (int b = tid; b < nb; b += kKppThreads)
                 if (__ldcg(bsum + b) > 0.0) lb = b;
             lb = block_max_ll<kKppThreads>(lb, redi);
-            const int64_t i = lb * kKppRows + tid;
-            const bool pos = lb >= 0 && i < m && __ldcg(D2 + i) > 0.f;
-            pick = block_max_ll<kKppThreads>(pos ? i : -1, redi);
+            long long lastpos = -1;
+            for (int q = tid; q < kKppRows; q += kKppThreads) {
+                const int64_t i = lb * kKppRows + q;
+                if (lb >= 0 && i < m && __ldcg(D2 + i) > 0.f) lastpos = i;
+            }
+            pick = block_max_ll<kKppThreads>(lastpos, redi);
         }
     } else {
         __syncthreads();
@@ -294,6 +343,7 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
         chosen[t] = pick;
         taken[pick] = 1;
         *counter = 0u;
+        *t_dev = t + 1;
     }
 }
 
@@ -573,14 +623,47 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
     Scratch<float> D2(m, s);
     Scratch<double> bsum(nb, s);
     Scratch<unsigned> counter(1, s);
+    Scratch<int> t_dev(1, s);
     Scratch<unsigned char> taken(m, s);
+    const int one = 1;
     MASK_CUDA(cudaMemsetAsync(counter.get(), 0, sizeof(unsigned), s));
     MASK_CUDA(cudaMemsetAsync(taken.get(), 0, m, s));
+    MASK_CUDA(cudaMemcpyAsync(t_dev.get(), &one, sizeof(int), cudaMemcpyHostToDevice, s));
     const int lpr = lanes_per_row(dp);
-    for (int t = 1; t < k; ++t) {
-        MASK_LPR_DISPATCH(lpr, (kpp_step_kernel<L><<<nb, kKppThreads, 0, s>>>(
-                                   Xs, m, dp, t, u_dev, D2.get(), bsum.get(), counter.get(),
-                                   chosen, taken.get())));
+    auto launch = [&](cudaStream_t st) {
+        MASK_LPR_DISPATCH(lpr, (kpp_step_kernel<L><<<nb, kKppThreads, 0, st>>>(
+                                   Xs, m, dp, t_dev.get(), u_dev, D2.get(), bsum.get(),
+                                   counter.get(), chosen, taken.get())));
+    };
+    // The steps are identical launches (the step number lives on the device),
+    // so a captured graph of kBatch steps is replayed; the rest run directly.
+    constexpr int kBatch = 64;
+    const int steps = k - 1;
+    int done = 0;
+    if (steps >= 2 * kBatch) {
+        cudaStream_t cs;
+        MASK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int i = 0; i < kBatch; ++i) launch(cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) {
+            for (; done + kBatch <= steps && e == cudaSuccess; done += kBatch) {
+                e = cudaGraphLaunch(exec, s);
+                for (int i = 0; i < kBatch; ++i) count_launch();
+            }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) fail(MASK_ECUDA, std::string("kmeans++ graph: ") + cudaGetErrorString(e));
+    }
+    for (; done < steps; ++done) {
+        launch(s);
         MASK_LAUNCHED("kpp_step");
     }
 }

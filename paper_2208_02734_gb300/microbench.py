@@ -1,0 +1,89 @@
+"""Run one MASK step on seeded synthetic data and time it (CUDA events).
+
+Used to look at a single kernel in isolation (e.g. under a profiler):
+
+  python -m paper_2208_02734_gb300.microbench assign --n 1000000 --d 64 --k 4096
+  python -m paper_2208_02734_gb300.microbench update --n 1000000 --d 64 --k 4096
+  python -m paper_2208_02734_gb300.microbench kmeanspp --n 262144 --d 64 --k 2048
+  python -m paper_2208_02734_gb300.microbench query --n 1000000 --d 64 --k 4096 \
+      --levels 4096,128 --probes 64,16 --nq 10000
+
+Points come from an anisotropic Gaussian mixture (synth.AnisotropicMixture,
+100 blobs); prints one JSON line with the mean time per call.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("step", choices=["assign", "update", "kmeanspp", "query", "build"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--d", type=int, default=64)
+    ap.add_argument("--k", type=int, default=4096)
+    ap.add_argument("--levels", type=str, default="")
+    ap.add_argument("--probes", type=str, default="")
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--topk", type=int, default=10)
+    ap.add_argument("--iters", type=int, default=5)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=1)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import mask as M
+    from . import synth
+
+    dev = torch.device("cuda:0")
+    mix = synth.AnisotropicMixture(d=a.d, n_blobs=100, seed=0)
+    X = torch.from_numpy(mix.sample(a.n, seed=0)).to(dev)
+    rng = np.random.default_rng(1)
+    C = X[torch.from_numpy(rng.choice(a.n, a.k, replace=False)).to(dev)].contiguous()
+    levels = [int(v) for v in a.levels.split(",")] if a.levels else [a.k]
+    probes = [int(v) for v in a.probes.split(",")] if a.probes else [8] * len(levels)
+
+    state = {}
+    if a.step == "update":
+        state["labels"], _ = M.mask_kmeans_assign(X, C, with_dist=False)
+    if a.step == "query":
+        state["index"] = M.mask_build(X, levels, a.iters, seed=0)
+        state["Q"] = torch.from_numpy(mix.sample(a.nq, seed=1)).to(dev)
+
+    def run():
+        if a.step == "assign":
+            M.mask_kmeans_assign(X, C, with_dist=False)
+        elif a.step == "update":
+            M.mask_kmeans_update(X, state["labels"], C)
+        elif a.step == "kmeanspp":
+            M.mask_kmeanspp(X, a.k, seed=0)
+        elif a.step == "query":
+            M.mask_query(state["index"], state["Q"], a.topk, probes)
+        else:
+            M.mask_build(X, levels, a.iters, seed=0).free()
+
+    for _ in range(a.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    out = {"step": a.step, "n": a.n, "d": a.d, "k": a.k, "ms": ms}
+    if a.step == "assign":
+        out["tflops"] = 2.0 * a.n * a.k * a.d / (ms / 1e3) / 1e12
+    print(json.dumps(out))
+    if "index" in state:
+        state["index"].free()
+
+
+if __name__ == "__main__":
+    main()
