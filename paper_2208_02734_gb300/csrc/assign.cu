@@ -218,6 +218,27 @@ void assign_labels(const float *X, const float *xn, int64_t n, int dp, const flo
 
 }  // namespace mask
 
+namespace mask {
+
+void assign_recheck_rows(const float *X, int dp, const float *C, int k, const int32_t *rows,
+                         const int *count, int32_t *labels, cudaStream_t s) {
+    const int lpr = lanes_per_row(dp);
+    const int grid = 152 * 8;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    const float4 *C4 = reinterpret_cast<const float4 *>(C);
+    switch (lpr) {
+    case 1: assign_recheck_kernel<1><<<grid, 256, 0, s>>>(X4, dp / 4, C4, k, rows, count, labels); break;
+    case 2: assign_recheck_kernel<2><<<grid, 256, 0, s>>>(X4, dp / 4, C4, k, rows, count, labels); break;
+    case 4: assign_recheck_kernel<4><<<grid, 256, 0, s>>>(X4, dp / 4, C4, k, rows, count, labels); break;
+    case 8: assign_recheck_kernel<8><<<grid, 256, 0, s>>>(X4, dp / 4, C4, k, rows, count, labels); break;
+    case 16: assign_recheck_kernel<16><<<grid, 256, 0, s>>>(X4, dp / 4, C4, k, rows, count, labels); break;
+    default: assign_recheck_kernel<32><<<grid, 256, 0, s>>>(X4, dp / 4, C4, k, rows, count, labels); break;
+    }
+    MASK_LAUNCHED("assign_recheck_rows");
+}
+
+}  // namespace mask
+
 // ------------------------------------------------- allocation-free variant
 //
 // mask_kmeans_assign_noalloc runs the same two kernels as mask_kmeans_assign,

@@ -1,0 +1,559 @@
+// assign_tc.cu -- Lloyd assignment half-step (§2.4) on the 5th-generation
+// tensor cores: labels[i] = argmin_j ||x_i - c_j||^2, ties to the smallest j.
+//
+// Distances in the expanded form ||x||^2 - 2 x.c + ||c||^2.  The cross term
+// x.c is a GEMM on tcgen05 (kind::tf32, FP32 accumulation in tensor memory)
+// made FP32-accurate with the 3xTF32 split: x = x_hi + x_lo with x_hi the
+// TF32-rounded value and x_lo = x - x_hi (exact), and
+//     x.c ~= x_hi.c_hi + x_hi.c_lo + x_lo.c_hi
+// (Ootomo & Yokota 2022, "Recovering single precision accuracy from Tensor
+// Cores while surpassing the FP32 theoretical peak performance").
+//
+// One CTA owns 128 rows of X.  Their hi/lo tiles stay in shared memory while
+// 128-centroid tiles of C stream through a TMA pipeline; the accumulator is
+// double-buffered in TMEM so the epilogue of tile j overlaps the MMAs of j+1.
+// Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer, warp 2 = TMEM
+// allocator, warps 4-7 = epilogue (one thread per row, TMEM lane = row), which
+// keeps the four smallest distances of its row over all k centroids.
+//
+// A row's label is certain when its best and second-best distances differ by
+// more than twice the error bound of the expanded form; otherwise the row is
+// re-decided exactly in the difference form sum_t (x_t - c_t)^2, over its
+// three best candidates when the fourth is clear of the bound, else over all
+// centroids.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cfloat>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace mask {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int TC_M = 128, TC_N = 128;   // MMA tile: 128 rows x 128 centroids
+constexpr int TC_THREADS = 256;
+constexpr int TC_BOX_K = 32;            // fp32 columns per TMA box (128 bytes)
+constexpr int TC_BOX_BYTES = TC_M * TC_BOX_K * 4;   // 16 KB
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                            ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase with the given parity to complete.  Gives up
+// after kWaitNs of wall time, or as soon as any CTA of the grid has raised the
+// abort word, and then raises it itself so the rest of the grid stops early.
+// A drain (waiting for this thread's own copies before the CTA exits) ignores
+// the abort word and is bounded by time only.
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s; a healthy wait takes microseconds
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *abort_word,
+                                          bool drain = false) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0;; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 255u) == 255u) {
+            if ((!drain && *(volatile int *)abort_word != 0) || globaltimer_ns() - t0 > kWaitNs) {
+                atomicExch(abort_word, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO); the leading offset is unused in this mode.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Keep the four smallest values (v0 <= v1 <= v2 <= v3) and the indices of
+// the first three; strict comparisons keep the earliest index on ties.
+struct Top4 {
+    float v0, v1, v2, v3;
+    int i0, i1, i2;
+    __device__ void init() {
+        v0 = v1 = v2 = v3 = FLT_MAX;
+        i0 = i1 = i2 = -1;
+    }
+    __device__ __forceinline__ void push(float d, int j) {
+        if (d < v3) {
+            if (d < v2) {
+                v3 = v2;
+                if (d < v1) {
+                    v2 = v1; i2 = i1;
+                    if (d < v0) { v1 = v0; i1 = i0; v0 = d; i0 = j; }
+                    else { v1 = d; i1 = j; }
+                } else { v2 = d; i2 = j; }
+            } else { v3 = d; }
+        }
+    }
+};
+
+// ------------------------------------------------------------- main kernel
+
+template <int KB, int S>
+__global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
+    const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl,
+    const __grid_constant__ CUtensorMap tmCh, const __grid_constant__ CUtensorMap tmCl,
+    const float *__restrict__ xn, int64_t n, int ksteps, const float *__restrict__ cn, int k,
+    const float *__restrict__ cn_max, float margin_coef, int32_t *__restrict__ labels,
+    int4 *__restrict__ list3, int *__restrict__ n3, int32_t *__restrict__ listF,
+    int *__restrict__ nF, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr uint32_t kStage = 2u * KB * TC_BOX_BYTES;  // hi + lo tiles of one C tile
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;        // swizzled tiles need 1 KB alignment
+    unsigned char *basep = smem_raw + (base - raw);
+    const uint32_t A_hi = base, A_lo = base + KB * TC_BOX_BYTES;
+    const uint32_t B0 = base + 2u * KB * TC_BOX_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(basep + 2u * KB * TC_BOX_BYTES + S * kStage);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
+    __shared__ int s_err;
+
+    // barriers: a_full | b_full[S] | b_empty[S] | acc_full[2] | acc_empty[2]
+    const uint32_t bar0 = smem_u32(bars);
+    const uint32_t a_full = bar0;
+    auto b_full = [&](int s) { return bar0 + 8u * (1 + s); };
+    auto b_empty = [&](int s) { return bar0 + 8u * (1 + S + s); };
+    auto acc_full = [&](int a) { return bar0 + 8u * (1 + 2 * S + a); };
+    auto acc_empty = [&](int a) { return bar0 + 8u * (3 + 2 * S + a); };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
+    const int ntiles = (k + TC_N - 1) / TC_N;
+
+    // a CTA that starts after the grid aborted does nothing
+    if (*(volatile int *)err != 0) return;
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        mbar_init(a_full, 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(b_full(s), 1);
+            mbar_init(b_empty(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(acc_full(a), 1);
+            mbar_init(acc_empty(a), 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                         smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        mbar_expect_tx(a_full, 2u * KB * TC_BOX_BYTES);
+        for (int kb = 0; kb < KB; ++kb) {
+            tma_load_2d(A_hi + kb * TC_BOX_BYTES, &tmXh, kb * TC_BOX_K, (int)row0, a_full);
+            tma_load_2d(A_lo + kb * TC_BOX_BYTES, &tmXl, kb * TC_BOX_K, (int)row0, a_full);
+        }
+        int armed = 0;
+        bool ok = true;
+        for (int j = 0; j < ntiles; ++j) {
+            const int s = j % S, u = j / S;
+            if (u > 0 && !mbar_wait(b_empty(s), (u - 1) & 1, err)) { ok = false; break; }
+            const uint32_t bh = B0 + s * kStage, bl = bh + KB * TC_BOX_BYTES;
+            mbar_expect_tx(b_full(s), kStage);
+            for (int kb = 0; kb < KB; ++kb) {
+                tma_load_2d(bh + kb * TC_BOX_BYTES, &tmCh, kb * TC_BOX_K, j * TC_N, b_full(s));
+                tma_load_2d(bl + kb * TC_BOX_BYTES, &tmCl, kb * TC_BOX_K, j * TC_N, b_full(s));
+            }
+            armed = j + 1;
+        }
+        // every load this thread issued must land before the CTA may exit
+        mbar_wait(a_full, 0, err, true);
+        for (int j = (armed > S ? armed - S : 0); j < armed; ++j)
+            mbar_wait(b_full(j % S), (j / S) & 1, err, true);
+        if (!ok) s_err = 1;
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        bool ok = mbar_wait(a_full, 0, err);
+        int last = -1;
+        for (int j = 0; ok && j < ntiles; ++j) {
+            const int s = j % S, u = j / S, a = j & 1, v = j >> 1;
+            ok = mbar_wait(b_full(s), u & 1, err);
+            if (ok && v > 0) ok = mbar_wait(acc_empty(a), (v - 1) & 1, err);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(a * TC_N);
+            const uint32_t bh = B0 + s * kStage, bl = bh + KB * TC_BOX_BYTES;
+            for (int kk = 0; kk < ksteps; ++kk) {
+                const uint32_t off = (uint32_t)(kk >> 2) * TC_BOX_BYTES + (uint32_t)(kk & 3) * 32u;
+                const uint64_t ah = sw128_desc(A_hi + off), al = sw128_desc(A_lo + off);
+                const uint64_t ch = sw128_desc(bh + off), cl = sw128_desc(bl + off);
+                mma_tf32(d, ah, ch, kk > 0 ? 1u : 0u);
+                mma_tf32(d, ah, cl, 1u);
+                mma_tf32(d, al, ch, 1u);
+            }
+            mma_commit(b_empty(s));    // the C tile's stage is free once these MMAs finish
+            mma_commit(acc_full(a));   // accumulator a is ready for the epilogue
+            last = j;
+        }
+        // the MMAs must be complete before tensor memory is released
+        if (last >= 0) mbar_wait(acc_full(last & 1), (last >> 1) & 1, err, true);
+        if (!ok) s_err = 1;
+    } else if (warp >= 4) {
+        // ---------------- epilogue: one thread per row ----------------
+        const int sub = warp & 3;
+        const int64_t row = row0 + sub * 32 + lane;
+        const float xr = row < n ? xn[row] : 0.f;
+        Top4 t4;
+        t4.init();
+        bool ok = true;
+        for (int j = 0; j < ntiles; ++j) {
+            const int a = j & 1, v = j >> 1;
+            ok = mbar_wait(acc_full(a), v & 1, err);
+            if (!ok) break;
+            tc_fence_after();
+            const int c0 = j * TC_N;
+#pragma unroll 1
+            for (int cc = 0; cc < TC_N; cc += 32) {
+                float acc[32];
+                tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * TC_N + cc), acc);
+                const int cb = c0 + cc;
+                if (cb + 32 <= k) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        t4.push(fmaf(-2.f, acc[e], xr) + __ldg(cn + cb + e), cb + e);
+                } else {
+                    for (int e = 0; e < 32; ++e)
+                        if (cb + e < k) t4.push(fmaf(-2.f, acc[e], xr) + __ldg(cn + cb + e), cb + e);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(a));
+        }
+        if (!ok) {
+            s_err = 1;
+        } else if (row < n) {
+            labels[row] = t4.i0;
+            const float margin = margin_coef * (xr + *cn_max);
+            if (k > 1 && !(t4.v1 - t4.v0 > margin)) {
+                if (k <= 3 || t4.v3 - t4.v0 > margin) {
+                    const int slot = atomicAdd(n3, 1);
+                    list3[slot] = make_int4((int)row, t4.i0, t4.i1, t4.i2);
+                } else {
+                    listF[atomicAdd(nF, 1)] = (int32_t)row;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+    if (threadIdx.x == 0 && s_err) atomicExch(err, 1);
+}
+
+// Exact re-decision among a row's three best candidates (difference form).
+template <int LPR>
+__global__ __launch_bounds__(256) void recheck3_kernel(const float4 *__restrict__ X, int dp4,
+                                                       const float4 *__restrict__ C,
+                                                       const int4 *__restrict__ list,
+                                                       const int *__restrict__ count,
+                                                       int32_t *__restrict__ labels) {
+    constexpr int GPW = 32 / LPR;  // lane groups per warp
+    const int lane = threadIdx.x & 31, g = lane / LPR, gl = lane % LPR;
+    const int wpb = blockDim.x / 32;
+    const int cnt = *count;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < cnt; e += gridDim.x * wpb) {
+        const int4 it = list[e];
+        const float4 *xr = X + (int64_t)it.x * dp4;
+        unsigned long long best = kNoKey;
+        for (int c0 = 0; c0 < 3; c0 += GPW) {
+            const int ci = c0 + g;
+            const int j = ci == 0 ? it.y : (ci == 1 ? it.z : (ci == 2 ? it.w : -1));
+            float acc = 0.f;
+            if (j >= 0) {
+                const float4 *cr = C + (int64_t)j * dp4;
+                for (int c = gl; c < dp4; c += LPR) {
+                    const float4 a = xr[c], b = cr[c];
+                    const float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+                    acc = fmaf(e0, e0, acc);
+                    acc = fmaf(e1, e1, acc);
+                    acc = fmaf(e2, e2, acc);
+                    acc = fmaf(e3, e3, acc);
+                }
+            }
+            for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if (j >= 0)
+                best = min(best, ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)j);
+        }
+        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
+        if (lane == 0) labels[it.x] = (int32_t)(best & 0xffffffffu);
+    }
+}
+
+// hi = x rounded to TF32 (10 explicit mantissa bits), lo = x - hi (exact);
+// columns dp..dpk-1 are zero.
+__global__ void split_tf32_kernel(const float *__restrict__ src, int64_t rows, int dp, int dpk,
+                                  float *__restrict__ hi, float *__restrict__ lo) {
+    const int64_t total = rows * dpk;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / dpk;
+        const int c = (int)(e - r * dpk);
+        const float x = c < dp ? src[r * dp + c] : 0.f;
+        const float h = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+        hi[e] = h;
+        lo[e] = x - h;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D tensor map of a [rows x dpk] fp32 array, boxes of 128 rows x 32 columns,
+// 128-byte swizzle, zero fill out of bounds.
+CUtensorMap make_map(const float *base, int64_t rows, int dpk) {
+    auto fn = encode_fn();
+    if (fn == nullptr) fail(MASK_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    const cuuint64_t dims[2] = {(cuuint64_t)dpk, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)dpk * 4u};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_BOX_K, (cuuint32_t)TC_M};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(MASK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return m;
+}
+
+int grid_cap(int64_t work) {
+    int64_t b = (work + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+template <int KB, int S>
+size_t tc_smem_bytes() {
+    return 1024 + 2u * KB * TC_BOX_BYTES + (size_t)S * 2u * KB * TC_BOX_BYTES + (2 * S + 5) * 8 + 16;
+}
+
+}  // namespace
+
+// ================================================================= host side
+
+struct TcAssign {
+    int64_t n = 0;
+    int dp = 0, dpk = 0;
+    const float *X = nullptr;      // padded points [n x dp]
+    Scratch<float> Xh, Xl;         // [n x dpk] TF32 hi / lo parts
+    CUtensorMap mXh, mXl;
+    Scratch<int> err;              // set by a kernel whose bounded wait ran out
+};
+
+bool tc_assign_enabled(int dp) {
+    const char *e = std::getenv("MASK_ASSIGN_KERNEL");
+    if (e && std::strcmp(e, "simt") == 0) return false;
+    return dp <= 64 && encode_fn() != nullptr;
+}
+
+std::shared_ptr<TcAssign> tc_assign_prepare(const float *X, int64_t n, int dp, cudaStream_t s) {
+    if (n == 0 || !tc_assign_enabled(dp)) return nullptr;
+    auto p = std::make_shared<TcAssign>();
+    p->n = n;
+    p->dp = dp;
+    p->dpk = dp <= 32 ? 32 : 64;
+    p->X = X;
+    p->Xh.alloc((size_t)n * p->dpk, s);
+    p->Xl.alloc((size_t)n * p->dpk, s);
+    split_tf32_kernel<<<grid_cap(n * p->dpk), 256, 0, s>>>(X, n, dp, p->dpk, p->Xh.get(), p->Xl.get());
+    MASK_LAUNCHED("split_tf32");
+    p->mXh = make_map(p->Xh.get(), n, p->dpk);
+    p->mXl = make_map(p->Xl.get(), n, p->dpk);
+    p->err.alloc(1, s);
+    MASK_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));
+    return p;
+}
+
+template <int KB, int S>
+void launch_tc(const TcAssign &p, const CUtensorMap &mCh, const CUtensorMap &mCl, const float *xn,
+               const float *cn, int k, const float *cmax, float coef, int32_t *labels,
+               int4 *list3, int *n3, int32_t *listF, int *nF, cudaStream_t s) {
+    const size_t smem = tc_smem_bytes<KB, S>();
+    auto kfn = assign_tc_kernel<KB, S>;
+    MASK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned blocks = (unsigned)((p.n + TC_M - 1) / TC_M);
+    kfn<<<blocks, TC_THREADS, smem, s>>>(p.mXh, p.mXl, mCh, mCl, xn, p.n, p.dp / 8, cn, k, cmax,
+                                        coef, labels, list3, n3, listF, nF, p.err.get());
+}
+
+void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *labels,
+               cudaStream_t s) {
+    const int dp = p.dp, dpk = p.dpk;
+    Scratch<float> cn(k, s), cmax(1, s), Ch((size_t)k * dpk, s), Cl((size_t)k * dpk, s);
+    Scratch<int4> list3(p.n, s);
+    Scratch<int32_t> listF(p.n, s);
+    Scratch<int> counts(2, s);
+    row_sqnorm(C, k, dp, cn.get(), s);
+    max_reduce(cn.get(), k, cmax.get(), s);
+    split_tf32_kernel<<<grid_cap((int64_t)k * dpk), 256, 0, s>>>(C, k, dp, dpk, Ch.get(), Cl.get());
+    MASK_LAUNCHED("split_tf32");
+    const CUtensorMap mCh = make_map(Ch.get(), k, dpk), mCl = make_map(Cl.get(), k, dpk);
+    MASK_CUDA(cudaMemsetAsync(counts.get(), 0, 2 * sizeof(int), s));
+    // Error bound of one expanded-form distance, relative to ||x||^2 + ||c||^2:
+    // the 3xTF32 cross term (split error 2.5 * 2^-21 and FP32 accumulation
+    // over 3*dp/8 MMA steps plus 8 in-MMA additions, counted at 2^-23 each,
+    // times 2 for the factor -2 and sum|x_t c_t| <= (||x||^2 + ||c||^2) / 2),
+    // the FP32 norms (dp * 2^-24) and two final roundings (4 * 2^-24).
+    // A label is certain when the best two differ by more than twice the
+    // bound; the coefficient is widened 2x beyond that.
+    const double per = 2.5 * 0x1.0p-21 + (3.0 * dp / 8.0 + 8.0) * 0x1.0p-23 +
+                       (dp + 4.0) * 0x1.0p-24;
+    const float coef = (float)(2.0 * 2.0 * per);
+    {
+        ProfRegion pr("assign_gemm", s, 2.0 * (double)p.n * (double)k * (double)dp);
+        if (dpk == 32)
+            launch_tc<1, 4>(p, mCh, mCl, xn, cn.get(), k, cmax.get(), coef, labels, list3.get(),
+                            counts.get(), listF.get(), counts.get() + 1, s);
+        else
+            launch_tc<2, 2>(p, mCh, mCl, xn, cn.get(), k, cmax.get(), coef, labels, list3.get(),
+                            counts.get(), listF.get(), counts.get() + 1, s);
+        MASK_LAUNCHED("assign_tc");
+    }
+    {
+        ProfRegion pr("assign_recheck", s, 0.0);
+        const int lpr = lanes_per_row(dp);
+        const float4 *X4 = reinterpret_cast<const float4 *>(p.X);
+        const float4 *C4 = reinterpret_cast<const float4 *>(C);
+        switch (lpr) {
+        case 1: recheck3_kernel<1><<<152 * 4, 256, 0, s>>>(X4, dp / 4, C4, list3.get(), counts.get(), labels); break;
+        case 2: recheck3_kernel<2><<<152 * 4, 256, 0, s>>>(X4, dp / 4, C4, list3.get(), counts.get(), labels); break;
+        case 4: recheck3_kernel<4><<<152 * 4, 256, 0, s>>>(X4, dp / 4, C4, list3.get(), counts.get(), labels); break;
+        case 8: recheck3_kernel<8><<<152 * 4, 256, 0, s>>>(X4, dp / 4, C4, list3.get(), counts.get(), labels); break;
+        case 16: recheck3_kernel<16><<<152 * 4, 256, 0, s>>>(X4, dp / 4, C4, list3.get(), counts.get(), labels); break;
+        default: recheck3_kernel<32><<<152 * 4, 256, 0, s>>>(X4, dp / 4, C4, list3.get(), counts.get(), labels); break;
+        }
+        MASK_LAUNCHED("recheck3");
+        assign_recheck_rows(p.X, dp, C, k, listF.get(), counts.get() + 1, labels, s);
+    }
+}
+
+void tc_assign_check(TcAssign &p, cudaStream_t s) {
+    int e = 0;
+    MASK_CUDA(cudaMemcpyAsync(&e, p.err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    MASK_CUDA(cudaStreamSynchronize(s));
+    if (e) fail(MASK_ETIMEOUT, "assignment kernel: a bounded pipeline wait ran out");
+}
+
+}  // namespace mask

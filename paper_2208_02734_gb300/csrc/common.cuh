@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <stdexcept>
 #include <string>
 
@@ -171,6 +172,20 @@ void count_bad_labels(const int32_t *labels, int64_t n, int k, int *bad, cudaStr
 // assign.cu -- labels[i] = argmin_j ||x_i - c_j||^2 (ties to the smallest j)
 void assign_labels(const float *X, const float *xn, int64_t n, int dp, const float *C, int k,
                    int32_t *labels, cudaStream_t s);
+
+// re-decide the listed rows exactly over all k centroids (difference form)
+void assign_recheck_rows(const float *X, int dp, const float *C, int k, const int32_t *rows,
+                         const int *count, int32_t *labels, cudaStream_t s);
+
+// assign_tc.cu -- the same assignment on tcgen05 (3xTF32), for dp <= 64
+struct TcAssign;
+bool tc_assign_enabled(int dp);
+// Splits X (padded, [n x dp]) into TF32 hi/lo parts once; null if unsupported.
+std::shared_ptr<TcAssign> tc_assign_prepare(const float *X, int64_t n, int dp, cudaStream_t s);
+void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *labels,
+               cudaStream_t s);
+// Raises MASK_ETIMEOUT if a kernel of this plan hit a wait limit (synchronises).
+void tc_assign_check(TcAssign &p, cudaStream_t s);
 
 // query.cu -- keep the K nearest rows among the children of each query's parents
 struct ScanArgs {

@@ -217,17 +217,24 @@ void lloyd(const float *X, int64_t n_in, int dp, int k, int iters, float *C, int
     Scratch<float> xn(n_in, s), Cn((size_t)k * dp, s), sse(k, s);
     Scratch<double> J(iters + 1, s);
     row_sqnorm(X, n_in, dp, xn.get(), s);
+    // tensor-core assignment when the row fits (X split into TF32 hi/lo once)
+    auto tc = tc_assign_prepare(X, n_in, dp, s);
+    auto assign = [&](const float *Cc) {
+        if (tc) tc_assign(*tc, xn.get(), Cc, k, labels, s);
+        else assign_labels(X, xn.get(), n_in, dp, Cc, k, labels, s);
+    };
     float *cur = C, *nxt = Cn.get();
     for (int it = 0; it < iters; ++it) {
-        assign_labels(X, xn.get(), n_in, dp, cur, k, labels, s);
+        assign(cur);
         label_sort(labels, n_in, k, off, perm, s);
         centroid_update(X, dp, perm, off, k, cur, nxt, sse.get(), true, s);
         sum_reduce_f32_to_f64(sse.get(), k, J.get() + it, s);
         std::swap(cur, nxt);
     }
-    assign_labels(X, xn.get(), n_in, dp, cur, k, labels, s);
+    assign(cur);
     label_sort(labels, n_in, k, off, perm, s);
     centroid_update(X, dp, perm, off, k, cur, nullptr, sse.get(), false, s);
+    if (tc) tc_assign_check(*tc, s);
     sum_reduce_f32_to_f64(sse.get(), k, J.get() + iters, s);
     if (cur != C)
         MASK_CUDA(cudaMemcpyAsync(C, cur, sizeof(float) * k * dp, cudaMemcpyDeviceToDevice, s));
@@ -555,7 +562,12 @@ mask_status mask_kmeans_assign(const float *X, int64_t n, int32_t d, const float
         pad_rows(Cin.p, k, d, Cp.get(), dp, s);
         row_sqnorm(Xp.get(), n, dp, xn.get(), s);
         Out<int32_t> lb(labels_out, (size_t)n, s);
-        assign_labels(Xp.get(), xn.get(), n, dp, Cp.get(), k, lb.p, s);
+        if (auto tc = tc_assign_prepare(Xp.get(), n, dp, s)) {
+            tc_assign(*tc, xn.get(), Cp.get(), k, lb.p, s);
+            tc_assign_check(*tc, s);
+        } else {
+            assign_labels(Xp.get(), xn.get(), n, dp, Cp.get(), k, lb.p, s);
+        }
         if (dist_out) {
             Out<float> dist(dist_out, (size_t)n, s);
             label_dist(Xp.get(), n, dp, Cp.get(), lb.p, dist.p, s);

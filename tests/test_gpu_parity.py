@@ -43,6 +43,23 @@ def test_assign_matches_oracle(n, d, k):
     check_close(arr(dist_g)[eq], dist_o[eq], atol=1e-30, what="assign dist")
 
 
+@pytest.mark.parametrize("kernel", ["simt", "auto"])
+@pytest.mark.parametrize("n,d,k", [(20_000, 16, 200), (30_000, 64, 1000), (5000, 40, 129),
+                                   (4000, 64, 3), (3000, 8, 2)])
+def test_assign_kernels_match_oracle(monkeypatch, kernel, n, d, k):
+    # "auto" takes the tcgen05 (3xTF32) kernel for these dimensions (<= 64)
+    monkeypatch.setenv("MASK_ASSIGN_KERNEL", kernel)
+    mix = synth.AnisotropicMixture(d=d, n_blobs=20, seed=d)
+    X = mix.sample(n, seed=1)
+    Cc = X[np.random.default_rng(2).choice(n, k, replace=False)]
+    lab_o, dist_o = O.assign(X, Cc)
+    lab_g, dist_g = M.mask_kmeans_assign(cuda(X), cuda(Cc))
+    check_labels(X, Cc, lab_g, lab_o)
+    eq = arr(lab_g) == lab_o
+    assert eq.mean() > 0.999
+    check_close(arr(dist_g)[eq], dist_o[eq], atol=1e-30, what="assign dist")
+
+
 def test_assign_exact_ties_go_to_smallest_index():
     rng = np.random.default_rng(3)
     base = rng.normal(size=(40, 16)).astype(np.float32)
