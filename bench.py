@@ -72,6 +72,10 @@ REF_SAMPLE = {
 
 # FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (maximum SM clock).
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Dense TF32 tensor peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1 / 2.25).
+TF32_PER_BF16 = 1.1 / 2.25
+# The FP32-accurate tensor-core assignment issues 3 TF32 MMAs per useful product.
+TC_PASSES = 3
 
 
 def log(*a):
@@ -289,10 +293,10 @@ def run_reference(args, w, wname):
 
 # ----------------------------------------------------------------- our arm
 
-KERNEL_KIND = {"assign_gemm": "alu", "assign_recheck": "alu", "scan_topk_leaf": "hbm",
+KERNEL_KIND = {"assign_tc": "tensor", "assign_gemm": "alu", "assign_recheck": "alu", "scan_topk_leaf": "hbm",
                "scan_topk_level": "hbm", "centroid_update": "hbm", "label_sort": "hbm",
                "kmeanspp": "hbm"}
-KERNEL_SRC = {"assign_gemm": "assign.cu", "scan_topk_leaf": "query.cu",
+KERNEL_SRC = {"assign_tc": "assign_tc.cu", "assign_gemm": "assign.cu", "scan_topk_leaf": "query.cu",
               "centroid_update": "kmeans.cu", "kmeanspp": "kmeans.cu", "label_sort": "kmeans.cu"}
 
 
@@ -430,7 +434,7 @@ def run_ours(args, w, wname):
     for name, kv in kernels.items():
         if kv["ms"] <= 0:
             continue
-        if KERNEL_KIND[name] == "alu":
+        if KERNEL_KIND[name] in ("alu", "tensor"):
             kv["achieved_tflops"] = kv["work"] / (kv["ms"] / 1e3) / 1e12
         else:
             kv["achieved_gbs"] = kv["work"] / (kv["ms"] / 1e3) / 1e9
@@ -438,7 +442,18 @@ def run_ours(args, w, wname):
     roofline = None
     if dom is not None:
         kv = kernels[dom]
-        if KERNEL_KIND[dom] == "alu":
+        if KERNEL_KIND[dom] == "tensor":
+            # timed inside a long step: the sustained BF16 figure scaled to TF32
+            peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
+            ach = kv.get("achieved_tflops", 0.0)
+            roofline = {"kernel": dom, "bound": "tensor", "achieved": ach * TC_PASSES,
+                        "peak": peak, "unit": "TFLOP/s", "frac": ach * TC_PASSES / peak,
+                        "achieved_useful": ach, "frac_useful": ach / peak,
+                        "peak_source": (f"{peak_kind} sustained BF16 x 1.1/2.25 (TF32); "
+                                        "achieved = issued TF32 flop (3 MMAs per useful "
+                                        "product, 3xTF32)"),
+                        "work_per_launch": kv["work"] / kv["launches"]}
+        elif KERNEL_KIND[dom] == "alu":
             peak = FP32_ALU_TFLOPS
             roofline = {"kernel": dom, "bound": "alu", "achieved": kv.get("achieved_tflops"),
                         "peak": peak, "unit": "TFLOP/s",

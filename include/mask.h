@@ -231,7 +231,8 @@ mask_status mask_kmeans_assign_noalloc(const float *X, int64_t n, int32_t d, con
  * Per-kernel device timing.  The paper reports wall-clock build and search
  * times only (§4.2, Tables 3-6); these split the device time by kernel.
  * While enabled, the library brackets its main kernels with CUDA events on
- * the launching stream.  Region names: "assign_gemm", "assign_recheck",
+ * the launching stream.  Region names: "assign_tc" (tensor-core distance
+ * GEMM), "assign_gemm" (CUDA-core distance GEMM), "assign_recheck",
  * "label_sort", "centroid_update", "kmeanspp", "scan_topk_level",
  * "scan_topk_leaf".  Off by default.
  */
@@ -242,8 +243,8 @@ void mask_profile_reset(void);
 
 /*
  * Totals for one region since the last reset: launches, summed device time
- * in ms, summed algorithmic work (flop for "assign_gemm", bytes for the
- * others).  Waits for the recorded events.  Returns 1, or 0 if nothing was
+ * in ms, summed algorithmic work (useful flop 2*n*k*d for "assign_tc" and
+ * "assign_gemm", bytes for the others).  Waits for the recorded events.  Returns 1, or 0 if nothing was
  * recorded under that name.  Any output pointer may be NULL.
  */
 int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,

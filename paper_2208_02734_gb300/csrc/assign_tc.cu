@@ -522,7 +522,7 @@ void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *lab
                        (dp + 4.0) * 0x1.0p-24;
     const float coef = (float)(2.0 * 2.0 * per);
     {
-        ProfRegion pr("assign_gemm", s, 2.0 * (double)p.n * (double)k * (double)dp);
+        ProfRegion pr("assign_tc", s, 2.0 * (double)p.n * (double)k * (double)dp);
         if (dpk == 32)
             launch_tc<1, 4>(p, mCh, mCl, xn, cn.get(), k, cmax.get(), coef, labels, list3.get(),
                             counts.get(), listF.get(), counts.get() + 1, s);
