@@ -140,9 +140,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
         : "memory");
 }
 
-// 32 consecutive fp32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 32 consecutive fp32 columns of this thread's TMEM lane (issue only; the
+// registers are valid after tmem_wait()).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -155,9 +155,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
           "=r"(r[31])
         : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Named barrier 1 over the 128 epilogue threads (warps 4-7) that also ANDs a
+// flag across them, so every epilogue warp takes the same exit decision.
+__device__ __forceinline__ bool epi_bar_and(bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(out)
+        : "r"((uint32_t)v)
+        : "memory");
+    return out != 0;
 }
 
 // Keep the four smallest values (v0 <= v1 <= v2 <= v3) and the indices of
@@ -189,7 +205,7 @@ template <int KB, int S>
 __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl,
     const __grid_constant__ CUtensorMap tmCh, const __grid_constant__ CUtensorMap tmCl,
-    const float *__restrict__ xn, int64_t n, int ksteps, const float *__restrict__ cn, int k,
+    const float *__restrict__ xn, int64_t n, int ksteps, const float *__restrict__ cn_pad, int k,
     const float *__restrict__ cn_max, float margin_coef, int32_t *__restrict__ labels,
     int4 *__restrict__ list3, int *__restrict__ n3, int32_t *__restrict__ listF,
     int *__restrict__ nF, int *__restrict__ err) {
@@ -203,6 +219,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     uint64_t *bars = reinterpret_cast<uint64_t *>(basep + 2u * KB * TC_BOX_BYTES + S * kStage);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
     __shared__ int s_err;
+    __shared__ __align__(16) float s_cn[2][TC_N];
 
     // barriers: a_full | b_full[S] | b_empty[S] | acc_full[2] | acc_empty[2]
     const uint32_t bar0 = smem_u32(bars);
@@ -296,30 +313,51 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         if (!ok) s_err = 1;
     } else if (warp >= 4) {
         // ---------------- epilogue: one thread per row ----------------
+        // Rows are ranked by key = ||c||^2 - 2 x.c (the row's ||x||^2 is
+        // added back at the end); the norms of each C tile are staged in
+        // shared memory (double-buffered with the accumulators).
         const int sub = warp & 3;
-        const int64_t row = row0 + sub * 32 + lane;
+        const int r = sub * 32 + lane;
+        const int64_t row = row0 + r;
         const float xr = row < n ? xn[row] : 0.f;
         Top4 t4;
         t4.init();
         bool ok = true;
         for (int j = 0; j < ntiles; ++j) {
             const int a = j & 1, v = j >> 1;
+            const int c0 = j * TC_N;
+            s_cn[a][r] = cn_pad[c0 + r];
             ok = mbar_wait(acc_full(a), v & 1, err);
+            ok = epi_bar_and(ok);  // also publishes s_cn[a] to all epilogue threads
             if (!ok) break;
             tc_fence_after();
-            const int c0 = j * TC_N;
+            const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * TC_N);
 #pragma unroll 1
-            for (int cc = 0; cc < TC_N; cc += 32) {
-                float acc[32];
-                tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * TC_N + cc), acc);
-                const int cb = c0 + cc;
-                if (cb + 32 <= k) {
+            for (int h = 0; h < TC_N; h += 64) {
+                uint32_t u0[32], u1[32];
+                tmem_ld32(tbase + h, u0);
+                tmem_ld32(tbase + h + 32, u1);
+                tmem_wait();
+                float key[64];
+                float mn = FLT_MAX;
+                const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][h]);
 #pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        t4.push(fmaf(-2.f, acc[e], xr) + __ldg(cn + cb + e), cb + e);
-                } else {
-                    for (int e = 0; e < 32; ++e)
-                        if (cb + e < k) t4.push(fmaf(-2.f, acc[e], xr) + __ldg(cn + cb + e), cb + e);
+                for (int e4 = 0; e4 < 16; ++e4) {
+                    const float4 c = cn4[e4];
+                    const uint32_t *uu = e4 < 8 ? u0 : u1;
+                    const int b = (e4 & 7) * 4;
+                    key[e4 * 4 + 0] = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
+                    key[e4 * 4 + 1] = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
+                    key[e4 * 4 + 2] = fmaf(-2.f, __uint_as_float(uu[b + 2]), c.z);
+                    key[e4 * 4 + 3] = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
+                    mn = fminf(mn, fminf(fminf(key[e4 * 4 + 0], key[e4 * 4 + 1]),
+                                         fminf(key[e4 * 4 + 2], key[e4 * 4 + 3])));
+                }
+                if (mn < t4.v3) {
+                    const int cb = c0 + h;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e)
+                        if (cb + e < k) t4.push(key[e], cb + e);
                 }
             }
             tc_fence_before();
@@ -330,6 +368,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             s_err = 1;
         } else if (row < n) {
             labels[row] = t4.i0;
+            // gaps are the same in key and distance units
             const float margin = margin_coef * (xr + *cn_max);
             if (k > 1 && !(t4.v1 - t4.v0 > margin)) {
                 if (k <= 3 || t4.v3 - t4.v0 > margin) {
@@ -501,7 +540,11 @@ void launch_tc(const TcAssign &p, const CUtensorMap &mCh, const CUtensorMap &mCl
 void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *labels,
                cudaStream_t s) {
     const int dp = p.dp, dpk = p.dpk;
-    Scratch<float> cn(k, s), cmax(1, s), Ch((size_t)k * dpk, s), Cl((size_t)k * dpk, s);
+    const int ntiles = (k + TC_N - 1) / TC_N;
+    // centroid norms padded to whole 128-centroid tiles (zeros past k)
+    Scratch<float> cn((size_t)ntiles * TC_N, s), cmax(1, s), Ch((size_t)k * dpk, s),
+        Cl((size_t)k * dpk, s);
+    MASK_CUDA(cudaMemsetAsync(cn.get(), 0, sizeof(float) * ntiles * TC_N, s));
     Scratch<int4> list3(p.n, s);
     Scratch<int32_t> listF(p.n, s);
     Scratch<int> counts(2, s);

@@ -184,7 +184,6 @@ __global__ void sum_f32_to_f64_kernel(const float *__restrict__ v, int64_t n, do
 
 constexpr int kKppThreads = 512;
 constexpr int kKppRows = 1024;   // rows per block; one D^2 block sum each
-constexpr int kKppPer = kKppRows / kKppThreads;  // rows per thread in the block search
 constexpr int kKppUnroll = 8;    // rows in flight per lane group
 
 // One k-means++ step (§3.2).  The step number t >= 1 is read from *t_dev.
@@ -200,17 +199,15 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
     unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
     unsigned char *__restrict__ taken) {
     __shared__ double red[kKppThreads / 32];
-    __shared__ long long redi[kKppThreads / 32];
-    __shared__ double incs[kKppThreads];
     __shared__ int s_last;
-    __shared__ long long s_pick;
 
     const int t = *t_dev;
     const int tid = threadIdx.x;
     constexpr int G = kKppThreads / LPR;
     const int g = tid / LPR, gl = tid % LPR;
     const int dp4 = dp / 4;
-    const int64_t c = chosen[t - 1];
+    int64_t c = chosen[t - 1];
+    if (c < 0 || c >= m) c = 0;  // never out of bounds (a valid pick is always in [0, m))
     const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
     const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
 
@@ -259,89 +256,107 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
     if (!s_last) return;
     __threadfence();
 
-    // ---------------- the last block draws centre t ----------------
+    // ---------------- the last block draws centre t (warp 0 alone) ----------------
+    if (tid >= 32) return;
+    const int lane = tid;
     const int nb = gridDim.x;
-    if (t == 1 && tid == 0) taken[chosen[0]] = 1;
-    double part = 0.0;
-    for (int b = tid; b < nb; b += kKppThreads) part += __ldcg(bsum + b);
-    const double S = block_sum_f64<kKppThreads>(part, red);
+    if (t == 1 && lane == 0) taken[chosen[0]] = 1;
+    __syncwarp();
+    // block sums: lane l owns blocks [l*per, (l+1)*per)
+    const int per = (nb + 31) / 32;
+    double ls = 0.0;
+    for (int q = 0; q < per; ++q) {
+        const int b = lane * per + q;
+        if (b < nb) ls += __ldcg(bsum + b);
+    }
+    double inc = ls;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const double S = __shfl_sync(kFull, inc, 31);
     long long pick = -1;
     if (S > 0.0) {
         const double target = u[t] * S;
         // first block whose inclusive prefix exceeds the target
-        double carry = 0.0, excl = 0.0;
-        long long fb = LLONG_MAX;
-        for (int c0 = 0; c0 < nb && fb == LLONG_MAX; c0 += kKppThreads) {
-            const int b = c0 + tid;
-            const double v = b < nb ? __ldcg(bsum + b) : 0.0;
-            const double inc = block_incl_scan_f64<kKppThreads>(v, red) + carry;
-            incs[tid] = inc;
-            fb = block_min_ll<kKppThreads>(b < nb && inc > target ? b : LLONG_MAX, redi);
-            if (fb != LLONG_MAX) {
-                const int lt = (int)(fb - c0);
-                excl = lt == 0 ? carry : incs[lt - 1];
-            }
-            carry = incs[kKppThreads - 1];
-            __syncthreads();
-        }
-        if (fb != LLONG_MAX) {
-            // within the block: each thread owns kKppPer consecutive rows
-            const int64_t i0 = fb * kKppRows + (int64_t)tid * kKppPer;
-            double v[kKppPer], vs = 0.0;
-#pragma unroll
-            for (int q = 0; q < kKppPer; ++q) {
-                v[q] = i0 + q < m ? (double)__ldcg(D2 + i0 + q) : 0.0;
-                vs += v[q];
-            }
-            const double inc = block_incl_scan_f64<kKppThreads>(vs, red) + excl;
-            const long long owner =
-                block_min_ll<kKppThreads>(inc > target && vs > 0.0 ? tid : LLONG_MAX, redi);
-            if (tid == 0) s_pick = -1;
-            __syncthreads();
-            if (owner != LLONG_MAX && tid == owner) {
-                double run = inc - vs;
-                long long p = -1;
-#pragma unroll
-                for (int q = 0; q < kKppPer; ++q) {
-                    if (v[q] > 0.0) p = i0 + q;
-                    run += v[q];
-                    if (run > target && v[q] > 0.0) { p = i0 + q; break; }
+        long long fb = -1;
+        double excl = 0.0;
+        const unsigned bal = __ballot_sync(kFull, inc > target && ls > 0.0);
+        if (bal) {
+            const int src = __ffs(bal) - 1;
+            if (lane == src) {
+                double run = inc - ls, lastrun = 0.0;
+                long long lastb = -1;
+                for (int q = 0; q < per; ++q) {
+                    const int b = lane * per + q;
+                    if (b >= nb) break;
+                    const double v = __ldcg(bsum + b);
+                    if (v > 0.0) {
+                        lastb = b;
+                        lastrun = run;
+                        if (run + v > target) { fb = b; excl = run; break; }
+                    }
+                    run += v;
                 }
-                s_pick = p;
+                if (fb < 0) { fb = lastb; excl = lastrun; }
             }
-            long long lastpos = -1;
-#pragma unroll
-            for (int q = 0; q < kKppPer; ++q)
-                if (v[q] > 0.0) lastpos = i0 + q;
-            __syncthreads();
-            const long long op = s_pick;
-            pick = op >= 0 ? op : block_max_ll<kKppThreads>(lastpos, redi);
+            fb = __shfl_sync(kFull, fb, src);
+            excl = __shfl_sync(kFull, excl, src);
         }
-        if (pick < 0) {
-            // rounding left the target past the end: last row with D^2 > 0
-            long long lb = -1;
-            for (int b = tid; b < nb; b += kKppThreads)
-                if (__ldcg(bsum + b) > 0.0) lb = b;
-            lb = block_max_ll<kKppThreads>(lb, redi);
-            long long lastpos = -1;
-            for (int q = tid; q < kKppRows; q += kKppThreads) {
-                const int64_t i = lb * kKppRows + q;
-                if (lb >= 0 && i < m && __ldcg(D2 + i) > 0.f) lastpos = i;
+        if (fb >= 0) {
+            // within block fb: lane l owns rows [l*RPL, (l+1)*RPL)
+            constexpr int RPL = kKppRows / 32;
+            const int64_t i0 = fb * kKppRows + (int64_t)lane * RPL;
+            double rs = 0.0;
+            for (int q = 0; q < RPL; ++q)
+                if (i0 + q < m) rs += (double)__ldcg(D2 + i0 + q);
+            double rinc = rs;
+            for (int o = 1; o < 32; o <<= 1) {
+                const double v = __shfl_up_sync(kFull, rinc, o);
+                if (lane >= o) rinc += v;
             }
-            pick = block_max_ll<kKppThreads>(lastpos, redi);
+            rinc += excl;
+            const unsigned b2 = __ballot_sync(kFull, rinc > target && rs > 0.0);
+            const unsigned pos = __ballot_sync(kFull, rs > 0.0);
+            // the crossing lane, or (rounding) the last lane holding mass
+            const int src2 = b2 ? __ffs(b2) - 1 : (pos ? 31 - __clz(pos) : -1);
+            if (src2 >= 0) {
+                long long p = -1;
+                if (lane == src2) {
+                    double run = rinc - rs;
+                    for (int q = 0; q < RPL; ++q) {
+                        const int64_t i = i0 + q;
+                        if (i >= m) break;
+                        const double v = (double)__ldcg(D2 + i);
+                        if (v > 0.0) {
+                            p = i;
+                            if (run + v > target) break;
+                        }
+                        run += v;
+                    }
+                }
+                pick = __shfl_sync(kFull, p, src2);
+            }
+        }
+        if (pick < 0 && lane == 0) {
+            // rounding left the target past the end: the last row with D^2 > 0
+            for (long long b = nb - 1; b >= 0 && pick < 0; --b) {
+                if (!(__ldcg(bsum + b) > 0.0)) continue;
+                for (long long i = b * kKppRows + kKppRows - 1; i >= b * kKppRows; --i)
+                    if (i < m && __ldcg(D2 + i) > 0.f) { pick = i; break; }
+            }
         }
     } else {
-        __syncthreads();
-        long long first = LLONG_MAX;
-        for (int64_t c0 = 0; c0 < m && first == LLONG_MAX; c0 += kKppThreads) {
-            const int64_t i = c0 + tid;
-            first = block_min_ll<kKppThreads>(i < m && !taken[i] ? i : LLONG_MAX, redi);
+        // all remaining points coincide with chosen centres: lowest unchosen index
+        for (int64_t c0 = 0; c0 < m; c0 += 32) {
+            const int64_t i = c0 + lane;
+            const unsigned b = __ballot_sync(kFull, i < m && !taken[i]);
+            if (b) { pick = c0 + __ffs(b) - 1; break; }
         }
-        pick = first;
     }
-    if (tid == 0) {
+    if (lane == 0) {
         chosen[t] = pick;
-        taken[pick] = 1;
+        if (pick >= 0 && pick < m) taken[pick] = 1;
         *counter = 0u;
         *t_dev = t + 1;
     }
