@@ -323,46 +323,49 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         Top4 t4;
         t4.init();
         bool ok = true;
+        s_cn[0][r] = cn_pad[r];  // norms of tile 0 (published by its barrier)
         for (int j = 0; j < ntiles; ++j) {
             const int a = j & 1, v = j >> 1;
             const int c0 = j * TC_N;
-            s_cn[a][r] = cn_pad[c0 + r];
+            // prefetch the next tile's norm one tile ahead
+            const float cn_next = j + 1 < ntiles ? cn_pad[c0 + TC_N + r] : 0.f;
             ok = mbar_wait(acc_full(a), v & 1, err);
             ok = epi_bar_and(ok);  // also publishes s_cn[a] to all epilogue threads
             if (!ok) break;
             tc_fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * TC_N);
-#pragma unroll 1
-            for (int h = 0; h < TC_N; h += 64) {
-                uint32_t u0[32], u1[32];
-                tmem_ld32(tbase + h, u0);
-                tmem_ld32(tbase + h + 32, u1);
-                tmem_wait();
-                float key[64];
-                float mn = FLT_MAX;
-                const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][h]);
-#pragma unroll
-                for (int e4 = 0; e4 < 16; ++e4) {
-                    const float4 c = cn4[e4];
-                    const uint32_t *uu = e4 < 8 ? u0 : u1;
-                    const int b = (e4 & 7) * 4;
-                    key[e4 * 4 + 0] = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
-                    key[e4 * 4 + 1] = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
-                    key[e4 * 4 + 2] = fmaf(-2.f, __uint_as_float(uu[b + 2]), c.z);
-                    key[e4 * 4 + 3] = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
-                    mn = fminf(mn, fminf(fminf(key[e4 * 4 + 0], key[e4 * 4 + 1]),
-                                         fminf(key[e4 * 4 + 2], key[e4 * 4 + 3])));
-                }
-                if (mn < t4.v3) {
-                    const int cb = c0 + h;
-#pragma unroll
-                    for (int e = 0; e < 64; ++e)
-                        if (cb + e < k) t4.push(key[e], cb + e);
-                }
-            }
+            uint32_t u[4][32];
+            tmem_ld32(tbase + 0, u[0]);
+            tmem_ld32(tbase + 32, u[1]);
+            tmem_ld32(tbase + 64, u[2]);
+            tmem_ld32(tbase + 96, u[3]);
+            tmem_wait();
+            // the accumulator is in registers: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty(a));
+            const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][0]);
+            float mn = FLT_MAX;
+#pragma unroll
+            for (int e4 = 0; e4 < 32; ++e4) {
+                const float4 c = cn4[e4];
+                const uint32_t *uu = u[e4 >> 3];
+                const int b = (e4 & 7) * 4;
+                const float k0 = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
+                const float k1 = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
+                const float k2 = fmaf(-2.f, __uint_as_float(uu[b + 2]), c.z);
+                const float k3 = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
+                mn = fminf(mn, fminf(fminf(k0, k1), fminf(k2, k3)));
+            }
+            if (mn < t4.v3) {
+                // rare after the first tiles: insert the candidates one by one
+#pragma unroll
+                for (int e = 0; e < TC_N; ++e) {
+                    const float key = fmaf(-2.f, __uint_as_float(u[e >> 5][e & 31]), s_cn[a][e]);
+                    if (key < t4.v3 && c0 + e < k) t4.push(key, c0 + e);
+                }
+            }
+            s_cn[a ^ 1][r] = cn_next;  // read after the next tile's barrier
         }
         if (!ok) {
             s_err = 1;

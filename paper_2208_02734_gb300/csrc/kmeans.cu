@@ -184,67 +184,63 @@ __global__ void sum_f32_to_f64_kernel(const float *__restrict__ v, int64_t n, do
 
 constexpr int kKppThreads = 512;
 constexpr int kKppRows = 1024;   // rows per block; one D^2 block sum each
-constexpr int kKppUnroll = 8;    // rows in flight per lane group
+constexpr int kKppRpt = kKppRows / kKppThreads;  // rows per thread
+constexpr int kKppSelMax = 2048; // block sums the selecting warp stages in shared memory
 
 // One k-means++ step (§3.2).  The step number t >= 1 is read from *t_dev.
-// Fold the centre picked at step t-1 into D^2 (FP32 difference form), then
-// the last block to finish draws centre t: the smallest row whose inclusive
-// prefix of D^2 exceeds u_t * sum(D^2) (all sums FP64); if that sum is 0, the
-// lowest-index row not chosen yet.  The last block then advances *t_dev, so
-// identical launches can be replayed step after step.
-template <int LPR>
-__global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
+// Fold the centre picked at step t-1 into D^2 (FP32 difference form, one
+// thread per row), then the last block to finish draws centre t: the smallest
+// row whose inclusive prefix of D^2 exceeds u_t * sum(D^2) (all sums FP64);
+// if that sum is 0, the lowest-index row not chosen yet.  The last block then
+// advances *t_dev, so identical launches can be replayed step after step.
+__global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
     const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
     const double *__restrict__ u, float *__restrict__ D2, double *__restrict__ bsum,
     unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
     unsigned char *__restrict__ taken) {
     __shared__ double red[kKppThreads / 32];
     __shared__ int s_last;
+    __shared__ double s_b[kKppSelMax];   // staged block sums (selecting warp)
+    __shared__ float s_r[kKppRows];      // staged D^2 of the selected block
 
     const int t = *t_dev;
     const int tid = threadIdx.x;
-    constexpr int G = kKppThreads / LPR;
-    const int g = tid / LPR, gl = tid % LPR;
     const int dp4 = dp / 4;
     int64_t c = chosen[t - 1];
     if (c < 0 || c >= m) c = 0;  // never out of bounds (a valid pick is always in [0, m))
     const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
     const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
 
-    double local = 0.0;
-    for (int rb = 0; rb < kKppRows; rb += G * kKppUnroll) {
-        float acc[kKppUnroll];
+    // D^2 update: thread owns rows r0 + tid + q * kKppThreads
+    float old[kKppRpt], acc[kKppRpt];
 #pragma unroll
-        for (int q = 0; q < kKppUnroll; ++q) acc[q] = 0.f;
-        for (int ch = gl; ch < dp4; ch += LPR) {
-            const float4 b = __ldg(crow + ch);
-            float4 a[kKppUnroll];
+    for (int q = 0; q < kKppRpt; ++q) {
+        const int64_t i = r0 + tid + q * kKppThreads;
+        old[q] = (t > 1 && i < m) ? D2[i] : FLT_MAX;
+        acc[q] = 0.f;
+    }
+#pragma unroll 2
+    for (int ch = 0; ch < dp4; ++ch) {
+        const float4 b = __ldg(crow + ch);
 #pragma unroll
-            for (int q = 0; q < kKppUnroll; ++q) {
-                const int r = rb + q * G + g;  // row within this block
-                const int64_t i = r0 + r;
-                a[q] = (r < kKppRows && i < m) ? reinterpret_cast<const float4 *>(X + i * dp)[ch] : b;
-            }
-#pragma unroll
-            for (int q = 0; q < kKppUnroll; ++q) {
-                const float e0 = a[q].x - b.x, e1 = a[q].y - b.y, e2 = a[q].z - b.z,
-                            e3 = a[q].w - b.w;
-                acc[q] = fmaf(e0, e0, acc[q]);
-                acc[q] = fmaf(e1, e1, acc[q]);
-                acc[q] = fmaf(e2, e2, acc[q]);
-                acc[q] = fmaf(e3, e3, acc[q]);
-            }
+        for (int q = 0; q < kKppRpt; ++q) {
+            const int64_t i = r0 + tid + q * kKppThreads;
+            const float4 a = i < m ? reinterpret_cast<const float4 *>(X + i * dp)[ch] : b;
+            const float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+            acc[q] = fmaf(e0, e0, acc[q]);
+            acc[q] = fmaf(e1, e1, acc[q]);
+            acc[q] = fmaf(e2, e2, acc[q]);
+            acc[q] = fmaf(e3, e3, acc[q]);
         }
+    }
+    double local = 0.0;
 #pragma unroll
-        for (int q = 0; q < kKppUnroll; ++q) {
-            for (int o = LPR / 2; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], o);
-            const int r = rb + q * G + g;
-            const int64_t i = r0 + r;
-            if (gl == 0 && r < kKppRows && i < m) {
-                const float nv = (t == 1) ? acc[q] : fminf(D2[i], acc[q]);
-                D2[i] = nv;
-                local += (double)nv;
-            }
+    for (int q = 0; q < kKppRpt; ++q) {
+        const int64_t i = r0 + tid + q * kKppThreads;
+        if (i < m) {
+            const float nv = fminf(old[q], acc[q]);
+            D2[i] = nv;
+            local += (double)nv;
         }
     }
     const double bs = block_sum_f64<kKppThreads>(local, red);
@@ -261,55 +257,83 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
     const int lane = tid;
     const int nb = gridDim.x;
     if (t == 1 && lane == 0) taken[chosen[0]] = 1;
-    __syncwarp();
-    // block sums: lane l owns blocks [l*per, (l+1)*per)
-    const int per = (nb + 31) / 32;
-    double ls = 0.0;
-    for (int q = 0; q < per; ++q) {
-        const int b = lane * per + q;
-        if (b < nb) ls += __ldcg(bsum + b);
-    }
-    double inc = ls;
-    for (int o = 1; o < 32; o <<= 1) {
-        const double v = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += v;
-    }
-    const double S = __shfl_sync(kFull, inc, 31);
     long long pick = -1;
+    double S = 0.0, target = 0.0;
+    long long fb = -1;
+    double excl = 0.0;
+    // pass over the block sums in chunks of kKppSelMax staged in shared memory
+    double carry = 0.0;
+    for (int c0 = 0; c0 < nb; c0 += kKppSelMax) {
+        const int cn = min(kKppSelMax, nb - c0);
+        for (int b = lane; b < cn; b += 32) s_b[b] = __ldcg(bsum + c0 + b);
+        __syncwarp();
+        double ls = 0.0;
+        const int per = (cn + 31) / 32;
+        for (int q = 0; q < per; ++q) {
+            const int b = lane * per + q;
+            if (b < cn) ls += s_b[b];
+        }
+        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(kFull, ls, o);
+        carry += ls;
+        __syncwarp();
+    }
+    S = carry;
     if (S > 0.0) {
-        const double target = u[t] * S;
-        // first block whose inclusive prefix exceeds the target
-        long long fb = -1;
-        double excl = 0.0;
-        const unsigned bal = __ballot_sync(kFull, inc > target && ls > 0.0);
-        if (bal) {
-            const int src = __ffs(bal) - 1;
-            if (lane == src) {
-                double run = inc - ls, lastrun = 0.0;
-                long long lastb = -1;
-                for (int q = 0; q < per; ++q) {
-                    const int b = lane * per + q;
-                    if (b >= nb) break;
-                    const double v = __ldcg(bsum + b);
-                    if (v > 0.0) {
-                        lastb = b;
-                        lastrun = run;
-                        if (run + v > target) { fb = b; excl = run; break; }
-                    }
-                    run += v;
-                }
-                if (fb < 0) { fb = lastb; excl = lastrun; }
+        target = u[t] * S;
+        carry = 0.0;
+        for (int c0 = 0; c0 < nb && fb < 0; c0 += kKppSelMax) {
+            const int cn = min(kKppSelMax, nb - c0);
+            for (int b = lane; b < cn; b += 32) s_b[b] = __ldcg(bsum + c0 + b);
+            __syncwarp();
+            const int per = (cn + 31) / 32;
+            double ls = 0.0;
+            for (int q = 0; q < per; ++q) {
+                const int b = lane * per + q;
+                if (b < cn) ls += s_b[b];
             }
-            fb = __shfl_sync(kFull, fb, src);
-            excl = __shfl_sync(kFull, excl, src);
+            double inc = ls;
+            for (int o = 1; o < 32; o <<= 1) {
+                const double v = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += v;
+            }
+            inc += carry;
+            const unsigned bal = __ballot_sync(kFull, inc > target && ls > 0.0);
+            if (bal) {
+                const int src = __ffs(bal) - 1;
+                long long f = -1;
+                double ex = 0.0;
+                if (lane == src) {
+                    double run = inc - ls, lastrun = 0.0;
+                    long long lastb = -1;
+                    for (int q = 0; q < per; ++q) {
+                        const int b = lane * per + q;
+                        if (b >= cn) break;
+                        const double v = s_b[b];
+                        if (v > 0.0) {
+                            lastb = c0 + b;
+                            lastrun = run;
+                            if (run + v > target) { f = c0 + b; ex = run; break; }
+                        }
+                        run += v;
+                    }
+                    if (f < 0) { f = lastb; ex = lastrun; }
+                }
+                fb = __shfl_sync(kFull, f, src);
+                excl = __shfl_sync(kFull, ex, src);
+            }
+            carry = __shfl_sync(kFull, inc, 31);
+            __syncwarp();
         }
         if (fb >= 0) {
-            // within block fb: lane l owns rows [l*RPL, (l+1)*RPL)
+            // stage the block's rows, then lane l walks rows [l*32, l*32 + 32)
+            for (int q = lane; q < kKppRows; q += 32) {
+                const int64_t i = fb * kKppRows + q;
+                s_r[q] = i < m ? __ldcg(D2 + i) : 0.f;
+            }
+            __syncwarp();
             constexpr int RPL = kKppRows / 32;
-            const int64_t i0 = fb * kKppRows + (int64_t)lane * RPL;
             double rs = 0.0;
-            for (int q = 0; q < RPL; ++q)
-                if (i0 + q < m) rs += (double)__ldcg(D2 + i0 + q);
+            for (int q = 0; q < RPL; ++q) rs += (double)s_r[lane * RPL + q];
             double rinc = rs;
             for (int o = 1; o < 32; o <<= 1) {
                 const double v = __shfl_up_sync(kFull, rinc, o);
@@ -325,11 +349,9 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_kernel(
                 if (lane == src2) {
                     double run = rinc - rs;
                     for (int q = 0; q < RPL; ++q) {
-                        const int64_t i = i0 + q;
-                        if (i >= m) break;
-                        const double v = (double)__ldcg(D2 + i);
+                        const double v = (double)s_r[lane * RPL + q];
                         if (v > 0.0) {
-                            p = i;
+                            p = fb * kKppRows + lane * RPL + q;
                             if (run + v > target) break;
                         }
                         run += v;
@@ -644,11 +666,10 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
     MASK_CUDA(cudaMemsetAsync(counter.get(), 0, sizeof(unsigned), s));
     MASK_CUDA(cudaMemsetAsync(taken.get(), 0, m, s));
     MASK_CUDA(cudaMemcpyAsync(t_dev.get(), &one, sizeof(int), cudaMemcpyHostToDevice, s));
-    const int lpr = lanes_per_row(dp);
     auto launch = [&](cudaStream_t st) {
-        MASK_LPR_DISPATCH(lpr, (kpp_step_kernel<L><<<nb, kKppThreads, 0, st>>>(
-                                   Xs, m, dp, t_dev.get(), u_dev, D2.get(), bsum.get(),
-                                   counter.get(), chosen, taken.get())));
+        kpp_step_kernel<<<nb, kKppThreads, 0, st>>>(Xs, m, dp, t_dev.get(), u_dev, D2.get(),
+                                                    bsum.get(), counter.get(), chosen,
+                                                    taken.get());
     };
     // The steps are identical launches (the step number lives on the device),
     // so a captured graph of kBatch steps is replayed; the rest run directly.

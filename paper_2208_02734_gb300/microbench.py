@@ -33,6 +33,8 @@ def main(argv=None) -> None:
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--profile", action="store_true",
+                    help="also report the library's per-kernel device times")
     a = ap.parse_args(argv)
 
     import torch
@@ -70,6 +72,9 @@ def main(argv=None) -> None:
     for _ in range(a.warmup):
         run()
     torch.cuda.synchronize()
+    if a.profile:
+        M.mask_profile_reset()
+        M.mask_profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.reps):
@@ -78,8 +83,20 @@ def main(argv=None) -> None:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.reps
     out = {"step": a.step, "n": a.n, "d": a.d, "k": a.k, "ms": ms}
+    if a.profile:
+        M.mask_profile_enable(False)
+        for name in ("assign_tc", "assign_gemm", "assign_recheck", "kmeanspp", "label_sort",
+                     "centroid_update", "scan_topk_level", "scan_topk_leaf"):
+            r = M.mask_profile_read(name)
+            if r:
+                out[name + "_ms"] = r[1] / max(1, r[0])
     if a.step == "assign":
         out["tflops"] = 2.0 * a.n * a.k * a.d / (ms / 1e3) / 1e12
+        kms = out.get("assign_tc_ms") or out.get("assign_gemm_ms")
+        if kms:
+            out["kernel_tflops"] = 2.0 * a.n * a.k * a.d / (kms / 1e3) / 1e12
+    if a.step == "kmeanspp" and "kmeanspp_ms" in out:
+        out["kpp_us_per_step"] = out["kmeanspp_ms"] * 1e3 / max(1, a.k - 1)
     print(json.dumps(out))
     if "index" in state:
         state["index"].free()
