@@ -37,7 +37,9 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int TC_M = 128, TC_N = 128;   // MMA tile: 128 rows x 128 centroids
-constexpr int TC_THREADS = 256;
+constexpr int TC_EPI_WARPS = 8;         // two epilogue warps per TMEM lane quadrant
+constexpr int TC_THREADS = (4 + TC_EPI_WARPS) * 32;
+constexpr int TC_EPI_COLS = TC_N / (TC_EPI_WARPS / 4);   // columns per epilogue thread per tile
 constexpr int TC_BOX_K = 32;            // fp32 columns per TMA box (128 bytes)
 constexpr int TC_BOX_BYTES = TC_M * TC_BOX_K * 4;   // 16 KB
 
@@ -161,14 +163,14 @@ __device__ __forceinline__ void tmem_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Named barrier 1 over the 128 epilogue threads (warps 4-7) that also ANDs a
+// Named barrier 1 over the 256 epilogue threads (warps 4-11) that also ANDs a
 // flag across them, so every epilogue warp takes the same exit decision.
 __device__ __forceinline__ bool epi_bar_and(bool v) {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "bar.red.and.pred q, 1, 256, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(out)
         : "r"((uint32_t)v)
@@ -199,6 +201,24 @@ struct Top4 {
     }
 };
 
+// Rare path of the epilogue: re-read this thread's TMEM columns and insert
+// every key below the current fourth-best.  Entered by whole warps (the TMEM
+// loads are warp-collective); kept out of line so the common path stays small.
+__device__ __noinline__ Top4 epi_insert(Top4 t, uint32_t taddr, const float *cn, int c0, int k) {
+#pragma unroll 1
+    for (int cc = 0; cc < TC_EPI_COLS; cc += 32) {
+        uint32_t u[32];
+        tmem_ld32(taddr + cc, u);
+        tmem_wait();
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const float key = fmaf(-2.f, __uint_as_float(u[e]), cn[cc + e]);
+            if (key < t.v3 && c0 + cc + e < k) t.push(key, c0 + cc + e);
+        }
+    }
+    return t;
+}
+
 // ------------------------------------------------------------- main kernel
 
 template <int KB, int S>
@@ -220,6 +240,8 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
     __shared__ int s_err;
     __shared__ __align__(16) float s_cn[2][TC_N];
+    __shared__ float s_top[TC_M][4];      // second-half top-4 lists, merged at the end
+    __shared__ int s_topi[TC_M][3];
 
     // barriers: a_full | b_full[S] | b_empty[S] | acc_full[2] | acc_empty[2]
     const uint32_t bar0 = smem_u32(bars);
@@ -244,7 +266,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(acc_full(a), 1);
-            mbar_init(acc_empty(a), 4);
+            mbar_init(acc_empty(a), TC_EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -312,44 +334,40 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         if (last >= 0) mbar_wait(acc_full(last & 1), (last >> 1) & 1, err, true);
         if (!ok) s_err = 1;
     } else if (warp >= 4) {
-        // ---------------- epilogue: one thread per row ----------------
+        // ---------------- epilogue: one row per thread, half the columns ----------------
         // Rows are ranked by key = ||c||^2 - 2 x.c (the row's ||x||^2 is
         // added back at the end); the norms of each C tile are staged in
         // shared memory (double-buffered with the accumulators).
-        const int sub = warp & 3;
-        const int r = sub * 32 + lane;
+        const int quad = warp & 3;                  // TMEM lane quadrant of this warp
+        const int half = (warp - 4) >> 2;           // column half of each tile
+        const int r = quad * 32 + lane;
         const int64_t row = row0 + r;
         const float xr = row < n ? xn[row] : 0.f;
         Top4 t4;
         t4.init();
         bool ok = true;
-        s_cn[0][r] = cn_pad[r];  // norms of tile 0 (published by its barrier)
+        if (half == 0) s_cn[0][r] = cn_pad[r];  // norms of tile 0
         for (int j = 0; j < ntiles; ++j) {
             const int a = j & 1, v = j >> 1;
             const int c0 = j * TC_N;
-            // prefetch the next tile's norm one tile ahead
-            const float cn_next = j + 1 < ntiles ? cn_pad[c0 + TC_N + r] : 0.f;
+            const float cn_next = (half == 0 && j + 1 < ntiles) ? cn_pad[c0 + TC_N + r] : 0.f;
             ok = mbar_wait(acc_full(a), v & 1, err);
             ok = epi_bar_and(ok);  // also publishes s_cn[a] to all epilogue threads
             if (!ok) break;
             tc_fence_after();
-            const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(a * TC_N);
-            uint32_t u[4][32];
-            tmem_ld32(tbase + 0, u[0]);
-            tmem_ld32(tbase + 32, u[1]);
-            tmem_ld32(tbase + 64, u[2]);
-            tmem_ld32(tbase + 96, u[3]);
+            const int col = half * TC_EPI_COLS;
+            const uint32_t taddr =
+                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * TC_N + col);
+            uint32_t u0[32], u1[32];
+            tmem_ld32(taddr, u0);
+            tmem_ld32(taddr + 32, u1);
             tmem_wait();
-            // the accumulator is in registers: hand the buffer back to the MMA warp
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty(a));
-            const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][0]);
+            const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][col]);
             float mn = FLT_MAX;
 #pragma unroll
-            for (int e4 = 0; e4 < 32; ++e4) {
+            for (int e4 = 0; e4 < 16; ++e4) {
                 const float4 c = cn4[e4];
-                const uint32_t *uu = u[e4 >> 3];
+                const uint32_t *uu = e4 < 8 ? u0 : u1;
                 const int b = (e4 & 7) * 4;
                 const float k0 = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
                 const float k1 = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
@@ -357,19 +375,30 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
                 const float k3 = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
                 mn = fminf(mn, fminf(fminf(k0, k1), fminf(k2, k3)));
             }
-            if (mn < t4.v3) {
-                // rare after the first tiles: insert the candidates one by one
-#pragma unroll
-                for (int e = 0; e < TC_N; ++e) {
-                    const float key = fmaf(-2.f, __uint_as_float(u[e >> 5][e & 31]), s_cn[a][e]);
-                    if (key < t4.v3 && c0 + e < k) t4.push(key, c0 + e);
-                }
-            }
-            s_cn[a ^ 1][r] = cn_next;  // read after the next tile's barrier
+            if (__any_sync(kFull, mn < t4.v3))
+                t4 = epi_insert(t4, taddr, &s_cn[a][col], c0 + col, k);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(a));
+            if (half == 0) s_cn[a ^ 1][r] = cn_next;  // read after the next tile's barrier
         }
-        if (!ok) {
+        // merge the two half-row lists: the second half hands its list over
+        if (half == 1) {
+            s_top[r][0] = t4.v0; s_top[r][1] = t4.v1; s_top[r][2] = t4.v2; s_top[r][3] = t4.v3;
+            s_topi[r][0] = t4.i0; s_topi[r][1] = t4.i1; s_topi[r][2] = t4.i2;
+        }
+        ok = epi_bar_and(ok);
+        if (half == 1) {
+            // nothing more to do
+        } else if (!ok) {
             s_err = 1;
-        } else if (row < n) {
+        } else {
+            t4.push(s_top[r][0], s_topi[r][0]);
+            t4.push(s_top[r][1], s_topi[r][1]);
+            t4.push(s_top[r][2], s_topi[r][2]);
+            t4.push(s_top[r][3], -1);
+        }
+        if (half == 0 && ok && row < n) {
             labels[row] = t4.i0;
             // gaps are the same in key and distance units
             const float margin = margin_coef * (xr + *cn_max);
