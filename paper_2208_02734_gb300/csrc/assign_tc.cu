@@ -201,24 +201,6 @@ struct Top4 {
     }
 };
 
-// Rare path of the epilogue: re-read this thread's TMEM columns and insert
-// every key below the current fourth-best.  Entered by whole warps (the TMEM
-// loads are warp-collective); kept out of line so the common path stays small.
-__device__ __noinline__ Top4 epi_insert(Top4 t, uint32_t taddr, const float *cn, int c0, int k) {
-#pragma unroll 1
-    for (int cc = 0; cc < TC_EPI_COLS; cc += 32) {
-        uint32_t u[32];
-        tmem_ld32(taddr + cc, u);
-        tmem_wait();
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const float key = fmaf(-2.f, __uint_as_float(u[e]), cn[cc + e]);
-            if (key < t.v3 && c0 + cc + e < k) t.push(key, c0 + cc + e);
-        }
-    }
-    return t;
-}
-
 // ------------------------------------------------------------- main kernel
 
 template <int KB, int S>
@@ -362,24 +344,31 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             tmem_ld32(taddr, u0);
             tmem_ld32(taddr + 32, u1);
             tmem_wait();
+            // the accumulator is in registers: hand the buffer back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(a));
             const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][col]);
+            float key[64];
             float mn = FLT_MAX;
 #pragma unroll
             for (int e4 = 0; e4 < 16; ++e4) {
                 const float4 c = cn4[e4];
                 const uint32_t *uu = e4 < 8 ? u0 : u1;
                 const int b = (e4 & 7) * 4;
-                const float k0 = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
-                const float k1 = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
-                const float k2 = fmaf(-2.f, __uint_as_float(uu[b + 2]), c.z);
-                const float k3 = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
-                mn = fminf(mn, fminf(fminf(k0, k1), fminf(k2, k3)));
+                key[e4 * 4 + 0] = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
+                key[e4 * 4 + 1] = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
+                key[e4 * 4 + 2] = fmaf(-2.f, __uint_as_float(uu[b + 2]), c.z);
+                key[e4 * 4 + 3] = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
+                mn = fminf(mn, fminf(fminf(key[e4 * 4 + 0], key[e4 * 4 + 1]),
+                                     fminf(key[e4 * 4 + 2], key[e4 * 4 + 3])));
             }
-            if (__any_sync(kFull, mn < t4.v3))
-                t4 = epi_insert(t4, taddr, &s_cn[a][col], c0 + col, k);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty(a));
+            if (mn < t4.v3) {
+                const int cb = c0 + col;
+#pragma unroll
+                for (int e = 0; e < 64; ++e)
+                    if (key[e] < t4.v3 && cb + e < k) t4.push(key[e], cb + e);
+            }
             if (half == 0) s_cn[a ^ 1][r] = cn_next;  // read after the next tile's barrier
         }
         // merge the two half-row lists: the second half hands its list over
