@@ -8,6 +8,7 @@
 // Algorithm 2) is a chain of scan_topk launches over contiguous row ranges.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -501,17 +502,30 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
             b.out_ids32 = sel[(size_t)l - 1].get();
             scan_topk(b, s);
         }
-        ScanArgs c = a;
-        c.R = index->Xs.get();
-        c.rid = index->xids.get();
-        c.off = index->lv[0].off.get();
-        c.sel = sel[0].get();
-        c.P = p[0];
-        c.K = k;
-        c.out_ids32 = nullptr;
-        c.out_ids64 = ids.p;
-        c.out_d = dd.p;
-        scan_topk(c, s);
+        // Leaf scan: cluster-major when the batch keeps each leaf cluster
+        // several times on average, else query by query (same arithmetic).
+        const int k0 = index->lv[0].k;
+        bool cluster_major = cm_leaf_supported(dp, k) && nq * (int64_t)p[0] >= 4 * (int64_t)k0;
+        if (const char *mode = std::getenv("MASK_LEAF_SCAN")) {
+            if (std::strcmp(mode, "cluster") == 0) cluster_major = cm_leaf_supported(dp, k);
+            if (std::strcmp(mode, "query") == 0) cluster_major = false;
+        }
+        if (cluster_major) {
+            cm_leaf_scan(index->Xs.get(), dp, index->xids.get(), index->lv[0].off.get(), k0,
+                         Qp.get(), nq, sel[0].get(), p[0], k, ids.p, dd.p, s);
+        } else {
+            ScanArgs c = a;
+            c.R = index->Xs.get();
+            c.rid = index->xids.get();
+            c.off = index->lv[0].off.get();
+            c.sel = sel[0].get();
+            c.P = p[0];
+            c.K = k;
+            c.out_ids32 = nullptr;
+            c.out_ids64 = ids.p;
+            c.out_d = dd.p;
+            scan_topk(c, s);
+        }
         ids.finish(s);
         dd.finish(s);
         if (ids.host || dd.host) MASK_CUDA(cudaStreamSynchronize(s));

@@ -81,6 +81,7 @@ void mask_profile_reset(void) {
     for (auto &n : names) mask::drain_locked(n);
     mask::g_totals.clear();
     mask::scan_bytes_reset();
+    mask::cm_bytes_reset();
 }
 
 int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms, double *work) {
@@ -94,6 +95,7 @@ int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,
     double w = it->second.work;
     if (it->first == "scan_topk_level") w = mask::scan_bytes(0);
     if (it->first == "scan_topk_leaf") w = mask::scan_bytes(1);
+    if (it->first == "scan_leaf_cm") w = mask::cm_bytes();
     if (work) *work = w;
     return 1;
 }

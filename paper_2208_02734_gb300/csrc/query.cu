@@ -12,11 +12,12 @@
 // (distance bits << 32 | id) -- a total order, so the result does not depend
 // on the order rows are visited in or on the other queries in the launch.
 //
-// One block per query.  Groups of LPR lanes read a row with coalesced float4
-// loads (consecutive lanes, consecutive 16-byte chunks of a contiguous row
-// range); U rows per group are in flight per round.  Candidates below the
-// current K-th key are appended to a shared-memory buffer, which is bitonic-
-// sorted together with the current top list whenever it could overflow.
+// One block per query; each thread owns whole rows and sums (r_t - q_t)^2 in
+// increasing t with FMAs -- the same arithmetic as the cluster-major leaf scan
+// (query_cm.cu), so a distance does not depend on which kernel computed it.
+// Candidates below the current K-th key are appended to a shared-memory
+// buffer, which is bitonic-sorted together with the current top list whenever
+// it could overflow.
 #include <climits>
 
 #include "common.cuh"
@@ -30,7 +31,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 2;  // rows per thread per round
 
 __device__ __forceinline__ void bitonic_sort_keys(unsigned long long *buf, int S) {
     for (int kk = 2; kk <= S; kk <<= 1)
@@ -47,7 +48,25 @@ __device__ __forceinline__ void bitonic_sort_keys(unsigned long long *buf, int S
         }
 }
 
-template <int LPR>
+// Squared distance of one row to the query, t ascending (FMA per term).
+__device__ __forceinline__ float row_sqdist(const float4 *__restrict__ row, const float4 *qs,
+                                            int dp4) {
+    float acc = 0.f;
+#pragma unroll 4
+    for (int c = 0; c < dp4; ++c) {
+        const float4 v = row[c], q = qs[c];
+        float e = v.x - q.x;
+        acc = fmaf(e, e, acc);
+        e = v.y - q.y;
+        acc = fmaf(e, e, acc);
+        e = v.z - q.z;
+        acc = fmaf(e, e, acc);
+        e = v.w - q.w;
+        acc = fmaf(e, e, acc);
+    }
+    return acc;
+}
+
 __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     const float4 *__restrict__ R, int dp4, const int32_t *__restrict__ rid,
     const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P, int64_t root_end,
@@ -61,9 +80,8 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     __shared__ int cnt;
     __shared__ unsigned long long thresh;
 
-    constexpr int G = kThreads / LPR;
-    constexpr int ROUND = G * kUnroll;
-    const int tid = threadIdx.x, g = tid / LPR, gl = tid % LPR;
+    constexpr int ROUND = kThreads * kUnroll;
+    const int tid = threadIdx.x;
     const int64_t q = blockIdx.x;
 
     for (int c = tid; c < dp4; c += kThreads) qs[c] = Q[q * dp4 + c];
@@ -97,12 +115,10 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
         atomicAdd(&g_scan_bytes[out64 ? 1 : 0], (unsigned long long)T * (dp4 * 16ull + 4ull));
 
     for (int64_t base = 0; base < T; base += ROUND) {
-        float acc[kUnroll];
-        int64_t row[kUnroll];
+        const unsigned long long th = thresh;
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const int64_t t = base + g + (int64_t)u * G;
-            row[u] = -1;
+            const int64_t t = base + tid + (int64_t)u * kThreads;
             if (t < T) {
                 // the range holding t: the last s with cum[s] <= t
                 int lo = 0, hi = nr - 1;
@@ -110,36 +126,10 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
                     const int mid = (lo + hi + 1) >> 1;
                     if (cum[mid] <= t) lo = mid; else hi = mid - 1;
                 }
-                row[u] = rb[lo] + (t - cum[lo]);
-            }
-            acc[u] = 0.f;
-        }
-        for (int c = gl; c < dp4; c += LPR) {
-            const float4 qv = qs[c];
-            float4 v[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                v[u] = row[u] >= 0 ? R[row[u] * dp4 + c] : qv;
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const float e0 = v[u].x - qv.x, e1 = v[u].y - qv.y, e2 = v[u].z - qv.z,
-                            e3 = v[u].w - qv.w;
-                acc[u] = fmaf(e0, e0, acc[u]);
-                acc[u] = fmaf(e1, e1, acc[u]);
-                acc[u] = fmaf(e2, e2, acc[u]);
-                acc[u] = fmaf(e3, e3, acc[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            for (int o = LPR / 2; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], o);
-        if (gl == 0) {
-            const unsigned long long th = thresh;
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                if (row[u] < 0) continue;
+                const int64_t row = rb[lo] + (t - cum[lo]);
+                const float dist = row_sqdist(R + row * dp4, qs, dp4);
                 const unsigned long long key =
-                    ((unsigned long long)__float_as_uint(acc[u]) << 32) | (unsigned)rid[row[u]];
+                    ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)rid[row];
                 if (key < th) buf[KP + atomicAdd(&cnt, 1)] = key;
             }
         }
@@ -180,34 +170,18 @@ int next_pow2(int v) {
 void scan_topk(const ScanArgs &a, cudaStream_t s) {
     if (a.nq == 0) return;
     MASK_REQUIRE(a.K >= 1 && a.K <= 4096, "scan_topk: K out of range");
-    const int lpr = lanes_per_row(a.dp);
-    const int round = kThreads / lpr * kUnroll;
+    constexpr int round = kThreads * kUnroll;
     const int KP = next_pow2(a.K);
-    const int S = next_pow2(KP + 4 * round > 4 * KP ? KP + 4 * round : 4 * KP);
+    const int S = next_pow2(KP + 2 * round > 4 * KP ? KP + 2 * round : 4 * KP);
     const int P = a.sel ? a.P : 1;
     const size_t smem = (size_t)S * 8 + (size_t)(2 * P + 2) * 8 + (size_t)a.dp * 4;
     MASK_REQUIRE(smem <= 220 * 1024, "scan_topk: K, probes or dimension too large");
-    const float4 *R = reinterpret_cast<const float4 *>(a.R);
-    const float4 *Qv = reinterpret_cast<const float4 *>(a.Q);
-#define MASK_SCAN(LPRV)                                                                     \
-    do {                                                                                    \
-        auto kfn = scan_topk_kernel<LPRV>;                                                  \
-        MASK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                       (int)smem));                                         \
-        kfn<<<(unsigned)a.nq, kThreads, smem, s>>>(R, a.dp / 4, a.rid, a.off, a.sel, P,     \
-                                                   a.root_end, Qv, a.K, KP, S, a.out_ids32, \
-                                                   a.out_ids64, a.out_d);                   \
-    } while (0)
+    MASK_CUDA(cudaFuncSetAttribute(scan_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
     ProfRegion pr(a.out_ids64 ? "scan_topk_leaf" : "scan_topk_level", s, 0.0);
-    switch (lpr) {
-    case 1: MASK_SCAN(1); break;
-    case 2: MASK_SCAN(2); break;
-    case 4: MASK_SCAN(4); break;
-    case 8: MASK_SCAN(8); break;
-    case 16: MASK_SCAN(16); break;
-    default: MASK_SCAN(32); break;
-    }
-#undef MASK_SCAN
+    scan_topk_kernel<<<(unsigned)a.nq, kThreads, smem, s>>>(
+        reinterpret_cast<const float4 *>(a.R), a.dp / 4, a.rid, a.off, a.sel, P, a.root_end,
+        reinterpret_cast<const float4 *>(a.Q), a.K, KP, S, a.out_ids32, a.out_ids64, a.out_d);
     MASK_LAUNCHED("scan_topk");
 }
 

@@ -193,14 +193,28 @@ def loaded(c1):
     idx.free()
 
 
+@pytest.mark.parametrize("leaf", ["query", "cluster"])
 @pytest.mark.parametrize("k,probes", [(10, [3, 3]), (1, [1, 1]), (10, [1, 1]), (100, [5, 4]),
-                                      (17, [2, 20])])
-def test_query_matches_oracle(loaded, k, probes):
+                                      (17, [2, 20]), (32, [40, 10])])
+def test_query_matches_oracle(monkeypatch, loaded, leaf, k, probes):
+    # leaf scan query by query, or cluster-major (k <= 32; larger k falls back)
+    monkeypatch.setenv("MASK_LEAF_SCAN", leaf)
     X, Q, ref, idx = loaded
     ids_o, d_o, clear = ref.query(Q, k, probes)
     ids_g, d_g = M.mask_query(idx, cuda(Q), k, probes)
     loose = check_knn(X, Q, ids_g, d_g, ids_o, d_o, clear)
     assert loose <= 0.01 * len(Q)
+
+
+def test_leaf_scan_paths_agree_bitwise(monkeypatch, loaded):
+    # both leaf scans evaluate sum_t (x_t - q_t)^2 in the same order
+    X, Q, ref, idx = loaded
+    out = {}
+    for leaf in ["query", "cluster"]:
+        monkeypatch.setenv("MASK_LEAF_SCAN", leaf)
+        out[leaf] = M.mask_query(idx, cuda(Q), 10, [12, 6])
+    assert torch.equal(out["query"][0], out["cluster"][0])
+    assert torch.equal(out["query"][1], out["cluster"][1])
 
 
 def test_probing_everything_is_exact_knn(loaded):
