@@ -293,10 +293,12 @@ def run_reference(args, w, wname):
 
 # ----------------------------------------------------------------- our arm
 
-KERNEL_KIND = {"assign_tc": "tensor", "assign_gemm": "alu", "assign_recheck": "alu", "scan_topk_leaf": "hbm",
+KERNEL_KIND = {"assign_tc": "tensor", "assign_gemm": "alu", "assign_recheck": "alu",
+               "scan_leaf_cm": "hbm", "leaf_group": "hbm", "leaf_merge": "hbm",
+               "scan_topk_leaf": "hbm",
                "scan_topk_level": "hbm", "centroid_update": "hbm", "label_sort": "hbm",
                "kmeanspp": "hbm"}
-KERNEL_SRC = {"assign_tc": "assign_tc.cu", "assign_gemm": "assign.cu", "scan_topk_leaf": "query.cu",
+KERNEL_SRC = {"assign_tc": "assign_tc.cu", "assign_gemm": "assign.cu", "scan_leaf_cm": "query_cm.cu", "scan_topk_leaf": "query.cu",
               "centroid_update": "kmeans.cu", "kmeanspp": "kmeans.cu", "label_sort": "kmeans.cu"}
 
 

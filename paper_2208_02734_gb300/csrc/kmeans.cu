@@ -193,11 +193,40 @@ constexpr int kKppSelMax = 2048; // block sums the selecting warp stages in shar
 // row whose inclusive prefix of D^2 exceeds u_t * sum(D^2) (all sums FP64);
 // if that sum is 0, the lowest-index row not chosen yet.  The last block then
 // advances *t_dev, so identical launches can be replayed step after step.
+// cc2[j] = ||c_{t-1} - c_j||^2 for the centres j < t-1 chosen so far (FP32
+// difference form): the distances the D^2 update prunes with.
+__global__ void kpp_centre_dist_kernel(const float *__restrict__ X, int64_t m, int dp,
+                                       const int *__restrict__ t_dev,
+                                       const int64_t *__restrict__ chosen,
+                                       float *__restrict__ cc2) {
+    const int t = *t_dev;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 2 || j >= t - 1) return;
+    int64_t a = chosen[t - 1], b = chosen[j];
+    if (a < 0 || a >= m) a = 0;
+    if (b < 0 || b >= m) b = 0;
+    const float4 *ca = reinterpret_cast<const float4 *>(X + a * dp);
+    const float4 *cb = reinterpret_cast<const float4 *>(X + b * dp);
+    float acc = 0.f;
+    for (int c = 0; c < dp / 4; ++c) {
+        const float4 x = __ldg(ca + c), y = __ldg(cb + c);
+        float e = x.x - y.x;
+        acc = fmaf(e, e, acc);
+        e = x.y - y.y;
+        acc = fmaf(e, e, acc);
+        e = x.z - y.z;
+        acc = fmaf(e, e, acc);
+        e = x.w - y.w;
+        acc = fmaf(e, e, acc);
+    }
+    cc2[j] = acc;
+}
+
 __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
     const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
-    const double *__restrict__ u, float *__restrict__ D2, double *__restrict__ bsum,
-    unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
-    unsigned char *__restrict__ taken) {
+    const double *__restrict__ u, float *__restrict__ D2, int32_t *__restrict__ asg,
+    const float *__restrict__ cc2, double *__restrict__ bsum, unsigned *__restrict__ counter,
+    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken) {
     __shared__ double red[kKppThreads / 32];
     __shared__ int s_last;
     __shared__ double s_b[kKppSelMax];   // staged block sums (selecting warp)
@@ -211,37 +240,44 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
     const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
     const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
 
-    // D^2 update: thread owns rows r0 + tid + q * kKppThreads
-    float old[kKppRpt], acc[kKppRpt];
-#pragma unroll
-    for (int q = 0; q < kKppRpt; ++q) {
-        const int64_t i = r0 + tid + q * kKppThreads;
-        old[q] = (t > 1 && i < m) ? D2[i] : FLT_MAX;
-        acc[q] = 0.f;
-    }
-#pragma unroll 2
-    for (int ch = 0; ch < dp4; ++ch) {
-        const float4 b = __ldg(crow + ch);
-#pragma unroll
-        for (int q = 0; q < kKppRpt; ++q) {
-            const int64_t i = r0 + tid + q * kKppThreads;
-            const float4 a = i < m ? reinterpret_cast<const float4 *>(X + i * dp)[ch] : b;
-            const float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
-            acc[q] = fmaf(e0, e0, acc[q]);
-            acc[q] = fmaf(e1, e1, acc[q]);
-            acc[q] = fmaf(e2, e2, acc[q]);
-            acc[q] = fmaf(e3, e3, acc[q]);
-        }
-    }
+    // D^2 update: thread owns rows r0 + tid + q * kKppThreads.  A row whose
+    // nearest centre a lies at least 2 sqrt(D^2) (with a 1e-3 margin for
+    // rounding) from the new centre cannot get closer to it (triangle
+    // inequality), so its distance is not evaluated: the result is the same
+    // as evaluating it and keeping min(D^2, distance).
     double local = 0.0;
 #pragma unroll
     for (int q = 0; q < kKppRpt; ++q) {
         const int64_t i = r0 + tid + q * kKppThreads;
-        if (i < m) {
-            const float nv = fminf(old[q], acc[q]);
-            D2[i] = nv;
-            local += (double)nv;
+        if (i >= m) continue;
+        float d2 = FLT_MAX;
+        int a = 0;
+        bool eval = true;
+        if (t > 1) {
+            d2 = D2[i];
+            a = asg[i];
+            eval = !(cc2[a] >= 4.004f * d2);
         }
+        if (eval) {
+            const float4 *xr = reinterpret_cast<const float4 *>(X + i * dp);
+            float acc = 0.f;
+#pragma unroll 4
+            for (int ch = 0; ch < dp4; ++ch) {
+                const float4 xa = xr[ch], b = __ldg(crow + ch);
+                const float e0 = xa.x - b.x, e1 = xa.y - b.y, e2 = xa.z - b.z, e3 = xa.w - b.w;
+                acc = fmaf(e0, e0, acc);
+                acc = fmaf(e1, e1, acc);
+                acc = fmaf(e2, e2, acc);
+                acc = fmaf(e3, e3, acc);
+            }
+            if (acc < d2) {
+                d2 = acc;
+                a = t - 1;
+            }
+            D2[i] = d2;
+            asg[i] = a;
+        }
+        local += (double)d2;
     }
     const double bs = block_sum_f64<kKppThreads>(local, red);
     if (tid == 0) bsum[blockIdx.x] = bs;
@@ -262,6 +298,8 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
     long long fb = -1;
     double excl = 0.0;
     // pass over the block sums in chunks of kKppSelMax staged in shared memory
+    // (one chunk -- every launch that seeds <= 2M rows -- is loaded only once)
+    const bool staged = nb <= kKppSelMax;
     double carry = 0.0;
     for (int c0 = 0; c0 < nb; c0 += kKppSelMax) {
         const int cn = min(kKppSelMax, nb - c0);
@@ -283,7 +321,8 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
         carry = 0.0;
         for (int c0 = 0; c0 < nb && fb < 0; c0 += kKppSelMax) {
             const int cn = min(kKppSelMax, nb - c0);
-            for (int b = lane; b < cn; b += 32) s_b[b] = __ldcg(bsum + c0 + b);
+            if (!staged)
+                for (int b = lane; b < cn; b += 32) s_b[b] = __ldcg(bsum + c0 + b);
             __syncwarp();
             const int per = (cn + 31) / 32;
             double ls = 0.0;
@@ -657,7 +696,8 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
     if (k <= 1) return;
     ProfRegion pr("kmeanspp", s, (double)(k - 1) * (double)m * dp * 4.0);
     const int nb = (int)((m + kKppRows - 1) / kKppRows);
-    Scratch<float> D2(m, s);
+    Scratch<float> D2(m, s), cc2(k, s);
+    Scratch<int32_t> asg(m, s);
     Scratch<double> bsum(nb, s);
     Scratch<unsigned> counter(1, s);
     Scratch<int> t_dev(1, s);
@@ -666,10 +706,12 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
     MASK_CUDA(cudaMemsetAsync(counter.get(), 0, sizeof(unsigned), s));
     MASK_CUDA(cudaMemsetAsync(taken.get(), 0, m, s));
     MASK_CUDA(cudaMemcpyAsync(t_dev.get(), &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    const int ccb = (k + 255) / 256;
     auto launch = [&](cudaStream_t st) {
+        kpp_centre_dist_kernel<<<ccb, 256, 0, st>>>(Xs, m, dp, t_dev.get(), chosen, cc2.get());
         kpp_step_kernel<<<nb, kKppThreads, 0, st>>>(Xs, m, dp, t_dev.get(), u_dev, D2.get(),
-                                                    bsum.get(), counter.get(), chosen,
-                                                    taken.get());
+                                                    asg.get(), cc2.get(), bsum.get(),
+                                                    counter.get(), chosen, taken.get());
     };
     // The steps are identical launches (the step number lives on the device),
     // so a captured graph of kBatch steps is replayed; the rest run directly.
@@ -683,14 +725,14 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
         cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int i = 0; i < kBatch; ++i) launch(cs);
+            for (int i = 0; i < kBatch; ++i) launch(cs);  // two kernels per step
             e = cudaStreamEndCapture(cs, &graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess) {
             for (; done + kBatch <= steps && e == cudaSuccess; done += kBatch) {
                 e = cudaGraphLaunch(exec, s);
-                for (int i = 0; i < kBatch; ++i) count_launch();
+                for (int i = 0; i < 2 * kBatch; ++i) count_launch();
             }
         }
         if (exec) cudaGraphExecDestroy(exec);
@@ -700,6 +742,7 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
     }
     for (; done < steps; ++done) {
         launch(s);
+        count_launch();
         MASK_LAUNCHED("kpp_step");
     }
 }

@@ -67,6 +67,11 @@ __device__ __forceinline__ float row_sqdist(const float4 *__restrict__ row, cons
     return acc;
 }
 
+// ROWWISE: one thread per row, t ascending (the leaf arithmetic shared with
+// the cluster-major scan).  Otherwise groups of LPR lanes read a row with
+// coalesced float4 loads and reduce by shuffles (the centroid levels, whose
+// results only ever come from this kernel).
+template <bool ROWWISE, int LPR>
 __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     const float4 *__restrict__ R, int dp4, const int32_t *__restrict__ rid,
     const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P, int64_t root_end,
@@ -116,21 +121,77 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
 
     for (int64_t base = 0; base < T; base += ROUND) {
         const unsigned long long th = thresh;
+        if (ROWWISE) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int64_t t = base + tid + (int64_t)u * kThreads;
-            if (t < T) {
-                // the range holding t: the last s with cum[s] <= t
-                int lo = 0, hi = nr - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (cum[mid] <= t) lo = mid; else hi = mid - 1;
+            for (int u = 0; u < kUnroll; ++u) {
+                const int64_t t = base + tid + (int64_t)u * kThreads;
+                if (t < T) {
+                    // the range holding t: the last s with cum[s] <= t
+                    int lo = 0, hi = nr - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (cum[mid] <= t) lo = mid; else hi = mid - 1;
+                    }
+                    const int64_t row = rb[lo] + (t - cum[lo]);
+                    const float dist = row_sqdist(R + row * dp4, qs, dp4);
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)rid[row];
+                    if (key < th) buf[KP + atomicAdd(&cnt, 1)] = key;
                 }
-                const int64_t row = rb[lo] + (t - cum[lo]);
-                const float dist = row_sqdist(R + row * dp4, qs, dp4);
-                const unsigned long long key =
-                    ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)rid[row];
-                if (key < th) buf[KP + atomicAdd(&cnt, 1)] = key;
+            }
+        } else {
+            // lane groups: ROUND rows = (kThreads / LPR) groups x (kUnroll * LPR) rows
+            // each, four rows in flight per group
+            constexpr int G = kThreads / LPR;
+            constexpr int PER = kUnroll * LPR;
+            const int g = tid / LPR, gl = tid % LPR;
+#pragma unroll 1
+            for (int u0 = 0; u0 < PER; u0 += 4) {
+                int64_t row[4];
+                float acc[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t t = base + g + (int64_t)(u0 + i) * G;
+                    row[i] = -1;
+                    acc[i] = 0.f;
+                    if (u0 + i < PER && t < T) {
+                        int lo = 0, hi = nr - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (cum[mid] <= t) lo = mid; else hi = mid - 1;
+                        }
+                        row[i] = rb[lo] + (t - cum[lo]);
+                    }
+                }
+                for (int c = gl; c < dp4; c += LPR) {
+                    const float4 qv = qs[c];
+                    float4 v[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v[i] = row[i] >= 0 ? R[row[i] * dp4 + c] : qv;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float e0 = v[i].x - qv.x, e1 = v[i].y - qv.y, e2 = v[i].z - qv.z,
+                                    e3 = v[i].w - qv.w;
+                        acc[i] = fmaf(e0, e0, acc[i]);
+                        acc[i] = fmaf(e1, e1, acc[i]);
+                        acc[i] = fmaf(e2, e2, acc[i]);
+                        acc[i] = fmaf(e3, e3, acc[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    for (int o = LPR / 2; o > 0; o >>= 1)
+                        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+                if (gl == 0) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (row[i] < 0) continue;
+                        const unsigned long long key =
+                            ((unsigned long long)__float_as_uint(acc[i]) << 32) |
+                            (unsigned)rid[row[i]];
+                        if (key < th) buf[KP + atomicAdd(&cnt, 1)] = key;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -176,12 +237,31 @@ void scan_topk(const ScanArgs &a, cudaStream_t s) {
     const int P = a.sel ? a.P : 1;
     const size_t smem = (size_t)S * 8 + (size_t)(2 * P + 2) * 8 + (size_t)a.dp * 4;
     MASK_REQUIRE(smem <= 220 * 1024, "scan_topk: K, probes or dimension too large");
-    MASK_CUDA(cudaFuncSetAttribute(scan_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
     ProfRegion pr(a.out_ids64 ? "scan_topk_leaf" : "scan_topk_level", s, 0.0);
-    scan_topk_kernel<<<(unsigned)a.nq, kThreads, smem, s>>>(
-        reinterpret_cast<const float4 *>(a.R), a.dp / 4, a.rid, a.off, a.sel, P, a.root_end,
-        reinterpret_cast<const float4 *>(a.Q), a.K, KP, S, a.out_ids32, a.out_ids64, a.out_d);
+    const float4 *R = reinterpret_cast<const float4 *>(a.R);
+    const float4 *Qv = reinterpret_cast<const float4 *>(a.Q);
+#define MASK_SCAN(ROWW, LPRV)                                                                \
+    do {                                                                                     \
+        auto kfn = scan_topk_kernel<ROWW, LPRV>;                                             \
+        MASK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                       (int)smem));                                          \
+        kfn<<<(unsigned)a.nq, kThreads, smem, s>>>(R, a.dp / 4, a.rid, a.off, a.sel, P,      \
+                                                   a.root_end, Qv, a.K, KP, S, a.out_ids32,  \
+                                                   a.out_ids64, a.out_d);                    \
+    } while (0)
+    if (a.out_ids64) {
+        MASK_SCAN(true, 1);  // the leaf: per-row arithmetic shared with the cluster-major scan
+    } else {
+        switch (lanes_per_row(a.dp)) {
+        case 1: MASK_SCAN(false, 1); break;
+        case 2: MASK_SCAN(false, 2); break;
+        case 4: MASK_SCAN(false, 4); break;
+        case 8: MASK_SCAN(false, 8); break;
+        case 16: MASK_SCAN(false, 16); break;
+        default: MASK_SCAN(false, 32); break;
+        }
+    }
+#undef MASK_SCAN
     MASK_LAUNCHED("scan_topk");
 }
 
