@@ -293,6 +293,23 @@ def run_reference(args, w, wname):
 
 # ----------------------------------------------------------------- our arm
 
+def reduce_max(vals, world, device):
+    """Element-wise max of a few numbers over all ranks (timing only)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def weak_scaling_value(world, steps, nq, local_query_ms, local_total_ms, device):
+    """Every rank answers nq queries per step on its own partition; the job's
+    throughput divides all ranks' queries by the slowest rank's query time."""
+    q_sum, tot = reduce_max([local_query_ms, local_total_ms], world, device)
+    return world * steps * nq / (q_sum / 1000.0), q_sum, tot
+
+
 KERNEL_KIND = {"assign_tc": "tensor", "assign_gemm": "alu", "assign_recheck": "alu",
                "scan_leaf_cm": "hbm", "leaf_group": "hbm", "leaf_merge": "hbm",
                "scan_topk_leaf": "hbm",
@@ -320,10 +337,7 @@ def run_ours(args, w, wname):
             dist.barrier()
 
     def max_over_ranks(vals):
-        t = torch.tensor(vals, dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.tolist()
+        return reduce_max(vals, world, dev)
 
     M.load()
     t_gen = time.perf_counter()
@@ -392,8 +406,8 @@ def run_ours(args, w, wname):
     build_ms = [r[2][0].elapsed_time(r[2][1]) for r in results]
     query_ms = [r[2][1].elapsed_time(r[2][2]) for r in results]
     total_ms = t_start.elapsed_time(t_end)
-    q_sum, tot = max_over_ranks([sum(query_ms), total_ms])
-    value = world * args.steps * w["nq"] / (q_sum / 1000.0)
+    value, q_sum, tot = weak_scaling_value(world, args.steps, w["nq"], sum(query_ms), total_ms,
+                                           dev)
 
     kernels = {}
     for name in KERNEL_KIND:

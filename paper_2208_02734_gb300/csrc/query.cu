@@ -85,7 +85,8 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     __shared__ int cnt;
     __shared__ unsigned long long thresh;
 
-    constexpr int ROUND = kThreads * kUnroll;
+    // rows per round: rowwise, kUnroll per thread; lane groups, 4 per group
+    constexpr int ROUND = ROWWISE ? kThreads * kUnroll : (kThreads / LPR) * 4;
     const int tid = threadIdx.x;
     const int64_t q = blockIdx.x;
 
@@ -143,7 +144,7 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
             // lane groups: ROUND rows = (kThreads / LPR) groups x (kUnroll * LPR) rows
             // each, four rows in flight per group
             constexpr int G = kThreads / LPR;
-            constexpr int PER = kUnroll * LPR;
+            constexpr int PER = 4;
             const int g = tid / LPR, gl = tid % LPR;
 #pragma unroll 1
             for (int u0 = 0; u0 < PER; u0 += 4) {
@@ -231,7 +232,7 @@ int next_pow2(int v) {
 void scan_topk(const ScanArgs &a, cudaStream_t s) {
     if (a.nq == 0) return;
     MASK_REQUIRE(a.K >= 1 && a.K <= 4096, "scan_topk: K out of range");
-    constexpr int round = kThreads * kUnroll;
+    const int round = a.out_ids64 ? kThreads * kUnroll : (kThreads / lanes_per_row(a.dp)) * 4;
     const int KP = next_pow2(a.K);
     const int S = next_pow2(KP + 2 * round > 4 * KP ? KP + 2 * round : 4 * KP);
     const int P = a.sel ? a.P : 1;
