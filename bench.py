@@ -417,6 +417,38 @@ def run_ours(args, w, wname):
     recall = recall_at_k(Xd, Qs, results[-1][0][sel], dk)
     n_rec = int(len(sel))
 
+    # BF16 / FP8 leaf scans (4k shortlist + exact FP32 re-rank) on the same
+    # index: each mode at the cheapest ladder probes reaching recall@10 >= 0.95
+    lowp = {}
+    if not args.no_lowp:
+        idx_lp = M.mask_build(Xd, kpl, w["iters"], seed=0)
+        for mode, prec in (("bf16", M.MASK_BF16), ("fp8", M.MASK_FP8E4M3)):
+            M.mask_query(idx_lp, Qs, k, w["ladder"][0], precision=prec)  # quantise once
+            rung = None
+            for pr in w["ladder"]:
+                ids_s, _ = M.mask_query(idx_lp, Qs, k, pr, precision=prec)
+                r = recall_at_k(Xd, Qs, ids_s, dk)
+                if r >= 0.95:
+                    rung = (pr, r)
+                    break
+            if rung is None:
+                lowp[mode] = {"error": "recall@10 >= 0.95 not reached on the ladder"}
+                continue
+            qms = []
+            for i in range(args.warmup + args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                M.mask_query(idx_lp, Qd, k, rung[0], precision=prec)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    qms.append(e0.elapsed_time(e1))
+            lowp[mode] = {"probes": rung[0], "recall_at_10": rung[1],
+                          "value": args.steps * w["nq"] / (sum(qms) / 1e3), "unit": "queries/s",
+                          "p50_ms": float(np.percentile(qms, 50)),
+                          "p99_ms": float(np.percentile(qms, 99))}
+        idx_lp.free()
+
     # end to end through the public API with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -503,6 +535,7 @@ def run_ours(args, w, wname):
         "build_s": statistics.mean(build_ms) / 1e3,
         "p50_ms": float(np.percentile(query_ms, 50)), "p99_ms": float(np.percentile(query_ms, 99)),
         "latency_note": "device time of one 10k-query batch (query phase), over the timed steps",
+        "low_precision": lowp,
         "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
         "clocks": clocks, "e2e": e2e,
     }
@@ -526,6 +559,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense10m")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lowp", action="store_true", help="skip the BF16/FP8 query modes")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

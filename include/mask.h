@@ -110,7 +110,13 @@ mask_status mask_build_csr(const int64_t *row_ptr, const int32_t *col, const flo
  *   queries   [nq x d] float32.
  *   k         neighbours per query (1 <= k <= 1024).
  *   probes    host array [n_levels], finest first; p_l >= 1, clamped to k_l.
- *   precision MASK_FP32 (others: MASK_EUNSUPPORTED until built).
+ *   precision MASK_FP32: every distance in FP32.  MASK_BF16 / MASK_FP8E4M3:
+ *             the leaf scan ranks points by distances between BF16 (or FP8
+ *             e4m3 with a per-row scale max|x|/448) copies of the points and
+ *             the query, keeps the 4k nearest, and re-ranks those by exact
+ *             FP32 distances (k <= 16 and d <= 256, else MASK_EUNSUPPORTED);
+ *             the quantised copy is made on the first such query (the index
+ *             grows by 2 or 1 bytes per coordinate plus 4-8 bytes per point).
  *   ids_out   [nq x k] int64 original point ids, ascending by (distance, id);
  *             -1 where fewer than k points were reached.
  *   dists_out [nq x k] float32 squared distances; +inf where ids_out is -1.

@@ -215,5 +215,20 @@ void cm_leaf_scan(const float *Xs, int dp, const int32_t *xids, const int64_t *l
                   float *dists, cudaStream_t s);
 double cm_bytes();
 void cm_bytes_reset();
+// groups the (query, kept leaf) pairs by leaf cluster; item_off[k0] = work items
+void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
+                    Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s);
+
+// query_lp.cu -- BF16 / FP8 leaf scan with exact FP32 re-rank of a 4k shortlist
+int lp_padded_dim(int dp);
+bool lp_supported(int dp, int k);
+// quantised copy ([rows x lp_padded_dim] BF16 or e4m3), per-row scale (FP8) and
+// squared norm of every quantised row
+void lp_quantize(const float *src, int64_t rows, int dp, bool fp8, void *dst, float *scale,
+                 float *norm2, cudaStream_t s);
+void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscale, const float *Xs,
+                  int dp, const int32_t *xids, const int64_t *leaf_off, int k0, const float *Qp,
+                  int64_t nq, const int32_t *sel, int P, int k, int64_t *ids, float *dists,
+                  cudaStream_t s);
 
 }  // namespace mask

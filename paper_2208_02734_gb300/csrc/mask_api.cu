@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -34,6 +35,10 @@ struct mask_index {
         std::vector<double> objective; // k-means objective after each assignment
     };
     std::vector<Level> lv;
+    // quantised copies of Xs for the BF16 / FP8 query modes, made on first use
+    mutable std::mutex lp_mu;
+    mutable mask::DevArray<unsigned char> Xlp[2];  // [0] BF16, [1] FP8 e4m3
+    mutable mask::DevArray<float> xn_lp[2], xscale_fp8;
 };
 
 namespace mask {
@@ -417,6 +422,8 @@ mask_status mask_index_get_info(const mask_index *index, mask_index_info *out) {
         out->iters = index->iters;
         out->sparse = index->sparse ? 1 : 0;
         int64_t bytes = (int64_t)(index->Xs.bytes() + index->xids.bytes());
+        for (int q = 0; q < 2; ++q) bytes += (int64_t)(index->Xlp[q].bytes() + index->xn_lp[q].bytes());
+        bytes += (int64_t)index->xscale_fp8.bytes();
         for (int l = 0; l < index->L; ++l) {
             const auto &L = index->lv[(size_t)l];
             out->k_per_level[l] = L.k;
@@ -462,7 +469,11 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
         MASK_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
         MASK_REQUIRE(probes != nullptr, "probes is NULL");
         MASK_REQUIRE(current_device() == index->device, "index lives on another device");
-        if (precision != MASK_FP32) fail(MASK_EUNSUPPORTED, "only MASK_FP32 is built in this version");
+        MASK_REQUIRE(precision == MASK_FP32 || precision == MASK_BF16 ||
+                         precision == MASK_FP8E4M3, "unknown precision");
+        const bool lowp = precision != MASK_FP32;
+        if (lowp && !lp_supported(index->dp, k))
+            fail(MASK_EUNSUPPORTED, "BF16/FP8 modes keep a 4k shortlist: k <= 16 and d <= 256");
         if (nq == 0) return;
         MASK_REQUIRE(queries && ids_out, "NULL queries or ids_out");
         cudaStream_t s = (cudaStream_t)stream;
@@ -502,9 +513,34 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
             b.out_ids32 = sel[(size_t)l - 1].get();
             scan_topk(b, s);
         }
+        const int k0 = index->lv[0].k;
+        if (lowp) {
+            // BF16 / FP8 distances for a 4k shortlist, exact FP32 re-rank
+            const bool fp8 = precision == MASK_FP8E4M3;
+            const int slot = fp8 ? 1 : 0;
+            {
+                std::lock_guard<std::mutex> lk(index->lp_mu);
+                if (index->Xlp[slot].p == nullptr) {
+                    const int dpl = lp_padded_dim(dp);
+                    index->Xlp[slot].alloc((size_t)index->n * dpl * (fp8 ? 1 : 2));
+                    index->xn_lp[slot].alloc((size_t)index->n);
+                    if (fp8) index->xscale_fp8.alloc((size_t)index->n);
+                    lp_quantize(index->Xs.get(), index->n, dp, fp8, index->Xlp[slot].get(),
+                                fp8 ? index->xscale_fp8.get() : nullptr,
+                                index->xn_lp[slot].get(), s);
+                }
+            }
+            lp_leaf_scan(fp8, index->Xlp[slot].get(), index->xn_lp[slot].get(),
+                         fp8 ? index->xscale_fp8.get() : nullptr, index->Xs.get(), dp,
+                         index->xids.get(), index->lv[0].off.get(), k0, Qp.get(), nq, sel[0].get(),
+                         p[0], k, ids.p, dd.p, s);
+            ids.finish(s);
+            dd.finish(s);
+            if (ids.host || dd.host) MASK_CUDA(cudaStreamSynchronize(s));
+            return;
+        }
         // Leaf scan: cluster-major when the batch keeps each leaf cluster
         // several times on average, else query by query (same arithmetic).
-        const int k0 = index->lv[0].k;
         bool cluster_major = cm_leaf_supported(dp, k) && nq * (int64_t)p[0] >= 4 * (int64_t)k0;
         if (const char *mode = std::getenv("MASK_LEAF_SCAN")) {
             if (std::strcmp(mode, "cluster") == 0) cluster_major = cm_leaf_supported(dp, k);

@@ -261,22 +261,30 @@ int grid_cap(int64_t work, int threads) {
 
 bool cm_leaf_supported(int dp, int K) { return dp <= 128 && K >= 1 && K <= 32; }
 
+void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
+                    Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s) {
+    const int64_t npairs = nq * P;
+    ProfRegion pr("leaf_group", s, 0.0);
+    Scratch<int32_t> lab(npairs, s);
+    pairs.alloc(npairs, s);
+    poff.alloc((size_t)k0 + 2, s);
+    item_off.alloc((size_t)k0 + 1, s);
+    pair_labels_kernel<<<grid_cap(npairs, 256), 256, 0, s>>>(sel, npairs, k0, lab.get());
+    MASK_LAUNCHED("pair_labels");
+    label_sort(lab.get(), npairs, k0 + 1, poff.get(), pairs.get(), s);
+    item_scan_kernel<<<1, 1024, 0, s>>>(poff.get(), k0, item_off.get());
+    MASK_LAUNCHED("item_scan");
+}
+
 void cm_leaf_scan(const float *Xs, int dp, const int32_t *xids, const int64_t *leaf_off, int k0,
                   const float *Qp, int64_t nq, const int32_t *sel, int P, int K, int64_t *ids,
                   float *dists, cudaStream_t s) {
     if (nq == 0) return;
     const int64_t npairs = nq * P;
-    Scratch<int32_t> lab(npairs, s), pairs(npairs, s);
-    Scratch<int64_t> poff((size_t)k0 + 2, s), item_off((size_t)k0 + 1, s);
+    Scratch<int32_t> pairs;
+    Scratch<int64_t> poff, item_off;
     Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
-    {
-        ProfRegion pr("leaf_group", s, 0.0);
-        pair_labels_kernel<<<grid_cap(npairs, 256), 256, 0, s>>>(sel, npairs, k0, lab.get());
-        MASK_LAUNCHED("pair_labels");
-        label_sort(lab.get(), npairs, k0 + 1, poff.get(), pairs.get(), s);
-        item_scan_kernel<<<1, 1024, 0, s>>>(poff.get(), k0, item_off.get());
-        MASK_LAUNCHED("item_scan");
-    }
+    cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
     {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         const size_t smem = ((size_t)dp * CM_R + (size_t)dp * CM_QB + CM_QB * CM_R) * 4 +

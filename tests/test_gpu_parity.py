@@ -288,3 +288,68 @@ def test_export_and_reload_gives_the_same_answers(c1):
     ids2, d2 = M.mask_query(idx2, cuda(Q), 10, [3, 3])
     idx2.free()
     assert torch.equal(ids1, ids2) and torch.equal(d1, d2)
+
+
+# ------------------------------------------------- BF16 / FP8 + FP32 re-rank
+
+@pytest.mark.parametrize("prec,min_overlap", [(M.MASK_BF16, 0.995), (M.MASK_FP8E4M3, 0.95)])
+@pytest.mark.parametrize("leafk", [1, 10, 16])
+def test_low_precision_query_reranks_exactly(loaded, prec, min_overlap, leafk):
+    # the shortlist is ranked in low precision; what is returned is re-ranked
+    # with exact FP32 distances, so every returned distance is exact
+    X, Q, ref, idx = loaded
+    probes = [3, 3]
+    ids_o, d_o, _ = ref.query(Q, leafk, probes)
+    ids_g, d_g = M.mask_query(idx, cuda(Q), leafk, probes, precision=prec)
+    ids_g, d_g = arr(ids_g), arr(d_g)
+    overlap = total = 0
+    for q in range(len(Q)):
+        ok = ids_g[q] >= 0
+        assert len(set(ids_g[q][ok].tolist())) == ok.sum()
+        assert np.all(np.diff(d_g[q][ok]) >= 0)
+        check_close(d_g[q][ok], O.sqdist_rows(X, ids_g[q][ok], Q[q]), atol=1e-30,
+                    what=f"re-ranked distances q={q}")
+        want = set(ids_o[q][ids_o[q] >= 0].tolist())
+        overlap += len(set(ids_g[q][ok].tolist()) & want)
+        total += len(want)
+    assert overlap / total >= min_overlap, overlap / total
+
+
+def test_low_precision_rejects_long_shortlists(loaded):
+    X, Q, ref, idx = loaded
+    with pytest.raises(M.MaskError) as e:
+        M.mask_query(idx, cuda(Q[:4]), 17, [3, 3], precision=M.MASK_BF16)
+    assert e.value.status == M.MASK_EUNSUPPORTED
+
+
+def test_mixed_precision_workload_recall_and_error(c1):
+    # the small dense data and index, 10,000 queries: recall@10 of each mode
+    # against the FP64 oracle's descent and against exact k-NN, and the
+    # largest relative error of returned distances
+    X, _, idx_o = c1
+    mix = synth.IsotropicMixture(d=16, n_blobs=10, sigma=1.0, box=10.0, seed=0)
+    Q = mix.sample(10_000, seed=2)
+    ref, cs = oracle_index_fp32(idx_o)
+    idx = M.mask_index_load(cuda(X), [cuda(c) for c in cs], [cuda(lb) for lb in idx_o.labels])
+    ids_d, d_d, _ = ref.query(Q, 10, [3, 3])
+    ids_b, d_b = O.bruteforce_knn(X, Q, 10)
+    report = {}
+    for name, prec in [("fp32", M.MASK_FP32), ("bf16", M.MASK_BF16), ("fp8", M.MASK_FP8E4M3)]:
+        ids_g, d_g = M.mask_query(idx, cuda(Q), 10, [3, 3], precision=prec)
+        ids_g, d_g = arr(ids_g), arr(d_g)
+        hit_desc = hit_exact = 0
+        err = 0.0
+        for q in range(len(Q)):
+            ok = ids_g[q] >= 0
+            ex = O.sqdist_rows(X, ids_g[q][ok], Q[q])
+            err = max(err, float(np.max(np.abs(d_g[q][ok] - ex) / np.maximum(ex, 1e-30))))
+            hit_desc += len(set(ids_g[q][ok].tolist()) & set(ids_d[q].tolist()))
+            hit_exact += int(np.sum(ex <= d_b[q, -1] * (1 + RTOL)))
+        report[name] = (hit_desc / (10 * len(Q)), hit_exact / (10 * len(Q)), err)
+    idx.free()
+    print("mixed-precision report (recall vs descent, recall vs exact, max rel err):", report)
+    assert report["fp32"][0] >= 0.999 and report["fp32"][2] <= RTOL
+    assert report["bf16"][0] >= 0.995 and report["bf16"][2] <= RTOL
+    assert report["fp8"][0] >= 0.95 and report["fp8"][2] <= RTOL
+    for name in report:
+        assert abs(report[name][1] - report["fp32"][1]) <= 0.05
