@@ -113,7 +113,7 @@ mask_status mask_build_csr(const int64_t *row_ptr, const int32_t *col, const flo
  *   precision MASK_FP32: every distance in FP32.  MASK_BF16 / MASK_FP8E4M3:
  *             the leaf scan ranks points by distances between BF16 (or FP8
  *             e4m3 with a per-row scale max|x|/448) copies of the points and
- *             the query, keeps the 4k nearest, and re-ranks those by exact
+ *             the query, keeps the max(4k, 16) nearest, and re-ranks those by exact
  *             FP32 distances (k <= 16 and d <= 256, else MASK_EUNSUPPORTED);
  *             the quantised copy is made on the first such query (the index
  *             grows by 2 or 1 bytes per coordinate plus 4-8 bytes per point).

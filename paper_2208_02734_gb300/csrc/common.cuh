@@ -221,6 +221,7 @@ void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32
 
 // query_lp.cu -- BF16 / FP8 leaf scan with exact FP32 re-rank of a 4k shortlist
 int lp_padded_dim(int dp);
+int lp_shortlist(int k);  // max(4k, 16)
 bool lp_supported(int dp, int k);
 // quantised copy ([rows x lp_padded_dim] BF16 or e4m3), per-row scale (FP8) and
 // squared norm of every quantised row

@@ -8,7 +8,7 @@
 // cluster-major scan; the distances of a group are
 //     ||x~||^2 + ||q~||^2 - 2 x~.q~    (x~, q~ the quantised vectors)
 // with x~.q~ from warp-level tensor-core MMAs (FP32 accumulation).  Every query
-// keeps a shortlist of its K' = 4k nearest by these distances, which is then
+// keeps a shortlist of its K' = max(4k, 16) nearest by these distances, which is then
 // re-ranked with exact FP32 distances sum_t (x_t - q_t)^2 of the FP32 rows; the
 // k best of the shortlist are returned.  Shortlist keys carry row positions in
 // the cluster-major point array, so the re-rank reads those rows directly.
@@ -356,6 +356,8 @@ int grid_cap(int64_t work, int threads) {
 
 int lp_padded_dim(int dp) { return (dp + 31) / 32 * 32; }
 
+int lp_shortlist(int k) { return std::max(4 * k, 16); }
+
 bool lp_supported(int dp, int k) { return k >= 1 && 4 * k <= LP_KMAX && lp_padded_dim(dp) <= 256; }
 
 void lp_quantize(const float *src, int64_t rows, int dp, bool fp8, void *dst, float *scale,
@@ -378,7 +380,7 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
                   cudaStream_t s) {
     if (nq == 0) return;
     const int dpl = lp_padded_dim(dp);
-    const int Kp = 4 * k;
+    const int Kp = lp_shortlist(k);
     Scratch<unsigned char> Ql((size_t)nq * dpl * (fp8 ? 1 : 2), s);
     Scratch<float> qn2(nq, s), qsc(fp8 ? nq : 1, s);
     lp_quantize(Qp, nq, dp, fp8, Ql.get(), qsc.get(), qn2.get(), s);
