@@ -7,8 +7,9 @@
 // norm of each quantised row.  Queries are grouped by cluster as in the FP32
 // cluster-major scan; the distances of a group are
 //     ||x~||^2 + ||q~||^2 - 2 x~.q~    (x~, q~ the quantised vectors)
-// with x~.q~ from warp-level tensor-core MMAs (FP32 accumulation).  Every query
-// keeps a shortlist of its K' = max(4k, 16) nearest by these distances, which is then
+// with x~.q~ from warp-level tensor-core MMAs (FP32 accumulation).  Every
+// (query, cluster) pair keeps its k nearest by these distances; every query
+// keeps a shortlist of the K' = max(4k, 16) nearest of those, which is then
 // re-ranked with exact FP32 distances sum_t (x_t - q_t)^2 of the FP32 rows; the
 // k best of the shortlist are returned.  Shortlist keys carry row positions in
 // the cluster-major point array, so the re-rank reads those rows directly.
@@ -273,28 +274,50 @@ __global__ __launch_bounds__(LP_THREADS) void lp_scan_kernel(
     }
 }
 
-// Per query: the K' best approximate keys over its P kept clusters; the row
-// positions go to the shortlist (-1 where fewer exist).  One warp per query.
+// Per query: the Kp best approximate keys among the P x Kpair keys of its
+// (query, cluster) pairs; their row positions form the shortlist (-1 where
+// fewer exist).  One warp per query; the keys stay in registers when they fit.
 __global__ __launch_bounds__(256) void lp_shortlist_kernel(
-    const unsigned long long *__restrict__ pair_out, int64_t nq, int P, int K,
+    const unsigned long long *__restrict__ pair_out, int64_t nq, int P, int Kpair, int Kp,
     int32_t *__restrict__ shortlist) {
+    constexpr int REG = 32;  // keys per lane held in registers
     const int lane = threadIdx.x & 31;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (q >= nq) return;
-    const unsigned long long *src = pair_out + q * (int64_t)P * K;
-    const int total = P * K;
+    const unsigned long long *src = pair_out + q * (int64_t)P * Kpair;
+    const int total = P * Kpair;
+    if (total <= 32 * REG) {
+        unsigned long long v[REG];
+#pragma unroll
+        for (int i = 0; i < REG; ++i) v[i] = lane + 32 * i < total ? src[lane + 32 * i] : kNoKey;
+        for (int r = 0; r < Kp; ++r) {
+            unsigned long long mine = kNoKey;
+#pragma unroll
+            for (int i = 0; i < REG; ++i) mine = umin64(mine, v[i]);
+            const unsigned long long w = warp_min64(mine);
+            if (lane == 0) shortlist[q * Kp + r] = w == kNoKey ? -1 : (int32_t)(w & 0xffffffffu);
+            if (w == kNoKey) {
+                for (int rr = r + 1 + lane; rr < Kp; rr += 32) shortlist[q * Kp + rr] = -1;
+                return;
+            }
+#pragma unroll
+            for (int i = 0; i < REG; ++i)
+                if (v[i] == w) v[i] = kNoKey;
+        }
+        return;
+    }
     unsigned long long last = 0;
     bool first = true;
-    for (int r = 0; r < K; ++r) {
+    for (int r = 0; r < Kp; ++r) {
         unsigned long long mine = kNoKey;
         for (int i = lane; i < total; i += 32) {
             const unsigned long long v = src[i];
             if ((first || v > last) && v < mine) mine = v;
         }
         const unsigned long long w = warp_min64(mine);
-        if (lane == 0) shortlist[q * K + r] = w == kNoKey ? -1 : (int32_t)(w & 0xffffffffu);
+        if (lane == 0) shortlist[q * Kp + r] = w == kNoKey ? -1 : (int32_t)(w & 0xffffffffu);
         if (w == kNoKey) {
-            for (int rr = r + 1 + lane; rr < K; rr += 32) shortlist[q * K + rr] = -1;
+            for (int rr = r + 1 + lane; rr < Kp; rr += 32) shortlist[q * Kp + rr] = -1;
             break;
         }
         last = w;
@@ -381,38 +404,43 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
     if (nq == 0) return;
     const int dpl = lp_padded_dim(dp);
     const int Kp = lp_shortlist(k);
+    // every (query, cluster) pair keeps its k best by approximate distance; the
+    // shortlist is the Kp best of their union (a cluster's (k+1)-th candidate
+    // can only enter the shortlist if that cluster holds k better ones)
+    const int Kpair = k;
     Scratch<unsigned char> Ql((size_t)nq * dpl * (fp8 ? 1 : 2), s);
     Scratch<float> qn2(nq, s), qsc(fp8 ? nq : 1, s);
     lp_quantize(Qp, nq, dp, fp8, Ql.get(), qsc.get(), qn2.get(), s);
     Scratch<int32_t> pairs;
     Scratch<int64_t> poff, item_off;
     cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
-    Scratch<unsigned long long> pair_out((size_t)nq * P * Kp, s);
+    Scratch<unsigned long long> pair_out((size_t)nq * P * Kpair, s);
     Scratch<int32_t> shortlist((size_t)nq * Kp, s);
     {
         ProfRegion pr(fp8 ? "scan_leaf_fp8" : "scan_leaf_bf16", s, 0.0);
         const int rowb = dpl * (fp8 ? 1 : 2) + 16;
         const size_t smem = (size_t)(LP_R + LP_QB) * rowb + (size_t)LP_QB * LP_R * 4 +
-                            (size_t)LP_R * 12 + LP_QB * 8 + (size_t)LP_QB * Kp * 8 + 16;
+                            (size_t)LP_R * 12 + LP_QB * 8 + (size_t)LP_QB * Kpair * 8 + 16;
         if (fp8) {
             MASK_CUDA(cudaFuncSetAttribute(lp_scan_kernel<true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             lp_scan_kernel<true><<<152 * 4, LP_THREADS, smem, s>>>(
                 static_cast<const uint8_t *>(Xl), dpl, xn2, xscale, leaf_off, Ql.get(), qn2.get(),
-                qsc.get(), P, poff.get(), pairs.get(), item_off.get(), k0, Kp, pair_out.get());
+                qsc.get(), P, poff.get(), pairs.get(), item_off.get(), k0, Kpair, pair_out.get());
         } else {
             MASK_CUDA(cudaFuncSetAttribute(lp_scan_kernel<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             lp_scan_kernel<false><<<152 * 4, LP_THREADS, smem, s>>>(
                 static_cast<const uint8_t *>(Xl), dpl, xn2, nullptr, leaf_off, Ql.get(), qn2.get(),
-                nullptr, P, poff.get(), pairs.get(), item_off.get(), k0, Kp, pair_out.get());
+                nullptr, P, poff.get(), pairs.get(), item_off.get(), k0, Kpair, pair_out.get());
         }
         MASK_LAUNCHED("lp_scan");
     }
     {
         ProfRegion pr("leaf_rerank", s, 0.0);
         const unsigned blocks = (unsigned)((nq + 7) / 8);
-        lp_shortlist_kernel<<<blocks, 256, 0, s>>>(pair_out.get(), nq, P, Kp, shortlist.get());
+        lp_shortlist_kernel<<<blocks, 256, 0, s>>>(pair_out.get(), nq, P, Kpair, Kp,
+                                                   shortlist.get());
         MASK_LAUNCHED("lp_shortlist");
         lp_rerank_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4 *>(Xs), dp / 4, xids,
                                                 reinterpret_cast<const float4 *>(Qp),
