@@ -8,7 +8,7 @@
 // cluster-major scan; the distances of a group are
 //     ||x~||^2 + ||q~||^2 - 2 x~.q~    (x~, q~ the quantised vectors)
 // with x~.q~ from warp-level tensor-core MMAs (FP32 accumulation).  Every
-// (query, cluster) pair keeps its k nearest by these distances; every query
+// (query, cluster) pair keeps its max(k, 4) nearest by these distances; every query
 // keeps a shortlist of the K' = max(4k, 16) nearest of those, which is then
 // re-ranked with exact FP32 distances sum_t (x_t - q_t)^2 of the FP32 rows; the
 // k best of the shortlist are returned.  Shortlist keys carry row positions in
@@ -404,10 +404,10 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
     if (nq == 0) return;
     const int dpl = lp_padded_dim(dp);
     const int Kp = lp_shortlist(k);
-    // every (query, cluster) pair keeps its k best by approximate distance; the
-    // shortlist is the Kp best of their union (a cluster's (k+1)-th candidate
-    // can only enter the shortlist if that cluster holds k better ones)
-    const int Kpair = k;
+    // every (query, cluster) pair keeps its max(k, 4) best by approximate
+    // distance (a floor, so a near-tie inside one cluster cannot drop the
+    // nearest point at k = 1); the shortlist is the Kp best of their union
+    const int Kpair = std::min(Kp, std::max(k, 4));
     Scratch<unsigned char> Ql((size_t)nq * dpl * (fp8 ? 1 : 2), s);
     Scratch<float> qn2(nq, s), qsc(fp8 ? nq : 1, s);
     lp_quantize(Qp, nq, dp, fp8, Ql.get(), qsc.get(), qn2.get(), s);
