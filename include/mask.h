@@ -95,9 +95,18 @@ mask_status mask_build(const float *points, int64_t n, int32_t d,
 
 /*
  * As mask_build, for n sparse points in CSR form (the TF-IDF shape of §4.3):
- *   row_ptr [n+1] int64, col [nnz] int32 (each in [0, d)), val [nnz] float32.
- * Centroids are dense.  Returns MASK_EUNSUPPORTED if sparse support is not
- * built in.
+ *   row_ptr [n+1] int64, row_ptr[0] = 0 and nondecreasing; nnz = row_ptr[n];
+ *   col     [nnz] int32, each in [0, d) and strictly increasing within a row;
+ *   val     [nnz] float32.
+ * Centroids are dense ([k_l x d] float32).  Level 0 runs on the CSR rows:
+ * k-means++ and the mean update use ||x - c||^2 = sum_{t in x} (x_t - c_t)^2
+ * + (||c||^2 - sum_{t in x} c_t^2); the assignment is a CSR-times-dense
+ * product with the argmin fused (rows whose best two centroids are closer
+ * than the FP32 rounding bound are re-decided in FP64).  The levels above run
+ * on the level-0 centroids as dense rows, exactly as in mask_build.
+ * d <= 40960 (k-means++ and the leaf scan stage a dense row in shared
+ * memory), else MASK_EUNSUPPORTED; malformed CSR arrays give MASK_EINVAL.
+ * Query the index with mask_query_csr.  Synchronises `stream`.
  */
 mask_status mask_build_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
                            int64_t n, int32_t d, const int32_t *k_per_level,
@@ -126,7 +135,16 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
                        int32_t k, const int32_t *probes, mask_precision precision,
                        int64_t *ids_out, float *dists_out, mask_stream stream);
 
-/* As mask_query, for CSR queries (row_ptr [nq+1], col [nnz], val [nnz]). */
+/*
+ * As mask_query, for nq CSR queries (row_ptr [nq+1], col, val as for
+ * mask_build_csr) against an index built by mask_build_csr (a dense index
+ * gives MASK_EINVAL, as does mask_query on a CSR index).  Distances to a
+ * level's centroids: sum_{t in q} (q_t - c_t)^2 + (||c||^2 - sum_{t in q}
+ * c_t^2); to a leaf point: sum_{t in x} (x_t - q_t)^2 + (||q||^2 -
+ * sum_{t in x} q_t^2), so a point equal to the query is at distance 0.
+ * MASK_FP32 only, and at most 8192 nonzeros per query; otherwise
+ * MASK_EUNSUPPORTED.  Synchronises `stream`.
+ */
 mask_status mask_query_csr(const mask_index *index, const int64_t *row_ptr,
                            const int32_t *col, const float *val, int64_t nq, int32_t k,
                            const int32_t *probes, mask_precision precision,
@@ -200,6 +218,23 @@ mask_status mask_kmeans_assign(const float *X, int64_t n, int32_t d, const float
 mask_status mask_kmeans_update(const float *X, int64_t n, int32_t d, const int32_t *labels,
                                int32_t k, const float *C_prev, float *C_out,
                                int64_t *counts_out, mask_stream stream);
+
+/*
+ * CSR forms of the three steps above (rows as for mask_build_csr; centroids
+ * dense [k x d]).  mask_kmeanspp_csr needs d <= 40960.  dist_out of
+ * mask_kmeans_assign_csr is sum_{t in x} (x_t - c_t)^2 + (||c||^2 -
+ * sum_{t in x} c_t^2) in FP32 for the chosen centroid.
+ */
+mask_status mask_kmeanspp_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                              int64_t n, int32_t d, int32_t k, uint64_t seed, int32_t level,
+                              float *centroids_out, int64_t *chosen_out, mask_stream stream);
+mask_status mask_kmeans_assign_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                                   int64_t n, int32_t d, const float *C, int32_t k,
+                                   int32_t *labels_out, float *dist_out, mask_stream stream);
+mask_status mask_kmeans_update_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                                   int64_t n, int32_t d, const int32_t *labels, int32_t k,
+                                   const float *C_prev, float *C_out, int64_t *counts_out,
+                                   mask_stream stream);
 
 /*
  * Allocation-free variant of mask_kmeans_assign, for callers that cannot let

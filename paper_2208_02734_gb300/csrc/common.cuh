@@ -142,6 +142,10 @@ inline int lanes_per_row(int dp) {
 
 constexpr uint64_t kNoKey = ~0ull;
 
+// Largest dimension of CSR inputs: k-means++ and the leaf scan hold one dense
+// row of it in shared memory.
+constexpr int kCsrMaxDim = 40960;
+
 // ------------------------------------------------------ kernel launchers
 
 // kmeans.cu
@@ -155,6 +159,9 @@ void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
 // k-means++ over the m rows of Xs; chosen[0] must be set; fills chosen[1..k)
 void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_dev,
                     int64_t *chosen, cudaStream_t s);
+// the same over CSR rows (dense row of dp <= kCsrMaxDim in shared memory)
+void kmeanspp_steps_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t m,
+                        int dp, int k, const double *u_dev, int64_t *chosen, cudaStream_t s);
 // counting sort of labels in [0,k): off[k+1] (int64), perm[n] (item ids by label)
 void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *perm,
                 cudaStream_t s);
@@ -168,6 +175,57 @@ void label_dist(const float *X, int64_t n, int dp, const float *C, const int32_t
 void sum_reduce_f32_to_f64(const float *v, int64_t n, double *out, cudaStream_t s);
 void off_to_counts(const int64_t *off, int k, int64_t *counts, cudaStream_t s);
 void count_bad_labels(const int32_t *labels, int64_t n, int k, int *bad, cudaStream_t s);
+
+// sparse.cu -- CSR rows (row_ptr int64 [n+1], col int32, val float32)
+// bad[0] = malformed rows (row_ptr decreasing, columns not strictly
+// increasing), bad[1] = column ids outside [0, d), bad[2] = longest row;
+// bad must hold 3 ints
+void csr_validate(const int64_t *rp, const int32_t *col, int64_t n, int64_t nnz, int d, int *bad,
+                  cudaStream_t s);
+void csr_row_sqnorm(const int64_t *rp, const float *val, int64_t n, float *xn, cudaStream_t s);
+void inclusive_scan_i64(int64_t *v, int64_t n, cudaStream_t s);
+// rows idx[0..m) of a CSR matrix as a new CSR matrix (synchronises s)
+template <class I>
+void csr_gather_rows(const int64_t *rp, const int32_t *col, const float *val, const I *idx,
+                     int64_t m, DevArray<int64_t> &orp, DevArray<int32_t> &ocol,
+                     DevArray<float> &oval, cudaStream_t s);
+// out [m x dp] = dense copies of rows rows[i] (rows == null: rows 0..m)
+void csr_densify_rows(const int64_t *rp, const int32_t *col, const float *val,
+                      const int64_t *rows, int64_t m, int dp, float *out, cudaStream_t s);
+// cn [kp] = ||c_j||^2 (FP64 sum rounded; +inf for j >= k), cn64 [k] the FP64 values
+void centroid_norms(const float *C, int k, int dp, int kp, float *cn, double *cn64,
+                    cudaStream_t s);
+// labels = argmin_j ||x_i - c_j||^2 for CSR rows and dense C [k x dp] (ties to
+// the smallest j); cn_out (optional, [k]) receives ||c_j||^2
+void csr_assign(const int64_t *rp, const int32_t *col, const float *val, int64_t n,
+                int64_t nnz, const float *xn, const float *C, int k, int dp, int32_t *labels,
+                float *cn_out, cudaStream_t s);
+// dist[i] = ||x_i - c_{labels[i]}||^2 (cn = ||c_j||^2)
+void csr_label_dist(const int64_t *rp, const int32_t *col, const float *val, int64_t n,
+                    const float *C, int dp, const float *cn, const int32_t *labels, float *dist,
+                    cudaStream_t s);
+// C_new = per-cluster means of CSR rows (C_prev kept for empty clusters; C_new
+// may be null), sse[j] = sum over members of ||x_i - c_prev_j||^2 (cn_prev =
+// ||c_prev_j||^2)
+void csr_centroid_update(const int64_t *rp, const int32_t *col, const float *val,
+                         const int32_t *perm, const int64_t *off, int64_t n_rows, int k, int dp,
+                         const float *C_prev, const float *cn_prev, float *C_new, float *sse,
+                         cudaStream_t s);
+
+// query_csr.cu -- the descent for CSR queries over a CSR index
+// level scan: dense centroid rows R (norms rcn) against the query nonzeros
+// (at most qcap per query, staged in shared memory)
+size_t csr_level_scan_smem(int K, int P, int qcap);
+void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid,
+                    const int64_t *off, const int32_t *sel, int P, int64_t root_end,
+                    const int64_t *qrp, const int32_t *qcol, const float *qval, int qcap,
+                    int64_t nq, int K, int32_t *out32, cudaStream_t s);
+// leaf scan: CSR point rows (cluster-major) against the query as a dense row
+size_t csr_leaf_scan_smem(int K, int P, int dp);
+void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
+                   const int32_t *xids, const int64_t *off, const int32_t *sel, int P,
+                   const int64_t *qrp, const int32_t *qcol, const float *qval, int dp, int64_t nq,
+                   int K, int64_t *out64, float *out_d, cudaStream_t s);
 
 // assign.cu -- labels[i] = argmin_j ||x_i - c_j||^2 (ties to the smallest j)
 void assign_labels(const float *X, const float *xn, int64_t n, int dp, const float *C, int k,

@@ -188,13 +188,16 @@ constexpr int kKppRpt = kKppRows / kKppThreads;  // rows per thread
 constexpr int kKppSelMax = 2048; // block sums the selecting warp stages in shared memory
 
 // One k-means++ step (§3.2).  The step number t >= 1 is read from *t_dev.
-// Fold the centre picked at step t-1 into D^2 (FP32 difference form, one
-// thread per row), then the last block to finish draws centre t: the smallest
-// row whose inclusive prefix of D^2 exceeds u_t * sum(D^2) (all sums FP64);
-// if that sum is 0, the lowest-index row not chosen yet.  The last block then
-// advances *t_dev, so identical launches can be replayed step after step.
+// Fold the centre picked at step t-1 into D^2, then the last block to finish
+// draws centre t: the smallest row whose inclusive prefix of D^2 exceeds
+// u_t * sum(D^2) (all sums FP64); if that sum is 0, the lowest-index row not
+// chosen yet.  The last block then advances *t_dev, so identical launches can
+// be replayed step after step.  Three kernels fold D^2 (dense rows one per
+// thread with triangle-inequality pruning, wide dense rows one per warp, CSR
+// rows one per lane group); they share the draw.
+//
 // cc2[j] = ||c_{t-1} - c_j||^2 for the centres j < t-1 chosen so far (FP32
-// difference form): the distances the D^2 update prunes with.
+// difference form): the distances the narrow dense D^2 update prunes with.
 __global__ void kpp_centre_dist_kernel(const float *__restrict__ X, int64_t m, int dp,
                                        const int *__restrict__ t_dev,
                                        const int64_t *__restrict__ chosen,
@@ -222,75 +225,40 @@ __global__ void kpp_centre_dist_kernel(const float *__restrict__ X, int64_t m, i
     cc2[j] = acc;
 }
 
-__global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
-    const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
-    const double *__restrict__ u, float *__restrict__ D2, int32_t *__restrict__ asg,
-    const float *__restrict__ cc2, double *__restrict__ bsum, unsigned *__restrict__ counter,
-    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken) {
-    __shared__ double red[kKppThreads / 32];
-    __shared__ int s_last;
-    __shared__ double s_b[kKppSelMax];   // staged block sums (selecting warp)
-    __shared__ float s_r[kKppRows];      // staged D^2 of the selected block
+// Shared memory of the draw: staged block sums and the selected block's D^2.
+template <int ROWS>
+struct KppDrawSmem {
+    double s_b[kKppSelMax];
+    float s_r[ROWS];
+};
 
-    const int t = *t_dev;
-    const int tid = threadIdx.x;
-    const int dp4 = dp / 4;
-    int64_t c = chosen[t - 1];
-    if (c < 0 || c >= m) c = 0;  // never out of bounds (a valid pick is always in [0, m))
-    const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
-    const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
-
-    // D^2 update: thread owns rows r0 + tid + q * kKppThreads.  A row whose
-    // nearest centre a lies at least 2 sqrt(D^2) (with a 1e-3 margin for
-    // rounding) from the new centre cannot get closer to it (triangle
-    // inequality), so its distance is not evaluated: the result is the same
-    // as evaluating it and keeping min(D^2, distance).
-    double local = 0.0;
-#pragma unroll
-    for (int q = 0; q < kKppRpt; ++q) {
-        const int64_t i = r0 + tid + q * kKppThreads;
-        if (i >= m) continue;
-        float d2 = FLT_MAX;
-        int a = 0;
-        bool eval = true;
-        if (t > 1) {
-            d2 = D2[i];
-            a = asg[i];
-            eval = !(cc2[a] >= 4.004f * d2);
-        }
-        if (eval) {
-            const float4 *xr = reinterpret_cast<const float4 *>(X + i * dp);
-            float acc = 0.f;
-#pragma unroll 4
-            for (int ch = 0; ch < dp4; ++ch) {
-                const float4 xa = xr[ch], b = __ldg(crow + ch);
-                const float e0 = xa.x - b.x, e1 = xa.y - b.y, e2 = xa.z - b.z, e3 = xa.w - b.w;
-                acc = fmaf(e0, e0, acc);
-                acc = fmaf(e1, e1, acc);
-                acc = fmaf(e2, e2, acc);
-                acc = fmaf(e3, e3, acc);
-            }
-            if (acc < d2) {
-                d2 = acc;
-                a = t - 1;
-            }
-            D2[i] = d2;
-            asg[i] = a;
-        }
-        local += (double)d2;
-    }
+// Block total of the D^2 fold -> bsum[blockIdx.x]; true in the last block to
+// finish (which then draws).
+__device__ bool kpp_block_done(double local, double *red, double *__restrict__ bsum,
+                               unsigned *__restrict__ counter, int *s_last) {
     const double bs = block_sum_f64<kKppThreads>(local, red);
-    if (tid == 0) bsum[blockIdx.x] = bs;
+    if (threadIdx.x == 0) bsum[blockIdx.x] = bs;
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) *s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    const bool last = *s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
 
-    // ---------------- the last block draws centre t (warp 0 alone) ----------------
-    if (tid >= 32) return;
-    const int lane = tid;
+// The draw of centre t, by warp 0 of the last block (blocks of ROWS rows).
+template <int ROWS>
+__device__ void kpp_draw(int t, int64_t m, const double *__restrict__ u,
+                         const float *__restrict__ D2, const double *__restrict__ bsum,
+                         unsigned *__restrict__ counter, int *__restrict__ t_dev,
+                         int64_t *__restrict__ chosen, unsigned char *__restrict__ taken,
+                         KppDrawSmem<ROWS> &sm) {
+    static_assert(ROWS % 32 == 0, "rows per block must be a multiple of 32");
+    if (threadIdx.x >= 32) return;
+    double *s_b = sm.s_b;
+    float *s_r = sm.s_r;
+    const int lane = threadIdx.x;
     const int nb = gridDim.x;
     if (t == 1 && lane == 0) taken[chosen[0]] = 1;
     long long pick = -1;
@@ -298,7 +266,7 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
     long long fb = -1;
     double excl = 0.0;
     // pass over the block sums in chunks of kKppSelMax staged in shared memory
-    // (one chunk -- every launch that seeds <= 2M rows -- is loaded only once)
+    // (one chunk -- every launch of at most kKppSelMax blocks -- is loaded once)
     const bool staged = nb <= kKppSelMax;
     double carry = 0.0;
     for (int c0 = 0; c0 < nb; c0 += kKppSelMax) {
@@ -364,13 +332,13 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
             __syncwarp();
         }
         if (fb >= 0) {
-            // stage the block's rows, then lane l walks rows [l*32, l*32 + 32)
-            for (int q = lane; q < kKppRows; q += 32) {
-                const int64_t i = fb * kKppRows + q;
+            // stage the block's rows, then lane l walks rows [l*RPL, (l+1)*RPL)
+            for (int q = lane; q < ROWS; q += 32) {
+                const int64_t i = fb * ROWS + q;
                 s_r[q] = i < m ? __ldcg(D2 + i) : 0.f;
             }
             __syncwarp();
-            constexpr int RPL = kKppRows / 32;
+            constexpr int RPL = ROWS / 32;
             double rs = 0.0;
             for (int q = 0; q < RPL; ++q) rs += (double)s_r[lane * RPL + q];
             double rinc = rs;
@@ -390,7 +358,7 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
                     for (int q = 0; q < RPL; ++q) {
                         const double v = (double)s_r[lane * RPL + q];
                         if (v > 0.0) {
-                            p = fb * kKppRows + lane * RPL + q;
+                            p = fb * ROWS + lane * RPL + q;
                             if (run + v > target) break;
                         }
                         run += v;
@@ -403,7 +371,7 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
             // rounding left the target past the end: the last row with D^2 > 0
             for (long long b = nb - 1; b >= 0 && pick < 0; --b) {
                 if (!(__ldcg(bsum + b) > 0.0)) continue;
-                for (long long i = b * kKppRows + kKppRows - 1; i >= b * kKppRows; --i)
+                for (long long i = b * ROWS + ROWS - 1; i >= b * ROWS; --i)
                     if (i < m && __ldcg(D2 + i) > 0.f) { pick = i; break; }
             }
         }
@@ -421,6 +389,202 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
         *counter = 0u;
         *t_dev = t + 1;
     }
+}
+
+// Narrow dense rows: one thread per row, FP32 difference form.
+__global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
+    const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
+    const double *__restrict__ u, float *__restrict__ D2, int32_t *__restrict__ asg,
+    const float *__restrict__ cc2, double *__restrict__ bsum, unsigned *__restrict__ counter,
+    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken) {
+    __shared__ double red[kKppThreads / 32];
+    __shared__ int s_last;
+    __shared__ KppDrawSmem<kKppRows> sm;
+
+    const int t = *t_dev;
+    const int tid = threadIdx.x;
+    const int dp4 = dp / 4;
+    int64_t c = chosen[t - 1];
+    if (c < 0 || c >= m) c = 0;  // never out of bounds (a valid pick is always in [0, m))
+    const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
+    const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
+
+    // D^2 update: thread owns rows r0 + tid + q * kKppThreads.  A row whose
+    // nearest centre a lies at least 2 sqrt(D^2) (with a 1e-3 margin for
+    // rounding) from the new centre cannot get closer to it (triangle
+    // inequality), so its distance is not evaluated: the result is the same
+    // as evaluating it and keeping min(D^2, distance).
+    double local = 0.0;
+#pragma unroll
+    for (int q = 0; q < kKppRpt; ++q) {
+        const int64_t i = r0 + tid + q * kKppThreads;
+        if (i >= m) continue;
+        float d2 = FLT_MAX;
+        int a = 0;
+        bool eval = true;
+        if (t > 1) {
+            d2 = D2[i];
+            a = asg[i];
+            eval = !(cc2[a] >= 4.004f * d2);
+        }
+        if (eval) {
+            const float4 *xr = reinterpret_cast<const float4 *>(X + i * dp);
+            float acc = 0.f;
+#pragma unroll 4
+            for (int ch = 0; ch < dp4; ++ch) {
+                const float4 xa = xr[ch], b = __ldg(crow + ch);
+                const float e0 = xa.x - b.x, e1 = xa.y - b.y, e2 = xa.z - b.z, e3 = xa.w - b.w;
+                acc = fmaf(e0, e0, acc);
+                acc = fmaf(e1, e1, acc);
+                acc = fmaf(e2, e2, acc);
+                acc = fmaf(e3, e3, acc);
+            }
+            if (acc < d2) {
+                d2 = acc;
+                a = t - 1;
+            }
+            D2[i] = d2;
+            asg[i] = a;
+        }
+        local += (double)d2;
+    }
+    if (!kpp_block_done(local, red, bsum, counter, &s_last)) return;
+    kpp_draw<kKppRows>(t, m, u, D2, bsum, counter, t_dev, chosen, taken, sm);
+}
+
+// Wide dense rows (dp > kKppWideDim): one warp per row with coalesced float4
+// loads, kKppWideRows rows per block so a few thousand rows still fill the
+// GPU.  In many dimensions the pruning test above almost never holds, so it
+// is not used here.
+constexpr int kKppWideDim = 256;
+constexpr int kKppWideRows = 64;
+__global__ __launch_bounds__(kKppThreads) void kpp_step_wide_kernel(
+    const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
+    const double *__restrict__ u, float *__restrict__ D2, double *__restrict__ bsum,
+    unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
+    unsigned char *__restrict__ taken) {
+    __shared__ double red[kKppThreads / 32];
+    __shared__ int s_last;
+    __shared__ KppDrawSmem<kKppWideRows> sm;
+    constexpr int W = kKppThreads / 32;       // warps
+    constexpr int RPW = kKppWideRows / W;     // rows per warp, all in flight
+
+    const int t = *t_dev;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int dp4 = dp / 4;
+    int64_t c = chosen[t - 1];
+    if (c < 0 || c >= m) c = 0;
+    const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
+    const int64_t r0 = (int64_t)blockIdx.x * kKppWideRows + (int64_t)w * RPW;
+    float acc[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) acc[q] = 0.f;
+    for (int ch = lane; ch < dp4; ch += 32) {
+        const float4 b = __ldg(crow + ch);
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int64_t i = r0 + q;
+            if (i < m) {
+                const float4 xa = reinterpret_cast<const float4 *>(X + i * dp)[ch];
+                const float e0 = xa.x - b.x, e1 = xa.y - b.y, e2 = xa.z - b.z, e3 = xa.w - b.w;
+                acc[q] = fmaf(e0, e0, acc[q]);
+                acc[q] = fmaf(e1, e1, acc[q]);
+                acc[q] = fmaf(e2, e2, acc[q]);
+                acc[q] = fmaf(e3, e3, acc[q]);
+            }
+        }
+    }
+    double local = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        float v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        const int64_t i = r0 + q;
+        if (lane == 0 && i < m) {
+            const float d2 = t > 1 ? fminf(D2[i], v) : v;
+            D2[i] = d2;
+            local += (double)d2;
+        }
+    }
+    if (!kpp_block_done(local, red, bsum, counter, &s_last)) return;
+    kpp_draw<kKppWideRows>(t, m, u, D2, bsum, counter, t_dev, chosen, taken, sm);
+}
+
+// CSR rows (§4.3 TF-IDF shape): the new centre (a CSR row) is scattered into a
+// dense row in shared memory, and kKppGroup lanes take each row's nonzeros.
+// With A = sum_{t in x} (x_t - c_t)^2 and B = sum_{t in x} c_t^2,
+//   ||x - c||^2 = A + (||c||^2 - B),
+// where ||c||^2 is summed by the same lane-group procedure over the centre's
+// own nonzeros, so a row equal to the centre gets exactly 0.
+constexpr int kKppGroup = 8;
+__device__ __forceinline__ void csr_row_ab(const int64_t b, const int64_t e,
+                                           const int32_t *__restrict__ col,
+                                           const float *__restrict__ val, const float *cden,
+                                           int gl, float &A, float &B) {
+    A = 0.f;
+    B = 0.f;
+    for (int64_t j = b + gl; j < e; j += kKppGroup) {
+        const float cv = cden[__ldg(col + j)];
+        const float e0 = __ldg(val + j) - cv;
+        A = fmaf(e0, e0, A);
+        B = fmaf(cv, cv, B);
+    }
+#pragma unroll
+    for (int o = kKppGroup / 2; o > 0; o >>= 1) {
+        A += __shfl_xor_sync(kFull, A, o, kKppGroup);
+        B += __shfl_xor_sync(kFull, B, o, kKppGroup);
+    }
+}
+
+__global__ __launch_bounds__(kKppThreads, 2) void kpp_step_csr_kernel(
+    const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+    const float *__restrict__ val, int64_t m, int dp, int *__restrict__ t_dev,
+    const double *__restrict__ u, float *__restrict__ D2, double *__restrict__ bsum,
+    unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
+    unsigned char *__restrict__ taken) {
+    extern __shared__ __align__(16) float cden[];  // [dp] the new centre, dense
+    __shared__ double red[kKppThreads / 32];
+    __shared__ int s_last;
+    __shared__ float s_cn;
+    __shared__ KppDrawSmem<kKppRows> sm;
+    constexpr int G = kKppThreads / kKppGroup;  // lane groups (rows in flight per block)
+
+    const int t = *t_dev;
+    const int tid = threadIdx.x;
+    const int g = tid / kKppGroup, gl = tid % kKppGroup;
+    int64_t c = chosen[t - 1];
+    if (c < 0 || c >= m) c = 0;
+    const int64_t cb = rp[c], ce = rp[c + 1];
+    for (int i = tid; i < dp; i += kKppThreads) cden[i] = 0.f;
+    __syncthreads();
+    for (int64_t j = cb + tid; j < ce; j += kKppThreads) cden[col[j]] = val[j];
+    __syncthreads();
+    if (tid < 32) {
+        // ||c||^2 by the row procedure: sum_{t in c} c_t^2 is B of the centre
+        // itself (every group of warp 0 computes it; the shuffles need the warp)
+        float A, B;
+        csr_row_ab(cb, ce, col, val, cden, gl, A, B);
+        if (tid == 0) s_cn = B;
+    }
+    __syncthreads();
+    const float cn = s_cn;
+    const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
+    double local = 0.0;
+#pragma unroll 2
+    for (int q = 0; q < kKppRows / G; ++q) {
+        const int64_t i = r0 + g + (int64_t)q * G;
+        const bool ok = i < m;  // every lane reaches the shuffles; a row past the end is empty
+        float A, B;
+        csr_row_ab(ok ? rp[i] : 0, ok ? rp[i + 1] : 0, col, val, cden, gl, A, B);
+        if (ok && gl == 0) {
+            const float v = A + fmaxf(cn - B, 0.f);
+            const float d2 = t > 1 ? fminf(D2[i], v) : v;
+            D2[i] = d2;
+            local += (double)d2;
+        }
+    }
+    if (!kpp_block_done(local, red, bsum, counter, &s_last)) return;
+    kpp_draw<kKppRows>(t, m, u, D2, bsum, counter, t_dev, chosen, taken, sm);
 }
 
 // ------------------------------------------------------------ label sort
@@ -691,32 +855,11 @@ void sum_reduce_f32_to_f64(const float *v, int64_t n, double *out, cudaStream_t 
     MASK_LAUNCHED("sum_reduce");
 }
 
-void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_dev,
-                    int64_t *chosen, cudaStream_t s) {
-    if (k <= 1) return;
-    ProfRegion pr("kmeanspp", s, (double)(k - 1) * (double)m * dp * 4.0);
-    const int nb = (int)((m + kKppRows - 1) / kKppRows);
-    Scratch<float> D2(m, s), cc2(k, s);
-    Scratch<int32_t> asg(m, s);
-    Scratch<double> bsum(nb, s);
-    Scratch<unsigned> counter(1, s);
-    Scratch<int> t_dev(1, s);
-    Scratch<unsigned char> taken(m, s);
-    const int one = 1;
-    MASK_CUDA(cudaMemsetAsync(counter.get(), 0, sizeof(unsigned), s));
-    MASK_CUDA(cudaMemsetAsync(taken.get(), 0, m, s));
-    MASK_CUDA(cudaMemcpyAsync(t_dev.get(), &one, sizeof(int), cudaMemcpyHostToDevice, s));
-    const int ccb = (k + 255) / 256;
-    auto launch = [&](cudaStream_t st) {
-        kpp_centre_dist_kernel<<<ccb, 256, 0, st>>>(Xs, m, dp, t_dev.get(), chosen, cc2.get());
-        kpp_step_kernel<<<nb, kKppThreads, 0, st>>>(Xs, m, dp, t_dev.get(), u_dev, D2.get(),
-                                                    asg.get(), cc2.get(), bsum.get(),
-                                                    counter.get(), chosen, taken.get());
-    };
-    // The steps are identical launches (the step number lives on the device),
-    // so a captured graph of kBatch steps is replayed; the rest run directly.
+// Run `steps` identical k-means++ step launches (the step number lives on the
+// device): a captured graph of kBatch steps is replayed, the rest run directly.
+template <class F>
+void replay_steps(int steps, int kernels_per_step, F &&launch, cudaStream_t s) {
     constexpr int kBatch = 64;
-    const int steps = k - 1;
     int done = 0;
     if (steps >= 2 * kBatch) {
         cudaStream_t cs;
@@ -725,14 +868,14 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
         cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int i = 0; i < kBatch; ++i) launch(cs);  // two kernels per step
+            for (int i = 0; i < kBatch; ++i) launch(cs);
             e = cudaStreamEndCapture(cs, &graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess) {
             for (; done + kBatch <= steps && e == cudaSuccess; done += kBatch) {
                 e = cudaGraphLaunch(exec, s);
-                for (int i = 0; i < 2 * kBatch; ++i) count_launch();
+                for (int i = 0; i < kernels_per_step * kBatch; ++i) count_launch();
             }
         }
         if (exec) cudaGraphExecDestroy(exec);
@@ -742,9 +885,70 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
     }
     for (; done < steps; ++done) {
         launch(s);
-        count_launch();
+        for (int i = 0; i < kernels_per_step; ++i) count_launch();
         MASK_LAUNCHED("kpp_step");
     }
+}
+
+struct KppState {
+    Scratch<float> D2;
+    Scratch<double> bsum;
+    Scratch<unsigned> counter;
+    Scratch<int> t_dev;
+    Scratch<unsigned char> taken;
+    KppState(int64_t m, int nb, cudaStream_t s)
+        : D2(m, s), bsum(nb, s), counter(1, s), t_dev(1, s), taken(m, s) {
+        const int one = 1;
+        MASK_CUDA(cudaMemsetAsync(counter.get(), 0, sizeof(unsigned), s));
+        MASK_CUDA(cudaMemsetAsync(taken.get(), 0, m, s));
+        MASK_CUDA(cudaMemcpyAsync(t_dev.get(), &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+};
+
+void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_dev,
+                    int64_t *chosen, cudaStream_t s) {
+    if (k <= 1) return;
+    ProfRegion pr("kmeanspp", s, (double)(k - 1) * (double)m * dp * 4.0);
+    if (dp > kKppWideDim) {
+        const int nb = (int)((m + kKppWideRows - 1) / kKppWideRows);
+        KppState st(m, nb, s);
+        replay_steps(k - 1, 1, [&](cudaStream_t cs) {
+            kpp_step_wide_kernel<<<nb, kKppThreads, 0, cs>>>(Xs, m, dp, st.t_dev.get(), u_dev,
+                                                             st.D2.get(), st.bsum.get(),
+                                                             st.counter.get(), chosen,
+                                                             st.taken.get());
+        }, s);
+        return;
+    }
+    const int nb = (int)((m + kKppRows - 1) / kKppRows);
+    KppState st(m, nb, s);
+    Scratch<float> cc2(k, s);
+    Scratch<int32_t> asg(m, s);
+    const int ccb = (k + 255) / 256;
+    replay_steps(k - 1, 2, [&](cudaStream_t cs) {
+        kpp_centre_dist_kernel<<<ccb, 256, 0, cs>>>(Xs, m, dp, st.t_dev.get(), chosen, cc2.get());
+        kpp_step_kernel<<<nb, kKppThreads, 0, cs>>>(Xs, m, dp, st.t_dev.get(), u_dev, st.D2.get(),
+                                                    asg.get(), cc2.get(), st.bsum.get(),
+                                                    st.counter.get(), chosen, st.taken.get());
+    }, s);
+}
+
+void kmeanspp_steps_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t m,
+                        int dp, int k, const double *u_dev, int64_t *chosen, cudaStream_t s) {
+    if (k <= 1) return;
+    const size_t smem = (size_t)dp * sizeof(float);
+    MASK_REQUIRE(smem <= (size_t)kCsrMaxDim * sizeof(float), "CSR dimension too large");
+    ProfRegion pr("kmeanspp", s, 0.0);
+    MASK_CUDA(cudaFuncSetAttribute(kpp_step_csr_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nb = (int)((m + kKppRows - 1) / kKppRows);
+    KppState st(m, nb, s);
+    replay_steps(k - 1, 1, [&](cudaStream_t cs) {
+        kpp_step_csr_kernel<<<nb, kKppThreads, smem, cs>>>(rp, col, val, m, dp, st.t_dev.get(),
+                                                           u_dev, st.D2.get(), st.bsum.get(),
+                                                           st.counter.get(), chosen,
+                                                           st.taken.get());
+    }, s);
 }
 
 void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *perm,

@@ -22,7 +22,11 @@ struct mask_index {
     int d = 0, dp = 0, L = 0, iters = 0;
     bool sparse = false;
     mask::DevArray<float> Xs;        // [n x dp] points, cluster-major (level-0 parent-major)
-    mask::DevArray<int32_t> xids;    // [n] original id of each row of Xs
+    mask::DevArray<int32_t> xids;    // [n] original id of each row of Xs (or of xrp)
+    // CSR index: the points' rows cluster-major (row i is point xids[i])
+    mask::DevArray<int64_t> xrp;     // [n+1]
+    mask::DevArray<int32_t> xcol;    // [nnz]
+    mask::DevArray<float> xval;      // [nnz]
     struct Level {
         int k = 0;
         mask::DevArray<float> C;       // [k x dp] centroids in k-means cluster order
@@ -31,6 +35,7 @@ struct mask_index {
         mask::DevArray<int64_t> off;   // [k+1] children of centroid j: rows off[j]..off[j+1]
                                        //       of the level below's parent-major array
         mask::DevArray<int32_t> labels;// [n_below] centroid of every item one level below
+        mask::DevArray<float> cns;     // [k] ||row of Cs||^2 (CSR index: level-scan norms)
         std::vector<int64_t> chosen;   // k-means++ picks (indices into the level's inputs)
         std::vector<double> objective; // k-means objective after each assignment
     };
@@ -170,6 +175,33 @@ int64_t seed_sample_size(int64_t n, int k) {
     return n;
 }
 
+// The partial Fisher-Yates draws of a seeding subsample of m of n inputs.
+std::vector<int64_t> draw_subsample(SplitMix64 &rng, int64_t n, int64_t m) {
+    std::vector<int64_t> idx((size_t)n);
+    for (int64_t i = 0; i < n; ++i) idx[(size_t)i] = i;
+    for (int64_t j = 0; j < m; ++j) {
+        int64_t r = j + (int64_t)std::floor(rng.uniform() * (double)(n - j));
+        if (r > n - 1) r = n - 1;
+        std::swap(idx[(size_t)j], idx[(size_t)r]);
+    }
+    idx.resize((size_t)m);
+    return idx;
+}
+
+// One draw per centre, on the device: ud [k] and chosen[0] = floor(u_0 m).
+void draw_centres(SplitMix64 &rng, int64_t m, int k, Scratch<double> &ud, Scratch<int64_t> &ch,
+                  cudaStream_t s) {
+    std::vector<double> u((size_t)k);
+    for (int t = 0; t < k; ++t) u[(size_t)t] = rng.uniform();
+    int64_t first = (int64_t)std::floor(u[0] * (double)m);
+    if (first > m - 1) first = m - 1;
+    ud.alloc(k, s);
+    ch.alloc(k, s);
+    MASK_CUDA(cudaMemcpyAsync(ud.get(), u.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    MASK_CUDA(cudaMemcpyAsync(ch.get(), &first, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MASK_CUDA(cudaStreamSynchronize(s));  // u and first are host temporaries
+}
+
 // k-means++ for one level: C_out [k x dp] = the chosen rows of X; `chosen`
 // receives their indices into X.  Random draws on the host (R1): first the
 // partial Fisher-Yates draws of the subsample (if any), then one per centre.
@@ -181,14 +213,7 @@ void seed_level(const float *X, int64_t n, int dp, int k, uint64_t seed, int lv,
     Scratch<float> Xsub;
     const float *S = X;
     if (m < n) {
-        std::vector<int64_t> idx((size_t)n);
-        for (int64_t i = 0; i < n; ++i) idx[(size_t)i] = i;
-        for (int64_t j = 0; j < m; ++j) {
-            int64_t r = j + (int64_t)std::floor(rng.uniform() * (double)(n - j));
-            if (r > n - 1) r = n - 1;
-            std::swap(idx[(size_t)j], idx[(size_t)r]);
-        }
-        sample.assign(idx.begin(), idx.begin() + m);
+        sample = draw_subsample(rng, n, m);
         Scratch<int64_t> sidx(m, s);
         MASK_CUDA(cudaMemcpyAsync(sidx.get(), sample.data(), m * sizeof(int64_t),
                                   cudaMemcpyHostToDevice, s));
@@ -197,16 +222,44 @@ void seed_level(const float *X, int64_t n, int dp, int k, uint64_t seed, int lv,
         S = Xsub.get();
         MASK_CUDA(cudaStreamSynchronize(s));  // sidx and sample are released below
     }
-    std::vector<double> u((size_t)k);
-    for (int t = 0; t < k; ++t) u[(size_t)t] = rng.uniform();
-    int64_t first = (int64_t)std::floor(u[0] * (double)m);
-    if (first > m - 1) first = m - 1;
-    Scratch<double> ud(k, s);
-    Scratch<int64_t> ch(k, s);
-    MASK_CUDA(cudaMemcpyAsync(ud.get(), u.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
-    MASK_CUDA(cudaMemcpyAsync(ch.get(), &first, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    Scratch<double> ud;
+    Scratch<int64_t> ch;
+    draw_centres(rng, m, k, ud, ch, s);
     kmeanspp_steps(S, m, dp, k, ud.get(), ch.get(), s);
     gather_rows<int64_t>(S, dp, ch.get(), k, C_out, s);
+    to_host(chosen, ch.get(), (size_t)k, s);
+    if (m < n)
+        for (auto &c : chosen) c = sample[(size_t)c];
+}
+
+// The same for CSR rows; C_out receives dense copies of the chosen rows.
+void seed_level_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t n, int dp,
+                    int k, uint64_t seed, int lv, float *C_out, std::vector<int64_t> &chosen,
+                    cudaStream_t s) {
+    SplitMix64 rng{level_state(seed, lv)};
+    const int64_t m = seed_sample_size(n, k);
+    std::vector<int64_t> sample;
+    DevArray<int64_t> srp;
+    DevArray<int32_t> scol;
+    DevArray<float> sval;
+    const int64_t *Rp = rp;
+    const int32_t *Cl = col;
+    const float *Vl = val;
+    if (m < n) {
+        sample = draw_subsample(rng, n, m);
+        Scratch<int64_t> sidx(m, s);
+        MASK_CUDA(cudaMemcpyAsync(sidx.get(), sample.data(), m * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, s));
+        csr_gather_rows<int64_t>(rp, col, val, sidx.get(), m, srp, scol, sval, s);
+        Rp = srp.get();
+        Cl = scol.get();
+        Vl = sval.get();
+    }
+    Scratch<double> ud;
+    Scratch<int64_t> ch;
+    draw_centres(rng, m, k, ud, ch, s);
+    kmeanspp_steps_csr(Rp, Cl, Vl, m, dp, k, ud.get(), ch.get(), s);
+    csr_densify_rows(Rp, Cl, Vl, ch.get(), k, dp, C_out, s);
     to_host(chosen, ch.get(), (size_t)k, s);
     if (m < n)
         for (auto &c : chosen) c = sample[(size_t)c];
@@ -247,16 +300,39 @@ void lloyd(const float *X, int64_t n_in, int dp, int k, int iters, float *C, int
     to_host(objective, J.get(), (size_t)iters + 1, s);
 }
 
+// Lloyd iterations on CSR rows (dense centroids C [k x dp], updated in place);
+// the same outputs as lloyd().
+void lloyd_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t n, int64_t nnz,
+               int dp, int k, int iters, float *C, int32_t *labels, int64_t *off, int32_t *perm,
+               std::vector<double> &objective, cudaStream_t s) {
+    Scratch<float> xn(n, s), Cn((size_t)k * dp, s), sse(k, s), cn(k, s);
+    Scratch<double> J(iters + 1, s);
+    csr_row_sqnorm(rp, val, n, xn.get(), s);
+    float *cur = C, *nxt = Cn.get();
+    for (int it = 0; it < iters; ++it) {
+        csr_assign(rp, col, val, n, nnz, xn.get(), cur, k, dp, labels, cn.get(), s);
+        label_sort(labels, n, k, off, perm, s);
+        csr_centroid_update(rp, col, val, perm, off, n, k, dp, cur, cn.get(), nxt, sse.get(), s);
+        sum_reduce_f32_to_f64(sse.get(), k, J.get() + it, s);
+        std::swap(cur, nxt);
+    }
+    csr_assign(rp, col, val, n, nnz, xn.get(), cur, k, dp, labels, cn.get(), s);
+    label_sort(labels, n, k, off, perm, s);
+    csr_centroid_update(rp, col, val, perm, off, n, k, dp, cur, cn.get(), nullptr, sse.get(), s);
+    sum_reduce_f32_to_f64(sse.get(), k, J.get() + iters, s);
+    if (cur != C)
+        MASK_CUDA(cudaMemcpyAsync(C, cur, sizeof(float) * k * dp, cudaMemcpyDeviceToDevice, s));
+    to_host(objective, J.get(), (size_t)iters + 1, s);
+}
+
 // ------------------------------------------------------------ index layout
 
 // Given every level's centroids C, labels and membership lists (level lv's
 // off, and the perm of its items, stored as the ids of the level below),
 // lay out the parent-major arrays: points cluster-major (Xs), and each
 // non-top level's centroids in the order of their parents (Cs).
-void finish_layout(mask_index &idx, const float *Xp, cudaStream_t s) {
+void finish_levels(mask_index &idx, cudaStream_t s) {
     const int dp = idx.dp;
-    idx.Xs.alloc((size_t)idx.n * dp);
-    gather_rows<int32_t>(Xp, dp, idx.xids.get(), idx.n, idx.Xs.get(), s);
     for (int lv = 0; lv < idx.L; ++lv) {
         auto &L = idx.lv[(size_t)lv];
         L.Cs.alloc((size_t)L.k * dp);
@@ -268,8 +344,27 @@ void finish_layout(mask_index &idx, const float *Xp, cudaStream_t s) {
         } else {
             gather_rows<int32_t>(L.C.get(), dp, L.ids.get(), L.k, L.Cs.get(), s);
         }
+        if (idx.sparse) {
+            L.cns.alloc((size_t)L.k);
+            Scratch<double> n64(L.k, s);
+            centroid_norms(L.Cs.get(), L.k, dp, L.k, L.cns.get(), n64.get(), s);
+            MASK_CUDA(cudaStreamSynchronize(s));
+        }
     }
     MASK_CUDA(cudaStreamSynchronize(s));
+}
+
+void finish_layout(mask_index &idx, const float *Xp, cudaStream_t s) {
+    idx.Xs.alloc((size_t)idx.n * idx.dp);
+    gather_rows<int32_t>(Xp, idx.dp, idx.xids.get(), idx.n, idx.Xs.get(), s);
+    finish_levels(idx, s);
+}
+
+// CSR index: the points' rows cluster-major (row i = point xids[i]).
+void finish_layout_csr(mask_index &idx, const int64_t *rp, const int32_t *col, const float *val,
+                       cudaStream_t s) {
+    csr_gather_rows<int32_t>(rp, col, val, idx.xids.get(), idx.n, idx.xrp, idx.xcol, idx.xval, s);
+    finish_levels(idx, s);
 }
 
 void check_common(int64_t n, int d, const int32_t *k_per_level, int n_levels, mask_index **out) {
@@ -310,10 +405,10 @@ int32_t *below_ids(mask_index &idx, int lv, int64_t n_in) {
     return B.ids.get();
 }
 
-void build_dense(mask_index &idx, const float *Xp, uint64_t seed, cudaStream_t s) {
-    const float *in = Xp;
-    int64_t n_in = idx.n;
-    for (int lv = 0; lv < idx.L; ++lv) {
+// Levels lv0.. of the build on the n_in dense rows `in` (level lv0's items).
+void build_dense_levels(mask_index &idx, int lv0, const float *in, int64_t n_in, uint64_t seed,
+                        cudaStream_t s) {
+    for (int lv = lv0; lv < idx.L; ++lv) {
         auto &L = idx.lv[(size_t)lv];
         L.C.alloc((size_t)L.k * idx.dp);
         L.labels.alloc((size_t)n_in);
@@ -325,8 +420,74 @@ void build_dense(mask_index &idx, const float *Xp, uint64_t seed, cudaStream_t s
         in = L.C.get();
         n_in = L.k;
     }
+}
+
+void build_dense(mask_index &idx, const float *Xp, uint64_t seed, cudaStream_t s) {
+    build_dense_levels(idx, 0, Xp, idx.n, seed, s);
     finish_layout(idx, Xp, s);
 }
+
+// CSR points: level 0 on the sparse rows (dense centroids), the levels above
+// on those centroids as dense rows.
+void build_csr(mask_index &idx, const int64_t *rp, const int32_t *col, const float *val,
+               int64_t nnz, uint64_t seed, cudaStream_t s) {
+    auto &L = idx.lv[0];
+    const int64_t n = idx.n;
+    L.C.alloc((size_t)L.k * idx.dp);
+    L.labels.alloc((size_t)n);
+    L.off.alloc((size_t)L.k + 1);
+    int32_t *perm = below_ids(idx, 0, n);
+    seed_level_csr(rp, col, val, n, idx.dp, L.k, seed, 0, L.C.get(), L.chosen, s);
+    lloyd_csr(rp, col, val, n, nnz, idx.dp, L.k, idx.iters, L.C.get(), L.labels.get(),
+              L.off.get(), perm, L.objective, s);
+    build_dense_levels(idx, 1, L.C.get(), L.k, seed, s);
+    finish_layout_csr(idx, rp, col, val, s);
+}
+
+// A value of a caller array that may live on the host or the device.
+template <class T>
+T read_value(const T *p, cudaStream_t s) {
+    T v{};
+    if (on_device(p)) {
+        MASK_CUDA(cudaMemcpyAsync(&v, p, sizeof(T), cudaMemcpyDeviceToHost, s));
+        MASK_CUDA(cudaStreamSynchronize(s));
+    } else {
+        v = *p;
+    }
+    return v;
+}
+
+// Stages and checks caller CSR arrays of `rows` rows over d columns; returns
+// the nonzero count and (optionally) the longest row.
+struct CsrIn {
+    int64_t nnz = 0;
+    int longest = 0;
+    std::unique_ptr<In<int64_t>> rp;
+    std::unique_ptr<In<int32_t>> col;
+    std::unique_ptr<In<float>> val;
+    CsrIn(const int64_t *row_ptr, const int32_t *c, const float *v, int64_t rows, int d,
+          cudaStream_t s) {
+        MASK_REQUIRE(row_ptr != nullptr, "row_ptr is NULL");
+        const int64_t r0 = read_value(row_ptr, s), rn = read_value(row_ptr + rows, s);
+        MASK_REQUIRE(r0 == 0, "row_ptr[0] must be 0");
+        MASK_REQUIRE(rn >= 0, "row_ptr[rows] must be >= 0");
+        nnz = rn;
+        MASK_REQUIRE(nnz == 0 || (c != nullptr && v != nullptr), "col or val is NULL");
+        rp = std::make_unique<In<int64_t>>(row_ptr, (size_t)rows + 1, s);
+        col = std::make_unique<In<int32_t>>(c, (size_t)nnz, s);
+        val = std::make_unique<In<float>>(v, (size_t)nnz, s);
+        Scratch<int> bad(3, s);
+        csr_validate(rp->p, col->p, rows, nnz, d, bad.get(), s);
+        int h[3] = {0, 0, 0};
+        MASK_CUDA(cudaMemcpyAsync(h, bad.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+        MASK_CUDA(cudaStreamSynchronize(s));
+        MASK_REQUIRE(h[0] == 0, std::to_string(h[0]) +
+                                    " CSR rows malformed (row_ptr decreasing or column ids not "
+                                    "strictly increasing within a row)");
+        MASK_REQUIRE(h[1] == 0, std::to_string(h[1]) + " CSR column ids outside [0, d)");
+        longest = h[2];
+    }
+};
 
 }  // namespace
 }  // namespace mask
@@ -358,11 +519,23 @@ mask_status mask_build(const float *points, int64_t n, int32_t d, const int32_t 
     });
 }
 
-mask_status mask_build_csr(const int64_t *, const int32_t *, const float *, int64_t, int32_t,
-                           const int32_t *, int32_t, int32_t, uint64_t, mask_stream,
-                           mask_index **) {
-    g_err = "sparse inputs are not built in this version";
-    return MASK_EUNSUPPORTED;
+mask_status mask_build_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                           int64_t n, int32_t d, const int32_t *k_per_level, int32_t n_levels,
+                           int32_t iters, uint64_t seed, mask_stream stream, mask_index **out) {
+    return guard([&] {
+        check_common(n, d, k_per_level, n_levels, out);
+        MASK_REQUIRE(iters >= 0, "iters must be >= 0");
+        if (d > kCsrMaxDim)
+            fail(MASK_EUNSUPPORTED, "CSR inputs need d <= " + std::to_string(kCsrMaxDim));
+        cudaStream_t s = (cudaStream_t)stream;
+        CsrIn in(row_ptr, col, val, n, d, s);
+        auto idx = new_index(n, d, k_per_level, n_levels);
+        idx->iters = iters;
+        idx->sparse = true;
+        build_csr(*idx, in.rp->p, in.col->p, in.val->p, in.nnz, seed, s);
+        MASK_CUDA(cudaStreamSynchronize(s));
+        *out = idx.release();
+    });
 }
 
 mask_status mask_index_load(const float *points, int64_t n, int32_t d, int32_t n_levels,
@@ -421,14 +594,15 @@ mask_status mask_index_get_info(const mask_index *index, mask_index_info *out) {
         out->n_levels = index->L;
         out->iters = index->iters;
         out->sparse = index->sparse ? 1 : 0;
-        int64_t bytes = (int64_t)(index->Xs.bytes() + index->xids.bytes());
+        int64_t bytes = (int64_t)(index->Xs.bytes() + index->xids.bytes() + index->xrp.bytes() +
+                                  index->xcol.bytes() + index->xval.bytes());
         for (int q = 0; q < 2; ++q) bytes += (int64_t)(index->Xlp[q].bytes() + index->xn_lp[q].bytes());
         bytes += (int64_t)index->xscale_fp8.bytes();
         for (int l = 0; l < index->L; ++l) {
             const auto &L = index->lv[(size_t)l];
             out->k_per_level[l] = L.k;
             bytes += (int64_t)(L.C.bytes() + L.Cs.bytes() + L.ids.bytes() + L.off.bytes() +
-                               L.labels.bytes());
+                               L.labels.bytes() + L.cns.bytes());
         }
         out->device_bytes = bytes;
     });
@@ -469,6 +643,7 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
         MASK_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
         MASK_REQUIRE(probes != nullptr, "probes is NULL");
         MASK_REQUIRE(current_device() == index->device, "index lives on another device");
+        MASK_REQUIRE(!index->sparse, "index built from CSR points: query it with mask_query_csr");
         MASK_REQUIRE(precision == MASK_FP32 || precision == MASK_BF16 ||
                          precision == MASK_FP8E4M3, "unknown precision");
         const bool lowp = precision != MASK_FP32;
@@ -568,11 +743,57 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
     });
 }
 
-mask_status mask_query_csr(const mask_index *, const int64_t *, const int32_t *, const float *,
-                           int64_t, int32_t, const int32_t *, mask_precision, int64_t *, float *,
-                           mask_stream) {
-    g_err = "sparse queries are not built in this version";
-    return MASK_EUNSUPPORTED;
+mask_status mask_query_csr(const mask_index *index, const int64_t *row_ptr, const int32_t *col,
+                           const float *val, int64_t nq, int32_t k, const int32_t *probes,
+                           mask_precision precision, int64_t *ids_out, float *dists_out,
+                           mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(index != nullptr, "index is NULL");
+        MASK_REQUIRE(nq >= 0, "nq must be >= 0");
+        MASK_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+        MASK_REQUIRE(probes != nullptr, "probes is NULL");
+        MASK_REQUIRE(current_device() == index->device, "index lives on another device");
+        MASK_REQUIRE(index->sparse, "index built from dense points: query it with mask_query");
+        MASK_REQUIRE(precision == MASK_FP32 || precision == MASK_BF16 ||
+                         precision == MASK_FP8E4M3, "unknown precision");
+        if (precision != MASK_FP32) fail(MASK_EUNSUPPORTED, "CSR queries run in FP32 only");
+        if (nq == 0) return;
+        MASK_REQUIRE(ids_out != nullptr, "ids_out is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int L = index->L, dp = index->dp;
+        std::vector<int> p((size_t)L);
+        for (int l = 0; l < L; ++l) {
+            MASK_REQUIRE(probes[l] >= 1, "probes must be >= 1");
+            p[(size_t)l] = std::min<int>(probes[l], index->lv[(size_t)l].k);
+        }
+        CsrIn in(row_ptr, col, val, nq, index->d, s);
+        constexpr int kQueryNnzMax = 8192;
+        if (in.longest > kQueryNnzMax)
+            fail(MASK_EUNSUPPORTED, "a CSR query has more than " + std::to_string(kQueryNnzMax) +
+                                        " nonzeros");
+        const int qcap = std::max(1, in.longest);
+        Out<int64_t> ids(ids_out, (size_t)nq * k, s);
+        Out<float> dd(dists_out, (size_t)nq * k, s);
+        std::vector<Scratch<int32_t>> sel((size_t)L);
+        for (int l = 0; l < L; ++l) sel[(size_t)l].alloc((size_t)nq * p[(size_t)l], s);
+        const int top = L - 1;
+        const auto &T = index->lv[(size_t)top];
+        csr_level_scan(T.Cs.get(), dp, T.cns.get(), T.ids.get(), nullptr, nullptr, 1, T.k,
+                       in.rp->p, in.col->p, in.val->p, qcap, nq, p[(size_t)top],
+                       sel[(size_t)top].get(), s);
+        for (int l = top; l >= 1; --l) {
+            const auto &B = index->lv[(size_t)l - 1];
+            csr_level_scan(B.Cs.get(), dp, B.cns.get(), B.ids.get(), index->lv[(size_t)l].off.get(),
+                           sel[(size_t)l].get(), p[(size_t)l], 0, in.rp->p, in.col->p, in.val->p,
+                           qcap, nq, p[(size_t)l - 1], sel[(size_t)l - 1].get(), s);
+        }
+        csr_leaf_scan(index->xrp.get(), index->xcol.get(), index->xval.get(), index->xids.get(),
+                      index->lv[0].off.get(), sel[0].get(), p[0], in.rp->p, in.col->p, in.val->p,
+                      dp, nq, k, ids.p, dd.p, s);
+        ids.finish(s);
+        dd.finish(s);
+        MASK_CUDA(cudaStreamSynchronize(s));  // the staged CSR copies are released on return
+    });
 }
 
 mask_status mask_kmeanspp(const float *X, int64_t n, int32_t d, int32_t k, uint64_t seed,
@@ -654,6 +875,99 @@ mask_status mask_kmeans_update(const float *X, int64_t n, int32_t d, const int32
         pad_rows(Cin.p, k, d, Cp.get(), dp, s);
         label_sort(Lin.p, n, k, off.get(), perm.get(), s);
         centroid_update(Xp.get(), dp, perm.get(), off.get(), k, Cp.get(), Cn.get(), sse.get(), true, s);
+        Out<float> Co(C_out, (size_t)k * d, s);
+        unpad_rows(Cn.get(), k, dp, Co.p, d, s);
+        Co.finish(s);
+        if (counts_out) {
+            Out<int64_t> cnt(counts_out, (size_t)k, s);
+            off_to_counts(off.get(), k, cnt.p, s);
+            cnt.finish(s);
+        }
+        MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+mask_status mask_kmeanspp_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                              int64_t n, int32_t d, int32_t k, uint64_t seed, int32_t level,
+                              float *centroids_out, int64_t *chosen_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(centroids_out != nullptr, "centroids_out is NULL");
+        MASK_REQUIRE(n >= 1 && n <= INT32_MAX && d >= 1, "bad n or d");
+        MASK_REQUIRE(k >= 1 && k <= n, "k must be in [1, n]");
+        MASK_REQUIRE(level >= 0, "level must be >= 0");
+        if (d > kCsrMaxDim)
+            fail(MASK_EUNSUPPORTED, "CSR inputs need d <= " + std::to_string(kCsrMaxDim));
+        cudaStream_t s = (cudaStream_t)stream;
+        CsrIn in(row_ptr, col, val, n, d, s);
+        const int dp = padded_dim(d);
+        Scratch<float> Cp((size_t)k * dp, s);
+        std::vector<int64_t> chosen;
+        seed_level_csr(in.rp->p, in.col->p, in.val->p, n, dp, k, seed, level, Cp.get(), chosen, s);
+        Out<float> C(centroids_out, (size_t)k * d, s);
+        unpad_rows(Cp.get(), k, dp, C.p, d, s);
+        C.finish(s);
+        MASK_CUDA(cudaStreamSynchronize(s));
+        copy_out_host_vec(chosen, chosen_out, s);
+    });
+}
+
+mask_status mask_kmeans_assign_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                                   int64_t n, int32_t d, const float *C, int32_t k,
+                                   int32_t *labels_out, float *dist_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(C && labels_out, "NULL argument");
+        MASK_REQUIRE(n >= 0 && n <= INT32_MAX && d >= 1 && k >= 1, "bad sizes");
+        if (n == 0) return;
+        cudaStream_t s = (cudaStream_t)stream;
+        CsrIn in(row_ptr, col, val, n, d, s);
+        const int dp = padded_dim(d);
+        In<float> Cin(C, (size_t)k * d, s);
+        Scratch<float> Cp((size_t)k * dp, s), xn(n, s), cn(k, s);
+        pad_rows(Cin.p, k, d, Cp.get(), dp, s);
+        csr_row_sqnorm(in.rp->p, in.val->p, n, xn.get(), s);
+        Out<int32_t> lb(labels_out, (size_t)n, s);
+        csr_assign(in.rp->p, in.col->p, in.val->p, n, in.nnz, xn.get(), Cp.get(), k, dp, lb.p,
+                   cn.get(), s);
+        if (dist_out) {
+            Out<float> dist(dist_out, (size_t)n, s);
+            csr_label_dist(in.rp->p, in.col->p, in.val->p, n, Cp.get(), dp, cn.get(), lb.p, dist.p,
+                           s);
+            dist.finish(s);
+            lb.finish(s);
+        } else {
+            lb.finish(s);
+        }
+        MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+mask_status mask_kmeans_update_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                                   int64_t n, int32_t d, const int32_t *labels, int32_t k,
+                                   const float *C_prev, float *C_out, int64_t *counts_out,
+                                   mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(labels && C_prev && C_out, "NULL argument");
+        MASK_REQUIRE(n >= 0 && n <= INT32_MAX && d >= 1 && k >= 1, "bad sizes");
+        cudaStream_t s = (cudaStream_t)stream;
+        CsrIn in(row_ptr, col, val, n, d, s);
+        const int dp = padded_dim(d);
+        In<float> Cin(C_prev, (size_t)k * d, s);
+        In<int32_t> Lin(labels, (size_t)n, s);
+        Scratch<int> bad(1, s);
+        count_bad_labels(Lin.p, n, k, bad.get(), s);
+        int nbad = 0;
+        MASK_CUDA(cudaMemcpyAsync(&nbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        MASK_CUDA(cudaStreamSynchronize(s));
+        MASK_REQUIRE(nbad == 0, "labels out of range");
+        Scratch<float> Cp((size_t)k * dp, s), Cn((size_t)k * dp, s), sse(k, s), cn(k, s);
+        Scratch<double> cn64(k, s);
+        Scratch<int64_t> off((size_t)k + 1, s);
+        Scratch<int32_t> perm((size_t)(n > 0 ? n : 1), s);
+        pad_rows(Cin.p, k, d, Cp.get(), dp, s);
+        centroid_norms(Cp.get(), k, dp, k, cn.get(), cn64.get(), s);
+        label_sort(Lin.p, n, k, off.get(), perm.get(), s);
+        csr_centroid_update(in.rp->p, in.col->p, in.val->p, perm.get(), off.get(), n, k, dp,
+                            Cp.get(), cn.get(), Cn.get(), sse.get(), s);
         Out<float> Co(C_out, (size_t)k * d, s);
         unpad_rows(Cn.get(), k, dp, Co.p, d, s);
         Co.finish(s);

@@ -1,0 +1,353 @@
+// query_csr.cu -- the top-down k-NN search (§3.3, Algorithm 2 with p kept
+// centroids per level) for CSR queries over an index built from CSR points.
+//
+// Two scans, both one block per query, keeping the K smallest keys
+// (distance bits << 32 | id) in shared memory exactly like the dense scans:
+//
+//  * level scan: the query's nonzeros are staged in shared memory and each
+//    centroid row (dense) is read only at those coordinates:
+//      ||q - c||^2 = sum_{t in q} (q_t - c_t)^2 + (||c||^2 - sum_{t in q} c_t^2),
+//    the second term being c's mass off the query's support (FP64 norm of c,
+//    rounded once; clamped at 0);
+//  * leaf scan: the query is scattered into a dense row in shared memory and
+//    each point (a CSR row of the cluster-major point matrix) reads it at its
+//    own nonzeros:
+//      ||x - q||^2 = sum_{t in x} (x_t - q_t)^2 + (||q||^2 - sum_{t in x} q_t^2),
+//    where ||q||^2 is summed by the same lane-group procedure over q's own
+//    nonzeros, so a point equal to the query gets exactly 0.
+//
+// Groups of kGroup lanes take one row each, four rows in flight per group.
+#include <climits>
+
+#include "common.cuh"
+
+namespace mask {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = 256;
+constexpr int kGroup = 8;                       // lanes per row
+constexpr int kGroups = kThreads / kGroup;      // rows in flight per block / 4
+constexpr int kInFlight = 4;                    // rows per group per round
+constexpr int kRound = kGroups * kInFlight;     // rows per round
+
+__device__ __forceinline__ void bitonic_sort_keys(unsigned long long *buf, int S) {
+    for (int kk = 2; kk <= S; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < S; i += kThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & kk) == 0;
+                    const unsigned long long a = buf[i], b = buf[ixj];
+                    if ((a > b) == up) { buf[i] = b; buf[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__device__ __forceinline__ void group_reduce2(float &A, float &B) {
+#pragma unroll
+    for (int o = kGroup / 2; o > 0; o >>= 1) {
+        A += __shfl_xor_sync(kFull, A, o, kGroup);
+        B += __shfl_xor_sync(kFull, B, o, kGroup);
+    }
+}
+
+// Shared state of one query's scan.
+struct ScanSmem {
+    unsigned long long *buf;  // [S] keys: [0, KP) the current list, then candidates
+    int64_t *rb;              // [P] range begins
+    int64_t *cum;             // [P+1] prefix sizes
+};
+
+// Row ranges of query q: the root range, or the children of its kept parents.
+__device__ void setup_ranges(const ScanSmem &sm, const int64_t *__restrict__ off,
+                             const int32_t *__restrict__ sel, int P, int64_t root_end,
+                             int64_t q) {
+    if (threadIdx.x != 0) return;
+    if (sel == nullptr) {
+        sm.rb[0] = 0;
+        sm.cum[0] = 0;
+        sm.cum[1] = root_end;
+        return;
+    }
+    int64_t tot = 0;
+    sm.cum[0] = 0;
+    for (int s = 0; s < P; ++s) {
+        const int32_t p = sel[q * P + s];
+        int64_t b = 0, e = 0;
+        if (p >= 0) { b = off[p]; e = off[p + 1]; }
+        sm.rb[s] = b;
+        tot += e - b;
+        sm.cum[s + 1] = tot;
+    }
+}
+
+__device__ __forceinline__ int64_t row_of(const ScanSmem &sm, int nr, int64_t t) {
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sm.cum[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return sm.rb[lo] + (t - sm.cum[lo]);
+}
+
+// After a round: merge the candidates into the list when the buffer could
+// overflow in the next round, or at the end.
+__device__ __forceinline__ void maybe_merge(const ScanSmem &sm, int S, int K, int KP, int lim,
+                                           bool last, int *cnt, unsigned long long *thresh) {
+    __syncthreads();
+    const int c_now = *cnt;
+    __syncthreads();
+    if (c_now > lim || last) {
+        for (int i = KP + c_now + threadIdx.x; i < S; i += kThreads) sm.buf[i] = kNoKey;
+        __syncthreads();
+        bitonic_sort_keys(sm.buf, S);
+        for (int i = K + threadIdx.x; i < KP; i += kThreads) sm.buf[i] = kNoKey;
+        if (threadIdx.x == 0) {
+            *thresh = sm.buf[K - 1];
+            *cnt = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ level scan
+
+__global__ __launch_bounds__(kThreads) void csr_level_scan_kernel(
+    const float *__restrict__ R, int dp, const float *__restrict__ rcn,
+    const int32_t *__restrict__ rid, const int64_t *__restrict__ off,
+    const int32_t *__restrict__ sel, int P, int64_t root_end, const int64_t *__restrict__ qrp,
+    const int32_t *__restrict__ qcol, const float *__restrict__ qval, int qcap, int K, int KP,
+    int S, int32_t *__restrict__ out32) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ScanSmem sm;
+    sm.buf = reinterpret_cast<unsigned long long *>(smem);
+    sm.rb = reinterpret_cast<int64_t *>(sm.buf + S);
+    sm.cum = sm.rb + P;
+    int32_t *qc = reinterpret_cast<int32_t *>(sm.cum + P + 2);
+    float *qv = reinterpret_cast<float *>(qc + qcap);
+    __shared__ int cnt;
+    __shared__ unsigned long long thresh;
+
+    const int tid = threadIdx.x;
+    const int64_t q = blockIdx.x;
+    const int64_t qb = qrp[q];
+    const int64_t qlen = qrp[q + 1] - qb;
+    const int qn = (int)(qlen < (int64_t)qcap ? qlen : (int64_t)qcap);
+    for (int j = tid; j < qn; j += kThreads) {
+        qc[j] = qcol[qb + j];
+        qv[j] = qval[qb + j];
+    }
+    for (int i = tid; i < S; i += kThreads) sm.buf[i] = kNoKey;
+    if (tid == 0) {
+        cnt = 0;
+        thresh = kNoKey;
+    }
+    setup_ranges(sm, off, sel, P, root_end, q);
+    __syncthreads();
+    const int nr = sel == nullptr ? 1 : P;
+    const int64_t T = sm.cum[nr];
+    const int lim = S - KP - kRound;
+    const int g = tid / kGroup, gl = tid % kGroup;
+
+    for (int64_t base = 0; base < T; base += kRound) {
+        const unsigned long long th = thresh;
+        int64_t row[kInFlight];
+        float A[kInFlight], B[kInFlight];
+#pragma unroll
+        for (int i = 0; i < kInFlight; ++i) {
+            const int64_t t = base + g + (int64_t)i * kGroups;
+            row[i] = t < T ? row_of(sm, nr, t) : -1;
+            A[i] = 0.f;
+            B[i] = 0.f;
+        }
+        for (int j = gl; j < qn; j += kGroup) {
+            const int c = qc[j];
+            const float x = qv[j];
+#pragma unroll
+            for (int i = 0; i < kInFlight; ++i) {
+                if (row[i] < 0) continue;
+                const float r = __ldg(R + row[i] * dp + c);
+                const float e = x - r;
+                A[i] = fmaf(e, e, A[i]);
+                B[i] = fmaf(r, r, B[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kInFlight; ++i) {
+            group_reduce2(A[i], B[i]);
+            if (gl == 0 && row[i] >= 0) {
+                const float dist = A[i] + fmaxf(rcn[row[i]] - B[i], 0.f);
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)rid[row[i]];
+                if (key < th) sm.buf[KP + atomicAdd(&cnt, 1)] = key;
+            }
+        }
+        maybe_merge(sm, S, K, KP, lim, base + kRound >= T, &cnt, &thresh);
+    }
+    for (int r = tid; r < K; r += kThreads) {
+        const unsigned long long key = sm.buf[r];
+        out32[q * K + r] = key != kNoKey ? (int32_t)(key & 0xffffffffu) : -1;
+    }
+}
+
+// ------------------------------------------------------------- leaf scan
+
+__global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
+    const int64_t *__restrict__ xrp, const int32_t *__restrict__ xcol,
+    const float *__restrict__ xval, const int32_t *__restrict__ xids,
+    const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P,
+    const int64_t *__restrict__ qrp, const int32_t *__restrict__ qcol,
+    const float *__restrict__ qval, int dp, int K, int KP, int S, int64_t *__restrict__ out64,
+    float *__restrict__ out_d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ScanSmem sm;
+    sm.buf = reinterpret_cast<unsigned long long *>(smem);
+    sm.rb = reinterpret_cast<int64_t *>(sm.buf + S);
+    sm.cum = sm.rb + P;
+    float *qd = reinterpret_cast<float *>(sm.cum + P + 2);  // [dp] dense query
+    __shared__ int cnt;
+    __shared__ unsigned long long thresh;
+    __shared__ float s_qn;
+
+    const int tid = threadIdx.x;
+    const int64_t q = blockIdx.x;
+    const int64_t qb = qrp[q], qe = qrp[q + 1];
+    for (int i = tid; i < dp; i += kThreads) qd[i] = 0.f;
+    for (int i = tid; i < S; i += kThreads) sm.buf[i] = kNoKey;
+    if (tid == 0) {
+        cnt = 0;
+        thresh = kNoKey;
+    }
+    setup_ranges(sm, off, sel, P, 0, q);
+    __syncthreads();
+    for (int64_t j = qb + tid; j < qe; j += kThreads) qd[qcol[j]] = qval[j];
+    __syncthreads();
+    const int g = tid / kGroup, gl = tid % kGroup;
+    if (tid < 32) {
+        // ||q||^2 as B of the query itself (every group of warp 0; shuffles need the warp)
+        float A = 0.f, B = 0.f;
+        for (int64_t j = qb + gl; j < qe; j += kGroup) {
+            const float c = qd[qcol[j]];
+            const float e = qval[j] - c;
+            A = fmaf(e, e, A);
+            B = fmaf(c, c, B);
+        }
+        group_reduce2(A, B);
+        if (tid == 0) s_qn = B;
+    }
+    __syncthreads();
+    const float qn = s_qn;
+    const int nr = P;
+    const int64_t T = sm.cum[nr];
+    const int lim = S - KP - kRound;
+
+    for (int64_t base = 0; base < T; base += kRound) {
+        const unsigned long long th = thresh;
+        int64_t row[kInFlight], rb[kInFlight];
+        int len[kInFlight];
+        int maxlen = 0;
+        float A[kInFlight], B[kInFlight];
+#pragma unroll
+        for (int i = 0; i < kInFlight; ++i) {
+            const int64_t t = base + g + (int64_t)i * kGroups;
+            row[i] = t < T ? row_of(sm, nr, t) : -1;
+            rb[i] = row[i] >= 0 ? xrp[row[i]] : 0;
+            len[i] = row[i] >= 0 ? (int)(xrp[row[i] + 1] - rb[i]) : 0;
+            maxlen = max(maxlen, len[i]);
+            A[i] = 0.f;
+            B[i] = 0.f;
+        }
+        for (int j = gl; j < maxlen; j += kGroup) {
+#pragma unroll
+            for (int i = 0; i < kInFlight; ++i) {
+                if (j >= len[i]) continue;
+                const float x = __ldg(xval + rb[i] + j);
+                const float c = qd[__ldg(xcol + rb[i] + j)];
+                const float e = x - c;
+                A[i] = fmaf(e, e, A[i]);
+                B[i] = fmaf(c, c, B[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kInFlight; ++i) {
+            group_reduce2(A[i], B[i]);
+            if (gl == 0 && row[i] >= 0) {
+                const float dist = A[i] + fmaxf(qn - B[i], 0.f);
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)xids[row[i]];
+                if (key < th) sm.buf[KP + atomicAdd(&cnt, 1)] = key;
+            }
+        }
+        maybe_merge(sm, S, K, KP, lim, base + kRound >= T, &cnt, &thresh);
+    }
+    for (int r = tid; r < K; r += kThreads) {
+        const unsigned long long key = sm.buf[r];
+        const bool ok = key != kNoKey;
+        out64[q * K + r] = ok ? (int64_t)(int32_t)(key & 0xffffffffu) : -1;
+        if (out_d)
+            out_d[q * K + r] = ok ? __uint_as_float((unsigned)(key >> 32))
+                                  : __int_as_float(0x7f800000);
+    }
+}
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+int list_size(int K) {
+    const int KP = next_pow2(K);
+    return next_pow2(KP + 2 * kRound > 4 * KP ? KP + 2 * kRound : 4 * KP);
+}
+
+}  // namespace
+
+size_t csr_level_scan_smem(int K, int P, int qcap) {
+    return (size_t)list_size(K) * 8 + (size_t)(2 * P + 2) * 8 + (size_t)qcap * 8;
+}
+
+size_t csr_leaf_scan_smem(int K, int P, int dp) {
+    return (size_t)list_size(K) * 8 + (size_t)(2 * P + 2) * 8 + (size_t)dp * 4;
+}
+
+void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid,
+                    const int64_t *off, const int32_t *sel, int P, int64_t root_end,
+                    const int64_t *qrp, const int32_t *qcol, const float *qval, int qcap,
+                    int64_t nq, int K, int32_t *out32, cudaStream_t s) {
+    if (nq == 0) return;
+    MASK_REQUIRE(K >= 1 && K <= 4096, "csr_level_scan: K out of range");
+    const int Pn = sel ? P : 1;
+    const size_t smem = csr_level_scan_smem(K, Pn, qcap);
+    MASK_REQUIRE(smem <= 220 * 1024, "csr_level_scan: probes or query length too large");
+    ProfRegion pr("csr_scan_level", s, 0.0);
+    MASK_CUDA(cudaFuncSetAttribute(csr_level_scan_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    csr_level_scan_kernel<<<(unsigned)nq, kThreads, smem, s>>>(
+        R, dp, rcn, rid, off, sel, Pn, root_end, qrp, qcol, qval, qcap, K, next_pow2(K),
+        list_size(K), out32);
+    MASK_LAUNCHED("csr_level_scan");
+}
+
+void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
+                   const int32_t *xids, const int64_t *off, const int32_t *sel, int P,
+                   const int64_t *qrp, const int32_t *qcol, const float *qval, int dp, int64_t nq,
+                   int K, int64_t *out64, float *out_d, cudaStream_t s) {
+    if (nq == 0) return;
+    MASK_REQUIRE(K >= 1 && K <= 4096, "csr_leaf_scan: K out of range");
+    const size_t smem = csr_leaf_scan_smem(K, P, dp);
+    MASK_REQUIRE(smem <= 220 * 1024, "csr_leaf_scan: k, probes or dimension too large");
+    ProfRegion pr("csr_scan_leaf", s, 0.0);
+    MASK_CUDA(cudaFuncSetAttribute(csr_leaf_scan_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    csr_leaf_scan_kernel<<<(unsigned)nq, kThreads, smem, s>>>(xrp, xcol, xval, xids, off, sel, P,
+                                                              qrp, qcol, qval, dp, K,
+                                                              next_pow2(K), list_size(K), out64,
+                                                              out_d);
+    MASK_LAUNCHED("csr_leaf_scan");
+}
+
+}  // namespace mask

@@ -30,7 +30,8 @@ EXPORTED = [
     "mask_free", "mask_index_get_info", "mask_index_export_level", "mask_index_load",
     "mask_kmeanspp", "mask_kmeans_assign", "mask_kmeans_update",
     "mask_profile_enable", "mask_profile_reset", "mask_profile_read", "mask_launch_count",
-    "mask_kmeans_assign_noalloc",
+    "mask_kmeans_assign_noalloc", "mask_kmeanspp_csr", "mask_kmeans_assign_csr",
+    "mask_kmeans_update_csr",
 ]
 
 
@@ -86,6 +87,12 @@ def load(build_if_stale: bool = True):
                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mask_launch_count": (C.c_int64, []),
             "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
+            "mask_kmeanspp_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _u64, _i32, _vp,
+                                            _vp, _vp]),
+            "mask_kmeans_assign_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp, _vp,
+                                                 _vp]),
+            "mask_kmeans_update_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp, _vp,
+                                                 _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -332,6 +339,47 @@ def mask_kmeans_update(X, labels, C_prev, stream=None):
     cnt, pcnt = _empty_like_kind(X, (k,), "int64")
     _check(load().mask_kmeans_update(px, n, d, pl, k, pc, pn, pcnt, _stream(X, stream)),
            "mask_kmeans_update")
+    return Cn, cnt
+
+
+def _csr(row_ptr, col, val):
+    rp, prp = _arr(row_ptr, "int64")
+    cl, pcl = _arr(col, "int32")
+    vl, pvl = _arr(val, "float32")
+    return (rp, cl, vl), (prp, pcl, pvl), len(rp) - 1
+
+
+def mask_kmeanspp_csr(row_ptr, col, val, n_cols: int, k: int, seed: int, level: int = 0,
+                      stream=None):
+    (rp, _, vl), (prp, pcl, pvl), n = _csr(row_ptr, col, val)
+    cen, pc = _empty_like_kind(rp, (k, n_cols), "float32")
+    chosen = np.empty(k, dtype=np.int64)
+    _check(load().mask_kmeanspp_csr(prp, pcl, pvl, n, n_cols, k, seed & 0xFFFFFFFFFFFFFFFF, level,
+                                    pc, chosen.ctypes.data, _stream(rp, stream)),
+           "mask_kmeanspp_csr")
+    return cen, chosen
+
+
+def mask_kmeans_assign_csr(row_ptr, col, val, n_cols: int, Cc, with_dist: bool = True,
+                           stream=None):
+    (rp, _, vl), (prp, pcl, pvl), n = _csr(row_ptr, col, val)
+    Cc, pc = _arr(Cc, "float32")
+    lab, pl = _empty_like_kind(rp, (n,), "int32")
+    dist, pd = _empty_like_kind(rp, (n,), "float32") if with_dist else (None, None)
+    _check(load().mask_kmeans_assign_csr(prp, pcl, pvl, n, n_cols, pc, Cc.shape[0], pl, pd,
+                                         _stream(rp, stream)), "mask_kmeans_assign_csr")
+    return lab, dist
+
+
+def mask_kmeans_update_csr(row_ptr, col, val, n_cols: int, labels, C_prev, stream=None):
+    (rp, _, vl), (prp, pcl, pvl), n = _csr(row_ptr, col, val)
+    lb, pl = _arr(labels, "int32")
+    Cp, pc = _arr(C_prev, "float32")
+    k = Cp.shape[0]
+    Cn, pn = _empty_like_kind(rp, (k, n_cols), "float32")
+    cnt, pcnt = _empty_like_kind(rp, (k,), "int64")
+    _check(load().mask_kmeans_update_csr(prp, pcl, pvl, n, n_cols, pl, k, pc, pn, pcnt,
+                                         _stream(rp, stream)), "mask_kmeans_update_csr")
     return Cn, cnt
 
 

@@ -142,17 +142,70 @@ class CSR:
         return out
 
 
+def _first_distinct(rng, m, d, cdf, vocab):
+    """Column ids of len(m) rows: row r keeps the first m[r] distinct values of
+    an iid sequence of Zipf draws (mapped through ``vocab``).  Returns the
+    (row, column) pairs sorted by row, then column."""
+    n = len(m)
+    kr = np.zeros(0, np.int64)   # kept rows / columns / sequence numbers
+    kc = np.zeros(0, np.int64)
+    ks = np.zeros(0, np.int64)
+    seq_base = np.zeros(n, np.int64)
+    need = m.copy()
+    active = np.arange(n, dtype=np.int64)
+    while len(active):
+        b = (need[active] * 13) // 10 + 8          # draws per active row this round
+        r = np.repeat(active, b)
+        starts = np.cumsum(b) - b
+        seq = seq_base[r] + (np.arange(len(r), dtype=np.int64) - np.repeat(starts, b))
+        seq_base[active] += b
+        rank = np.minimum(np.searchsorted(cdf, rng.random(len(r)), side="right"), d - 1)
+        c = vocab[rank].astype(np.int64)
+        # candidates of the active rows: what they kept so far (earlier in
+        # their sequences) and the new draws
+        ka = np.isin(kr, active)
+        R = np.concatenate([kr[ka], r])
+        Cc = np.concatenate([kc[ka], c])
+        S = np.concatenate([ks[ka], seq])
+        kr, kc, ks = kr[~ka], kc[~ka], ks[~ka]
+        # first occurrence of each (row, column) in sequence order
+        key = (R * d + Cc) * (1 << 24) + S
+        key.sort()
+        rc = key >> 24
+        first = np.ones(len(key), bool)
+        first[1:] = rc[1:] != rc[:-1]
+        rc, s1 = rc[first], key[first] & ((1 << 24) - 1)
+        rr = rc // d
+        cc = rc - rr * d
+        # per row in sequence order, keep the first m[row]
+        o = np.argsort(rr * (1 << 24) + s1, kind="stable")
+        rr, cc, s1 = rr[o], cc[o], s1[o]
+        bnd = np.flatnonzero(np.r_[True, rr[1:] != rr[:-1]])
+        pos = np.arange(len(rr)) - np.repeat(bnd, np.diff(np.r_[bnd, len(rr)]))
+        keep = pos < m[rr]
+        kr = np.concatenate([kr, rr[keep]])
+        kc = np.concatenate([kc, cc[keep]])
+        ks = np.concatenate([ks, s1[keep]])
+        need = m - np.bincount(kr, minlength=n)
+        active = np.flatnonzero(need > 0)
+    key = np.sort(kr * d + kc)
+    rows = key // d
+    return rows, key - rows * d
+
+
 def sparse_tfidf_like(n: int, d: int, nnz_mean: float = 60.0,
                       nnz_sigma: float = 0.8, zipf_s: float = 1.0,
-                      seed: int = 0, vocab_seed: int = 0) -> CSR:
+                      seed: int = 0, vocab_seed: int = 0, chunk: int = 1 << 16) -> CSR:
     """Sparse rows shaped like an L2-normalised TF-IDF matrix.
 
     Row length m_r ~ round(LogNormal(mu, nnz_sigma)) clipped to [1, d], with mu
     chosen so the arithmetic mean is ``nnz_mean`` (mu = ln(mean) - sigma^2/2).
     Column ids follow Zipf(``zipf_s``) over a fixed permutation of the d ids
     (drawn from ``vocab_seed``, so data and queries share the vocabulary), drawn
-    without replacement within a row (draw, drop repeats, redraw the deficit).
-    Values are |N(0,1)|, then each row is scaled to unit L2 norm.
+    without replacement within a row: the first m_r distinct values of an iid
+    sequence of draws (the same as draw, drop repeats, redraw the deficit).
+    Values are |N(0,1)|, then each row is scaled to unit L2 norm.  Rows are
+    generated in chunks of ``chunk`` rows.
     """
     rng = np.random.default_rng([seed, 0x5BA5])
     vocab = np.random.default_rng([vocab_seed, 0x70CA]).permutation(d)
@@ -161,23 +214,14 @@ def sparse_tfidf_like(n: int, d: int, nnz_mean: float = 60.0,
     w = np.arange(1, d + 1, dtype=np.float64) ** (-zipf_s)
     cdf = np.cumsum(w / w.sum())
     cdf[-1] = 1.0
-
-    have = np.zeros(n, dtype=np.int64)
-    keys = np.zeros(0, dtype=np.int64)
-    while True:
-        need = m - have
-        if not need.any():
-            break
-        rows = np.repeat(np.arange(n, dtype=np.int64), need)
-        rank = np.minimum(np.searchsorted(cdf, rng.random(len(rows)), side="right"), d - 1)
-        # each row draws exactly its deficit, so a row never exceeds m_r
-        keys = np.unique(np.concatenate([keys, rows * d + vocab[rank]]))
-        have = np.bincount(keys // d, minlength=n)
-    rows = keys // d
-    col = (keys - rows * d).astype(np.int32)
+    cols = []
+    for c0 in range(0, n, chunk):
+        _, c = _first_distinct(rng, m[c0:c0 + chunk], d, cdf, vocab)
+        cols.append(c.astype(np.int32))
+    col = np.concatenate(cols) if cols else np.zeros(0, np.int32)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(np.bincount(rows, minlength=n), out=row_ptr[1:])
+    np.cumsum(m, out=row_ptr[1:])
     val = np.abs(rng.standard_normal(len(col)))
     sq = np.add.reduceat(val * val, row_ptr[:-1]) if len(val) else np.zeros(n)
-    val = val / np.sqrt(np.repeat(sq, np.diff(row_ptr)))
+    val = val / np.sqrt(np.repeat(sq, m))
     return CSR(row_ptr, col, val.astype(np.float32), d)
