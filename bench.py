@@ -51,6 +51,18 @@ WORKLOADS = {
                              [512, 96, 24]],
                      desc="10M x 64 fp32, 1000 anisotropic blobs (eig log-U[0.1,10], Zipf 1.1), "
                           "index 32768/1024/32, 15 Lloyd iters, 10k queries, k=10, probes 8/4/2"),
+    "sparse1m": dict(n=1_000_000, d=20_000, nnz_mean=60.0, kind="sparse", k_per_level=[4096, 64],
+                     iters=10, nq=5_000, k=10, probes=[16, 4],
+                     ladder=[[16, 4], [24, 6], [32, 8], [48, 8], [64, 12], [96, 16], [128, 24],
+                             [192, 32], [256, 48], [384, 64]],
+                     desc="1M CSR rows x 20000 (nnz log-normal mean 60 sigma 0.8, Zipf(1.0) "
+                          "columns, |N(0,1)| values, rows L2-normalised), index 4096/64, 10 Lloyd "
+                          "iters, 5k CSR queries, k=10, probes 16/4"),
+    "sparse_small": dict(n=50_000, d=20_000, nnz_mean=60.0, kind="sparse", k_per_level=[256, 16],
+                         iters=10, nq=1_000, k=10, probes=[8, 4],
+                         ladder=[[8, 4], [16, 4], [32, 8], [64, 16], [128, 16]],
+                         desc="50k CSR rows x 20000 (as sparse1m), index 256/16, 10 Lloyd iters, "
+                              "1k CSR queries, k=10, probes 8/4"),
     "small": dict(n=20_000, d=16, blobs=10, kind="isotropic", k_per_level=[200, 20], iters=20,
                   nq=1_000, k=10, probes=[3, 3],
                   ladder=[[3, 3], [6, 4], [10, 6], [16, 8], [24, 10], [40, 14], [64, 20]],
@@ -63,10 +75,14 @@ WORKLOADS = {
 # cheapest with oracle recall@10 >= 0.95 on that sample.
 CPU_SAMPLE = {
     "dense10m": dict(n=100_000, k_per_level=[328, 10], nq=1000),
+    "sparse1m": dict(n=2_000, k_per_level=[8, 2], nq=100),
+    "sparse_small": dict(n=2_000, k_per_level=[8, 2], nq=100),
     "small": dict(n=20_000, k_per_level=[200, 20], nq=1000),
 }
 REF_SAMPLE = {
     "dense10m": dict(n=50_000, k_per_level=[164, 5], nq=1000),
+    "sparse1m": dict(n=2_000, k_per_level=[8, 2], nq=100),
+    "sparse_small": dict(n=2_000, k_per_level=[8, 2], nq=100),
     "small": dict(n=20_000, k_per_level=[200, 20], nq=1000),
 }
 
@@ -83,7 +99,12 @@ def log(*a):
 
 
 def make_data(w, rank=0):
+    """Points and queries: dense arrays, or synth.CSR for the sparse workloads."""
     from paper_2208_02734_gb300 import synth
+    if w["kind"] == "sparse":
+        A = synth.sparse_tfidf_like(w["n"], w["d"], nnz_mean=w["nnz_mean"], seed=2 * rank)
+        Qa = synth.sparse_tfidf_like(w["nq"], w["d"], nnz_mean=w["nnz_mean"], seed=2 * rank + 1)
+        return A, Qa
     if w["kind"] == "anisotropic":
         mix = synth.AnisotropicMixture(d=w["d"], n_blobs=w["blobs"], seed=0)
     else:
@@ -233,10 +254,18 @@ def oracle_operating_point(O, idx, Xs, Qs, k, k1, k2):
     return [k1, k2], r
 
 
+def dense_sample(X, Q, n, nq):
+    """The first n points and nq queries as dense arrays (the oracle has no
+    sparse code: a CSR row is the dense row with zeros elsewhere)."""
+    if hasattr(X, "rows"):
+        return X.rows(np.arange(n)).to_dense(), Q.rows(np.arange(nq)).to_dense()
+    return np.ascontiguousarray(X[:n]), np.ascontiguousarray(Q[:nq])
+
+
 def cpu_baseline(X, Q, w, wname):
     import oracle as O
     s = CPU_SAMPLE[wname]
-    Xs, Qs = np.ascontiguousarray(X[: s["n"]]), np.ascontiguousarray(Q[: s["nq"]])
+    Xs, Qs = dense_sample(X, Q, s["n"], s["nq"])
     t0 = time.perf_counter()
     idx = O.build(Xs, s["k_per_level"], iters=w["iters"], seed=0)
     t1 = time.perf_counter()
@@ -260,6 +289,7 @@ def run_reference(args, w, wname):
     import oracle as O
     s = REF_SAMPLE[wname]
     X, Q = make_data(dict(w, n=s["n"], nq=s["nq"]), 0)
+    X, Q = dense_sample(X, Q, s["n"], s["nq"])
     probes, rec = oracle_operating_point(
         O, O.build(X, s["k_per_level"], iters=w["iters"], seed=0), X, Q, w["k"], *s["k_per_level"])
     q_times, b_times = [], []
@@ -273,7 +303,7 @@ def run_reference(args, w, wname):
             b_times.append(t1 - t0)
             q_times.append(t2 - t1)
     value = args.steps * s["nq"] / sum(q_times)
-    sample = (f"{s['n']} points x {w['d']} from the same mixture, index "
+    sample = (f"{s['n']} points x {w['d']} from the same generator, index "
               f"{'/'.join(map(str, s['k_per_level']))}, {w['iters']} Lloyd iters, {s['nq']} queries, "
               f"k={w['k']}, probes {'/'.join(map(str, probes))} (cheapest with oracle recall@10 "
               f">= 0.95: {rec:.3f}); FP64 oracle on host cores")
@@ -311,15 +341,238 @@ def weak_scaling_value(world, steps, nq, local_query_ms, local_total_ms, device)
 
 
 KERNEL_KIND = {"assign_tc": "tensor", "assign_gemm": "alu", "assign_recheck": "alu",
+               "csr_spmm_assign": "alu", "csr_scan_leaf": "hbm", "csr_scan_level": "hbm",
+               "csr_centroid_update": "hbm",
                "scan_leaf_cm": "hbm", "leaf_group": "hbm", "leaf_merge": "hbm",
                "scan_topk_leaf": "hbm",
                "scan_topk_level": "hbm", "centroid_update": "hbm", "label_sort": "hbm",
                "kmeanspp": "hbm"}
 KERNEL_SRC = {"assign_tc": "assign_tc.cu", "assign_gemm": "assign.cu", "scan_leaf_cm": "query_cm.cu", "scan_topk_leaf": "query.cu",
+              "csr_spmm_assign": "sparse.cu", "csr_scan_leaf": "query_csr.cu",
               "centroid_update": "kmeans.cu", "kmeanspp": "kmeans.cu", "label_sort": "kmeans.cu"}
 
 
+def roofline_of(kernels, wname, step_ms):
+    """Roofline entry for the kernel with the most device time."""
+    peaks, peak_kind = measured_peaks()
+    for name, kv in kernels.items():
+        if kv["ms"] <= 0:
+            continue
+        if KERNEL_KIND[name] in ("alu", "tensor"):
+            kv["achieved_tflops"] = kv["work"] / (kv["ms"] / 1e3) / 1e12
+        else:
+            kv["achieved_gbs"] = kv["work"] / (kv["ms"] / 1e3) / 1e9
+    dom = max(kernels, key=lambda n: kernels[n]["ms"]) if kernels else None
+    if dom is None:
+        return None
+    kv = kernels[dom]
+    if KERNEL_KIND[dom] == "tensor":
+        # timed inside a long step: the sustained BF16 figure scaled to TF32
+        peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
+        ach = kv.get("achieved_tflops", 0.0)
+        roofline = {"kernel": dom, "bound": "tensor", "achieved": ach * TC_PASSES,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach * TC_PASSES / peak,
+                    "achieved_useful": ach, "frac_useful": ach / peak,
+                    "peak_source": (f"{peak_kind} sustained BF16 x 1.1/2.25 (TF32); "
+                                    "achieved = issued TF32 flop (3 MMAs per useful "
+                                    "product, 3xTF32)")}
+    elif KERNEL_KIND[dom] == "alu":
+        peak = FP32_ALU_TFLOPS
+        roofline = {"kernel": dom, "bound": "alu", "achieved": kv.get("achieved_tflops"),
+                    "peak": peak, "unit": "TFLOP/s",
+                    "frac": kv.get("achieved_tflops", 0) / peak,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        peak = peaks["hbm_gbs"]
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": kv.get("achieved_gbs"),
+                    "peak": peak, "unit": "GB/s", "frac": kv.get("achieved_gbs", 0) / peak,
+                    "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)"}
+    roofline["work_per_launch"] = kv["work"] / kv["launches"]
+    roofline["traffic"] = ncu_traffic(dom, wname) if dom in KERNEL_SRC else None
+    roofline["ms_share_of_step"] = kv["ms"] / max(1e-9, step_ms)
+    return roofline
+
+
+def exact_knn_csr_fp64(rp, col, val, n, d, Qs, k):
+    """Exact k-NN of a few dense queries over CSR points in FP64 on the device
+    (torch sparse matmul): ground truth for recall@k only.  Returns the k
+    nearest ids, their distances, and the full [n x s] distance matrix."""
+    import torch
+    X = torch.sparse_csr_tensor(rp, col.long(), val.double(), size=(n, d))
+    q = Qs.double()
+    xn = torch.zeros(n, dtype=torch.float64, device=q.device)
+    rows = torch.repeat_interleave(torch.arange(n, device=q.device), rp[1:] - rp[:-1])
+    xn.index_add_(0, rows, val.double() ** 2)
+    D = (xn[:, None] + (q * q).sum(1)[None, :] - 2.0 * (X @ q.T)).clamp_min_(0)
+    v, i = torch.topk(D, k, dim=0, largest=False)
+    return i.T.contiguous(), v.T.contiguous(), D
+
+
+def recall_from_matrix(D, got, dk):
+    import torch
+    valid = got >= 0
+    cols = torch.arange(got.shape[0], device=got.device)[:, None].expand_as(got)
+    dist = D[got.clamp_min(0), cols]
+    return ((valid & (dist <= dk * (1 + 1e-5))).sum().item()) / got.numel()
+
+
+def run_ours_sparse(args, w, wname):
+    """The sparse workloads: mask_build_csr + mask_query_csr per step."""
+    import torch
+    import torch.distributed as dist
+    from paper_2208_02734_gb300 import mask as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    M.load()
+    t_gen = time.perf_counter()
+    A, Qa = make_data(w, rank)
+    log(f"[bench] CSR {A.n_rows} x {A.n_cols}, nnz {A.nnz} generated in "
+        f"{time.perf_counter() - t_gen:.1f} s")
+    rp, cl, vl = (torch.from_numpy(a).to(dev) for a in (A.row_ptr, A.col, A.val))
+    qrp, qcl, qvl = (torch.from_numpy(a).to(dev) for a in (Qa.row_ptr, Qa.col, Qa.val))
+    stream = torch.cuda.current_stream(dev)
+    kpl, k, d = w["k_per_level"], w["k"], w["d"]
+
+    t_op = time.perf_counter()
+    sel = recall_sample(qrp[:-1])
+    Qsub = Qa.rows(sel.cpu().numpy())
+    sq = tuple(torch.from_numpy(a).to(dev) for a in (Qsub.row_ptr, Qsub.col, Qsub.val))
+    _, gt_d, Dfull = exact_knn_csr_fp64(rp, cl, vl, A.n_rows, d,
+                                         torch.from_numpy(Qsub.to_dense(np.float64)).to(dev), k)
+    dk = gt_d[:, -1:]
+    idx_eval = M.mask_build_csr(rp, cl, vl, d, kpl, w["iters"], seed=0)
+    ladder = []
+    for pr in w["ladder"]:
+        ids_s, _ = M.mask_query_csr(idx_eval, *sq, k, pr)
+        ladder.append({"probes": pr, "recall_at_10": recall_from_matrix(Dfull, ids_s, dk)})
+    idx_eval.free()
+    ok = [e for e in ladder if e["recall_at_10"] >= 0.95]
+    op = ok[0] if ok else ladder[-1]
+    probes = op["probes"]
+    stated = ladder[0] if ladder[0]["probes"] == w["probes"] else None
+    log(f"[bench] operating point {probes} recall {op['recall_at_10']:.4f} "
+        f"({time.perf_counter() - t_op:.1f} s)")
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        idx = M.mask_build_csr(rp, cl, vl, d, kpl, w["iters"], seed=0)
+        ev[1].record(stream)
+        ids, dd = M.mask_query_csr(idx, qrp, qcl, qvl, k, probes)
+        ev[2].record(stream)
+        idx.free()
+        return ids, dd, ev
+
+    for i in range(args.warmup):
+        t = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        log(f"[bench] warmup {i}: {time.perf_counter() - t:.2f} s")
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    M.mask_profile_reset()
+    M.mask_profile_enable(True)
+    sampler.start()
+    lc0 = M.mask_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("mask_timed")
+    t_start.record(stream)
+    results = [step() for _ in range(args.steps)]
+    t_end.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    barrier()
+    launches = M.mask_launch_count() - lc0
+    clocks = sampler.stop()
+    M.mask_profile_enable(False)
+    build_ms = [r[2][0].elapsed_time(r[2][1]) for r in results]
+    query_ms = [r[2][1].elapsed_time(r[2][2]) for r in results]
+    total_ms = t_start.elapsed_time(t_end)
+    value, q_sum, tot = weak_scaling_value(world, args.steps, w["nq"], sum(query_ms), total_ms,
+                                           dev)
+    kernels = {}
+    for name in KERNEL_KIND:
+        r = M.mask_profile_read(name)
+        if r is not None:
+            kernels[name] = {"launches": r[0], "ms": r[1], "work": r[2]}
+    recall = recall_from_matrix(Dfull, results[-1][0][sel], dk)
+
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(a).pin_memory() for a in (A.row_ptr, A.col, A.val,
+                                                            Qa.row_ptr, Qa.col, Qa.val)]
+        ke = max(1, min(args.steps, 2))
+        qt, bt = [], []
+        for i in range(1 + ke):
+            t0 = time.perf_counter()
+            idx = M.mask_build_csr(host[0], host[1], host[2], d, kpl, w["iters"], seed=0)
+            t1 = time.perf_counter()
+            ids_h, d_h = M.mask_query_csr(idx, host[3], host[4], host[5], k, probes)
+            t2 = time.perf_counter()
+            idx.free()
+            if i > 0:
+                bt.append(t1 - t0)
+                qt.append(t2 - t1)
+        qe, = reduce_max([sum(qt)], world, dev)
+        e2e = {"value": world * ke * w["nq"] / qe, "unit": "queries/s",
+               "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host)),
+               "d2h_bytes_per_step": int(ids_h.nbytes + d_h.nbytes),
+               "build_s": statistics.mean(bt), "steps": ke,
+               "note": "host-pinned CSR points and queries in, host ids/dists out, wall clock"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "n": w["n"], "d": d, "nnz": int(A.nnz),
+                   "k_per_level": kpl, "iters": w["iters"], "queries": w["nq"], "k": k,
+                   "probes": probes, "stated_probes": w["probes"],
+                   "probes_rule": "cheapest probes of a fixed ladder with recall@10 >= 0.95 "
+                                  "(200-query sample vs FP64 exact k-NN)",
+                   "l2": "points 0.48 GB of CSR (col + val) per copy, above L2; no flush",
+                   "parallelism": f"independent index per GPU x{world}"},
+        "recall_at_10": recall, "recall_queries": int(len(sel)),
+        "recall_at_stated_probes": stated["recall_at_10"] if stated else None,
+        "probe_ladder": ladder,
+        "build_s": statistics.mean(build_ms) / 1e3,
+        "p50_ms": float(np.percentile(query_ms, 50)), "p99_ms": float(np.percentile(query_ms, 99)),
+        "latency_note": f"device time of one {w['nq']}-query batch (query phase)",
+        "roofline": roofline_of(kernels, wname, sum(build_ms) + sum(query_ms)),
+        "kernels": kernels, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(A, Qa, w, wname)
+        except Exception as ex:  # report, do not hide, a baseline failure
+            line["cpu_baseline"] = {"error": repr(ex)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args, w, wname):
+    if w["kind"] == "sparse":
+        return run_ours_sparse(args, w, wname)
     import torch
     import torch.distributed as dist
     from paper_2208_02734_gb300 import mask as M
@@ -478,44 +731,7 @@ def run_ours(args, w, wname):
             dist.destroy_process_group()
         return 0
 
-    peaks, peak_kind = measured_peaks()
-    for name, kv in kernels.items():
-        if kv["ms"] <= 0:
-            continue
-        if KERNEL_KIND[name] in ("alu", "tensor"):
-            kv["achieved_tflops"] = kv["work"] / (kv["ms"] / 1e3) / 1e12
-        else:
-            kv["achieved_gbs"] = kv["work"] / (kv["ms"] / 1e3) / 1e9
-    dom = max(kernels, key=lambda n: kernels[n]["ms"]) if kernels else None
-    roofline = None
-    if dom is not None:
-        kv = kernels[dom]
-        if KERNEL_KIND[dom] == "tensor":
-            # timed inside a long step: the sustained BF16 figure scaled to TF32
-            peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
-            ach = kv.get("achieved_tflops", 0.0)
-            roofline = {"kernel": dom, "bound": "tensor", "achieved": ach * TC_PASSES,
-                        "peak": peak, "unit": "TFLOP/s", "frac": ach * TC_PASSES / peak,
-                        "achieved_useful": ach, "frac_useful": ach / peak,
-                        "peak_source": (f"{peak_kind} sustained BF16 x 1.1/2.25 (TF32); "
-                                        "achieved = issued TF32 flop (3 MMAs per useful "
-                                        "product, 3xTF32)"),
-                        "work_per_launch": kv["work"] / kv["launches"]}
-        elif KERNEL_KIND[dom] == "alu":
-            peak = FP32_ALU_TFLOPS
-            roofline = {"kernel": dom, "bound": "alu", "achieved": kv.get("achieved_tflops"),
-                        "peak": peak, "unit": "TFLOP/s",
-                        "frac": kv.get("achieved_tflops", 0) / peak,
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                        "work_per_launch": kv["work"] / kv["launches"]}
-        else:
-            peak = peaks["hbm_gbs"]
-            roofline = {"kernel": dom, "bound": "hbm", "achieved": kv.get("achieved_gbs"),
-                        "peak": peak, "unit": "GB/s", "frac": kv.get("achieved_gbs", 0) / peak,
-                        "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
-                        "work_per_launch": kv["work"] / kv["launches"]}
-        roofline["traffic"] = ncu_traffic(dom, wname) if dom in KERNEL_SRC else None
-        roofline["ms_share_of_step"] = kv["ms"] / max(1e-9, sum(build_ms) + sum(query_ms))
+    roofline = roofline_of(kernels, wname, sum(build_ms) + sum(query_ms))
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,

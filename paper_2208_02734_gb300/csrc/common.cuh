@@ -161,7 +161,8 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
                     int64_t *chosen, cudaStream_t s);
 // the same over CSR rows (dense row of dp <= kCsrMaxDim in shared memory)
 void kmeanspp_steps_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t m,
-                        int dp, int k, const double *u_dev, int64_t *chosen, cudaStream_t s);
+                        int64_t nnz, int dp, int k, const double *u_dev, int64_t *chosen,
+                        cudaStream_t s);
 // counting sort of labels in [0,k): off[k+1] (int64), perm[n] (item ids by label)
 void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *perm,
                 cudaStream_t s);
@@ -220,6 +221,9 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
                     const int64_t *off, const int32_t *sel, int P, int64_t root_end,
                     const int64_t *qrp, const int32_t *qcol, const float *qval, int qcap,
                     int64_t nq, int K, int32_t *out32, cudaStream_t s);
+// bytes the CSR scans read since the last reset ([0] levels, [1] leaf)
+double csr_scan_bytes(int which);
+void csr_scan_bytes_reset();
 // leaf scan: CSR point rows (cluster-major) against the query as a dense row
 size_t csr_leaf_scan_smem(int K, int P, int dp);
 void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,

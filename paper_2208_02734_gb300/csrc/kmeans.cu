@@ -934,11 +934,13 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
 }
 
 void kmeanspp_steps_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t m,
-                        int dp, int k, const double *u_dev, int64_t *chosen, cudaStream_t s) {
+                        int64_t nnz, int dp, int k, const double *u_dev, int64_t *chosen,
+                        cudaStream_t s) {
     if (k <= 1) return;
     const size_t smem = (size_t)dp * sizeof(float);
     MASK_REQUIRE(smem <= (size_t)kCsrMaxDim * sizeof(float), "CSR dimension too large");
-    ProfRegion pr("kmeanspp", s, 0.0);
+    // per step: every nonzero (column + value) and, per row, its pointer and D^2
+    ProfRegion pr("kmeanspp", s, (double)(k - 1) * (8.0 * (double)nnz + 16.0 * (double)m));
     MASK_CUDA(cudaFuncSetAttribute(kpp_step_csr_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nb = (int)((m + kKppRows - 1) / kKppRows);

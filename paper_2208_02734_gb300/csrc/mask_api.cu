@@ -258,7 +258,10 @@ void seed_level_csr(const int64_t *rp, const int32_t *col, const float *val, int
     Scratch<double> ud;
     Scratch<int64_t> ch;
     draw_centres(rng, m, k, ud, ch, s);
-    kmeanspp_steps_csr(Rp, Cl, Vl, m, dp, k, ud.get(), ch.get(), s);
+    int64_t nnz = 0;
+    MASK_CUDA(cudaMemcpyAsync(&nnz, Rp + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MASK_CUDA(cudaStreamSynchronize(s));
+    kmeanspp_steps_csr(Rp, Cl, Vl, m, nnz, dp, k, ud.get(), ch.get(), s);
     csr_densify_rows(Rp, Cl, Vl, ch.get(), k, dp, C_out, s);
     to_host(chosen, ch.get(), (size_t)k, s);
     if (m < n)

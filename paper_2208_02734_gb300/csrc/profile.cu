@@ -82,6 +82,7 @@ void mask_profile_reset(void) {
     mask::g_totals.clear();
     mask::scan_bytes_reset();
     mask::cm_bytes_reset();
+    mask::csr_scan_bytes_reset();
 }
 
 int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms, double *work) {
@@ -96,6 +97,8 @@ int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,
     if (it->first == "scan_topk_level") w = mask::scan_bytes(0);
     if (it->first == "scan_topk_leaf") w = mask::scan_bytes(1);
     if (it->first == "scan_leaf_cm") w = mask::cm_bytes();
+    if (it->first == "csr_scan_level") w = mask::csr_scan_bytes(0);
+    if (it->first == "csr_scan_leaf") w = mask::csr_scan_bytes(1);
     if (work) *work = w;
     return 1;
 }

@@ -22,6 +22,12 @@
 #include "common.cuh"
 
 namespace mask {
+
+// Bytes the CSR scans read ([0] levels: gathered centroid values, 4 per
+// query nonzero per row; [1] leaf: 8 per nonzero + row pointer and id, 12
+// per row), counted per block.
+__device__ unsigned long long g_csr_scan_bytes[2];
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -151,6 +157,8 @@ __global__ __launch_bounds__(kThreads) void csr_level_scan_kernel(
     const int64_t T = sm.cum[nr];
     const int lim = S - KP - kRound;
     const int g = tid / kGroup, gl = tid % kGroup;
+    if (tid == 0)
+        atomicAdd(&g_csr_scan_bytes[0], (unsigned long long)T * (4ull * qn + 8ull));
 
     for (int64_t base = 0; base < T; base += kRound) {
         const unsigned long long th = thresh;
@@ -211,6 +219,7 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     __shared__ int cnt;
     __shared__ unsigned long long thresh;
     __shared__ float s_qn;
+    __shared__ unsigned long long s_nnz;
 
     const int tid = threadIdx.x;
     const int64_t q = blockIdx.x;
@@ -220,6 +229,7 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     if (tid == 0) {
         cnt = 0;
         thresh = kNoKey;
+        s_nnz = 0;
     }
     setup_ranges(sm, off, sel, P, 0, q);
     __syncthreads();
@@ -260,6 +270,12 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
             A[i] = 0.f;
             B[i] = 0.f;
         }
+        if (gl == 0) {
+            int tot = 0;
+#pragma unroll
+            for (int i = 0; i < kInFlight; ++i) tot += len[i];
+            if (tot) atomicAdd(&s_nnz, (unsigned long long)tot);
+        }
         for (int j = gl; j < maxlen; j += kGroup) {
 #pragma unroll
             for (int i = 0; i < kInFlight; ++i) {
@@ -283,6 +299,7 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
         }
         maybe_merge(sm, S, K, KP, lim, base + kRound >= T, &cnt, &thresh);
     }
+    if (tid == 0) atomicAdd(&g_csr_scan_bytes[1], 8ull * s_nnz + 12ull * (unsigned long long)T);
     for (int r = tid; r < K; r += kThreads) {
         const unsigned long long key = sm.buf[r];
         const bool ok = key != kNoKey;
@@ -305,6 +322,20 @@ int list_size(int K) {
 }
 
 }  // namespace
+
+double csr_scan_bytes(int which) {
+    unsigned long long v[2] = {0, 0};
+    if (cudaMemcpyFromSymbol(v, g_csr_scan_bytes, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return (double)v[which];
+}
+
+void csr_scan_bytes_reset() {
+    const unsigned long long z[2] = {0, 0};
+    if (cudaMemcpyToSymbol(g_csr_scan_bytes, z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+}
 
 size_t csr_level_scan_smem(int K, int P, int qcap) {
     return (size_t)list_size(K) * 8 + (size_t)(2 * P + 2) * 8 + (size_t)qcap * 8;

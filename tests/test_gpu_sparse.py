@@ -241,7 +241,7 @@ def test_csr_rejects_malformed_inputs(sparse_c):
     A, Qa, _, _, idx = sparse_c
     rp, col, val = A.row_ptr.copy(), A.col.copy(), A.val.copy()
     bad_col = col.copy()
-    bad_col[5] = 600
+    bad_col[rp[1] - 1] = 600      # the last (largest) column of row 0: still increasing
     with pytest.raises(M.MaskError, match="outside"):
         M.mask_build_csr(rp, bad_col, val, 600, [8], 1, seed=0)
     unsorted = col.copy()
