@@ -47,6 +47,7 @@ typedef struct mask_index mask_index;
 typedef void *mask_stream;
 
 typedef enum {
+    MASK_PENDING = 1,       /* (serving) the request has not finished yet */
     MASK_OK = 0,
     MASK_EINVAL = -1,       /* bad argument (sizes, k > items below, NULL) */
     MASK_ENOMEM = -2,       /* device or host allocation failed */
@@ -293,6 +294,69 @@ int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,
 
 /* Kernel launches the library has issued since it was loaded. */
 int64_t mask_launch_count(void);
+
+/* ---- serving: continuous batching over a resident index ----------------
+ *
+ * The paper answers queries one at a time (§3.3); a service takes a stream
+ * of requests (batches of queries of any size, each with its own k, probes
+ * and precision) against one resident dense index.  The paper has no
+ * counterpart: this is the interface of the query path as a service.
+ *
+ * A worker thread merges pending requests with equal probes and precision
+ * (low precision: also equal k) into one launch of up to max_batch queries
+ * (a larger request is split), replays the captured CUDA graph of that batch
+ * shape on one of max_slots streams, and admits a batch only while the
+ * device bytes of the batches in flight (graph buffers and kernel scratch,
+ * estimated per shape) stay within mem_budget.  Requests arriving while
+ * others run join the next batch as slots and memory free up.  A request's
+ * result is the same as mask_query's on its queries alone (bit for bit).
+ * For FP32 shapes where both leaf scans apply, the first batch of a shape
+ * times both and keeps the faster (autotuning; results are identical).
+ *
+ * The index must stay alive until mask_server_close.  Queries and outputs
+ * are HOST memory: queries are copied at submit; ids_out / dists_out are
+ * written by the worker and must stay valid until poll or wait returns
+ * something other than MASK_PENDING for the ticket.
+ */
+typedef struct mask_server mask_server;
+
+typedef struct {
+    int64_t requests_done, requests_failed, queries_done;
+    int64_t batches;              /* launches (graph replays) of merged batches */
+    int64_t graph_launches;
+    int64_t graph_captures;       /* batch shapes captured so far */
+    int64_t autotuned_shapes;
+    double mean_batch_queries;    /* queries per batch (before padding) */
+    double latency_mean_ms, latency_p50_ms, latency_p99_ms, latency_max_ms;  /* submit -> done */
+    double elapsed_s;             /* first submit -> last completion */
+    int64_t peak_inflight_bytes;  /* most estimated device bytes in flight at once */
+    int64_t mem_budget;
+} mask_server_info;
+
+/* Opens a server on a dense index: mem_budget (> 0) device bytes for batches
+ * in flight, max_slots in [1, 64] concurrent batches (streams), max_batch in
+ * [8, 2^20] queries per launch (rounded up to a power of two). */
+mask_status mask_server_open(const mask_index *index, int64_t mem_budget, int32_t max_slots,
+                             int32_t max_batch, mask_server **out);
+
+/* Queues a request (arguments as mask_query, host pointers only) and returns
+ * its ticket; errors in the arguments are returned here. */
+mask_status mask_server_submit(mask_server *server, const float *queries, int64_t nq, int32_t k,
+                               const int32_t *probes, mask_precision precision,
+                               int64_t *ids_out, float *dists_out, uint64_t *ticket_out);
+
+/* MASK_PENDING while the request runs; otherwise its final status (MASK_OK:
+ * outputs written), after which the ticket is forgotten. */
+mask_status mask_server_poll(mask_server *server, uint64_t ticket);
+
+/* As poll, waiting up to timeout_ms (< 0: no limit). */
+mask_status mask_server_wait(mask_server *server, uint64_t ticket, int32_t timeout_ms);
+
+/* Counters and latency percentiles since open (or the last reset). */
+mask_status mask_server_stats(mask_server *server, mask_server_info *out, int32_t reset);
+
+/* Finishes every queued request, then releases the server (NULL is ignored). */
+void mask_server_close(mask_server *server);
 
 #ifdef __cplusplus
 }

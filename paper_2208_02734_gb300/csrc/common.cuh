@@ -28,6 +28,8 @@ void set_last_error(const std::string &msg);
 
 // Counts one kernel launch (called by MASK_LAUNCHED at every launch site).
 void count_launch();
+// Counts n launches at once (the kernel nodes of a replayed graph).
+void count_launches(long long n);
 
 // While profiling is enabled, brackets its scope with CUDA events on stream s
 // and books the elapsed device time and `work` (flop or bytes) under `name`.

@@ -14,37 +14,7 @@
 #include <mutex>
 #include <vector>
 
-#include "common.cuh"
-
-struct mask_index {
-    int device = 0;
-    int64_t n = 0;
-    int d = 0, dp = 0, L = 0, iters = 0;
-    bool sparse = false;
-    mask::DevArray<float> Xs;        // [n x dp] points, cluster-major (level-0 parent-major)
-    mask::DevArray<int32_t> xids;    // [n] original id of each row of Xs (or of xrp)
-    // CSR index: the points' rows cluster-major (row i is point xids[i])
-    mask::DevArray<int64_t> xrp;     // [n+1]
-    mask::DevArray<int32_t> xcol;    // [nnz]
-    mask::DevArray<float> xval;      // [nnz]
-    struct Level {
-        int k = 0;
-        mask::DevArray<float> C;       // [k x dp] centroids in k-means cluster order
-        mask::DevArray<float> Cs;      // [k x dp] centroids parent-major (top: cluster order)
-        mask::DevArray<int32_t> ids;   // [k] cluster id of each row of Cs
-        mask::DevArray<int64_t> off;   // [k+1] children of centroid j: rows off[j]..off[j+1]
-                                       //       of the level below's parent-major array
-        mask::DevArray<int32_t> labels;// [n_below] centroid of every item one level below
-        mask::DevArray<float> cns;     // [k] ||row of Cs||^2 (CSR index: level-scan norms)
-        std::vector<int64_t> chosen;   // k-means++ picks (indices into the level's inputs)
-        std::vector<double> objective; // k-means objective after each assignment
-    };
-    std::vector<Level> lv;
-    // quantised copies of Xs for the BF16 / FP8 query modes, made on first use
-    mutable std::mutex lp_mu;
-    mutable mask::DevArray<unsigned char> Xlp[2];  // [0] BF16, [1] FP8 e4m3
-    mutable mask::DevArray<float> xn_lp[2], xscale_fp8;
-};
+#include "index.cuh"
 
 namespace mask {
 
@@ -493,6 +463,83 @@ struct CsrIn {
 };
 
 }  // namespace
+
+void ensure_lowp(const mask_index &idx, bool fp8, cudaStream_t s) {
+    const int slot = fp8 ? 1 : 0;
+    std::lock_guard<std::mutex> lk(idx.lp_mu);
+    if (idx.Xlp[slot].p != nullptr) return;
+    const int dpl = lp_padded_dim(idx.dp);
+    idx.Xlp[slot].alloc((size_t)idx.n * dpl * (fp8 ? 1 : 2));
+    idx.xn_lp[slot].alloc((size_t)idx.n);
+    if (fp8) idx.xscale_fp8.alloc((size_t)idx.n);
+    lp_quantize(idx.Xs.get(), idx.n, idx.dp, fp8, idx.Xlp[slot].get(),
+                fp8 ? idx.xscale_fp8.get() : nullptr, idx.xn_lp[slot].get(), s);
+    MASK_CUDA(cudaStreamSynchronize(s));
+}
+
+void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
+                 const std::vector<int> &p, mask_precision prec, LeafMode mode, int64_t *ids,
+                 float *dists, cudaStream_t s) {
+    if (nq == 0) return;
+    const int L = idx.L, dp = idx.dp;
+    std::vector<Scratch<int32_t>> sel((size_t)L);
+    for (int l = 0; l < L; ++l) sel[(size_t)l].alloc((size_t)nq * p[(size_t)l], s);
+    ScanArgs a;
+    a.Q = Qp;
+    a.nq = nq;
+    a.dp = dp;
+    const int top = L - 1;
+    a.R = idx.lv[(size_t)top].Cs.get();
+    a.rid = idx.lv[(size_t)top].ids.get();
+    a.root_end = idx.lv[(size_t)top].k;
+    a.K = p[(size_t)top];
+    a.out_ids32 = sel[(size_t)top].get();
+    scan_topk(a, s);
+    for (int l = top; l >= 1; --l) {
+        ScanArgs b = a;
+        b.R = idx.lv[(size_t)l - 1].Cs.get();
+        b.rid = idx.lv[(size_t)l - 1].ids.get();
+        b.off = idx.lv[(size_t)l].off.get();
+        b.sel = sel[(size_t)l].get();
+        b.P = p[(size_t)l];
+        b.K = p[(size_t)l - 1];
+        b.out_ids32 = sel[(size_t)l - 1].get();
+        scan_topk(b, s);
+    }
+    const int k0 = idx.lv[0].k;
+    if (prec != MASK_FP32) {
+        // BF16 / FP8 distances for a max(4k, 16) shortlist, exact FP32 re-rank
+        const bool fp8 = prec == MASK_FP8E4M3;
+        const int slot = fp8 ? 1 : 0;
+        MASK_REQUIRE(idx.Xlp[slot].p != nullptr, "low-precision copy missing");
+        lp_leaf_scan(fp8, idx.Xlp[slot].get(), idx.xn_lp[slot].get(),
+                     fp8 ? idx.xscale_fp8.get() : nullptr, idx.Xs.get(), dp, idx.xids.get(),
+                     idx.lv[0].off.get(), k0, Qp, nq, sel[0].get(), p[0], k, ids, dists, s);
+        return;
+    }
+    // Leaf scan: cluster-major when the batch keeps each leaf cluster several
+    // times on average, else query by query (same arithmetic, same results).
+    bool cluster_major = cm_leaf_supported(dp, k) && nq * (int64_t)p[0] >= 4 * (int64_t)k0;
+    if (mode == LeafMode::Cluster) cluster_major = cm_leaf_supported(dp, k);
+    if (mode == LeafMode::Query) cluster_major = false;
+    if (cluster_major) {
+        cm_leaf_scan(idx.Xs.get(), dp, idx.xids.get(), idx.lv[0].off.get(), k0, Qp, nq, sel[0].get(),
+                     p[0], k, ids, dists, s);
+    } else {
+        ScanArgs c = a;
+        c.R = idx.Xs.get();
+        c.rid = idx.xids.get();
+        c.off = idx.lv[0].off.get();
+        c.sel = sel[0].get();
+        c.P = p[0];
+        c.K = k;
+        c.out_ids32 = nullptr;
+        c.out_ids64 = ids;
+        c.out_d = dists;
+        scan_topk(c, s);
+    }
+}
+
 }  // namespace mask
 
 using namespace mask;
@@ -661,85 +708,18 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
             MASK_REQUIRE(probes[l] >= 1, "probes must be >= 1");
             p[(size_t)l] = std::min<int>(probes[l], index->lv[(size_t)l].k);
         }
+        if (lowp) ensure_lowp(*index, precision == MASK_FP8E4M3, s);
+        LeafMode mode = LeafMode::Auto;
+        if (const char *m = std::getenv("MASK_LEAF_SCAN")) {
+            if (std::strcmp(m, "cluster") == 0) mode = LeafMode::Cluster;
+            if (std::strcmp(m, "query") == 0) mode = LeafMode::Query;
+        }
         In<float> Qin(queries, (size_t)nq * index->d, s);
         Scratch<float> Qp((size_t)nq * dp, s);
         pad_rows(Qin.p, nq, index->d, Qp.get(), dp, s);
         Out<int64_t> ids(ids_out, (size_t)nq * k, s);
         Out<float> dd(dists_out, (size_t)nq * k, s);
-        std::vector<Scratch<int32_t>> sel((size_t)L);
-        for (int l = 0; l < L; ++l) sel[(size_t)l].alloc((size_t)nq * p[(size_t)l], s);
-
-        ScanArgs a;
-        a.Q = Qp.get();
-        a.nq = nq;
-        a.dp = dp;
-        const int top = L - 1;
-        a.R = index->lv[(size_t)top].Cs.get();
-        a.rid = index->lv[(size_t)top].ids.get();
-        a.root_end = index->lv[(size_t)top].k;
-        a.K = p[(size_t)top];
-        a.out_ids32 = sel[(size_t)top].get();
-        scan_topk(a, s);
-        for (int l = top; l >= 1; --l) {
-            ScanArgs b = a;
-            b.R = index->lv[(size_t)l - 1].Cs.get();
-            b.rid = index->lv[(size_t)l - 1].ids.get();
-            b.off = index->lv[(size_t)l].off.get();
-            b.sel = sel[(size_t)l].get();
-            b.P = p[(size_t)l];
-            b.K = p[(size_t)l - 1];
-            b.out_ids32 = sel[(size_t)l - 1].get();
-            scan_topk(b, s);
-        }
-        const int k0 = index->lv[0].k;
-        if (lowp) {
-            // BF16 / FP8 distances for a 4k shortlist, exact FP32 re-rank
-            const bool fp8 = precision == MASK_FP8E4M3;
-            const int slot = fp8 ? 1 : 0;
-            {
-                std::lock_guard<std::mutex> lk(index->lp_mu);
-                if (index->Xlp[slot].p == nullptr) {
-                    const int dpl = lp_padded_dim(dp);
-                    index->Xlp[slot].alloc((size_t)index->n * dpl * (fp8 ? 1 : 2));
-                    index->xn_lp[slot].alloc((size_t)index->n);
-                    if (fp8) index->xscale_fp8.alloc((size_t)index->n);
-                    lp_quantize(index->Xs.get(), index->n, dp, fp8, index->Xlp[slot].get(),
-                                fp8 ? index->xscale_fp8.get() : nullptr,
-                                index->xn_lp[slot].get(), s);
-                }
-            }
-            lp_leaf_scan(fp8, index->Xlp[slot].get(), index->xn_lp[slot].get(),
-                         fp8 ? index->xscale_fp8.get() : nullptr, index->Xs.get(), dp,
-                         index->xids.get(), index->lv[0].off.get(), k0, Qp.get(), nq, sel[0].get(),
-                         p[0], k, ids.p, dd.p, s);
-            ids.finish(s);
-            dd.finish(s);
-            if (ids.host || dd.host) MASK_CUDA(cudaStreamSynchronize(s));
-            return;
-        }
-        // Leaf scan: cluster-major when the batch keeps each leaf cluster
-        // several times on average, else query by query (same arithmetic).
-        bool cluster_major = cm_leaf_supported(dp, k) && nq * (int64_t)p[0] >= 4 * (int64_t)k0;
-        if (const char *mode = std::getenv("MASK_LEAF_SCAN")) {
-            if (std::strcmp(mode, "cluster") == 0) cluster_major = cm_leaf_supported(dp, k);
-            if (std::strcmp(mode, "query") == 0) cluster_major = false;
-        }
-        if (cluster_major) {
-            cm_leaf_scan(index->Xs.get(), dp, index->xids.get(), index->lv[0].off.get(), k0,
-                         Qp.get(), nq, sel[0].get(), p[0], k, ids.p, dd.p, s);
-        } else {
-            ScanArgs c = a;
-            c.R = index->Xs.get();
-            c.rid = index->xids.get();
-            c.off = index->lv[0].off.get();
-            c.sel = sel[0].get();
-            c.P = p[0];
-            c.K = k;
-            c.out_ids32 = nullptr;
-            c.out_ids64 = ids.p;
-            c.out_d = dd.p;
-            scan_topk(c, s);
-        }
+        query_dense(*index, Qp.get(), nq, k, p, precision, mode, ids.p, dd.p, s);
         ids.finish(s);
         dd.finish(s);
         if (ids.host || dd.host) MASK_CUDA(cudaStreamSynchronize(s));

@@ -49,9 +49,17 @@ void drain_locked(const std::string &name) {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 ProfRegion::ProfRegion(const char *name, cudaStream_t s, double work)
     : name_(name), s_(s), work_(work) {
     if (!g_enabled.load(std::memory_order_relaxed)) return;
+    // regions inside a stream capture (a graph being built) are not timed
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;
+    }
     if (cudaEventCreate(&a_) != cudaSuccess) return;
     if (cudaEventCreate(&b_) != cudaSuccess) {
         cudaEventDestroy(a_);

@@ -18,11 +18,12 @@ import numpy as np
 
 from . import _build
 
+MASK_PENDING = 1
 MASK_OK, MASK_EINVAL, MASK_ENOMEM, MASK_ECUDA, MASK_ETIMEOUT, MASK_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 MASK_FP32, MASK_BF16, MASK_FP8E4M3 = 0, 1, 2
 MASK_MAX_LEVELS = 16
 
-_STATUS = {0: "MASK_OK", -1: "MASK_EINVAL", -2: "MASK_ENOMEM", -3: "MASK_ECUDA",
+_STATUS = {1: "MASK_PENDING", 0: "MASK_OK", -1: "MASK_EINVAL", -2: "MASK_ENOMEM", -3: "MASK_ECUDA",
            -4: "MASK_ETIMEOUT", -5: "MASK_EUNSUPPORTED"}
 
 EXPORTED = [
@@ -31,7 +32,8 @@ EXPORTED = [
     "mask_kmeanspp", "mask_kmeans_assign", "mask_kmeans_update",
     "mask_profile_enable", "mask_profile_reset", "mask_profile_read", "mask_launch_count",
     "mask_kmeans_assign_noalloc", "mask_kmeanspp_csr", "mask_kmeans_assign_csr",
-    "mask_kmeans_update_csr",
+    "mask_kmeans_update_csr", "mask_server_open", "mask_server_submit", "mask_server_poll",
+    "mask_server_wait", "mask_server_stats", "mask_server_close",
 ]
 
 
@@ -45,6 +47,20 @@ class mask_index_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("n_levels", C.c_int32),
                 ("k_per_level", C.c_int32 * MASK_MAX_LEVELS), ("iters", C.c_int32),
                 ("sparse", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+class mask_server_info(C.Structure):
+    _fields_ = [("requests_done", C.c_int64), ("requests_failed", C.c_int64),
+                ("queries_done", C.c_int64), ("batches", C.c_int64),
+                ("graph_launches", C.c_int64), ("graph_captures", C.c_int64),
+                ("autotuned_shapes", C.c_int64), ("mean_batch_queries", C.c_double),
+                ("latency_mean_ms", C.c_double), ("latency_p50_ms", C.c_double),
+                ("latency_p99_ms", C.c_double), ("latency_max_ms", C.c_double),
+                ("elapsed_s", C.c_double), ("peak_inflight_bytes", C.c_int64),
+                ("mem_budget", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lock = threading.Lock()
@@ -93,6 +109,13 @@ def load(build_if_stale: bool = True):
                                                  _vp]),
             "mask_kmeans_update_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp, _vp,
                                                  _vp, _vp]),
+            "mask_server_open": (C.c_int, [_vp, _i64, _i32, _i32, _vp]),
+            "mask_server_submit": (C.c_int, [_vp, _vp, _i64, _i32, _vp, C.c_int, _vp, _vp,
+                                             C.POINTER(C.c_uint64)]),
+            "mask_server_poll": (C.c_int, [_vp, _u64]),
+            "mask_server_wait": (C.c_int, [_vp, _u64, _i32]),
+            "mask_server_stats": (C.c_int, [_vp, C.POINTER(mask_server_info), _i32]),
+            "mask_server_close": (None, [_vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -381,6 +404,87 @@ def mask_kmeans_update_csr(row_ptr, col, val, n_cols: int, labels, C_prev, strea
     _check(load().mask_kmeans_update_csr(prp, pcl, pvl, n, n_cols, pl, k, pc, pn, pcnt,
                                          _stream(rp, stream)), "mask_kmeans_update_csr")
     return Cn, cnt
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """Continuous-batching query service over a resident dense index (host
+    queries in, host ids/dists out).  submit() returns a Ticket whose
+    result() waits for the answer."""
+
+    def __init__(self, index, mem_budget: int, max_slots: int = 4, max_batch: int = 4096):
+        self._index = index          # the index must outlive the server
+        self._live = {}              # ticket -> arrays the worker writes into
+        out = C.c_void_p()
+        _check(load().mask_server_open(_handle(index), int(mem_budget), max_slots, max_batch,
+                                       C.byref(out)), "mask_server_open")
+        self.handle = out
+
+    def submit(self, queries, k: int, probes, precision: int = MASK_FP32) -> "Ticket":
+        Q = np.ascontiguousarray(queries, dtype=np.float32)
+        nq = Q.shape[0]
+        pr, pp = _host_i32(probes)
+        ids = np.empty((nq, k), dtype=np.int64)
+        dists = np.empty((nq, k), dtype=np.float32)
+        t = C.c_uint64()
+        _check(load().mask_server_submit(self.handle, Q.ctypes.data, nq, k, pp, precision,
+                                         ids.ctypes.data, dists.ctypes.data, C.byref(t)),
+               "mask_server_submit")
+        self._live[t.value] = (ids, dists)
+        return Ticket(self, t.value, ids, dists)
+
+    def stats(self, reset: bool = False) -> dict:
+        info = mask_server_info()
+        _check(load().mask_server_stats(self.handle, C.byref(info), 1 if reset else 0),
+               "mask_server_stats")
+        return info.as_dict()
+
+    def close(self) -> None:
+        """Finishes every queued request (their arrays are filled), then frees."""
+        if self.handle and self.handle.value:
+            load().mask_server_close(self.handle)
+            self.handle = C.c_void_p(None)
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ticket:
+    def __init__(self, server: Server, ticket: int, ids, dists):
+        self.server, self.ticket, self.ids, self.dists = server, ticket, ids, dists
+        self.done = False
+
+    def poll(self) -> bool:
+        if self.done:
+            return True
+        st = load().mask_server_poll(self.server.handle, self.ticket)
+        if st == MASK_PENDING:
+            return False
+        self.done = True
+        self.server._live.pop(self.ticket, None)
+        _check(st, "mask_server_poll")
+        return True
+
+    def result(self, timeout_ms: int = -1):
+        if not self.done:
+            st = load().mask_server_wait(self.server.handle, self.ticket, timeout_ms)
+            if st == MASK_PENDING:
+                raise TimeoutError("request still running")
+            self.done = True
+            self.server._live.pop(self.ticket, None)
+            _check(st, "mask_server_wait")
+        return self.ids, self.dists
 
 
 # ------------------------------------------------------------ observability
