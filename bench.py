@@ -54,7 +54,8 @@ WORKLOADS = {
     "sparse1m": dict(n=1_000_000, d=20_000, nnz_mean=60.0, kind="sparse", k_per_level=[4096, 64],
                      iters=10, nq=5_000, k=10, probes=[16, 4],
                      ladder=[[16, 4], [24, 6], [32, 8], [48, 8], [64, 12], [96, 16], [128, 24],
-                             [192, 32], [256, 48], [384, 64]],
+                             [192, 32], [256, 48], [384, 64], [512, 64], [768, 64], [1024, 64],
+                             [1536, 64], [2048, 64]],
                      desc="1M CSR rows x 20000 (nnz log-normal mean 60 sigma 0.8, Zipf(1.0) "
                           "columns, |N(0,1)| values, rows L2-normalised), index 4096/64, 10 Lloyd "
                           "iters, 5k CSR queries, k=10, probes 16/4"),
@@ -63,6 +64,12 @@ WORKLOADS = {
                          ladder=[[8, 4], [16, 4], [32, 8], [64, 16], [128, 16]],
                          desc="50k CSR rows x 20000 (as sparse1m), index 256/16, 10 Lloyd iters, "
                               "1k CSR queries, k=10, probes 8/4"),
+    "serving": dict(n=20_000, d=16, blobs=10, kind="serving", k_per_level=[200, 20], iters=20,
+                    nq=20_000, k=10, probes=[3, 3],
+                    desc="open-loop Poisson requests on the resident 20k x 16 index (10 blobs, "
+                         "200/20): batch ~ U[1,512], k in {1,10,100}, probes ~ U{P..P+2} x "
+                         "U{3..5}, arrival rates 0.1/0.25/0.5/0.75/0.95 x saturation; FP32, "
+                         "BF16, FP8 (+ FP32 re-rank)"),
     "small": dict(n=20_000, d=16, blobs=10, kind="isotropic", k_per_level=[200, 20], iters=20,
                   nq=1_000, k=10, probes=[3, 3],
                   ladder=[[3, 3], [6, 4], [10, 6], [16, 8], [24, 10], [40, 14], [64, 20]],
@@ -77,12 +84,14 @@ CPU_SAMPLE = {
     "dense10m": dict(n=100_000, k_per_level=[328, 10], nq=1000),
     "sparse1m": dict(n=2_000, k_per_level=[8, 2], nq=100),
     "sparse_small": dict(n=2_000, k_per_level=[8, 2], nq=100),
+    "serving": dict(n=20_000, k_per_level=[200, 20], nq=1000),
     "small": dict(n=20_000, k_per_level=[200, 20], nq=1000),
 }
 REF_SAMPLE = {
     "dense10m": dict(n=50_000, k_per_level=[164, 5], nq=1000),
     "sparse1m": dict(n=2_000, k_per_level=[8, 2], nq=100),
     "sparse_small": dict(n=2_000, k_per_level=[8, 2], nq=100),
+    "serving": dict(n=20_000, k_per_level=[200, 20], nq=1000),
     "small": dict(n=20_000, k_per_level=[200, 20], nq=1000),
 }
 
@@ -101,6 +110,9 @@ def log(*a):
 def make_data(w, rank=0):
     """Points and queries: dense arrays, or synth.CSR for the sparse workloads."""
     from paper_2208_02734_gb300 import synth
+    if w["kind"] == "serving":
+        mix = synth.IsotropicMixture(d=w["d"], n_blobs=w["blobs"], sigma=1.0, box=10.0, seed=0)
+        return mix.sample(w["n"], seed=2 * rank), mix.sample(w["nq"], seed=2 * rank + 1)
     if w["kind"] == "sparse":
         A = synth.sparse_tfidf_like(w["n"], w["d"], nnz_mean=w["nnz_mean"], seed=2 * rank)
         Qa = synth.sparse_tfidf_like(w["nq"], w["d"], nnz_mean=w["nnz_mean"], seed=2 * rank + 1)
@@ -570,9 +582,146 @@ def run_ours_sparse(args, w, wname):
     return 0
 
 
+def serving_requests(rng, Q, n, P, lowp):
+    """Requests of the serving workload: batch ~ U[1,512] queries, k in
+    {1, 10, 100}, probes ~ U{P..P+2} x U{3..5}.  In the BF16/FP8 runs a
+    request with k = 100 (shortlist 400, beyond the low-precision scan) runs
+    in FP32."""
+    out = []
+    for _ in range(n):
+        nq = int(rng.integers(1, 513))
+        q0 = int(rng.integers(0, len(Q) - nq))
+        k = int(rng.choice([1, 10, 100]))
+        probes = [int(rng.integers(P, P + 3)), int(rng.integers(3, 6))]
+        out.append((q0, nq, k, probes, lowp if k <= 16 else 0))
+    return out
+
+
+def run_serving(args, w, wname):
+    """Serving workload: continuous batching (mask_server_*) on the resident
+    small index; saturation throughput, then open-loop Poisson arrivals at
+    five fractions of it, per precision mode."""
+    import torch
+    from paper_2208_02734_gb300 import mask as M
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    M.load()
+    X, Q = make_data(w, 0)
+    Xd, Qd = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    idx = M.mask_build(Xd, w["k_per_level"], w["iters"], seed=0)
+    rng = np.random.default_rng(0)
+    # recall of a probe range on 1000 queries (FP32, k = 10) vs FP64 exact k-NN
+    sub = torch.arange(0, 1000, device=dev)
+    _, gt = exact_knn_fp64(Xd, Qd[sub], 10)
+    dk = gt[:, -1:]
+    P, rec = None, 0.0
+    for P_try in (3, 4, 6, 8, 12, 16, 24, 32, 48, 64):
+        ids = torch.empty((1000, 10), dtype=torch.int64, device=dev)
+        for i in range(0, 1000, 50):
+            pr = [int(rng.integers(P_try, P_try + 3)), int(rng.integers(3, 6))]
+            ids[i:i + 50] = M.mask_query(idx, Qd[i:i + 50], 10, pr)[0]
+        rec = recall_at_k(Xd, Qd[sub], ids, dk)
+        if rec >= 0.95:
+            P = P_try
+            break
+    if P is None:
+        P = 64
+    log(f"[serving] probes U{{{P}..{P + 2}}} x U{{3..5}}: recall@10 {rec:.4f}")
+    secs = args.serve_seconds
+    modes = {"fp32": M.MASK_FP32, "bf16": M.MASK_BF16, "fp8": M.MASK_FP8E4M3}
+    out = {}
+    lc0 = M.mask_launch_count()
+    for mname, prec in modes.items():
+        srv = M.Server(idx, mem_budget=2 << 30, max_slots=4, max_batch=4096)
+
+        def submit(r):
+            q0, nq, k, probes, pr = r
+            return srv.submit(Q[q0:q0 + nq], k, probes, pr), r
+
+        # warm-up: capture the graphs of the shapes the stream will use
+        warm = serving_requests(rng, Q, 400, P, prec)
+        for t, _ in [submit(r) for r in warm]:
+            t.result()
+        # saturation: a backlog submitted at once
+        srv.stats(reset=True)
+        sat = serving_requests(rng, Q, 800, P, prec)
+        t0 = time.perf_counter()
+        done = [submit(r) for r in sat]
+        for t, _ in done:
+            t.result()
+        t_sat = time.perf_counter() - t0
+        st = srv.stats(reset=True)
+        sat_qps = st["queries_done"] / t_sat
+        mean_q = st["queries_done"] / max(1, st["requests_done"])
+        # recall of the served results (k = 10 requests of this run)
+        hits, tot = 0, 0
+        for t, r in done:
+            q0, nq, k, probes, pr = r
+            if k != 10:
+                continue
+            ids = torch.from_numpy(t.ids).to(dev)
+            qq = Qd[q0:q0 + nq]
+            _, g = exact_knn_fp64(Xd, qq, 10)
+            hits += recall_at_k(Xd, qq, ids, g[:, -1:]) * ids.numel()
+            tot += ids.numel()
+        rates = []
+        for frac in (0.1, 0.25, 0.5, 0.75, 0.95):
+            lam = frac * sat_qps / mean_q       # requests per second
+            reqs = serving_requests(rng, Q, int(lam * secs * 1.2) + 10, P, prec)
+            arr = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+            srv.stats(reset=True)
+            tickets = []
+            start = time.perf_counter()
+            for r, ta in zip(reqs, arr):
+                if ta > secs:
+                    break
+                delay = start + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(submit(r))
+            for t, _ in tickets:
+                t.result()
+            st = srv.stats(reset=True)
+            rates.append({"offered_fraction": frac, "offered_qps": frac * sat_qps,
+                          "achieved_qps": st["queries_done"] / max(1e-9, st["elapsed_s"]),
+                          "requests": st["requests_done"], "p50_ms": st["latency_p50_ms"],
+                          "p99_ms": st["latency_p99_ms"], "max_ms": st["latency_max_ms"],
+                          "mean_batch_queries": st["mean_batch_queries"],
+                          "peak_inflight_mb": st["peak_inflight_bytes"] / 2 ** 20})
+            log(f"[serving] {mname} {frac:.2f}: {rates[-1]['achieved_qps']:.0f} q/s "
+                f"p50 {st['latency_p50_ms']:.2f} ms p99 {st['latency_p99_ms']:.2f} ms")
+        info = srv.stats()
+        srv.close()
+        out[mname] = {"saturation_qps": sat_qps, "recall_at_10": hits / max(1, tot),
+                      "rates": rates, "graph_captures": info["graph_captures"],
+                      "autotuned_shapes": info["autotuned_shapes"],
+                      "k100_requests_in_fp32": mname != "fp32"}
+    launches = M.mask_launch_count() - lc0
+    idx.free()
+    fp = out["fp32"]
+    line = {"metric": METRIC, "value": fp["saturation_qps"], "unit": "queries/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["desc"], "probes_P": P, "recall_at_10_calibration": rec,
+                       "seconds_per_rate": secs, "mem_budget_bytes": 2 << 30, "max_slots": 4,
+                       "max_batch": 4096},
+            "serving": out, "gpu_launches": int(launches),
+            "latency_note": "submit -> completion on the host, per request"}
+    if not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(X, Q, w, wname)
+        except Exception as ex:  # report, do not hide, a baseline failure
+            line["cpu_baseline"] = {"error": repr(ex)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, w, wname):
     if w["kind"] == "sparse":
         return run_ours_sparse(args, w, wname)
+    if w["kind"] == "serving":
+        return run_serving(args, w, wname)
     import torch
     import torch.distributed as dist
     from paper_2208_02734_gb300 import mask as M
@@ -776,6 +925,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowp", action="store_true", help="skip the BF16/FP8 query modes")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="serving workload: seconds of arrivals per rate")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
