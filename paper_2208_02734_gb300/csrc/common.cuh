@@ -292,7 +292,7 @@ bool lp_supported(int dp, int k);
 void lp_quantize(const float *src, int64_t rows, int dp, bool fp8, void *dst, float *scale,
                  float *norm2, cudaStream_t s);
 void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscale, const float *Xs,
-                  int dp, const int32_t *xids, const int64_t *leaf_off, int k0, const float *Qp,
+                  int64_t leaf_rows, int dp, const int32_t *xids, const int64_t *leaf_off, int k0, const float *Qp,
                   int64_t nq, const int32_t *sel, int P, int k, int64_t *ids, float *dists,
                   cudaStream_t s);
 

@@ -513,7 +513,7 @@ void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
         const int slot = fp8 ? 1 : 0;
         MASK_REQUIRE(idx.Xlp[slot].p != nullptr, "low-precision copy missing");
         lp_leaf_scan(fp8, idx.Xlp[slot].get(), idx.xn_lp[slot].get(),
-                     fp8 ? idx.xscale_fp8.get() : nullptr, idx.Xs.get(), dp, idx.xids.get(),
+                     fp8 ? idx.xscale_fp8.get() : nullptr, idx.Xs.get(), idx.n, dp, idx.xids.get(),
                      idx.lv[0].off.get(), k0, Qp, nq, sel[0].get(), p[0], k, ids, dists, s);
         return;
     }

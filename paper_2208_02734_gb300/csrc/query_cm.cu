@@ -284,6 +284,9 @@ void cm_leaf_scan(const float *Xs, int dp, const int32_t *xids, const int64_t *l
     Scratch<int32_t> pairs;
     Scratch<int64_t> poff, item_off;
     Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
+    // pairs of an absent parent (sel = -1, fewer children than probes) are in
+    // no work item: their lists stay empty
+    MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
     cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
     {
         ProfRegion pr("scan_leaf_cm", s, 0.0);

@@ -331,7 +331,7 @@ __global__ __launch_bounds__(256) void lp_shortlist_kernel(
 __global__ __launch_bounds__(256) void lp_rerank_kernel(
     const float4 *__restrict__ Xs, int dp4, const int32_t *__restrict__ xids,
     const float4 *__restrict__ Qp, const int32_t *__restrict__ shortlist, int64_t nq, int Kp,
-    int k, int64_t *__restrict__ ids, float *__restrict__ dists) {
+    int k, int64_t n_rows, int64_t *__restrict__ ids, float *__restrict__ dists) {
     const int lane = threadIdx.x & 31;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (q >= nq) return;
@@ -342,7 +342,7 @@ __global__ __launch_bounds__(256) void lp_rerank_kernel(
         const int j = lane + 32 * h;
         if (j >= Kp) continue;
         const int32_t p = shortlist[q * Kp + j];
-        if (p < 0) continue;
+        if (p < 0 || p >= n_rows) continue;
         const float4 *row = Xs + (int64_t)p * dp4;
         float acc = 0.f;
         for (int c = 0; c < dp4; ++c) {
@@ -398,7 +398,7 @@ void lp_quantize(const float *src, int64_t rows, int dp, bool fp8, void *dst, fl
 }
 
 void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscale, const float *Xs,
-                  int dp, const int32_t *xids, const int64_t *leaf_off, int k0, const float *Qp,
+                  int64_t leaf_rows, int dp, const int32_t *xids, const int64_t *leaf_off, int k0, const float *Qp,
                   int64_t nq, const int32_t *sel, int P, int k, int64_t *ids, float *dists,
                   cudaStream_t s) {
     if (nq == 0) return;
@@ -415,6 +415,9 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
     Scratch<int64_t> poff, item_off;
     cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
     Scratch<unsigned long long> pair_out((size_t)nq * P * Kpair, s);
+    // pairs of an absent parent (sel = -1, fewer children than probes) are in
+    // no work item: their lists stay empty
+    MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * nq * P * Kpair, s));
     Scratch<int32_t> shortlist((size_t)nq * Kp, s);
     {
         ProfRegion pr(fp8 ? "scan_leaf_fp8" : "scan_leaf_bf16", s, 0.0);
@@ -444,7 +447,8 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
         MASK_LAUNCHED("lp_shortlist");
         lp_rerank_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4 *>(Xs), dp / 4, xids,
                                                 reinterpret_cast<const float4 *>(Qp),
-                                                shortlist.get(), nq, Kp, k, ids, dists);
+                                                shortlist.get(), nq, Kp, k, leaf_rows, ids,
+                                                dists);
         MASK_LAUNCHED("lp_rerank");
     }
 }

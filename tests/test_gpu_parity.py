@@ -206,6 +206,33 @@ def test_query_matches_oracle(monkeypatch, loaded, leaf, k, probes):
     assert loose <= 0.01 * len(Q)
 
 
+@pytest.mark.parametrize("leaf", ["query", "cluster"])
+def test_probes_beyond_the_children_kept(monkeypatch, loaded, leaf):
+    # one top centroid kept (about 10 children) but 60 leaf probes: most of a
+    # query's leaf slots are absent (-1) and must contribute nothing
+    monkeypatch.setenv("MASK_LEAF_SCAN", leaf)
+    X, Q, ref, idx = loaded
+    ids_o, d_o, clear = ref.query(Q, 10, [60, 1])
+    ids_g, d_g = M.mask_query(idx, cuda(Q), 10, [60, 1])
+    loose = check_knn(X, Q, ids_g, d_g, ids_o, d_o, clear)
+    assert loose <= 0.01 * len(Q)
+
+
+@pytest.mark.parametrize("prec", [M.MASK_BF16, M.MASK_FP8E4M3])
+def test_low_precision_probes_beyond_the_children_kept(loaded, prec):
+    X, Q, ref, idx = loaded
+    ids_f, _ = M.mask_query(idx, cuda(Q), 10, [60, 1])
+    ids_l, d_l = M.mask_query(idx, cuda(Q), 10, [60, 1], precision=prec)
+    ids_f, ids_l, d_l = arr(ids_f), arr(ids_l), arr(d_l)
+    assert ids_l.min() >= -1 and ids_l.max() < len(X)
+    for q in range(0, len(Q), 25):
+        ok = ids_l[q] >= 0
+        check_close(d_l[q][ok], O.sqdist_rows(X, ids_l[q][ok], Q[q]), rtol=RTOL, atol=1e-30,
+                    what=f"re-ranked distances q={q}")
+    overlap = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids_f, ids_l)])
+    assert overlap >= 0.9, overlap
+
+
 def test_leaf_scan_paths_agree_bitwise(monkeypatch, loaded):
     # both leaf scans evaluate sum_t (x_t - q_t)^2 in the same order
     X, Q, ref, idx = loaded

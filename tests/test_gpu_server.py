@@ -31,10 +31,10 @@ def c1_index():
     idx.free()
 
 
-def mixed_requests(Q, n_req, seed, precisions=(M.MASK_FP32, M.MASK_BF16, M.MASK_FP8E4M3)):
+def mixed_requests(Q, n_req, seed, precisions=(M.MASK_FP32, M.MASK_BF16, M.MASK_FP8E4M3), P=3):
     """Requests shaped like the serving workload: batch ~ U[1, 512], k in
-    {1, 10, 100}, probes ~ U{3..5} per level, mixed precision (k <= 16 for the
-    low-precision modes)."""
+    {1, 10, 100}, probes ~ U{P..P+2} x U{3..5}, mixed precision (k <= 16 for
+    the low-precision modes)."""
     rng = np.random.default_rng(seed)
     reqs = []
     for _ in range(n_req):
@@ -42,7 +42,7 @@ def mixed_requests(Q, n_req, seed, precisions=(M.MASK_FP32, M.MASK_BF16, M.MASK_
         q0 = int(rng.integers(0, len(Q) - nq))
         prec = int(rng.choice(precisions))
         k = int(rng.choice([1, 10, 100] if prec == M.MASK_FP32 else [1, 10, 16]))
-        probes = [int(rng.integers(3, 6)), int(rng.integers(3, 6))]
+        probes = [int(rng.integers(P, P + 3)), int(rng.integers(3, 6))]
         reqs.append((Q[q0:q0 + nq], k, probes, prec))
     return reqs
 
@@ -54,9 +54,11 @@ def alone(idx, req):
     return ids.cpu().numpy(), d.cpu().numpy()
 
 
-def test_results_are_the_same_alone_and_in_the_mix(c1_index):
+@pytest.mark.parametrize("P", [3, 12, 40])
+def test_results_are_the_same_alone_and_in_the_mix(c1_index, P):
+    # P >= 12: some queries keep fewer leaf clusters than probed (absent slots)
     X, Q, idx = c1_index
-    reqs = mixed_requests(Q, 120, seed=0)
+    reqs = mixed_requests(Q, 120, seed=P, P=P)
     want = [alone(idx, r) for r in reqs]
     with M.Server(idx, mem_budget=256 << 20, max_slots=4, max_batch=1024) as srv:
         tickets = [None] * len(reqs)
