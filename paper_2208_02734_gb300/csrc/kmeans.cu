@@ -523,6 +523,7 @@ __device__ __forceinline__ void csr_row_ab(const int64_t b, const int64_t e,
                                            int gl, float &A, float &B) {
     A = 0.f;
     B = 0.f;
+#pragma unroll 4
     for (int64_t j = b + gl; j < e; j += kKppGroup) {
         const float cv = cden[__ldg(col + j)];
         const float e0 = __ldg(val + j) - cv;
@@ -570,49 +571,17 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_csr_kernel(
     const float cn = s_cn;
     const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
     double local = 0.0;
-    // four rows in flight per lane group; lane gl takes nonzeros gl, gl+8, ...
-    // of each row, exactly as csr_row_ab (so a row equal to the centre gets 0)
-    constexpr int F = 4;
 #pragma unroll 1
-    for (int q0 = 0; q0 < kKppRows / G; q0 += F) {
-        int64_t b[F];
-        int len[F];
-        int maxlen = 0;
-        float A[F], B[F];
-#pragma unroll
-        for (int u = 0; u < F; ++u) {
-            const int64_t i = r0 + g + (int64_t)(q0 + u) * G;
-            const bool ok = i < m;  // a row past the end is empty; every lane reaches the shuffles
-            b[u] = ok ? rp[i] : 0;
-            len[u] = ok ? (int)(rp[i + 1] - b[u]) : 0;
-            maxlen = max(maxlen, len[u]);
-            A[u] = 0.f;
-            B[u] = 0.f;
-        }
-        for (int j = gl; j < maxlen; j += kKppGroup) {
-#pragma unroll
-            for (int u = 0; u < F; ++u) {
-                if (j >= len[u]) continue;
-                const float cv = cden[__ldg(col + b[u] + j)];
-                const float e0 = __ldg(val + b[u] + j) - cv;
-                A[u] = fmaf(e0, e0, A[u]);
-                B[u] = fmaf(cv, cv, B[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < F; ++u) {
-#pragma unroll
-            for (int o = kKppGroup / 2; o > 0; o >>= 1) {
-                A[u] += __shfl_xor_sync(kFull, A[u], o, kKppGroup);
-                B[u] += __shfl_xor_sync(kFull, B[u], o, kKppGroup);
-            }
-            const int64_t i = r0 + g + (int64_t)(q0 + u) * G;
-            if (i < m && gl == 0) {
-                const float v = A[u] + fmaxf(cn - B[u], 0.f);
-                const float d2 = t > 1 ? fminf(D2[i], v) : v;
-                D2[i] = d2;
-                local += (double)d2;
-            }
+    for (int q = 0; q < kKppRows / G; ++q) {
+        const int64_t i = r0 + g + (int64_t)q * G;
+        const bool ok = i < m;  // every lane reaches the shuffles; a row past the end is empty
+        float A, B;
+        csr_row_ab(ok ? rp[i] : 0, ok ? rp[i + 1] : 0, col, val, cden, gl, A, B);
+        if (ok && gl == 0) {
+            const float v = A + fmaxf(cn - B, 0.f);
+            const float d2 = t > 1 ? fminf(D2[i], v) : v;
+            D2[i] = d2;
+            local += (double)d2;
         }
     }
     if (!kpp_block_done(local, red, bsum, counter, &s_last)) return;
