@@ -105,8 +105,8 @@ mask_status mask_build(const float *points, int64_t n, int32_t d,
  * product with the argmin fused (rows whose best two centroids are closer
  * than the FP32 rounding bound are re-decided in FP64).  The levels above run
  * on the level-0 centroids as dense rows, exactly as in mask_build.
- * d <= 40960 (k-means++ and the leaf scan stage a dense row in shared
- * memory), else MASK_EUNSUPPORTED; malformed CSR arrays give MASK_EINVAL.
+ * d <= 40960 (k-means++ stages a dense row in shared memory), else
+ * MASK_EUNSUPPORTED; malformed CSR arrays give MASK_EINVAL.
  * Query the index with mask_query_csr.  Synchronises `stream`.
  */
 mask_status mask_build_csr(const int64_t *row_ptr, const int32_t *col, const float *val,

@@ -144,8 +144,8 @@ inline int lanes_per_row(int dp) {
 
 constexpr uint64_t kNoKey = ~0ull;
 
-// Largest dimension of CSR inputs: k-means++ and the leaf scan hold one dense
-// row of it in shared memory.
+// Largest dimension of CSR inputs: k-means++ holds one dense row of it in
+// shared memory.
 constexpr int kCsrMaxDim = 40960;
 
 // ------------------------------------------------------ kernel launchers
@@ -226,12 +226,13 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
 // bytes the CSR scans read since the last reset ([0] levels, [1] leaf)
 double csr_scan_bytes(int which);
 void csr_scan_bytes_reset();
-// leaf scan: CSR point rows (cluster-major) against the query as a dense row
-size_t csr_leaf_scan_smem(int K, int P, int dp);
+// leaf scan: CSR point rows (cluster-major) against the query's nonzeros held
+// in a shared-memory table sized for the longest query (`longest` nonzeros)
+size_t csr_leaf_scan_smem(int K, int P, int longest);
 void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                    const int32_t *xids, const int64_t *off, const int32_t *sel, int P,
-                   const int64_t *qrp, const int32_t *qcol, const float *qval, int dp, int64_t nq,
-                   int K, int64_t *out64, float *out_d, cudaStream_t s);
+                   const int64_t *qrp, const int32_t *qcol, const float *qval, int longest,
+                   int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s);
 
 // assign.cu -- labels[i] = argmin_j ||x_i - c_j||^2 (ties to the smallest j)
 void assign_labels(const float *X, const float *xn, int64_t n, int dp, const float *C, int k,

@@ -772,7 +772,7 @@ mask_status mask_query_csr(const mask_index *index, const int64_t *row_ptr, cons
         }
         csr_leaf_scan(index->xrp.get(), index->xcol.get(), index->xval.get(), index->xids.get(),
                       index->lv[0].off.get(), sel[0].get(), p[0], in.rp->p, in.col->p, in.val->p,
-                      dp, nq, k, ids.p, dd.p, s);
+                      qcap, nq, k, ids.p, dd.p, s);
         ids.finish(s);
         dd.finish(s);
         MASK_CUDA(cudaStreamSynchronize(s));  // the staged CSR copies are released on return

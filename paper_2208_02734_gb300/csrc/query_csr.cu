@@ -9,9 +9,10 @@
 //      ||q - c||^2 = sum_{t in q} (q_t - c_t)^2 + (||c||^2 - sum_{t in q} c_t^2),
 //    the second term being c's mass off the query's support (FP64 norm of c,
 //    rounded once; clamped at 0);
-//  * leaf scan: the query is scattered into a dense row in shared memory and
-//    each point (a CSR row of the cluster-major point matrix) reads it at its
-//    own nonzeros:
+//  * leaf scan: the query's nonzeros go into a small open-addressing table in
+//    shared memory (column -> value, at most a quarter full) and each point (a
+//    CSR row of the cluster-major point matrix) looks the query up at its own
+//    nonzeros (q_t, or 0 where the query has no entry):
 //      ||x - q||^2 = sum_{t in x} (x_t - q_t)^2 + (||q||^2 - sum_{t in x} q_t^2),
 //    where ||q||^2 is summed by the same lane-group procedure over q's own
 //    nonzeros, so a point equal to the query gets exactly 0.
@@ -203,19 +204,37 @@ __global__ __launch_bounds__(kThreads) void csr_level_scan_kernel(
 
 // ------------------------------------------------------------- leaf scan
 
+// Open-addressing table of a query's nonzeros: H slots (a power of two),
+// linear probing from a multiplicative hash; key -1 = empty.
+__device__ __forceinline__ unsigned qhash(int32_t col, unsigned mask) {
+    return ((unsigned)col * 0x9E3779B1u) & mask;
+}
+
+__device__ __forceinline__ float qlookup(const int32_t *keys, const float *vals, unsigned mask,
+                                         int32_t col) {
+    unsigned h = qhash(col, mask);
+    for (;;) {
+        const int32_t k = keys[h];
+        if (k == col) return vals[h];
+        if (k < 0) return 0.f;
+        h = (h + 1) & mask;
+    }
+}
+
 __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     const int64_t *__restrict__ xrp, const int32_t *__restrict__ xcol,
     const float *__restrict__ xval, const int32_t *__restrict__ xids,
     const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P,
     const int64_t *__restrict__ qrp, const int32_t *__restrict__ qcol,
-    const float *__restrict__ qval, int dp, int K, int KP, int S, int64_t *__restrict__ out64,
-    float *__restrict__ out_d) {
+    const float *__restrict__ qval, int hslots, int K, int KP, int S,
+    int64_t *__restrict__ out64, float *__restrict__ out_d) {
     extern __shared__ __align__(16) unsigned char smem[];
     ScanSmem sm;
     sm.buf = reinterpret_cast<unsigned long long *>(smem);
     sm.rb = reinterpret_cast<int64_t *>(sm.buf + S);
     sm.cum = sm.rb + P;
-    float *qd = reinterpret_cast<float *>(sm.cum + P + 2);  // [dp] dense query
+    int32_t *hkey = reinterpret_cast<int32_t *>(sm.cum + P + 2);  // [hslots] query table
+    float *hval = reinterpret_cast<float *>(hkey + hslots);
     __shared__ int cnt;
     __shared__ unsigned long long thresh;
     __shared__ float s_qn;
@@ -224,7 +243,11 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     const int tid = threadIdx.x;
     const int64_t q = blockIdx.x;
     const int64_t qb = qrp[q], qe = qrp[q + 1];
-    for (int i = tid; i < dp; i += kThreads) qd[i] = 0.f;
+    // this query's table: the smallest power of two >= 4 x its nonzeros (>= 32)
+    unsigned hsize = 32;
+    while ((int64_t)hsize < 4 * (qe - qb) && (int)hsize < hslots) hsize <<= 1;
+    const unsigned hmask = hsize - 1;
+    for (int i = tid; i < (int)hsize; i += kThreads) hkey[i] = -1;
     for (int i = tid; i < S; i += kThreads) sm.buf[i] = kNoKey;
     if (tid == 0) {
         cnt = 0;
@@ -233,14 +256,20 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     }
     setup_ranges(sm, off, sel, P, 0, q);
     __syncthreads();
-    for (int64_t j = qb + tid; j < qe; j += kThreads) qd[qcol[j]] = qval[j];
+    for (int64_t j = qb + tid; j < qe; j += kThreads) {
+        // column ids of a row are distinct, so every insert claims its own slot
+        const int32_t c = qcol[j];
+        unsigned h = qhash(c, hmask);
+        while (atomicCAS(hkey + h, -1, c) != -1) h = (h + 1) & hmask;
+        hval[h] = qval[j];
+    }
     __syncthreads();
     const int g = tid / kGroup, gl = tid % kGroup;
     if (tid < 32) {
         // ||q||^2 as B of the query itself (every group of warp 0; shuffles need the warp)
         float A = 0.f, B = 0.f;
         for (int64_t j = qb + gl; j < qe; j += kGroup) {
-            const float c = qd[qcol[j]];
+            const float c = qlookup(hkey, hval, hmask, qcol[j]);
             const float e = qval[j] - c;
             A = fmaf(e, e, A);
             B = fmaf(c, c, B);
@@ -281,7 +310,7 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
             for (int i = 0; i < kInFlight; ++i) {
                 if (j >= len[i]) continue;
                 const float x = __ldg(xval + rb[i] + j);
-                const float c = qd[__ldg(xcol + rb[i] + j)];
+                const float c = qlookup(hkey, hval, hmask, __ldg(xcol + rb[i] + j));
                 const float e = x - c;
                 A[i] = fmaf(e, e, A[i]);
                 B[i] = fmaf(c, c, B[i]);
@@ -341,8 +370,15 @@ size_t csr_level_scan_smem(int K, int P, int qcap) {
     return (size_t)list_size(K) * 8 + (size_t)(2 * P + 2) * 8 + (size_t)qcap * 8;
 }
 
-size_t csr_leaf_scan_smem(int K, int P, int dp) {
-    return (size_t)list_size(K) * 8 + (size_t)(2 * P + 2) * 8 + (size_t)dp * 4;
+int csr_leaf_table_slots(int longest) {
+    int h = 32;
+    while (h < 4 * longest) h <<= 1;
+    return h;
+}
+
+size_t csr_leaf_scan_smem(int K, int P, int longest) {
+    return (size_t)list_size(K) * 8 + (size_t)(2 * P + 2) * 8 +
+           (size_t)csr_leaf_table_slots(longest) * 8;
 }
 
 void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid,
@@ -365,17 +401,18 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
 
 void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                    const int32_t *xids, const int64_t *off, const int32_t *sel, int P,
-                   const int64_t *qrp, const int32_t *qcol, const float *qval, int dp, int64_t nq,
-                   int K, int64_t *out64, float *out_d, cudaStream_t s) {
+                   const int64_t *qrp, const int32_t *qcol, const float *qval, int longest,
+                   int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s) {
     if (nq == 0) return;
     MASK_REQUIRE(K >= 1 && K <= 4096, "csr_leaf_scan: K out of range");
-    const size_t smem = csr_leaf_scan_smem(K, P, dp);
-    MASK_REQUIRE(smem <= 220 * 1024, "csr_leaf_scan: k, probes or dimension too large");
+    const size_t smem = csr_leaf_scan_smem(K, P, longest);
+    MASK_REQUIRE(smem <= 220 * 1024, "csr_leaf_scan: k, probes or query length too large");
     ProfRegion pr("csr_scan_leaf", s, 0.0);
     MASK_CUDA(cudaFuncSetAttribute(csr_leaf_scan_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     csr_leaf_scan_kernel<<<(unsigned)nq, kThreads, smem, s>>>(xrp, xcol, xval, xids, off, sel, P,
-                                                              qrp, qcol, qval, dp, K,
+                                                              qrp, qcol, qval,
+                                                              csr_leaf_table_slots(longest), K,
                                                               next_pow2(K), list_size(K), out64,
                                                               out_d);
     MASK_LAUNCHED("csr_leaf_scan");
