@@ -275,9 +275,11 @@ void scan_bytes_reset();
 
 // query_cm.cu -- cluster-major leaf scan for large batches (K <= 32, dp <= 128)
 bool cm_leaf_supported(int dp, int K);
-void cm_leaf_scan(const float *Xs, int dp, const int32_t *xids, const int64_t *leaf_off, int k0,
-                  const float *Qp, int64_t nq, const int32_t *sel, int P, int K, int64_t *ids,
-                  float *dists, cudaStream_t s);
+// xn [rows] = ||row of Xs||^2 (FP32); the scan evaluates a row exactly only
+// where its expanded-form distance can reach the query's current K-th
+void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
+                  const int64_t *leaf_off, int k0, const float *Qp, int64_t nq,
+                  const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s);
 double cm_bytes();
 void cm_bytes_reset();
 // groups the (query, kept leaf) pairs by leaf cluster; item_off[k0] = work items

@@ -15,6 +15,7 @@ struct mask_index {
     bool sparse = false;
     mask::DevArray<float> Xs;        // [n x dp] points, cluster-major (level-0 parent-major)
     mask::DevArray<int32_t> xids;    // [n] original id of each row of Xs (or of xrp)
+    mask::DevArray<float> xn;        // [n] ||row of Xs||^2 (FP32), for the leaf-scan filter
     // CSR index: the points' rows cluster-major (row i is point xids[i])
     mask::DevArray<int64_t> xrp;     // [n+1]
     mask::DevArray<int32_t> xcol;    // [nnz]

@@ -330,6 +330,8 @@ void finish_levels(mask_index &idx, cudaStream_t s) {
 void finish_layout(mask_index &idx, const float *Xp, cudaStream_t s) {
     idx.Xs.alloc((size_t)idx.n * idx.dp);
     gather_rows<int32_t>(Xp, idx.dp, idx.xids.get(), idx.n, idx.Xs.get(), s);
+    idx.xn.alloc((size_t)idx.n);
+    row_sqnorm(idx.Xs.get(), idx.n, idx.dp, idx.xn.get(), s);
     finish_levels(idx, s);
 }
 
@@ -523,8 +525,8 @@ void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
     if (mode == LeafMode::Cluster) cluster_major = cm_leaf_supported(dp, k);
     if (mode == LeafMode::Query) cluster_major = false;
     if (cluster_major) {
-        cm_leaf_scan(idx.Xs.get(), dp, idx.xids.get(), idx.lv[0].off.get(), k0, Qp, nq, sel[0].get(),
-                     p[0], k, ids, dists, s);
+        cm_leaf_scan(idx.Xs.get(), idx.xn.get(), dp, idx.xids.get(), idx.lv[0].off.get(), k0, Qp,
+                     nq, sel[0].get(), p[0], k, ids, dists, s);
     } else {
         ScanArgs c = a;
         c.R = idx.Xs.get();
@@ -644,7 +646,8 @@ mask_status mask_index_get_info(const mask_index *index, mask_index_info *out) {
         out->n_levels = index->L;
         out->iters = index->iters;
         out->sparse = index->sparse ? 1 : 0;
-        int64_t bytes = (int64_t)(index->Xs.bytes() + index->xids.bytes() + index->xrp.bytes() +
+        int64_t bytes = (int64_t)(index->Xs.bytes() + index->xids.bytes() + index->xn.bytes() +
+                                  index->xrp.bytes() +
                                   index->xcol.bytes() + index->xval.bytes());
         for (int q = 0; q < 2; ++q) bytes += (int64_t)(index->Xlp[q].bytes() + index->xn_lp[q].bytes());
         bytes += (int64_t)index->xscale_fp8.bytes();

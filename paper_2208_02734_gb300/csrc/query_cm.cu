@@ -9,9 +9,16 @@
 // of the group are computed from shared memory.  Each pair leaves its K best
 // keys; a merge pass then keeps every query's K best over its kept clusters.
 //
-// Distances use the same arithmetic as query.cu (one thread per (row, query)
-// pair, sum_t (r_t - q_t)^2 in increasing t with FMAs), so a query's result is
-// the same whichever kernel served it and whatever else is in the batch.
+// Every key that can enter a result is computed with the arithmetic of
+// query.cu (one thread per (row, query) pair, sum_t (r_t - q_t)^2 in
+// increasing t with FMAs), so a query's result is the same whichever kernel
+// served it and whatever else is in the batch.  The scan first ranks rows by
+// the cheaper expanded form ||x||^2 + ||q||^2 - 2 x.q (one FMA per dimension)
+// and evaluates a row exactly only where that value, less its rounding bound,
+// can reach the smaller of the pair's current K-th distance and T_q -- the K-th
+// exact distance within the query's nearest kept cluster (a seed pass), which
+// bounds the query's final K-th from above.  Rows the test drops cannot be
+// among the query's K nearest, so the result equals the full exact scan's.
 #include <algorithm>
 #include <climits>
 
@@ -37,6 +44,14 @@ __device__ __forceinline__ unsigned long long umin64(unsigned long long a,
 __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v = umin64(v, __shfl_xor_sync(kFull, v, o));
     return v;
+}
+
+// out[q] = sel[q * P] (each query's nearest kept cluster, or -1)
+__global__ void first_col_kernel(const int32_t *__restrict__ sel, int64_t nq, int P,
+                                 int32_t *__restrict__ out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = sel[q * P];
 }
 
 // labels for grouping: the kept cluster of each pair, or k0 for "none"
@@ -75,22 +90,27 @@ __global__ void __launch_bounds__(1024) item_scan_kernel(const int64_t *__restri
     if (tid == 1023) item_off[k0] = part[1023];
 }
 
-// One work item = (cluster c, up to CM_QB of its pairs).
+// One work item = (cluster c, up to CM_QB of its pairs).  xn: row norms;
+// qn: query norms; seed_d [nq x K]: each query's K nearest distances within
+// its nearest kept cluster (the K-th is T_q); mcoef: rounding bound of
+// |expanded form - exact key| per unit of ||x||^2 + ||q||^2.
 __global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
-    const float4 *__restrict__ Xs, int dp4, const int32_t *__restrict__ xids,
-    const int64_t *__restrict__ leaf_off, const float4 *__restrict__ Qp, int P,
-    const int64_t *__restrict__ poff, const int32_t *__restrict__ pairs,
-    const int64_t *__restrict__ item_off, int k0, int K,
+    const float4 *__restrict__ Xs, const float *__restrict__ xn, int dp4,
+    const int32_t *__restrict__ xids, const int64_t *__restrict__ leaf_off,
+    const float4 *__restrict__ Qp, const float *__restrict__ qn,
+    const float *__restrict__ seed_d, float mcoef, int P, const int64_t *__restrict__ poff,
+    const int32_t *__restrict__ pairs, const int64_t *__restrict__ item_off, int k0, int K,
     unsigned long long *__restrict__ pair_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int dp = dp4 * 4;
     float *xs = reinterpret_cast<float *>(smem);                 // [dp][CM_R] rows, transposed
     float *qs = xs + (size_t)dp * CM_R;                          // [dp][CM_QB] queries, transposed
-    float *D = qs + (size_t)dp * CM_QB;                          // [CM_QB][CM_R] distances
+    float *D = qs + (size_t)dp * CM_QB;                          // [CM_QB][CM_R] expanded-form distances
     int32_t *ids = reinterpret_cast<int32_t *>(D + CM_QB * CM_R);// [CM_R] row ids
     unsigned long long *top = reinterpret_cast<unsigned long long *>(ids + CM_R);  // [CM_QB][K]
     __shared__ int s_c;
     __shared__ int64_t s_pb, s_pe;
+    __shared__ float s_xn[CM_R], s_qn[CM_QB], s_tq[CM_QB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n_items = item_off[k0];
@@ -121,6 +141,16 @@ __global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
             qs[(c4 * 4 + 3) * CM_QB + qb] = v.w;
         }
         for (int i = tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
+        if (tid < CM_QB) {
+            float qv = 0.f, tv = -1.f;  // missing queries: nothing passes the test
+            if (tid < nqb) {
+                const int64_t qq = pairs[pb + tid] / P;
+                qv = qn[qq];
+                tv = seed_d[qq * K + K - 1];  // +inf when the seed cluster has < K rows
+            }
+            s_qn[tid] = qv;
+            s_tq[tid] = tv;
+        }
         const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
         if (tid == 0)
             atomicAdd(&g_cm_bytes, (unsigned long long)(re - rb) * (dp4 * 16ull + 4ull));
@@ -136,9 +166,12 @@ __global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
                 xs[(c4 * 4 + 2) * CM_R + rr] = v.z;
                 xs[(c4 * 4 + 3) * CM_R + rr] = v.w;
             }
-            for (int i = tid; i < CM_R; i += CM_THREADS) ids[i] = i < nr ? xids[r0 + i] : -1;
+            for (int i = tid; i < CM_R; i += CM_THREADS) {
+                ids[i] = i < nr ? xids[r0 + i] : -1;
+                s_xn[i] = i < nr ? xn[r0 + i] : 0.f;
+            }
             __syncthreads();
-            // distances: warp w -> queries 2w, 2w+1; lane -> rows 4*lane .. 4*lane+3
+            // expanded-form distances: warp w -> queries 2w, 2w+1; lane -> rows 4*lane .. +3
             {
                 float acc[2][4];
 #pragma unroll
@@ -146,24 +179,27 @@ __global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
                 const int q0 = warp * 2;
-#pragma unroll 4
+#pragma unroll 8
                 for (int t = 0; t < dp; ++t) {
                     const float4 xv = *reinterpret_cast<const float4 *>(&xs[t * CM_R + lane * 4]);
                     const float qa = qs[t * CM_QB + q0], qb2 = qs[t * CM_QB + q0 + 1];
-                    float e;
-                    e = xv.x - qa; acc[0][0] = fmaf(e, e, acc[0][0]);
-                    e = xv.y - qa; acc[0][1] = fmaf(e, e, acc[0][1]);
-                    e = xv.z - qa; acc[0][2] = fmaf(e, e, acc[0][2]);
-                    e = xv.w - qa; acc[0][3] = fmaf(e, e, acc[0][3]);
-                    e = xv.x - qb2; acc[1][0] = fmaf(e, e, acc[1][0]);
-                    e = xv.y - qb2; acc[1][1] = fmaf(e, e, acc[1][1]);
-                    e = xv.z - qb2; acc[1][2] = fmaf(e, e, acc[1][2]);
-                    e = xv.w - qb2; acc[1][3] = fmaf(e, e, acc[1][3]);
+                    acc[0][0] = fmaf(xv.x, qa, acc[0][0]);
+                    acc[0][1] = fmaf(xv.y, qa, acc[0][1]);
+                    acc[0][2] = fmaf(xv.z, qa, acc[0][2]);
+                    acc[0][3] = fmaf(xv.w, qa, acc[0][3]);
+                    acc[1][0] = fmaf(xv.x, qb2, acc[1][0]);
+                    acc[1][1] = fmaf(xv.y, qb2, acc[1][1]);
+                    acc[1][2] = fmaf(xv.z, qb2, acc[1][2]);
+                    acc[1][3] = fmaf(xv.w, qb2, acc[1][3]);
                 }
+                const float4 xr = *reinterpret_cast<const float4 *>(&s_xn[lane * 4]);
 #pragma unroll
-                for (int i = 0; i < 2; ++i)
+                for (int i = 0; i < 2; ++i) {
+                    const float qv = s_qn[q0 + i];
                     *reinterpret_cast<float4 *>(&D[(q0 + i) * CM_R + lane * 4]) =
-                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                        make_float4(fmaf(-2.f, acc[i][0], xr.x + qv), fmaf(-2.f, acc[i][1], xr.y + qv),
+                                    fmaf(-2.f, acc[i][2], xr.z + qv), fmaf(-2.f, acc[i][3], xr.w + qv));
+                }
             }
             __syncthreads();
             // merge the chunk into each query's K best: warp w owns queries 2w, 2w+1
@@ -172,16 +208,26 @@ __global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
                 if (qb >= nqb) break;
                 unsigned long long *tq = top + qb * K;
                 const unsigned long long th = tq[K - 1];
+                // distance bound a row must be able to reach (key of the list's K-th, or T_q)
+                const float lim = fminf(s_tq[qb], th == kNoKey ? __int_as_float(0x7f800000)
+                                                               : __uint_as_float((unsigned)(th >> 32)));
+                const float qv = s_qn[qb];
                 unsigned long long cand[CM_R / 32];
                 bool any = false;
 #pragma unroll
                 for (int i = 0; i < CM_R / 32; ++i) {
                     const int rr = lane + 32 * i;
                     cand[i] = kNoKey;
-                    if (rr < nr) {
+                    if (rr < nr && D[qb * CM_R + rr] <= lim + mcoef * (s_xn[rr] + qv)) {
+                        // exact key, the arithmetic of the per-query scan
+                        float e2 = 0.f;
+#pragma unroll 4
+                        for (int t = 0; t < dp; ++t) {
+                            const float e = xs[t * CM_R + rr] - qs[t * CM_QB + qb];
+                            e2 = fmaf(e, e, e2);
+                        }
                         const unsigned long long key =
-                            ((unsigned long long)__float_as_uint(D[qb * CM_R + rr]) << 32) |
-                            (unsigned)ids[rr];
+                            ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)ids[rr];
                         if (key < th) { cand[i] = key; any = true; }
                     }
                 }
@@ -276,11 +322,40 @@ void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32
     MASK_LAUNCHED("item_scan");
 }
 
-void cm_leaf_scan(const float *Xs, int dp, const int32_t *xids, const int64_t *leaf_off, int k0,
-                  const float *Qp, int64_t nq, const int32_t *sel, int P, int K, int64_t *ids,
-                  float *dists, cudaStream_t s) {
+void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
+                  const int64_t *leaf_off, int k0, const float *Qp, int64_t nq,
+                  const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s) {
     if (nq == 0) return;
     const int64_t npairs = nq * P;
+    // seed: each query's K nearest within its nearest kept cluster (the
+    // first of sel, which is ordered by distance); the K-th is T_q
+    Scratch<float> qn(nq, s), seed_d((size_t)nq * K, s);
+    Scratch<int64_t> seed_i((size_t)nq * K, s);
+    Scratch<int32_t> sel0(nq, s);
+    row_sqnorm(Qp, nq, dp, qn.get(), s);
+    first_col_kernel<<<grid_cap(nq, 256), 256, 0, s>>>(sel, nq, P, sel0.get());
+    MASK_LAUNCHED("first_col");
+    {
+        ScanArgs a;
+        a.R = Xs;
+        a.rid = xids;
+        a.off = leaf_off;
+        a.sel = sel0.get();
+        a.P = 1;
+        a.Q = Qp;
+        a.nq = nq;
+        a.dp = dp;
+        a.K = K;
+        a.out_ids64 = seed_i.get();
+        a.out_d = seed_d.get();
+        scan_topk(a, s);
+    }
+    // |expanded form - exact key| <= (4 dp + 8) 2^-24 (||x||^2 + ||q||^2):
+    // FP32 norms (dp terms each), the dot product (dp FMAs of products bounded
+    // by (||x||^2 + ||q||^2) / 2, times 2), three roundings of the combination,
+    // and the exact key's own dp FMAs over a distance <= 2 (||x||^2 + ||q||^2);
+    // widened by 1/8
+    const float mcoef = (float)((4.0 * dp + 8.0) * 0x1.0p-24 * 1.125);
     Scratch<int32_t> pairs;
     Scratch<int64_t> poff, item_off;
     Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
@@ -295,9 +370,9 @@ void cm_leaf_scan(const float *Xs, int dp, const int32_t *xids, const int64_t *l
         MASK_CUDA(cudaFuncSetAttribute(cm_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         cm_scan_kernel<<<152 * 4, CM_THREADS, smem, s>>>(
-            reinterpret_cast<const float4 *>(Xs), dp / 4, xids, leaf_off,
-            reinterpret_cast<const float4 *>(Qp), P, poff.get(), pairs.get(), item_off.get(), k0, K,
-            pair_out.get());
+            reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids, leaf_off,
+            reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef, P, poff.get(),
+            pairs.get(), item_off.get(), k0, K, pair_out.get());
         MASK_LAUNCHED("cm_scan");
     }
     {
