@@ -110,7 +110,8 @@ __global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
     unsigned long long *top = reinterpret_cast<unsigned long long *>(ids + CM_R);  // [CM_QB][K]
     __shared__ int s_c;
     __shared__ int64_t s_pb, s_pe;
-    __shared__ float s_xn[CM_R], s_qn[CM_QB], s_tq[CM_QB];
+    __shared__ __align__(16) float s_xn[CM_R];  // read as float4
+    __shared__ float s_qn[CM_QB], s_tq[CM_QB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n_items = item_off[k0];
