@@ -221,6 +221,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     uint64_t *bars = reinterpret_cast<uint64_t *>(basep + 2u * KB * TC_BOX_BYTES + S * kStage);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
     __shared__ int s_err;
+    __shared__ __align__(16) float s_cn[2][TC_N];
     __shared__ float s_top[TC_M][4];      // second-half top-4 lists, merged at the end
     __shared__ int s_topi[TC_M][3];
 
@@ -317,10 +318,8 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     } else if (warp >= 4) {
         // ---------------- epilogue: one row per thread, half the columns ----------------
         // Rows are ranked by key = ||c||^2 - 2 x.c (the row's ||x||^2 is
-        // added back at the end).  Each warp follows the accumulators on its
-        // own (a failed wait sets the grid's abort word, which ends every
-        // other wait of the CTA), and reads the tile's norms straight from
-        // global memory: all threads of a half read the same 64 floats.
+        // added back at the end); the norms of each C tile are staged in
+        // shared memory (double-buffered with the accumulators).
         const int quad = warp & 3;                  // TMEM lane quadrant of this warp
         const int half = (warp - 4) >> 2;           // column half of each tile
         const int r = quad * 32 + lane;
@@ -329,46 +328,48 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         Top4 t4;
         t4.init();
         bool ok = true;
-        const int col = half * TC_EPI_COLS;
+        if (half == 0) s_cn[0][r] = cn_pad[r];  // norms of tile 0
         for (int j = 0; j < ntiles; ++j) {
             const int a = j & 1, v = j >> 1;
             const int c0 = j * TC_N;
+            const float cn_next = (half == 0 && j + 1 < ntiles) ? cn_pad[c0 + TC_N + r] : 0.f;
             ok = mbar_wait(acc_full(a), v & 1, err);
+            ok = epi_bar_and(ok);  // also publishes s_cn[a] to all epilogue threads
             if (!ok) break;
             tc_fence_after();
+            const int col = half * TC_EPI_COLS;
             const uint32_t taddr =
                 tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * TC_N + col);
             uint32_t u0[32], u1[32];
             tmem_ld32(taddr, u0);
             tmem_ld32(taddr + 32, u1);
-            const float4 *cn4 = reinterpret_cast<const float4 *>(cn_pad + c0 + col);
             tmem_wait();
             // the accumulator is in registers: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty(a));
+            const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][col]);
             float key[64];
-            float m0 = FLT_MAX, m1 = FLT_MAX, m2 = FLT_MAX, m3 = FLT_MAX;
+            float mn = FLT_MAX;
 #pragma unroll
             for (int e4 = 0; e4 < 16; ++e4) {
-                const float4 c = __ldg(cn4 + e4);
+                const float4 c = cn4[e4];
                 const uint32_t *uu = e4 < 8 ? u0 : u1;
                 const int b = (e4 & 7) * 4;
                 key[e4 * 4 + 0] = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
                 key[e4 * 4 + 1] = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
                 key[e4 * 4 + 2] = fmaf(-2.f, __uint_as_float(uu[b + 2]), c.z);
                 key[e4 * 4 + 3] = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
-                m0 = fminf(m0, key[e4 * 4 + 0]);
-                m1 = fminf(m1, key[e4 * 4 + 1]);
-                m2 = fminf(m2, key[e4 * 4 + 2]);
-                m3 = fminf(m3, key[e4 * 4 + 3]);
+                mn = fminf(mn, fminf(fminf(key[e4 * 4 + 0], key[e4 * 4 + 1]),
+                                     fminf(key[e4 * 4 + 2], key[e4 * 4 + 3])));
             }
-            if (fminf(fminf(m0, m1), fminf(m2, m3)) < t4.v3) {
+            if (mn < t4.v3) {
                 const int cb = c0 + col;
 #pragma unroll
                 for (int e = 0; e < 64; ++e)
                     if (key[e] < t4.v3 && cb + e < k) t4.push(key[e], cb + e);
             }
+            if (half == 0) s_cn[a ^ 1][r] = cn_next;  // read after the next tile's barrier
         }
         // merge the two half-row lists: the second half hands its list over
         if (half == 1) {

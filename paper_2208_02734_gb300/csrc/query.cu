@@ -199,9 +199,13 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
         const int c_now = cnt;
         __syncthreads();
         if (c_now > lim || base + ROUND >= T) {
-            for (int i = KP + c_now + tid; i < S; i += kThreads) buf[i] = kNoKey;
+            // sort only the filled prefix (the list and this round's candidates,
+            // rounded up to a power of two; the rest are empty keys)
+            int L = KP;
+            while (L < KP + c_now) L <<= 1;
+            for (int i = KP + c_now + tid; i < L; i += kThreads) buf[i] = kNoKey;
             __syncthreads();
-            bitonic_sort_keys(buf, S);
+            bitonic_sort_keys(buf, L);
             for (int i = K + tid; i < KP; i += kThreads) buf[i] = kNoKey;
             if (tid == 0) {
                 thresh = buf[K - 1];

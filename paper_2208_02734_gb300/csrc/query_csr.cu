@@ -108,9 +108,12 @@ __device__ __forceinline__ void maybe_merge(const ScanSmem &sm, int S, int K, in
     const int c_now = *cnt;
     __syncthreads();
     if (c_now > lim || last) {
-        for (int i = KP + c_now + threadIdx.x; i < S; i += kThreads) sm.buf[i] = kNoKey;
+        // sort only the filled prefix (rounded up to a power of two)
+        int L = KP;
+        while (L < KP + c_now) L <<= 1;
+        for (int i = KP + c_now + threadIdx.x; i < L; i += kThreads) sm.buf[i] = kNoKey;
         __syncthreads();
-        bitonic_sort_keys(sm.buf, S);
+        bitonic_sort_keys(sm.buf, L);
         for (int i = K + threadIdx.x; i < KP; i += kThreads) sm.buf[i] = kNoKey;
         if (threadIdx.x == 0) {
             *thresh = sm.buf[K - 1];
