@@ -275,6 +275,12 @@ void scan_bytes_reset();
 
 // query_cm.cu -- cluster-major leaf scan for large batches (K <= 32, dp <= 128)
 bool cm_leaf_supported(int dp, int K);
+// seed_d [nq x K] = each query's K nearest exact (FP32, per-query scan)
+// distances within its nearest kept cluster (the first of its kept list);
+// the K-th bounds the query's final K-th distance from above (+inf if short)
+void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, int dp,
+               const float *Qp, int64_t nq, const int32_t *sel, int P, int K, float *seed_d,
+               cudaStream_t s);
 // xn [rows] = ||row of Xs||^2 (FP32); the scan evaluates a row exactly only
 // where its expanded-form distance can reach the query's current K-th
 void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,

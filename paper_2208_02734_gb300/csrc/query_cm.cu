@@ -323,34 +323,37 @@ void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32
     MASK_LAUNCHED("item_scan");
 }
 
+void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, int dp,
+               const float *Qp, int64_t nq, const int32_t *sel, int P, int K, float *seed_d,
+               cudaStream_t s) {
+    if (nq == 0) return;
+    Scratch<int64_t> seed_i((size_t)nq * K, s);
+    Scratch<int32_t> sel0(nq, s);
+    first_col_kernel<<<grid_cap(nq, 256), 256, 0, s>>>(sel, nq, P, sel0.get());
+    MASK_LAUNCHED("first_col");
+    ScanArgs a;
+    a.R = Xs;
+    a.rid = xids;
+    a.off = leaf_off;
+    a.sel = sel0.get();
+    a.P = 1;
+    a.Q = Qp;
+    a.nq = nq;
+    a.dp = dp;
+    a.K = K;
+    a.out_ids64 = seed_i.get();
+    a.out_d = seed_d;
+    scan_topk(a, s);
+}
+
 void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
                   const int64_t *leaf_off, int k0, const float *Qp, int64_t nq,
                   const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s) {
     if (nq == 0) return;
     const int64_t npairs = nq * P;
-    // seed: each query's K nearest within its nearest kept cluster (the
-    // first of sel, which is ordered by distance); the K-th is T_q
     Scratch<float> qn(nq, s), seed_d((size_t)nq * K, s);
-    Scratch<int64_t> seed_i((size_t)nq * K, s);
-    Scratch<int32_t> sel0(nq, s);
     row_sqnorm(Qp, nq, dp, qn.get(), s);
-    first_col_kernel<<<grid_cap(nq, 256), 256, 0, s>>>(sel, nq, P, sel0.get());
-    MASK_LAUNCHED("first_col");
-    {
-        ScanArgs a;
-        a.R = Xs;
-        a.rid = xids;
-        a.off = leaf_off;
-        a.sel = sel0.get();
-        a.P = 1;
-        a.Q = Qp;
-        a.nq = nq;
-        a.dp = dp;
-        a.K = K;
-        a.out_ids64 = seed_i.get();
-        a.out_d = seed_d.get();
-        scan_topk(a, s);
-    }
+    leaf_seed(Xs, xids, leaf_off, dp, Qp, nq, sel, P, K, seed_d.get(), s);
     // |expanded form - exact key| <= (4 dp + 8) 2^-24 (||x||^2 + ||q||^2):
     // FP32 norms (dp terms each), the dot product (dp FMAs of products bounded
     // by (||x||^2 + ||q||^2) / 2, times 2), three roundings of the combination,

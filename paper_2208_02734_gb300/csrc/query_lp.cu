@@ -119,7 +119,8 @@ __global__ __launch_bounds__(LP_THREADS) void lp_scan_kernel(
     const uint8_t *__restrict__ Xl, int dpl, const float *__restrict__ xn2,
     const float *__restrict__ xscale, const int64_t *__restrict__ leaf_off,
     const uint8_t *__restrict__ Ql, const float *__restrict__ qn2, const float *__restrict__ qscale,
-    int P, const int64_t *__restrict__ poff, const int32_t *__restrict__ pairs,
+    const float *__restrict__ seed_d, int kseed, float eta, float rslack, int P,
+    const int64_t *__restrict__ poff, const int32_t *__restrict__ pairs,
     const int64_t *__restrict__ item_off, int k0, int K, unsigned long long *__restrict__ pair_out) {
     constexpr int ES = FP8 ? 1 : 2;                   // bytes per element
     constexpr int KSTEP = FP8 ? 32 : 16;              // elements per MMA k-step
@@ -136,6 +137,7 @@ __global__ __launch_bounds__(LP_THREADS) void lp_scan_kernel(
     unsigned long long *top = reinterpret_cast<unsigned long long *>(qsc + LP_QB);  // [LP_QB][K]
     __shared__ int s_c;
     __shared__ int64_t s_pb, s_pe;
+    __shared__ float s_rt[LP_QB];  // sqrt(T_q): the seed's k-th exact distance, as a length
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, tig = lane & 3;
@@ -170,6 +172,7 @@ __global__ __launch_bounds__(LP_THREADS) void lp_scan_kernel(
             const int64_t q = ok ? pairs[pb + tid] / P : 0;
             qn[tid] = ok ? qn2[q] : 0.f;
             qsc[tid] = (ok && FP8) ? qscale[q] : 1.f;
+            s_rt[tid] = ok ? sqrtf(seed_d[q * kseed + kseed - 1]) : 0.f;
         }
         for (int i = tid; i < LP_QB * K; i += LP_THREADS) top[i] = kNoKey;
         const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
@@ -229,6 +232,9 @@ __global__ __launch_bounds__(LP_THREADS) void lp_scan_kernel(
                 if (qb >= nqb) break;
                 unsigned long long *tq = top + qb * K;
                 const unsigned long long th = tq[K - 1];
+                // a row whose quantised distance exceeds sqrt(T_q) + eta (|x| + |q|)
+                // is farther than T_q exactly: it cannot be among the k nearest
+                const float rt = s_rt[qb], qlen = sqrtf(qn[qb]);
                 unsigned long long cand[LP_R / 32];
                 bool any = false;
 #pragma unroll
@@ -236,10 +242,13 @@ __global__ __launch_bounds__(LP_THREADS) void lp_scan_kernel(
                     const int rr = lane + 32 * i;
                     cand[i] = kNoKey;
                     if (rr < nr) {
+                        const float dq = D[qb * LP_R + rr];
+                        const float lim = rt + eta * (sqrtf(rn[rr]) + qlen);
+                        // plus the rounding of the FP32 expanded form dq itself
+                        const float slack = rslack * (rn[rr] + qn[qb]);
                         const unsigned long long key =
-                            ((unsigned long long)__float_as_uint(D[qb * LP_R + rr]) << 32) |
-                            (unsigned)pos[rr];
-                        if (key < th) { cand[i] = key; any = true; }
+                            ((unsigned long long)__float_as_uint(dq) << 32) | (unsigned)pos[rr];
+                        if (key < th && dq <= fmaf(lim, lim, slack)) { cand[i] = key; any = true; }
                     }
                 }
                 if (!__any_sync(kFull, any)) continue;
@@ -414,6 +423,17 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
     Scratch<int32_t> pairs;
     Scratch<int64_t> poff, item_off;
     cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
+    // the FP32 seed: each query's k-th exact distance within its nearest kept
+    // cluster bounds the distance of its k nearest
+    Scratch<float> seed_d((size_t)nq * k, s);
+    leaf_seed(Xs, xids, leaf_off, dp, Qp, nq, sel, P, k, seed_d.get(), s);
+    // element-wise quantisation error, relative to the element, with 2x margin:
+    // BF16 rounds to 8 significant bits, e4m3 to 4 (normal range; the
+    // subnormals of the per-row scaled range add at most 2^-9 of max |x|)
+    const float eta = fp8 ? 0x1.0p-3f : 0x1.0p-7f;
+    // |FP32 expanded form - exact distance of the quantised rows| per unit of
+    // their squared norms (dot over dpl terms x 2, norms, final roundings), x2
+    const float rslack = (float)((4.0 * dpl + 16.0) * 0x1.0p-24);
     Scratch<unsigned long long> pair_out((size_t)nq * P * Kpair, s);
     // pairs of an absent parent (sel = -1, fewer children than probes) are in
     // no work item: their lists stay empty
@@ -429,13 +449,15 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             lp_scan_kernel<true><<<152 * 4, LP_THREADS, smem, s>>>(
                 static_cast<const uint8_t *>(Xl), dpl, xn2, xscale, leaf_off, Ql.get(), qn2.get(),
-                qsc.get(), P, poff.get(), pairs.get(), item_off.get(), k0, Kpair, pair_out.get());
+                qsc.get(), seed_d.get(), k, eta, rslack, P, poff.get(), pairs.get(), item_off.get(), k0,
+                Kpair, pair_out.get());
         } else {
             MASK_CUDA(cudaFuncSetAttribute(lp_scan_kernel<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             lp_scan_kernel<false><<<152 * 4, LP_THREADS, smem, s>>>(
                 static_cast<const uint8_t *>(Xl), dpl, xn2, nullptr, leaf_off, Ql.get(), qn2.get(),
-                nullptr, P, poff.get(), pairs.get(), item_off.get(), k0, Kpair, pair_out.get());
+                nullptr, seed_d.get(), k, eta, rslack, P, poff.get(), pairs.get(), item_off.get(), k0,
+                Kpair, pair_out.get());
         }
         MASK_LAUNCHED("lp_scan");
     }
