@@ -427,10 +427,11 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
     // cluster bounds the distance of its k nearest
     Scratch<float> seed_d((size_t)nq * k, s);
     leaf_seed(Xs, xids, leaf_off, dp, Qp, nq, sel, P, k, seed_d.get(), s);
-    // element-wise quantisation error, relative to the element, with 2x margin:
-    // BF16 rounds to 8 significant bits, e4m3 to 4 (normal range; the
-    // subnormals of the per-row scaled range add at most 2^-9 of max |x|)
-    const float eta = fp8 ? 0x1.0p-3f : 0x1.0p-7f;
+    // element-wise quantisation error relative to the element: BF16 rounds to
+    // 8 significant bits (2^-8; 2x margin), e4m3 to 4 (2^-4, and |x| <=
+    // |x~| / (1 - 2^-4): 2^-4 x 1.125; the subnormals of the per-row scaled
+    // range add at most 2^-10 x max|x| / 448 per element)
+    const float eta = fp8 ? 0x1.2p-4f : 0x1.0p-7f;
     // |FP32 expanded form - exact distance of the quantised rows| per unit of
     // their squared norms (dot over dpl terms x 2, norms, final roundings), x2
     const float rslack = (float)((4.0 * dpl + 16.0) * 0x1.0p-24);
