@@ -275,6 +275,10 @@ void scan_bytes_reset();
 
 // query_cm.cu -- cluster-major leaf scan for large batches (K <= 32, dp <= 128)
 bool cm_leaf_supported(int dp, int K);
+// ids/dists [nq x K] = each query's K smallest keys over its P per-pair lists
+// (pair_out [nq*P x K], keys = distance bits << 32 | original id)
+void cm_merge(const unsigned long long *pair_out, int64_t nq, int P, int K, int64_t *ids,
+              float *dists, cudaStream_t s);
 // seed_d [nq x K] = each query's K nearest exact (FP32, per-query scan)
 // distances within its nearest kept cluster (the first of its kept list);
 // the K-th bounds the query's final K-th distance from above (+inf if short)
@@ -292,17 +296,17 @@ void cm_bytes_reset();
 void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
                     Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s);
 
-// query_lp.cu -- BF16 / FP8 leaf scan with exact FP32 re-rank of a 4k shortlist
+// query_lp.cu -- BF16 / FP8 leaf scan: tensor-core distances of quantised
+// copies filter the rows, exact FP32 keys for every row that can enter
 int lp_padded_dim(int dp);
-int lp_shortlist(int k);  // max(4k, 16)
 bool lp_supported(int dp, int k);
 // quantised copy ([rows x lp_padded_dim] BF16 or e4m3), per-row scale (FP8) and
 // squared norm of every quantised row
 void lp_quantize(const float *src, int64_t rows, int dp, bool fp8, void *dst, float *scale,
                  float *norm2, cudaStream_t s);
 void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscale, const float *Xs,
-                  int64_t leaf_rows, int dp, const int32_t *xids, const int64_t *leaf_off, int k0, const float *Qp,
-                  int64_t nq, const int32_t *sel, int P, int k, int64_t *ids, float *dists,
-                  cudaStream_t s);
+                  int64_t leaf_rows, int dp, const int32_t *xids, const int64_t *leaf_off, int k0,
+                  const float *Qp, int64_t nq, const int32_t *sel, int P, int k, int64_t *ids,
+                  float *dists, cudaStream_t s);
 
 }  // namespace mask

@@ -634,7 +634,8 @@ __global__ void label_scatter_kernel(const int32_t *__restrict__ labels, int64_t
 }
 
 // Put each membership list in ascending item order (bitonic sort in shared
-// memory), so sums over a cluster run in the same order on every build.
+// memory; longer lists below), so sums over a cluster run in the same order
+// on every build.
 constexpr int kSegSortMax = 4096;
 __global__ void __launch_bounds__(512) segment_sort_kernel(const int64_t *__restrict__ off,
                                                            int32_t *__restrict__ perm) {
@@ -659,6 +660,35 @@ __global__ void __launch_bounds__(512) segment_sort_kernel(const int64_t *__rest
             __syncthreads();
         }
     for (int i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = s[i];
+}
+
+// Lists longer than kSegSortMax: one block each, bitonic sort in global
+// memory over a padded copy (tmp holds 2 x n ints: list j uses [2 b, 2 b + S)
+// with S < 2 m, so the regions of different lists never overlap).
+__global__ void __launch_bounds__(1024) segment_sort_big_kernel(const int64_t *__restrict__ off,
+                                                                int32_t *__restrict__ perm,
+                                                                int32_t *__restrict__ tmp) {
+    const int64_t b = off[blockIdx.x], e = off[blockIdx.x + 1];
+    const int64_t m = e - b;
+    if (m <= kSegSortMax) return;
+    int64_t S = 1;
+    while (S < m) S <<= 1;
+    int32_t *t = tmp + 2 * b;
+    for (int64_t i = threadIdx.x; i < S; i += blockDim.x) t[i] = i < m ? perm[b + i] : INT_MAX;
+    __syncthreads();
+    for (int64_t kk = 2; kk <= S; kk <<= 1)
+        for (int64_t j = kk >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < S; i += blockDim.x) {
+                const int64_t ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & kk) == 0;
+                    const int32_t a = t[i], c = t[ixj];
+                    if ((a > c) == up) { t[i] = c; t[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = t[i];
 }
 
 // --------------------------------------------------------- centroid update
@@ -971,6 +1001,12 @@ void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *
         MASK_LAUNCHED("label_scatter");
         segment_sort_kernel<<<k, 512, 0, s>>>(off, perm);
         MASK_LAUNCHED("segment_sort");
+        if (n > kSegSortMax) {
+            // only lists longer than kSegSortMax do work here
+            Scratch<int32_t> tmp((size_t)2 * n, s);
+            segment_sort_big_kernel<<<k, 1024, 0, s>>>(off, perm, tmp.get());
+            MASK_LAUNCHED("segment_sort_big");
+        }
     }
 }
 

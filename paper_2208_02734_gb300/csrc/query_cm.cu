@@ -323,6 +323,14 @@ void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32
     MASK_LAUNCHED("item_scan");
 }
 
+void cm_merge(const unsigned long long *pair_out, int64_t nq, int P, int K, int64_t *ids,
+              float *dists, cudaStream_t s) {
+    if (nq == 0) return;
+    ProfRegion pr("leaf_merge", s, 0.0);
+    cm_merge_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(pair_out, nq, P, K, ids, dists);
+    MASK_LAUNCHED("cm_merge");
+}
+
 void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, int dp,
                const float *Qp, int64_t nq, const int32_t *sel, int P, int K, float *seed_d,
                cudaStream_t s) {
@@ -379,12 +387,7 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
             pairs.get(), item_off.get(), k0, K, pair_out.get());
         MASK_LAUNCHED("cm_scan");
     }
-    {
-        ProfRegion pr("leaf_merge", s, 0.0);
-        cm_merge_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(pair_out.get(), nq, P, K, ids,
-                                                                 dists);
-        MASK_LAUNCHED("cm_merge");
-    }
+    cm_merge(pair_out.get(), nq, P, K, ids, dists, s);
 }
 
 double cm_bytes() {
