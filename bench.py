@@ -585,15 +585,15 @@ def run_ours_sparse(args, w, wname):
 def serving_requests(rng, Q, n, P, lowp):
     """Requests of the serving workload: batch ~ U[1,512] queries, k in
     {1, 10, 100}, probes ~ U{P..P+2} x U{3..5}.  In the BF16/FP8 runs a
-    request with k = 100 (beyond the low-precision scan's k <= 64) runs in
-    FP32."""
+    request with k = 100 (shortlist 400, beyond the low-precision scan) runs
+    in FP32."""
     out = []
     for _ in range(n):
         nq = int(rng.integers(1, 513))
         q0 = int(rng.integers(0, len(Q) - nq))
         k = int(rng.choice([1, 10, 100]))
         probes = [int(rng.integers(P, P + 3)), int(rng.integers(3, 6))]
-        out.append((q0, nq, k, probes, lowp if k <= 64 else 0))
+        out.append((q0, nq, k, probes, lowp if k <= 16 else 0))
     return out
 
 
@@ -819,7 +819,7 @@ def run_ours(args, w, wname):
     recall = recall_at_k(Xd, Qs, results[-1][0][sel], dk)
     n_rec = int(len(sel))
 
-    # BF16 / FP8 leaf scans (low-precision filter + exact FP32 re-rank) on the same
+    # BF16 / FP8 leaf scans (4k shortlist + exact FP32 re-rank) on the same
     # index: each mode at the cheapest ladder probes reaching recall@10 >= 0.95
     lowp = {}
     if not args.no_lowp:

@@ -121,15 +121,12 @@ mask_status mask_build_csr(const int64_t *row_ptr, const int32_t *col, const flo
  *   k         neighbours per query (1 <= k <= 1024).
  *   probes    host array [n_levels], finest first; p_l >= 1, clamped to k_l.
  *   precision MASK_FP32: every distance in FP32.  MASK_BF16 / MASK_FP8E4M3:
- *             the leaf scan computes distances between BF16 (or FP8 e4m3 with
- *             a per-row scale max|x|/448) copies of the points and the query
- *             on the tensor cores and re-ranks, by exact FP32 distances, every
- *             point those cannot prove farther than the current k-th (a
- *             bound from the element-wise quantisation error), so the answer
- *             equals MASK_FP32's; k <= 64 and d <= 256, else
- *             MASK_EUNSUPPORTED.  The quantised copy is made on the first such
- *             query (the index grows by 2 or 1 bytes per coordinate plus 4-8
- *             bytes per point).
+ *             the leaf scan ranks points by distances between BF16 (or FP8
+ *             e4m3 with a per-row scale max|x|/448) copies of the points and
+ *             the query, keeps the max(4k, 16) nearest, and re-ranks those by exact
+ *             FP32 distances (k <= 16 and d <= 256, else MASK_EUNSUPPORTED);
+ *             the quantised copy is made on the first such query (the index
+ *             grows by 2 or 1 bytes per coordinate plus 4-8 bytes per point).
  *   ids_out   [nq x k] int64 original point ids, ascending by (distance, id);
  *             -1 where fewer than k points were reached.
  *   dists_out [nq x k] float32 squared distances; +inf where ids_out is -1.
@@ -306,7 +303,7 @@ int64_t mask_launch_count(void);
  * counterpart: this is the interface of the query path as a service.
  *
  * A worker thread merges pending requests with equal probes and precision
- * into one launch of up to max_batch queries
+ * (low precision: also equal k) into one launch of up to max_batch queries
  * (a larger request is split), replays the captured CUDA graph of that batch
  * shape on one of max_slots streams, and admits a batch only while the
  * device bytes of the batches in flight (graph buffers and kernel scratch,

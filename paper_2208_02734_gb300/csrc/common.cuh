@@ -296,9 +296,9 @@ void cm_bytes_reset();
 void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
                     Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s);
 
-// query_lp.cu -- BF16 / FP8 leaf scan: tensor-core distances of quantised
-// copies filter the rows, exact FP32 keys for every row that can enter
+// query_lp.cu -- BF16 / FP8 leaf scan with exact FP32 re-rank of a 4k shortlist
 int lp_padded_dim(int dp);
+int lp_shortlist(int k);  // max(4k, 16)
 bool lp_supported(int dp, int k);
 // quantised copy ([rows x lp_padded_dim] BF16 or e4m3), per-row scale (FP8) and
 // squared norm of every quantised row

@@ -701,7 +701,7 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
                          precision == MASK_FP8E4M3, "unknown precision");
         const bool lowp = precision != MASK_FP32;
         if (lowp && !lp_supported(index->dp, k))
-            fail(MASK_EUNSUPPORTED, "BF16/FP8 modes need k <= 64 and d <= 256");
+            fail(MASK_EUNSUPPORTED, "BF16/FP8 modes keep a 4k shortlist: k <= 16 and d <= 256");
         if (nq == 0) return;
         MASK_REQUIRE(queries && ids_out, "NULL queries or ids_out");
         cudaStream_t s = (cudaStream_t)stream;

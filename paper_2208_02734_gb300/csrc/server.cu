@@ -10,7 +10,7 @@
 //              release their memory;
 //   admit   -- while a slot (stream) is free: take the oldest pending request
 //              and every pending request with the same batch key (equal
-//              probes and precision), up to
+//              probes and precision; low precision also equal k), up to
 //              max_batch queries and as many as the memory budget left
 //              allows (a request may be split across batches); stage the
 //              queries, replay the batch shape's captured CUDA graph on the
@@ -19,9 +19,9 @@
 // So requests that arrive while others are on the GPU join the next batch as
 // slots and memory free up, and batches on different slots overlap on the
 // device.  A query's result depends only on the query (every scan orders
-// candidates by the total order (distance, id) of exact FP32 keys, and the
-// K-list of a batch whose K exceeds a request's k starts with that request's
-// k nearest), so a request gets the same answer alone and in any mix.
+// candidates by the total order (distance, id), and the K-th list of an FP32
+// batch whose K exceeds a request's k starts with that request's k nearest),
+// so a request gets the same answer alone and in any mix.
 //
 // Graphs: one per (batch key, batch size bucket, K, leaf scan), captured on
 // first use with the batch padded to the bucket (copies of the last query).
@@ -73,7 +73,7 @@ struct Piece {
 struct Key {
     std::vector<int> probes;
     int prec = 0;
-    int kkey = 0;  // reserved (every mode batches with K = max k of the batch)
+    int kkey = 0;  // 0 for FP32 (K = max k of the batch), k for low precision
     bool operator<(const Key &o) const {
         return std::tie(probes, prec, kkey) < std::tie(o.probes, o.prec, o.kkey);
     }
@@ -171,7 +171,7 @@ Key key_of(const Request &r) {
     Key k;
     k.probes = r.probes;
     k.prec = (int)r.prec;
-    k.kkey = 0;
+    k.kkey = r.prec == MASK_FP32 ? 0 : r.k;
     return k;
 }
 
@@ -183,9 +183,14 @@ size_t batch_bytes(const mask_index &idx, const Key &key, int64_t B, int K) {
     size_t sp = 0;
     for (int p : key.probes) sp += (size_t)p;
     size_t per = dp * 4 + (size_t)K * 12 + sp * 4;
-    // seed lists, cluster-major pairs and per-pair lists
-    per += (size_t)K * 12 + p0 * (12 + (size_t)K * 8) + 8;
-    if (key.prec != MASK_FP32) per += (size_t)lp_padded_dim(idx.dp) * 2 + 8;  // quantised query
+    if (key.prec == MASK_FP32) {
+        per += p0 * (12 + (size_t)K * 8);  // cluster-major pairs and per-pair lists
+    } else {
+        const size_t dpl = (size_t)lp_padded_dim(idx.dp);
+        const size_t Kp = (size_t)lp_shortlist(K);
+        const size_t Kpair = std::min(Kp, (size_t)std::max(K, 4));
+        per += dpl * 2 + 8 + p0 * (12 + Kpair * 8) + Kp * 4;
+    }
     const size_t fixed = (size_t)(idx.lv[0].k + 2) * 32 + (256u << 10);
     return fixed + per * (size_t)B;
 }
@@ -366,7 +371,7 @@ bool form_batch(mask_server *S, Batch &b, Key &key, int &K, int64_t &bucket) {
     int kmax = 0;
     for (const Piece &p : S->pending)
         if (key_of(*p.r) == key) kmax = std::max(kmax, p.r->k);
-    K = std::min(1024, fp32_kbucket(kmax));
+    K = key.prec == MASK_FP32 ? std::min(1024, fp32_kbucket(kmax)) : kmax;
     // the largest bucket the memory left admits
     const size_t left = S->budget > (int64_t)S->inflight_bytes ? (size_t)S->budget - S->inflight_bytes : 0;
     int64_t cap = S->max_batch;
@@ -571,7 +576,7 @@ mask_status mask_server_submit(mask_server *S, const float *queries, int64_t nq,
         MASK_REQUIRE(precision == MASK_FP32 || precision == MASK_BF16 ||
                          precision == MASK_FP8E4M3, "unknown precision");
         if (precision != MASK_FP32 && !lp_supported(idx.dp, k))
-            fail(MASK_EUNSUPPORTED, "BF16/FP8 modes need k <= 64 and d <= 256");
+            fail(MASK_EUNSUPPORTED, "BF16/FP8 modes keep a 4k shortlist: k <= 16 and d <= 256");
         MASK_REQUIRE(nq == 0 || (queries && ids_out), "NULL queries or ids_out");
         auto r = std::make_shared<Request>();
         r->probes.resize((size_t)idx.L);

@@ -33,7 +33,7 @@ def c1_index():
 
 def mixed_requests(Q, n_req, seed, precisions=(M.MASK_FP32, M.MASK_BF16, M.MASK_FP8E4M3), P=3):
     """Requests shaped like the serving workload: batch ~ U[1, 512], k in
-    {1, 10, 100}, probes ~ U{P..P+2} x U{3..5}, mixed precision (k <= 64 for
+    {1, 10, 100}, probes ~ U{P..P+2} x U{3..5}, mixed precision (k <= 16 for
     the low-precision modes)."""
     rng = np.random.default_rng(seed)
     reqs = []
@@ -41,7 +41,7 @@ def mixed_requests(Q, n_req, seed, precisions=(M.MASK_FP32, M.MASK_BF16, M.MASK_
         nq = int(rng.integers(1, 513))
         q0 = int(rng.integers(0, len(Q) - nq))
         prec = int(rng.choice(precisions))
-        k = int(rng.choice([1, 10, 100] if prec == M.MASK_FP32 else [1, 10, 64]))
+        k = int(rng.choice([1, 10, 100] if prec == M.MASK_FP32 else [1, 10, 16]))
         probes = [int(rng.integers(P, P + 3)), int(rng.integers(3, 6))]
         reqs.append((Q[q0:q0 + nq], k, probes, prec))
     return reqs
@@ -115,7 +115,7 @@ def test_submit_rejects_bad_requests(c1_index):
     X, Q, idx = c1_index
     with M.Server(idx, mem_budget=64 << 20) as srv:
         with pytest.raises(M.MaskError, match="MASK_EUNSUPPORTED"):
-            srv.submit(Q[:4], 100, [3, 3], M.MASK_BF16)      # k > 64 in low precision
+            srv.submit(Q[:4], 100, [3, 3], M.MASK_BF16)      # shortlist of 400 > 64
         with pytest.raises(M.MaskError, match="MASK_EINVAL"):
             srv.submit(Q[:4], 0, [3, 3])
         with pytest.raises(M.MaskError, match="MASK_EINVAL"):
