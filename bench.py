@@ -34,6 +34,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -582,6 +583,9 @@ def run_ours_sparse(args, w, wname):
     return 0
 
 
+SUBMITTERS = 4  # client threads of the serving workload
+
+
 def serving_requests(rng, Q, n, P, lowp):
     """Requests of the serving workload: batch ~ U[1,512] queries, k in
     {1, 10, 100}, probes ~ U{P..P+2} x U{3..5}.  In the BF16/FP8 runs a
@@ -643,11 +647,24 @@ def run_serving(args, w, wname):
         warm = serving_requests(rng, Q, 400, P, prec)
         for t, _ in [submit(r) for r in warm]:
             t.result()
-        # saturation: a backlog submitted at once
+        # saturation: a backlog of 2,000 requests submitted by 4 threads at once
         srv.stats(reset=True)
-        sat = serving_requests(rng, Q, 800, P, prec)
+        sat = serving_requests(rng, Q, 2000, P, prec)
+        done = [None] * len(sat)
+        sub_s = [0.0] * SUBMITTERS
+
+        def backlog(c):
+            t = time.perf_counter()
+            for i in range(c, len(sat), SUBMITTERS):
+                done[i] = submit(sat[i])
+            sub_s[c] = time.perf_counter() - t
+
         t0 = time.perf_counter()
-        done = [submit(r) for r in sat]
+        th = [threading.Thread(target=backlog, args=(c,)) for c in range(SUBMITTERS)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
         for t, _ in done:
             t.result()
         t_sat = time.perf_counter() - t0
@@ -667,21 +684,33 @@ def run_serving(args, w, wname):
             tot += ids.numel()
         rates = []
         for frac in (0.1, 0.25, 0.5, 0.75, 0.95):
-            lam = frac * sat_qps / mean_q       # requests per second
-            reqs = serving_requests(rng, Q, int(lam * secs * 1.2) + 10, P, prec)
-            arr = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+            lam = frac * sat_qps / mean_q       # requests per second, SUBMITTERS streams
+            streams = []
+            for c in range(SUBMITTERS):
+                reqs = serving_requests(rng, Q, int(lam / SUBMITTERS * secs * 1.2) + 10, P, prec)
+                arr = np.cumsum(rng.exponential(SUBMITTERS / lam, size=len(reqs)))
+                streams.append((reqs, arr))
             srv.stats(reset=True)
-            tickets = []
+            tickets = [[] for _ in range(SUBMITTERS)]
             start = time.perf_counter()
-            for r, ta in zip(reqs, arr):
-                if ta > secs:
-                    break
-                delay = start + ta - time.perf_counter()
-                if delay > 0:
-                    time.sleep(delay)
-                tickets.append(submit(r))
-            for t, _ in tickets:
-                t.result()
+
+            def open_loop(c):
+                for r, ta in zip(*streams[c]):
+                    if ta > secs:
+                        break
+                    delay = start + ta - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    tickets[c].append(submit(r))
+
+            th = [threading.Thread(target=open_loop, args=(c,)) for c in range(SUBMITTERS)]
+            for x in th:
+                x.start()
+            for x in th:
+                x.join()
+            for tl in tickets:
+                for t, _ in tl:
+                    t.result()
             st = srv.stats(reset=True)
             rates.append({"offered_fraction": frac, "offered_qps": frac * sat_qps,
                           "achieved_qps": st["queries_done"] / max(1e-9, st["elapsed_s"]),
@@ -694,6 +723,7 @@ def run_serving(args, w, wname):
         info = srv.stats()
         srv.close()
         out[mname] = {"saturation_qps": sat_qps, "recall_at_10": hits / max(1, tot),
+                      "backlog_submit_s": max(sub_s), "backlog_s": t_sat,
                       "rates": rates, "graph_captures": info["graph_captures"],
                       "autotuned_shapes": info["autotuned_shapes"],
                       "k100_requests_in_fp32": mname != "fp32"}
