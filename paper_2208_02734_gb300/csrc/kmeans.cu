@@ -1,6 +1,7 @@
 // kmeans.cu -- k-means building blocks of the MASK build (§2.4, §3.1, §3.2):
 // row padding and norms, k-means++ seeding steps, the label counting sort that
 // turns a labelling into membership lists, and the per-cluster mean update.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -662,15 +663,9 @@ __global__ void __launch_bounds__(512) segment_sort_kernel(const int64_t *__rest
     for (int i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = s[i];
 }
 
-// Lists longer than kSegSortMax: one block each, bitonic sort in global
-// memory over a padded copy (tmp holds 2 x n ints: list j uses [2 b, 2 b + S)
-// with S < 2 m, so the regions of different lists never overlap).
-__global__ void __launch_bounds__(1024) segment_sort_big_kernel(const int64_t *__restrict__ off,
-                                                                int32_t *__restrict__ perm,
-                                                                int32_t *__restrict__ tmp) {
-    const int64_t b = off[blockIdx.x], e = off[blockIdx.x + 1];
-    const int64_t m = e - b;
-    if (m <= kSegSortMax) return;
+// Bitonic sort of perm[b, b + m) (block-wide) through tmp[2 b, 2 b + S).
+__device__ void sort_long_list(int32_t *__restrict__ perm, int32_t *__restrict__ tmp, int64_t b,
+                               int64_t m) {
     int64_t S = 1;
     while (S < m) S <<= 1;
     int32_t *t = tmp + 2 * b;
@@ -689,6 +684,22 @@ __global__ void __launch_bounds__(1024) segment_sort_big_kernel(const int64_t *_
             __syncthreads();
         }
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = t[i];
+    __syncthreads();
+}
+
+// Lists longer than kSegSortMax: blocks stride over the lists and sort each
+// long one by a bitonic sort in global memory over a padded copy (tmp holds
+// 2 x n ints: list j uses [2 b, 2 b + S) with S < 2 m, so the regions of
+// different lists never overlap).
+__global__ void __launch_bounds__(1024) segment_sort_big_kernel(const int64_t *__restrict__ off,
+                                                                int k,
+                                                                int32_t *__restrict__ perm,
+                                                                int32_t *__restrict__ tmp) {
+    for (int j = blockIdx.x; j < k; j += gridDim.x) {
+        const int64_t b = off[j], e = off[j + 1];
+        const int64_t m = e - b;
+        if (m > kSegSortMax) sort_long_list(perm, tmp, b, m);
+    }
 }
 
 // --------------------------------------------------------- centroid update
@@ -1004,7 +1015,7 @@ void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *
         if (n > kSegSortMax) {
             // only lists longer than kSegSortMax do work here
             Scratch<int32_t> tmp((size_t)2 * n, s);
-            segment_sort_big_kernel<<<k, 1024, 0, s>>>(off, perm, tmp.get());
+            segment_sort_big_kernel<<<std::min(k, 152 * 2), 1024, 0, s>>>(off, k, perm, tmp.get());
             MASK_LAUNCHED("segment_sort_big");
         }
     }
