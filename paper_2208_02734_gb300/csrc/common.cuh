@@ -223,6 +223,13 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
                     const int64_t *off, const int32_t *sel, int P, int64_t root_end,
                     const int64_t *qrp, const int32_t *qcol, const float *qval, int qcap,
                     int64_t nq, int K, int32_t *out32, cudaStream_t s);
+// cluster-major leaf scan for large CSR batches (K <= 64, queries of at most
+// 2,048 nonzeros): same keys as csr_leaf_scan
+bool csr_cm_supported(int K, int longest);
+void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
+                      const int32_t *xids, const int64_t *leaf_off, int k0, const int32_t *sel,
+                      int P, const int64_t *qrp, const int32_t *qcol, const float *qval,
+                      int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s);
 // bytes the CSR scans read since the last reset ([0] levels, [1] leaf)
 double csr_scan_bytes(int which);
 void csr_scan_bytes_reset();

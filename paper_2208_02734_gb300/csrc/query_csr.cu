@@ -18,6 +18,7 @@
 //    nonzeros, so a point equal to the query gets exactly 0.
 //
 // Groups of kGroup lanes take one row each, four rows in flight per group.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -342,6 +343,201 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     }
 }
 
+// ------------------------------------------------- cluster-major leaf scan
+//
+// For large batches the (query, kept leaf cluster) pairs are grouped by
+// cluster (cm_group_pairs, kCmQB pairs per work item) and a cluster's CSR rows
+// are read once per item.  Each query of the item has its own table in shared
+// memory; a lane group takes a row and every lane accumulates, for each
+// query, the same partial sums over the same nonzeros (gl, gl+8, ...) as the
+// per-query scan, reduced by the same shuffle tree: the keys are bit-identical
+// to the per-query scan's.  Each pair keeps its K smallest keys (cm_merge then
+// takes each query's K over its pairs).
+
+constexpr int kCmQB = 16;           // pairs per work item (the grouping's item size)
+constexpr int kCmSlots = 8192;      // table slots of one pass (64 KB)
+constexpr int kCmLongestQuery = kCmSlots / 4;  // tables a quarter full: one query always fits
+
+// ||q||^2 of every CSR query by the per-query scan's procedure (lanes gl of a
+// group of 8 over nonzeros gl, gl+8, ..., then the xor tree), one warp each.
+__global__ void csr_query_norm_kernel(const int64_t *__restrict__ qrp,
+                                      const float *__restrict__ qval, int64_t nq,
+                                      float *__restrict__ qn) {
+    const int lane = threadIdx.x & 31, gl = lane % kGroup;
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
+         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        float A = 0.f, B = 0.f;
+        for (int64_t j = qrp[q] + gl; j < qrp[q + 1]; j += kGroup) {
+            const float c = qval[j];
+            B = fmaf(c, c, B);
+        }
+        group_reduce2(A, B);
+        if (lane == 0) qn[q] = B;
+    }
+}
+
+__device__ __forceinline__ unsigned table_slots(int64_t nnz) {
+    unsigned h = 32;
+    while ((int64_t)h < 4 * nnz) h <<= 1;
+    return h;
+}
+
+__global__ __launch_bounds__(kThreads) void csr_cm_scan_kernel(
+    const int64_t *__restrict__ xrp, const int32_t *__restrict__ xcol,
+    const float *__restrict__ xval, const int32_t *__restrict__ xids,
+    const int64_t *__restrict__ leaf_off, int P, const int64_t *__restrict__ poff,
+    const int32_t *__restrict__ pairs, const int64_t *__restrict__ item_off, int k0,
+    const int64_t *__restrict__ qrp, const int32_t *__restrict__ qcol,
+    const float *__restrict__ qval, const float *__restrict__ qn_all, int K,
+    unsigned long long *__restrict__ pair_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t *hkey = reinterpret_cast<int32_t *>(smem);                       // [kCmSlots]
+    float *hval = reinterpret_cast<float *>(hkey + kCmSlots);               // [kCmSlots]
+    unsigned long long *cand = reinterpret_cast<unsigned long long *>(hval + kCmSlots);
+    unsigned long long *top = cand + kCmQB * kGroups;                        // [kCmQB][K]
+    __shared__ int s_c, s_hi;
+    __shared__ int64_t s_pb, s_pe;
+    __shared__ unsigned s_hoff[kCmQB], s_hmask[kCmQB];
+    __shared__ float s_qn[kCmQB];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = tid / kGroup, gl = tid % kGroup;
+    const int64_t n_items = item_off[k0];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        if (tid == 0) {
+            int lo = 0, hi = k0 - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            s_c = lo;
+            s_pb = poff[lo] + (item - item_off[lo]) * kCmQB;
+            s_pe = min(poff[lo + 1], s_pb + kCmQB);
+        }
+        __syncthreads();
+        const int c = s_c;
+        const int64_t pb = s_pb;
+        const int nqb = (int)(s_pe - pb);
+        for (int i = tid; i < kCmQB * K; i += kThreads) top[i] = kNoKey;
+        const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
+        for (int lo = 0; lo < nqb;) {
+            // the queries of this pass: as many as their tables fit
+            if (tid == 0) {
+                unsigned used = 0;
+                int hi = lo;
+                while (hi < nqb) {
+                    const int64_t q = pairs[pb + hi] / P;
+                    const unsigned h = table_slots(qrp[q + 1] - qrp[q]);
+                    if (used + h > (unsigned)kCmSlots) break;
+                    s_hoff[hi - lo] = used;
+                    s_hmask[hi - lo] = h - 1;
+                    s_qn[hi - lo] = qn_all[q];
+                    used += h;
+                    ++hi;
+                }
+                s_hi = hi;
+            }
+            __syncthreads();
+            const int hi = s_hi, np = hi - lo;
+            const int total = (int)(s_hoff[np - 1] + s_hmask[np - 1] + 1);
+            for (int i = tid; i < total; i += kThreads) hkey[i] = -1;
+            __syncthreads();
+            for (int j = 0; j < np; ++j) {
+                const int64_t q = pairs[pb + lo + j] / P;
+                int32_t *hk = hkey + s_hoff[j];
+                float *hv = hval + s_hoff[j];
+                const unsigned hm = s_hmask[j];
+                for (int64_t e = qrp[q] + tid; e < qrp[q + 1]; e += kThreads) {
+                    // column ids of a row are distinct, so every insert claims its own slot
+                    const int32_t cc = qcol[e];
+                    unsigned h = qhash(cc, hm);
+                    while (atomicCAS(hk + h, -1, cc) != -1) h = (h + 1) & hm;
+                    hv[h] = qval[e];
+                }
+            }
+            __syncthreads();
+            for (int64_t r0 = rb; r0 < re; r0 += kGroups) {
+                const int64_t row = r0 + g;
+                const bool ok = row < re;
+                float A[kCmQB], B[kCmQB];
+#pragma unroll
+                for (int j = 0; j < kCmQB; ++j) {
+                    A[j] = 0.f;
+                    B[j] = 0.f;
+                }
+                if (ok) {
+                    for (int64_t e = xrp[row] + gl; e < xrp[row + 1]; e += kGroup) {
+                        const int32_t cc = __ldg(xcol + e);
+                        const float v = __ldg(xval + e);
+#pragma unroll
+                        for (int j = 0; j < kCmQB; ++j) {
+                            if (j < np) {
+                                const float cv = qlookup(hkey + s_hoff[j], hval + s_hoff[j],
+                                                         s_hmask[j], cc);
+                                const float d = v - cv;
+                                A[j] = fmaf(d, d, A[j]);
+                                B[j] = fmaf(cv, cv, B[j]);
+                            }
+                        }
+                    }
+                }
+                const int32_t xid = ok ? xids[row] : -1;
+#pragma unroll
+                for (int j = 0; j < kCmQB; ++j) {
+                    if (j < np) {  // np is the same for the whole block: every lane shuffles
+                        group_reduce2(A[j], B[j]);
+                        if (gl == 0) {
+                            const float dist = A[j] + fmaxf(s_qn[j] - B[j], 0.f);
+                            cand[j * kGroups + g] =
+                                ok ? (((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)xid)
+                                   : kNoKey;
+                        }
+                    }
+                }
+                __syncthreads();
+                // merge: warp w owns the pass's queries 2w, 2w+1 (one candidate per lane)
+                for (int qi = 0; qi < 2; ++qi) {
+                    const int j = warp * 2 + qi;
+                    if (j >= np) break;
+                    unsigned long long *tq = top + (lo + j) * K;
+                    const unsigned long long th = tq[K - 1];
+                    unsigned long long mine = cand[j * kGroups + lane];
+                    if (!(mine < th)) mine = kNoKey;
+                    if (!__any_sync(kFull, mine != kNoKey)) continue;
+                    unsigned long long old0 = lane < K ? tq[lane] : kNoKey;
+                    unsigned long long old1 = lane + 32 < K ? tq[lane + 32] : kNoKey;
+                    unsigned long long out0 = kNoKey, out1 = kNoKey;
+                    for (int r = 0; r < K; ++r) {
+                        unsigned long long m = old0 < old1 ? old0 : old1;
+                        m = m < mine ? m : mine;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const unsigned long long t = __shfl_xor_sync(kFull, m, o);
+                            m = t < m ? t : m;
+                        }
+                        if (m == kNoKey) break;
+                        if (lane == (r & 31)) { if (r < 32) out0 = m; else out1 = m; }
+                        // keys are distinct (ids differ): exactly one holder drops it
+                        if (old0 == m) old0 = kNoKey;
+                        if (old1 == m) old1 = kNoKey;
+                        if (mine == m) mine = kNoKey;
+                    }
+                    __syncwarp();
+                    if (lane < K) tq[lane] = out0;
+                    if (lane + 32 < K) tq[lane + 32] = out1;
+                    __syncwarp();
+                }
+                __syncthreads();
+            }
+            lo = hi;
+        }
+        for (int i = tid; i < nqb * K; i += kThreads) {
+            const int j = i / K, r = i % K;
+            pair_out[(int64_t)pairs[pb + j] * K + r] = top[j * K + r];
+        }
+        __syncthreads();
+    }
+}
+
 int next_pow2(int v) {
     int p = 1;
     while (p < v) p <<= 1;
@@ -400,6 +596,38 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
         R, dp, rcn, rid, off, sel, Pn, root_end, qrp, qcol, qval, qcap, K, next_pow2(K),
         list_size(K), out32);
     MASK_LAUNCHED("csr_level_scan");
+}
+
+bool csr_cm_supported(int K, int longest) { return K >= 1 && K <= 64 && longest <= kCmLongestQuery; }
+
+void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
+                      const int32_t *xids, const int64_t *leaf_off, int k0, const int32_t *sel,
+                      int P, const int64_t *qrp, const int32_t *qcol, const float *qval,
+                      int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s) {
+    if (nq == 0) return;
+    Scratch<float> qn(nq, s);
+    csr_query_norm_kernel<<<(unsigned)std::min<int64_t>((nq + 7) / 8, 152 * 32), 256, 0, s>>>(
+        qrp, qval, nq, qn.get());
+    MASK_LAUNCHED("csr_query_norm");
+    Scratch<int32_t> pairs;
+    Scratch<int64_t> poff, item_off;
+    cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
+    const int64_t npairs = nq * P;
+    Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
+    // pairs of an absent parent (sel = -1) are in no work item: empty lists
+    MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
+    {
+        ProfRegion pr("csr_scan_leaf_cm", s, 0.0);
+        const size_t smem = (size_t)kCmSlots * 8 + (size_t)kCmQB * kGroups * 8 + (size_t)kCmQB * K * 8;
+        MASK_CUDA(cudaFuncSetAttribute(csr_cm_scan_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        csr_cm_scan_kernel<<<152 * 2, kThreads, smem, s>>>(xrp, xcol, xval, xids, leaf_off, P,
+                                                           poff.get(), pairs.get(), item_off.get(),
+                                                           k0, qrp, qcol, qval, qn.get(), K,
+                                                           pair_out.get());
+        MASK_LAUNCHED("csr_cm_scan");
+    }
+    cm_merge(pair_out.get(), nq, P, K, out64, out_d, s);
 }
 
 void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,

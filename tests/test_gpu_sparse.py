@@ -183,9 +183,12 @@ def oracle_of(idx, X):
     return O.Index(X, [e["centroids"].astype(np.float64) for e in es], [e["labels"] for e in es])
 
 
+@pytest.mark.parametrize("leaf", ["query", "cluster"])
 @pytest.mark.parametrize("k,probes", [(10, [16, 4]), (1, [1, 1]), (10, [3, 2]), (50, [64, 8]),
                                       (100, [2, 1])])
-def test_csr_query_matches_oracle(sparse_c, k, probes):
+def test_csr_query_matches_oracle(monkeypatch, sparse_c, leaf, k, probes):
+    # per-query leaf scan, or cluster-major (k <= 64; k = 100 falls back)
+    monkeypatch.setenv("MASK_LEAF_SCAN", leaf)
     A, Qa, X, _, idx = sparse_c
     Q = Qa.to_dense()
     ref = oracle_of(idx, X)
@@ -193,6 +196,19 @@ def test_csr_query_matches_oracle(sparse_c, k, probes):
     ids_g, d_g = M.mask_query_csr(idx, *dcsr(Qa), k, probes)
     loose = check_knn(X, Q, ids_g, d_g, ids_o, d_o, clear)
     assert loose <= 0.01 * len(Q)
+
+
+@pytest.mark.parametrize("k,probes", [(10, [16, 4]), (1, [3, 2]), (64, [32, 8]), (10, [60, 1])])
+def test_csr_leaf_scans_agree_bitwise(monkeypatch, sparse_c, k, probes):
+    # the cluster-major scan accumulates every (query, row) pair exactly like
+    # the per-query scan; [60, 1] leaves absent leaf slots
+    _, Qa, _, _, idx = sparse_c
+    out = {}
+    for leaf in ["query", "cluster"]:
+        monkeypatch.setenv("MASK_LEAF_SCAN", leaf)
+        out[leaf] = M.mask_query_csr(idx, *dcsr(Qa), k, probes)
+    assert torch.equal(out["query"][0], out["cluster"][0])
+    assert torch.equal(out["query"][1], out["cluster"][1])
 
 
 def test_csr_probing_everything_is_exact_knn(sparse_c):
