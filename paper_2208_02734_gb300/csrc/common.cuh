@@ -224,7 +224,7 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
                     const int64_t *qrp, const int32_t *qcol, const float *qval, int qcap,
                     int64_t nq, int K, int32_t *out32, cudaStream_t s);
 // cluster-major leaf scan for large CSR batches (K <= 64, queries of at most
-// 2,048 nonzeros): same keys as csr_leaf_scan
+// 1,024 nonzeros): same keys as csr_leaf_scan
 bool csr_cm_supported(int K, int longest);
 void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                       const int32_t *xids, const int64_t *leaf_off, int k0, const int32_t *sel,

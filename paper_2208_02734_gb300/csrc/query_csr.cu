@@ -347,16 +347,18 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
 //
 // For large batches the (query, kept leaf cluster) pairs are grouped by
 // cluster (cm_group_pairs, kCmQB pairs per work item) and a cluster's CSR rows
-// are read once per item.  Each query of the item has its own table in shared
-// memory; a lane group takes a row and every lane accumulates, for each
-// query, the same partial sums over the same nonzeros (gl, gl+8, ...) as the
-// per-query scan, reduced by the same shuffle tree: the keys are bit-identical
-// to the per-query scan's.  Each pair keeps its K smallest keys (cm_merge then
-// takes each query's K over its pairs).
+// are read once per item.  The item's queries share one table in shared
+// memory: column -> the kCmQB query values at that column (0 where a query
+// has no entry).  A lane group takes a row; for each nonzero every lane looks
+// the column up once and updates, for each query, the same partial sums as the
+// per-query scan (c = the query's value or 0), reduced by the same shuffle
+// tree: the keys are bit-identical to the per-query scan's.  Each pair keeps
+// its K smallest keys (cm_merge then takes each query's K over its pairs).
 
-constexpr int kCmQB = 16;           // pairs per work item (the grouping's item size)
-constexpr int kCmSlots = 8192;      // table slots of one pass (64 KB)
-constexpr int kCmLongestQuery = kCmSlots / 4;  // tables a quarter full: one query always fits
+constexpr int kCmQB = 16;            // pairs per work item (the grouping's item size)
+constexpr int kCmEntries = 1024;     // distinct columns one pass holds
+constexpr int kCmSlots = 2 * kCmEntries;  // hash slots (at most half full)
+constexpr int kCmLongestQuery = kCmEntries;  // one query always fits a pass
 
 // ||q||^2 of every CSR query by the per-query scan's procedure (lanes gl of a
 // group of 8 over nonzeros gl, gl+8, ..., then the xor tree), one warp each.
@@ -376,10 +378,15 @@ __global__ void csr_query_norm_kernel(const int64_t *__restrict__ qrp,
     }
 }
 
-__device__ __forceinline__ unsigned table_slots(int64_t nnz) {
-    unsigned h = 32;
-    while ((int64_t)h < 4 * nnz) h <<= 1;
-    return h;
+// slot of column col in the union table (or -1 if absent)
+__device__ __forceinline__ int union_find(const int32_t *keys, int32_t col) {
+    unsigned h = qhash(col, kCmSlots - 1);
+    for (;;) {
+        const int32_t k = keys[h];
+        if (k == col) return (int)h;
+        if (k < 0) return -1;
+        h = (h + 1) & (kCmSlots - 1);
+    }
 }
 
 __global__ __launch_bounds__(kThreads) void csr_cm_scan_kernel(
@@ -391,17 +398,18 @@ __global__ __launch_bounds__(kThreads) void csr_cm_scan_kernel(
     const float *__restrict__ qval, const float *__restrict__ qn_all, int K,
     unsigned long long *__restrict__ pair_out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    int32_t *hkey = reinterpret_cast<int32_t *>(smem);                       // [kCmSlots]
-    float *hval = reinterpret_cast<float *>(hkey + kCmSlots);               // [kCmSlots]
-    unsigned long long *cand = reinterpret_cast<unsigned long long *>(hval + kCmSlots);
-    unsigned long long *top = cand + kCmQB * kGroups;                        // [kCmQB][K]
-    __shared__ int s_c, s_hi;
+    float4 *uval = reinterpret_cast<float4 *>(smem);                          // [kCmEntries][4]
+    int32_t *ukey = reinterpret_cast<int32_t *>(uval + kCmEntries * 4);       // [kCmSlots]
+    int32_t *uidx = ukey + kCmSlots;                                          // [kCmSlots]
+    unsigned long long *cand = reinterpret_cast<unsigned long long *>(uidx + kCmSlots);
+    unsigned long long *top = cand + kCmQB * kGroups;                         // [kCmQB][K]
+    __shared__ int s_c, s_hi, s_nent;
     __shared__ int64_t s_pb, s_pe;
-    __shared__ unsigned s_hoff[kCmQB], s_hmask[kCmQB];
     __shared__ float s_qn[kCmQB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = tid / kGroup, gl = tid % kGroup;
+    float *uv = reinterpret_cast<float *>(uval);
     const int64_t n_items = item_off[k0];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         if (tid == 0) {
@@ -421,39 +429,51 @@ __global__ __launch_bounds__(kThreads) void csr_cm_scan_kernel(
         for (int i = tid; i < kCmQB * K; i += kThreads) top[i] = kNoKey;
         const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
         for (int lo = 0; lo < nqb;) {
-            // the queries of this pass: as many as their tables fit
+            // the queries of this pass: as many as fit kCmEntries columns
             if (tid == 0) {
-                unsigned used = 0;
+                int64_t used = 0;
                 int hi = lo;
                 while (hi < nqb) {
                     const int64_t q = pairs[pb + hi] / P;
-                    const unsigned h = table_slots(qrp[q + 1] - qrp[q]);
-                    if (used + h > (unsigned)kCmSlots) break;
-                    s_hoff[hi - lo] = used;
-                    s_hmask[hi - lo] = h - 1;
+                    const int64_t m = qrp[q + 1] - qrp[q];
+                    if (hi > lo && used + m > kCmEntries) break;
                     s_qn[hi - lo] = qn_all[q];
-                    used += h;
+                    used += m;
                     ++hi;
                 }
                 s_hi = hi;
+                s_nent = 0;
             }
+            for (int i = tid; i < kCmSlots; i += kThreads) ukey[i] = -1;
             __syncthreads();
             const int hi = s_hi, np = hi - lo;
-            const int total = (int)(s_hoff[np - 1] + s_hmask[np - 1] + 1);
-            for (int i = tid; i < total; i += kThreads) hkey[i] = -1;
+            // keys of the union (distinct columns claim distinct slots)
+            for (int j = 0; j < np; ++j) {
+                const int64_t q = pairs[pb + lo + j] / P;
+                for (int64_t e = qrp[q] + tid; e < qrp[q + 1]; e += kThreads) {
+                    const int32_t cc = qcol[e];
+                    unsigned h = qhash(cc, kCmSlots - 1);
+                    for (;;) {
+                        const int32_t old = atomicCAS(ukey + h, -1, cc);
+                        if (old == -1 || old == cc) break;
+                        h = (h + 1) & (kCmSlots - 1);
+                    }
+                }
+            }
+            __syncthreads();
+            // an entry (row of kCmQB values, zeroed) per occupied slot
+            for (int i = tid; i < kCmSlots; i += kThreads)
+                if (ukey[i] >= 0) {
+                    const int e = atomicAdd(&s_nent, 1);
+                    uidx[i] = e;
+#pragma unroll
+                    for (int v4 = 0; v4 < 4; ++v4) uval[e * 4 + v4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             __syncthreads();
             for (int j = 0; j < np; ++j) {
                 const int64_t q = pairs[pb + lo + j] / P;
-                int32_t *hk = hkey + s_hoff[j];
-                float *hv = hval + s_hoff[j];
-                const unsigned hm = s_hmask[j];
-                for (int64_t e = qrp[q] + tid; e < qrp[q + 1]; e += kThreads) {
-                    // column ids of a row are distinct, so every insert claims its own slot
-                    const int32_t cc = qcol[e];
-                    unsigned h = qhash(cc, hm);
-                    while (atomicCAS(hk + h, -1, cc) != -1) h = (h + 1) & hm;
-                    hv[h] = qval[e];
-                }
+                for (int64_t e = qrp[q] + tid; e < qrp[q + 1]; e += kThreads)
+                    uv[uidx[union_find(ukey, qcol[e])] * kCmQB + j] = qval[e];
             }
             __syncthreads();
             for (int64_t r0 = rb; r0 < re; r0 += kGroups) {
@@ -467,16 +487,27 @@ __global__ __launch_bounds__(kThreads) void csr_cm_scan_kernel(
                 }
                 if (ok) {
                     for (int64_t e = xrp[row] + gl; e < xrp[row + 1]; e += kGroup) {
-                        const int32_t cc = __ldg(xcol + e);
                         const float v = __ldg(xval + e);
+                        const int slot = union_find(ukey, __ldg(xcol + e));
+                        if (slot >= 0) {
+                            const float4 *qv = uval + uidx[slot] * 4;
 #pragma unroll
-                        for (int j = 0; j < kCmQB; ++j) {
-                            if (j < np) {
-                                const float cv = qlookup(hkey + s_hoff[j], hval + s_hoff[j],
-                                                         s_hmask[j], cc);
-                                const float d = v - cv;
-                                A[j] = fmaf(d, d, A[j]);
-                                B[j] = fmaf(cv, cv, B[j]);
+                            for (int v4 = 0; v4 < 4; ++v4) {
+                                const float4 w = qv[v4];
+                                const float cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                for (int t = 0; t < 4; ++t) {
+                                    const float d = v - cv[t];
+                                    A[v4 * 4 + t] = fmaf(d, d, A[v4 * 4 + t]);
+                                    B[v4 * 4 + t] = fmaf(cv[t], cv[t], B[v4 * 4 + t]);
+                                }
+                            }
+                        } else {
+                            // no query has this column: c = 0 for every query
+#pragma unroll
+                            for (int j = 0; j < kCmQB; ++j) {
+                                A[j] = fmaf(v, v, A[j]);
+                                B[j] = fmaf(0.f, 0.f, B[j]);
                             }
                         }
                     }
@@ -618,7 +649,8 @@ void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval
     MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
     {
         ProfRegion pr("csr_scan_leaf_cm", s, 0.0);
-        const size_t smem = (size_t)kCmSlots * 8 + (size_t)kCmQB * kGroups * 8 + (size_t)kCmQB * K * 8;
+        const size_t smem = (size_t)kCmEntries * kCmQB * 4 + (size_t)kCmSlots * 8 +
+                            (size_t)kCmQB * kGroups * 8 + (size_t)kCmQB * K * 8;
         MASK_CUDA(cudaFuncSetAttribute(csr_cm_scan_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         csr_cm_scan_kernel<<<152 * 2, kThreads, smem, s>>>(xrp, xcol, xval, xids, leaf_off, P,
