@@ -223,9 +223,11 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
                     const int64_t *off, const int32_t *sel, int P, int64_t root_end,
                     const int64_t *qrp, const int32_t *qcol, const float *qval, int qcap,
                     int64_t nq, int K, int32_t *out32, cudaStream_t s);
-// cluster-major leaf scan for large CSR batches (K <= 64, queries of at most
-// 1,024 nonzeros): same keys as csr_leaf_scan
-bool csr_cm_supported(int K, int longest);
+// cluster-major leaf scan for large CSR batches (K <= 64): same keys as
+// csr_leaf_scan; queries longer than csr_cm_longest_query() nonzeros come out
+// empty and must be served by csr_leaf_scan(..., min_nnz = that length)
+bool csr_cm_supported(int K);
+int csr_cm_longest_query();
 void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                       const int32_t *xids, const int64_t *leaf_off, int k0, const int32_t *sel,
                       int P, const int64_t *qrp, const int32_t *qcol, const float *qval,
@@ -239,7 +241,8 @@ size_t csr_leaf_scan_smem(int K, int P, int longest);
 void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                    const int32_t *xids, const int64_t *off, const int32_t *sel, int P,
                    const int64_t *qrp, const int32_t *qcol, const float *qval, int longest,
-                   int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s);
+                   int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s,
+                   int64_t min_nnz = -1);  // only queries with more nonzeros than this
 
 // assign.cu -- labels[i] = argmin_j ||x_i - c_j||^2 (ties to the smallest j)
 void assign_labels(const float *X, const float *xn, int64_t n, int dp, const float *C, int k,

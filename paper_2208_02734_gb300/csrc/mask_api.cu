@@ -776,16 +776,22 @@ mask_status mask_query_csr(const mask_index *index, const int64_t *row_ptr, cons
         // leaf scan: cluster-major when the batch keeps each leaf cluster several
         // times on average (same keys), else query by query
         const int k0 = index->lv[0].k;
-        bool cluster_major = csr_cm_supported(k, in.longest) && nq * (int64_t)p[0] >= 4 * (int64_t)k0;
+        bool cluster_major = csr_cm_supported(k) && nq * (int64_t)p[0] >= 4 * (int64_t)k0;
         if (const char *m = std::getenv("MASK_LEAF_SCAN")) {
-            if (std::strcmp(m, "cluster") == 0) cluster_major = csr_cm_supported(k, in.longest);
+            if (std::strcmp(m, "cluster") == 0) cluster_major = csr_cm_supported(k);
             if (std::strcmp(m, "query") == 0) cluster_major = false;
         }
-        if (cluster_major)
+        if (cluster_major) {
             csr_cm_leaf_scan(index->xrp.get(), index->xcol.get(), index->xval.get(),
                              index->xids.get(), index->lv[0].off.get(), k0, sel[0].get(), p[0],
                              in.rp->p, in.col->p, in.val->p, nq, k, ids.p, dd.p, s);
-        else
+            // queries too long for the cluster-major tables, query by query
+            if (in.longest > csr_cm_longest_query())
+                csr_leaf_scan(index->xrp.get(), index->xcol.get(), index->xval.get(),
+                              index->xids.get(), index->lv[0].off.get(), sel[0].get(), p[0],
+                              in.rp->p, in.col->p, in.val->p, qcap, nq, k, ids.p, dd.p, s,
+                              csr_cm_longest_query());
+        } else
             csr_leaf_scan(index->xrp.get(), index->xcol.get(), index->xval.get(),
                           index->xids.get(), index->lv[0].off.get(), sel[0].get(), p[0], in.rp->p,
                           in.col->p, in.val->p, qcap, nq, k, ids.p, dd.p, s);

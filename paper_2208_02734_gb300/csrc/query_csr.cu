@@ -230,7 +230,7 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     const float *__restrict__ xval, const int32_t *__restrict__ xids,
     const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P,
     const int64_t *__restrict__ qrp, const int32_t *__restrict__ qcol,
-    const float *__restrict__ qval, int hslots, int K, int KP, int S,
+    const float *__restrict__ qval, int hslots, int64_t min_nnz, int K, int KP, int S,
     int64_t *__restrict__ out64, float *__restrict__ out_d) {
     extern __shared__ __align__(16) unsigned char smem[];
     ScanSmem sm;
@@ -247,6 +247,7 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     const int tid = threadIdx.x;
     const int64_t q = blockIdx.x;
     const int64_t qb = qrp[q], qe = qrp[q + 1];
+    if (qe - qb <= min_nnz) return;  // served by another scan (block-uniform exit)
     // this query's table: the smallest power of two >= 4 x its nonzeros (>= 32)
     unsigned hsize = 32;
     while ((int64_t)hsize < 4 * (qe - qb) && (int)hsize < hslots) hsize <<= 1;
@@ -629,7 +630,19 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
     MASK_LAUNCHED("csr_level_scan");
 }
 
-bool csr_cm_supported(int K, int longest) { return K >= 1 && K <= 64 && longest <= kCmLongestQuery; }
+bool csr_cm_supported(int K) { return K >= 1 && K <= 64; }
+
+int csr_cm_longest_query() { return kCmLongestQuery; }
+
+// sel_cm = sel with the slots of queries longer than kCmLongestQuery blanked
+__global__ void blank_long_kernel(const int32_t *__restrict__ sel, const int64_t *__restrict__ qrp,
+                                  int64_t nq, int P, int32_t *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nq * P;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / P;
+        out[e] = qrp[q + 1] - qrp[q] > kCmLongestQuery ? -1 : sel[e];
+    }
+}
 
 void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                       const int32_t *xids, const int64_t *leaf_off, int k0, const int32_t *sel,
@@ -640,9 +653,15 @@ void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval
     csr_query_norm_kernel<<<(unsigned)std::min<int64_t>((nq + 7) / 8, 152 * 32), 256, 0, s>>>(
         qrp, qval, nq, qn.get());
     MASK_LAUNCHED("csr_query_norm");
+    // queries longer than one pass holds are served by the per-query scan:
+    // their slots are blanked here (their rows come out empty and are rewritten)
+    Scratch<int32_t> sel_cm((size_t)nq * P, s);
+    blank_long_kernel<<<(unsigned)std::min<int64_t>((nq * P + 255) / 256, 152 * 32), 256, 0, s>>>(
+        sel, qrp, nq, P, sel_cm.get());
+    MASK_LAUNCHED("blank_long");
     Scratch<int32_t> pairs;
     Scratch<int64_t> poff, item_off;
-    cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
+    cm_group_pairs(sel_cm.get(), nq, P, k0, pairs, poff, item_off, s);
     const int64_t npairs = nq * P;
     Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
     // pairs of an absent parent (sel = -1) are in no work item: empty lists
@@ -665,7 +684,8 @@ void csr_cm_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval
 void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                    const int32_t *xids, const int64_t *off, const int32_t *sel, int P,
                    const int64_t *qrp, const int32_t *qcol, const float *qval, int longest,
-                   int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s) {
+                   int64_t nq, int K, int64_t *out64, float *out_d, cudaStream_t s,
+                   int64_t min_nnz) {
     if (nq == 0) return;
     MASK_REQUIRE(K >= 1 && K <= 4096, "csr_leaf_scan: K out of range");
     const size_t smem = csr_leaf_scan_smem(K, P, longest);
@@ -675,7 +695,7 @@ void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     csr_leaf_scan_kernel<<<(unsigned)nq, kThreads, smem, s>>>(xrp, xcol, xval, xids, off, sel, P,
                                                               qrp, qcol, qval,
-                                                              csr_leaf_table_slots(longest), K,
+                                                              csr_leaf_table_slots(longest), min_nnz, K,
                                                               next_pow2(K), list_size(K), out64,
                                                               out_d);
     MASK_LAUNCHED("csr_leaf_scan");

@@ -211,6 +211,29 @@ def test_csr_leaf_scans_agree_bitwise(monkeypatch, sparse_c, k, probes):
     assert torch.equal(out["query"][1], out["cluster"][1])
 
 
+def test_csr_long_queries_in_a_cluster_major_batch():
+    # queries with more nonzeros than a cluster-major pass holds are served by
+    # the per-query scan inside the same batch: both modes agree bit for bit
+    A = synth.sparse_tfidf_like(3000, 3000, nnz_mean=30.0, seed=4)
+    Qa = synth.sparse_tfidf_like(120, 3000, nnz_mean=700.0, nnz_sigma=0.5, seed=5)
+    assert np.diff(Qa.row_ptr).max() > 1024
+    with M.mask_build_csr(*dcsr(A), 3000, [40, 5], 4, seed=0) as idx:
+        out = {}
+        for leaf in ["query", "cluster"]:
+            import os
+            os.environ["MASK_LEAF_SCAN"] = leaf
+            try:
+                out[leaf] = M.mask_query_csr(idx, *dcsr(Qa), 10, [12, 3])
+            finally:
+                del os.environ["MASK_LEAF_SCAN"]
+        assert torch.equal(out["query"][0], out["cluster"][0])
+        assert torch.equal(out["query"][1], out["cluster"][1])
+        X, Q = A.to_dense(), Qa.to_dense()
+        ref = oracle_of(idx, X)
+        ids_o, d_o, clear = ref.query(Q, 10, [12, 3])
+        check_knn(X, Q, out["cluster"][0], out["cluster"][1], ids_o, d_o, clear)
+
+
 def test_csr_probing_everything_is_exact_knn(sparse_c):
     A, Qa, X, _, idx = sparse_c
     Q = Qa.to_dense()[:100]
