@@ -355,6 +355,7 @@ def weak_scaling_value(world, steps, nq, local_query_ms, local_total_ms, device)
 
 KERNEL_KIND = {"assign_tc": "tensor", "assign_gemm": "alu", "assign_recheck": "alu",
                "csr_spmm_assign": "alu", "csr_scan_leaf": "hbm", "csr_scan_level": "hbm",
+               "csr_scan_leaf_cm": "hbm",
                "csr_centroid_update": "hbm",
                "scan_leaf_cm": "hbm", "leaf_group": "hbm", "leaf_merge": "hbm",
                "scan_topk_leaf": "hbm",

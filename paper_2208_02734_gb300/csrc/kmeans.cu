@@ -524,7 +524,6 @@ __device__ __forceinline__ void csr_row_ab(const int64_t b, const int64_t e,
                                            int gl, float &A, float &B) {
     A = 0.f;
     B = 0.f;
-#pragma unroll 4
     for (int64_t j = b + gl; j < e; j += kKppGroup) {
         const float cv = cden[__ldg(col + j)];
         const float e0 = __ldg(val + j) - cv;
@@ -572,7 +571,7 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_csr_kernel(
     const float cn = s_cn;
     const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
     double local = 0.0;
-#pragma unroll 1
+#pragma unroll 2
     for (int q = 0; q < kKppRows / G; ++q) {
         const int64_t i = r0 + g + (int64_t)q * G;
         const bool ok = i < m;  // every lane reaches the shuffles; a row past the end is empty
