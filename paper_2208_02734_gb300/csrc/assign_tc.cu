@@ -76,12 +76,9 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // A drain (waiting for this thread's own copies before the CTA exits) ignores
 // the abort word and is bounded by time only.
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s; a healthy wait takes microseconds
-// The clock starts at the first check (after 256 failed polls), not on
-// entry: a wait that succeeds at once -- the common case, several per tile in
-// the producer and MMA loops -- never reads %globaltimer.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *abort_word,
                                           bool drain = false) {
-    uint64_t t0 = 0;
+    const uint64_t t0 = globaltimer_ns();
     for (uint32_t i = 0;; ++i) {
         uint32_t ok;
         asm volatile(
@@ -93,9 +90,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *ab
             : "memory");
         if (ok) return true;
         if ((i & 255u) == 255u) {
-            const uint64_t now = globaltimer_ns();
-            if (t0 == 0) t0 = now;
-            if ((!drain && *(volatile int *)abort_word != 0) || now - t0 > kWaitNs) {
+            if ((!drain && *(volatile int *)abort_word != 0) || globaltimer_ns() - t0 > kWaitNs) {
                 atomicExch(abort_word, 1);
                 return false;
             }
