@@ -199,6 +199,18 @@ struct Top4 {
             } else { v3 = d; }
         }
     }
+    // The same insertion without branches (a no-op when d >= v3): with the
+    // list sorted, d < v0 implies d < v1 implies d < v2.
+    __device__ __forceinline__ void push_nb(float d, int j) {
+        const bool c0 = d < v0, c1 = d < v1, c2 = d < v2;
+        v3 = c2 ? v2 : fminf(v3, d);
+        v2 = c1 ? v1 : (c2 ? d : v2);
+        i2 = c1 ? i1 : (c2 ? j : i2);
+        v1 = c0 ? v0 : (c1 ? d : v1);
+        i1 = c0 ? i0 : (c1 ? j : i1);
+        v0 = c0 ? d : v0;
+        i0 = c0 ? j : i0;
+    }
 };
 
 // ------------------------------------------------------------- main kernel
@@ -348,26 +360,42 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty(a));
+            // keys of this thread's 64 columns, with the minimum of each
+            // group of 8; columns past k have norm +inf, so their keys never
+            // enter the list
             const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][col]);
-            float key[64];
-            float mn = FLT_MAX;
+            float key[64], gm[8];
 #pragma unroll
-            for (int e4 = 0; e4 < 16; ++e4) {
-                const float4 c = cn4[e4];
-                const uint32_t *uu = e4 < 8 ? u0 : u1;
-                const int b = (e4 & 7) * 4;
-                key[e4 * 4 + 0] = fmaf(-2.f, __uint_as_float(uu[b + 0]), c.x);
-                key[e4 * 4 + 1] = fmaf(-2.f, __uint_as_float(uu[b + 1]), c.y);
-                key[e4 * 4 + 2] = fmaf(-2.f, __uint_as_float(uu[b + 2]), c.z);
-                key[e4 * 4 + 3] = fmaf(-2.f, __uint_as_float(uu[b + 3]), c.w);
-                mn = fminf(mn, fminf(fminf(key[e4 * 4 + 0], key[e4 * 4 + 1]),
-                                     fminf(key[e4 * 4 + 2], key[e4 * 4 + 3])));
+            for (int g = 0; g < 8; ++g) {
+                const uint32_t *uu = g < 4 ? u0 : u1;
+                const int b = (g & 3) * 8;
+                const float4 c0v = cn4[2 * g], c1v = cn4[2 * g + 1];
+                float *kk = key + 8 * g;
+                kk[0] = fmaf(-2.f, __uint_as_float(uu[b + 0]), c0v.x);
+                kk[1] = fmaf(-2.f, __uint_as_float(uu[b + 1]), c0v.y);
+                kk[2] = fmaf(-2.f, __uint_as_float(uu[b + 2]), c0v.z);
+                kk[3] = fmaf(-2.f, __uint_as_float(uu[b + 3]), c0v.w);
+                kk[4] = fmaf(-2.f, __uint_as_float(uu[b + 4]), c1v.x);
+                kk[5] = fmaf(-2.f, __uint_as_float(uu[b + 5]), c1v.y);
+                kk[6] = fmaf(-2.f, __uint_as_float(uu[b + 6]), c1v.z);
+                kk[7] = fmaf(-2.f, __uint_as_float(uu[b + 7]), c1v.w);
+                gm[g] = fminf(fminf(fminf(kk[0], kk[1]), fminf(kk[2], kk[3])),
+                              fminf(fminf(kk[4], kk[5]), fminf(kk[6], kk[7])));
             }
-            if (mn < t4.v3) {
+            const float mn = fminf(fminf(fminf(gm[0], gm[1]), fminf(gm[2], gm[3])),
+                                   fminf(fminf(gm[4], gm[5]), fminf(gm[6], gm[7])));
+            // insertions in column order (ties keep the earliest column);
+            // a group is scanned when a key of some lane's group is below that
+            // lane's current fourth, branch-free, so the warp never diverges
+            if (__any_sync(kFull, mn < t4.v3)) {
                 const int cb = c0 + col;
 #pragma unroll
-                for (int e = 0; e < 64; ++e)
-                    if (key[e] < t4.v3 && cb + e < k) t4.push(key[e], cb + e);
+                for (int g = 0; g < 8; ++g) {
+                    if (__any_sync(kFull, gm[g] < t4.v3)) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) t4.push_nb(key[8 * g + e], cb + 8 * g + e);
+                    }
+                }
             }
             if (half == 0) s_cn[a ^ 1][r] = cn_next;  // read after the next tile's barrier
         }
@@ -463,6 +491,13 @@ __global__ void split_tf32_kernel(const float *__restrict__ src, int64_t rows, i
         hi[e] = h;
         lo[e] = x - h;
     }
+}
+
+// Norms of the padding columns of the last 128-centroid tile: +inf, so their
+// keys (-2 * 0 + inf) never enter a row's list.
+__global__ void pad_inf_kernel(float *__restrict__ cn, int k, int total) {
+    const int i = k + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) cn[i] = __int_as_float(0x7f800000);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -562,14 +597,17 @@ void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *lab
                cudaStream_t s) {
     const int dp = p.dp, dpk = p.dpk;
     const int ntiles = (k + TC_N - 1) / TC_N;
-    // centroid norms padded to whole 128-centroid tiles (zeros past k)
+    // centroid norms padded to whole 128-centroid tiles (+inf past k)
     Scratch<float> cn((size_t)ntiles * TC_N, s), cmax(1, s), Ch((size_t)k * dpk, s),
         Cl((size_t)k * dpk, s);
-    MASK_CUDA(cudaMemsetAsync(cn.get(), 0, sizeof(float) * ntiles * TC_N, s));
     Scratch<int4> list3(p.n, s);
     Scratch<int32_t> listF(p.n, s);
     Scratch<int> counts(2, s);
     row_sqnorm(C, k, dp, cn.get(), s);
+    if (ntiles * TC_N > k) {
+        pad_inf_kernel<<<1, TC_N, 0, s>>>(cn.get(), k, ntiles * TC_N);
+        MASK_LAUNCHED("pad_inf");
+    }
     max_reduce(cn.get(), k, cmax.get(), s);
     split_tf32_kernel<<<grid_cap((int64_t)k * dpk), 256, 0, s>>>(C, k, dp, dpk, Ch.get(), Cl.get());
     MASK_LAUNCHED("split_tf32");
