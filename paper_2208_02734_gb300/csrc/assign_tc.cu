@@ -12,9 +12,10 @@
 // One CTA owns 128 rows of X.  Their hi/lo tiles stay in shared memory while
 // 128-centroid tiles of C stream through a TMA pipeline; the accumulator is
 // double-buffered in TMEM so the epilogue of tile j overlaps the MMAs of j+1.
-// Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer, warp 2 = TMEM
-// allocator, warps 4-7 = epilogue (one thread per row, TMEM lane = row), which
-// keeps the four smallest distances of its row over all k centroids.
+// Warp roles: warp 0 = TMA producer (C tiles and their norms), warp 1 = MMA
+// issuer, warp 2 = TMEM allocator, warps 4-11 = epilogue (one thread per row
+// and half of each tile's columns, TMEM lane = row), which keeps the four
+// smallest distances of its row over all k centroids.
 //
 // A row's label is certain when its best and second-best distances differ by
 // more than twice the error bound of the expanded form; otherwise the row is
@@ -42,6 +43,7 @@ constexpr int TC_THREADS = (4 + TC_EPI_WARPS) * 32;
 constexpr int TC_EPI_COLS = TC_N / (TC_EPI_WARPS / 4);   // columns per epilogue thread per tile
 constexpr int TC_BOX_K = 32;            // fp32 columns per TMA box (128 bytes)
 constexpr int TC_BOX_BYTES = TC_M * TC_BOX_K * 4;   // 16 KB
+constexpr int TC_NRING = 8;             // slots of the centroid-norm ring
 
 // instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
@@ -104,6 +106,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
         "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
 
@@ -231,19 +243,22 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     const uint32_t A_hi = base, A_lo = base + KB * TC_BOX_BYTES;
     const uint32_t B0 = base + 2u * KB * TC_BOX_BYTES;
     uint64_t *bars = reinterpret_cast<uint64_t *>(basep + 2u * KB * TC_BOX_BYTES + S * kStage);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5 + 2 * TC_NRING);
     __shared__ int s_err;
-    __shared__ __align__(16) float s_cn[2][TC_N];
+    __shared__ __align__(16) float s_cn[TC_NRING][TC_N];   // norms of the C tiles in flight
     __shared__ float s_top[TC_M][4];      // second-half top-4 lists, merged at the end
     __shared__ int s_topi[TC_M][3];
 
-    // barriers: a_full | b_full[S] | b_empty[S] | acc_full[2] | acc_empty[2]
+    // barriers: a_full | b_full[S] | b_empty[S] | acc_full[2] | acc_empty[2] |
+    //           n_full[TC_NRING] | n_empty[TC_NRING]
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t a_full = bar0;
     auto b_full = [&](int s) { return bar0 + 8u * (1 + s); };
     auto b_empty = [&](int s) { return bar0 + 8u * (1 + S + s); };
     auto acc_full = [&](int a) { return bar0 + 8u * (1 + 2 * S + a); };
     auto acc_empty = [&](int a) { return bar0 + 8u * (3 + 2 * S + a); };
+    auto n_full = [&](int q) { return bar0 + 8u * (5 + 2 * S + q); };
+    auto n_empty = [&](int q) { return bar0 + 8u * (5 + 2 * S + TC_NRING + q); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TC_M;
@@ -261,6 +276,10 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         for (int a = 0; a < 2; ++a) {
             mbar_init(acc_full(a), 1);
             mbar_init(acc_empty(a), TC_EPI_WARPS);
+        }
+        for (int q = 0; q < TC_NRING; ++q) {
+            mbar_init(n_full(q), 1);
+            mbar_init(n_empty(q), TC_EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -282,7 +301,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             tma_load_2d(A_hi + kb * TC_BOX_BYTES, &tmXh, kb * TC_BOX_K, (int)row0, a_full);
             tma_load_2d(A_lo + kb * TC_BOX_BYTES, &tmXl, kb * TC_BOX_K, (int)row0, a_full);
         }
-        int armed = 0;
+        int armed = 0, armedN = 0;
         bool ok = true;
         for (int j = 0; j < ntiles; ++j) {
             const int s = j % S, u = j / S;
@@ -294,15 +313,25 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
                 tma_load_2d(bl + kb * TC_BOX_BYTES, &tmCl, kb * TC_BOX_K, j * TC_N, b_full(s));
             }
             armed = j + 1;
+            // the tile's 128 norms (the ring is 8 tiles deep, far ahead of the epilogue)
+            const int q = j % TC_NRING, w = j / TC_NRING;
+            if (w > 0 && !mbar_wait(n_empty(q), (w - 1) & 1, err)) { ok = false; break; }
+            mbar_expect_tx(n_full(q), TC_N * 4u);
+            bulk_load(smem_u32(&s_cn[q][0]), cn_pad + (int64_t)j * TC_N, TC_N * 4u, n_full(q));
+            armedN = j + 1;
         }
         // every load this thread issued must land before the CTA may exit
         mbar_wait(a_full, 0, err, true);
         for (int j = (armed > S ? armed - S : 0); j < armed; ++j)
             mbar_wait(b_full(j % S), (j / S) & 1, err, true);
+        for (int j = (armedN > TC_NRING ? armedN - TC_NRING : 0); j < armedN; ++j)
+            mbar_wait(n_full(j % TC_NRING), (j / TC_NRING) & 1, err, true);
         if (!ok) s_err = 1;
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         bool ok = mbar_wait(a_full, 0, err);
+        // descriptors advance by (byte offset >> 4) in their address field
+        const uint64_t dAh = sw128_desc(A_hi), dAl = sw128_desc(A_lo);
         int last = -1;
         for (int j = 0; ok && j < ntiles; ++j) {
             const int s = j % S, u = j / S, a = j & 1, v = j >> 1;
@@ -312,13 +341,16 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(a * TC_N);
             const uint32_t bh = B0 + s * kStage, bl = bh + KB * TC_BOX_BYTES;
-            for (int kk = 0; kk < ksteps; ++kk) {
-                const uint32_t off = (uint32_t)(kk >> 2) * TC_BOX_BYTES + (uint32_t)(kk & 3) * 32u;
-                const uint64_t ah = sw128_desc(A_hi + off), al = sw128_desc(A_lo + off);
-                const uint64_t ch = sw128_desc(bh + off), cl = sw128_desc(bl + off);
-                mma_tf32(d, ah, ch, kk > 0 ? 1u : 0u);
-                mma_tf32(d, ah, cl, 1u);
-                mma_tf32(d, al, ch, 1u);
+            const uint64_t dBh = sw128_desc(bh), dBl = sw128_desc(bl);
+#pragma unroll
+            for (int kk = 0; kk < 4 * KB; ++kk) {
+                if (kk < ksteps) {
+                    const uint64_t off =
+                        (uint64_t)((kk >> 2) * (TC_BOX_BYTES >> 4) + (kk & 3) * 2);
+                    mma_tf32(d, dAh + off, dBh + off, kk > 0 ? 1u : 0u);
+                    mma_tf32(d, dAh + off, dBl + off, 1u);
+                    mma_tf32(d, dAl + off, dBh + off, 1u);
+                }
             }
             mma_commit(b_empty(s));    // the C tile's stage is free once these MMAs finish
             mma_commit(acc_full(a));   // accumulator a is ready for the epilogue
@@ -330,8 +362,8 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     } else if (warp >= 4) {
         // ---------------- epilogue: one row per thread, half the columns ----------------
         // Rows are ranked by key = ||c||^2 - 2 x.c (the row's ||x||^2 is
-        // added back at the end); the norms of each C tile are staged in
-        // shared memory (double-buffered with the accumulators).
+        // added back at the end); the norms of each C tile arrive in a ring
+        // of shared-memory slots filled by the producer.
         const int quad = warp & 3;                  // TMEM lane quadrant of this warp
         const int half = (warp - 4) >> 2;           // column half of each tile
         const int r = quad * 32 + lane;
@@ -340,14 +372,12 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         Top4 t4;
         t4.init();
         bool ok = true;
-        if (half == 0) s_cn[0][r] = cn_pad[r];  // norms of tile 0
         for (int j = 0; j < ntiles; ++j) {
             const int a = j & 1, v = j >> 1;
+            const int q = j % TC_NRING, w = j / TC_NRING;
             const int c0 = j * TC_N;
-            const float cn_next = (half == 0 && j + 1 < ntiles) ? cn_pad[c0 + TC_N + r] : 0.f;
-            ok = mbar_wait(acc_full(a), v & 1, err);
-            ok = epi_bar_and(ok);  // also publishes s_cn[a] to all epilogue threads
-            if (!ok) break;
+            ok = mbar_wait(acc_full(a), v & 1, err) && mbar_wait(n_full(q), w & 1, err);
+            if (!__all_sync(kFull, ok)) { ok = false; break; }  // the warp leaves as one
             tc_fence_after();
             const int col = half * TC_EPI_COLS;
             const uint32_t taddr =
@@ -363,7 +393,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             // keys of this thread's 64 columns, with the minimum of each
             // group of 8; columns past k have norm +inf, so their keys never
             // enter the list
-            const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[a][col]);
+            const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[q][col]);
             float key[64], gm[8];
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
@@ -382,22 +412,38 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
                 gm[g] = fminf(fminf(fminf(kk[0], kk[1]), fminf(kk[2], kk[3])),
                               fminf(fminf(kk[4], kk[5]), fminf(kk[6], kk[7])));
             }
+            // the norms are in registers: hand the ring slot back
+            __syncwarp();
+            if (lane == 0) mbar_arrive(n_empty(q));
             const float mn = fminf(fminf(fminf(gm[0], gm[1]), fminf(gm[2], gm[3])),
                                    fminf(fminf(gm[4], gm[5]), fminf(gm[6], gm[7])));
-            // insertions in column order (ties keep the earliest column);
-            // a group is scanned when a key of some lane's group is below that
-            // lane's current fourth, branch-free, so the warp never diverges
+            // insertions in column order (ties keep the earliest column),
+            // under warp-uniform branches only.  A group is visited when some
+            // lane has a key in it below that lane's current fourth; when no
+            // lane has more than one such key, each lane inserts just its
+            // group minimum (a no-op where it is not below the fourth),
+            // otherwise all eight keys go through the branch-free insertion.
             if (__any_sync(kFull, mn < t4.v3)) {
                 const int cb = c0 + col;
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
                     if (__any_sync(kFull, gm[g] < t4.v3)) {
+                        int cnt = 0, first = 7;
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) t4.push_nb(key[8 * g + e], cb + 8 * g + e);
+                        for (int e = 7; e >= 0; --e) {
+                            cnt += key[8 * g + e] < t4.v3 ? 1 : 0;
+                            first = key[8 * g + e] == gm[g] ? e : first;
+                        }
+                        if (__any_sync(kFull, cnt > 1)) {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                t4.push_nb(key[8 * g + e], cb + 8 * g + e);
+                        } else {
+                            t4.push_nb(gm[g], cb + 8 * g + first);
+                        }
                     }
                 }
             }
-            if (half == 0) s_cn[a ^ 1][r] = cn_next;  // read after the next tile's barrier
         }
         // merge the two half-row lists: the second half hands its list over
         if (half == 1) {
@@ -541,7 +587,8 @@ int grid_cap(int64_t work) {
 
 template <int KB, int S>
 size_t tc_smem_bytes() {
-    return 1024 + 2u * KB * TC_BOX_BYTES + (size_t)S * 2u * KB * TC_BOX_BYTES + (2 * S + 5) * 8 + 16;
+    return 1024 + 2u * KB * TC_BOX_BYTES + (size_t)S * 2u * KB * TC_BOX_BYTES +
+           (2 * S + 5 + 2 * TC_NRING) * 8 + 16;
 }
 
 }  // namespace
