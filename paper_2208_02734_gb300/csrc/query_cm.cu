@@ -90,151 +90,297 @@ __global__ void __launch_bounds__(1024) item_scan_kernel(const int64_t *__restri
     if (tid == 1023) item_off[k0] = part[1023];
 }
 
+// item_c[i] = the cluster of work item i (items of cluster c are
+// item_off[c] .. item_off[c+1]-1).
+__global__ void item_cluster_kernel(const int64_t *__restrict__ item_off, int k0,
+                                    int32_t *__restrict__ item_c) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k0; c += gridDim.x * blockDim.x)
+        for (int64_t i = item_off[c]; i < item_off[c + 1]; ++i) item_c[i] = c;
+}
+
+// Asynchronous global -> shared copies; a zero size writes zeros (the source
+// is then not read, but is still a valid address).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// hi = x rounded to TF32, lo = x - hi (exact in FP32; the MMA reads its TF32 part)
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = h;
+    lo = __float_as_uint(x - __uint_as_float(h));
+}
+
+// D += A (16 x 8, row-major) * B (8 x 8, column-major), TF32 in, FP32 accumulate
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                                uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Floats per staged row: dp + 4 or dp + 8, so the row stride is an odd number
+// of float4s and the 8 lanes of each 128-bit shared-memory phase that read 8
+// consecutive rows hit 8 different bank groups (and the MMA fragment loads,
+// 8 rows x 4 consecutive columns, hit 32 different banks).  The padding
+// columns hold zeros: the MMA's last k-step may read them.
+__host__ __device__ inline int cm_stride(int dp4) { return 4 * (dp4 + ((dp4 & 1) ? 2 : 1)); }
+
+// One chunk of a block's work: up to CM_R rows of the cluster of one item.
+struct CmChunk {
+    int64_t item;   // < 0: no more work
+    int c, nqb, nr;
+    int64_t pb, r0, re;
+    bool first;     // first chunk of its item
+};
+
+// The first chunk at or after item `it` (stepping by `step`) whose cluster
+// has rows; items of empty clusters have nothing to scan (their pair lists
+// stay empty).
+__device__ __forceinline__ CmChunk cm_first_chunk(int64_t it, int64_t step, int64_t n_items,
+                                                  const int32_t *__restrict__ item_c,
+                                                  const int64_t *__restrict__ item_off,
+                                                  const int64_t *__restrict__ poff,
+                                                  const int64_t *__restrict__ leaf_off) {
+    CmChunk ch;
+    ch.item = -1;
+    for (; it < n_items; it += step) {
+        const int c = item_c[it];
+        const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
+        if (re <= rb) continue;
+        const int64_t pb = poff[c] + (it - item_off[c]) * CM_QB;
+        const int64_t pe = min(poff[c + 1], pb + CM_QB);
+        ch.item = it;
+        ch.c = c;
+        ch.pb = pb;
+        ch.nqb = (int)(pe - pb);
+        ch.r0 = rb;
+        ch.re = re;
+        ch.nr = (int)min((int64_t)CM_R, re - rb);
+        ch.first = true;
+        break;
+    }
+    return ch;
+}
+
 // One work item = (cluster c, up to CM_QB of its pairs).  xn: row norms;
 // qn: query norms; seed_d [nq x K]: each query's K nearest distances within
 // its nearest kept cluster (the K-th is T_q); mcoef: rounding bound of
 // |expanded form - exact key| per unit of ||x||^2 + ||q||^2.
-__global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
+//
+// A block walks its items' chunks in order; the rows and norms of the next
+// chunk (and the queries of the next item) are copied asynchronously into the
+// other half of double-buffered shared memory while the current chunk is
+// ranked.  Rows are staged row-major (stride cm_stride floats).  The
+// expanded-form dot products run on the tensor cores (mma.sync, 3xTF32:
+// x.q ~ x_hi.q_hi + x_hi.q_lo + x_lo.q_hi); mcoef covers their error.
+__global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
     const float4 *__restrict__ Xs, const float *__restrict__ xn, int dp4,
     const int32_t *__restrict__ xids, const int64_t *__restrict__ leaf_off,
     const float4 *__restrict__ Qp, const float *__restrict__ qn,
     const float *__restrict__ seed_d, float mcoef, int P, const int64_t *__restrict__ poff,
-    const int32_t *__restrict__ pairs, const int64_t *__restrict__ item_off, int k0, int K,
+    const int32_t *__restrict__ pairs, const int64_t *__restrict__ item_off,
+    const int32_t *__restrict__ item_c, int k0, int K,
     unsigned long long *__restrict__ pair_out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int dp = dp4 * 4;
-    float *xs = reinterpret_cast<float *>(smem);                 // [dp][CM_R] rows, transposed
-    float *qs = xs + (size_t)dp * CM_R;                          // [dp][CM_QB] queries, transposed
-    float *D = qs + (size_t)dp * CM_QB;                          // [CM_QB][CM_R] expanded-form distances
-    int32_t *ids = reinterpret_cast<int32_t *>(D + CM_QB * CM_R);// [CM_R] row ids
-    unsigned long long *top = reinterpret_cast<unsigned long long *>(ids + CM_R);  // [CM_QB][K]
-    __shared__ int s_c;
-    __shared__ int64_t s_pb, s_pe;
-    __shared__ __align__(16) float s_xn[CM_R];  // read as float4
-    __shared__ float s_qn[CM_QB], s_tq[CM_QB];
+    const int XS = cm_stride(dp4), XS4 = XS / 4;
+    float *xs = reinterpret_cast<float *>(smem);                 // [2][CM_R][XS] rows
+    float *qs = xs + 2 * CM_R * XS;                              // [2][CM_QB][XS] queries
+    float *D = qs + 2 * CM_QB * XS;                              // [CM_QB][CM_R] expanded form
+    float *xnb = D + CM_QB * CM_R;                               // [2][CM_R] row norms
+    unsigned long long *top = reinterpret_cast<unsigned long long *>(xnb + 2 * CM_R);  // [CM_QB][K]
+    __shared__ float s_qn[2][CM_QB], s_tq[2][CM_QB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n_items = item_off[k0];
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        if (tid == 0) {
-            // the cluster holding this item: last c with item_off[c] <= item
-            int lo = 0, hi = k0 - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
+
+    // stage chunk `ch` into row buffer b (and, for an item's first chunk,
+    // its queries into query buffer qb)
+    // thread -> (row offset, float4 column) of the staging copies
+    const int rstep = CM_THREADS / dp4, rfirst = tid / dp4, c4 = tid - rfirst * dp4;
+    const bool copier = rfirst < rstep;
+    auto prefetch = [&](const CmChunk ch, int b, int qb) {
+        float *xsb = xs + b * CM_R * XS;
+        if (copier)
+            for (int rr = rfirst; rr < CM_R; rr += rstep) {
+                const bool v = rr < ch.nr;
+                cp_async16(xsb + rr * XS + c4 * 4,
+                           v ? (const void *)(Xs + (ch.r0 + rr) * dp4 + c4) : (const void *)Xs, v);
             }
-            s_c = lo;
-            s_pb = poff[lo] + (item - item_off[lo]) * CM_QB;
-            s_pe = min(poff[lo + 1], s_pb + CM_QB);
+        if (tid < CM_R) {
+            const bool v = tid < ch.nr;
+            cp_async4(xnb + b * CM_R + tid, v ? xn + ch.r0 + tid : xn, v);
+        }
+        if (ch.first) {
+            float *qsb = qs + qb * CM_QB * XS;
+            if (copier)
+                for (int q = rfirst; q < CM_QB; q += rstep) {
+                    const bool v = q < ch.nqb;
+                    const int64_t qq = v ? (int64_t)(pairs[ch.pb + q] / P) : 0;
+                    cp_async16(qsb + q * XS + c4 * 4, Qp + qq * dp4 + c4, v);
+                }
+            if (tid < CM_QB) {
+                const bool v = tid < ch.nqb;
+                const int64_t qq = v ? (int64_t)(pairs[ch.pb + tid] / P) : 0;
+                cp_async4(&s_qn[qb][tid], qn + qq, v);
+                cp_async4(&s_tq[qb][tid], seed_d + qq * K + K - 1, v);  // +inf: seed cluster < K rows
+            }
+        }
+        cp_commit();
+    };
+
+    CmChunk cur = cm_first_chunk(blockIdx.x, gridDim.x, n_items, item_c, item_off, poff, leaf_off);
+    if (cur.item < 0) return;
+    for (int i = tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
+    {
+        const int padw = XS - 4 * dp4;  // zero padding columns of every staged row and query
+        for (int i = tid; i < (2 * CM_R + 2 * CM_QB) * padw; i += CM_THREADS)
+            xs[(i / padw) * XS + 4 * dp4 + i % padw] = 0.f;
+    }
+    int buf = 0, qbuf = 0;
+    prefetch(cur, 0, 0);
+    for (;;) {
+        cp_wait_all();
+        __syncthreads();  // cur is staged; every warp is done with the other buffers
+        // the next chunk: the rest of this cluster, else the block's next item
+        CmChunk nxt;
+        if (cur.r0 + CM_R < cur.re) {
+            nxt = cur;
+            nxt.r0 = cur.r0 + CM_R;
+            nxt.nr = (int)min((int64_t)CM_R, cur.re - nxt.r0);
+            nxt.first = false;
+        } else {
+            nxt = cm_first_chunk(cur.item + gridDim.x, gridDim.x, n_items, item_c, item_off, poff,
+                                 leaf_off);
+        }
+        const int nbuf = buf ^ 1, nqbuf = (nxt.item >= 0 && nxt.first) ? (qbuf ^ 1) : qbuf;
+        if (nxt.item >= 0) prefetch(nxt, nbuf, nqbuf);
+
+        const float *xsb = xs + buf * CM_R * XS;
+        const float *qsb = qs + qbuf * CM_QB * XS;
+        const float *xnc = xnb + buf * CM_R;
+        const int nr = cur.nr, nqb = cur.nqb;
+        // expanded-form distances on the tensor cores: warp w -> rows 16w ..
+        // 16w+15 (two 8-row tiles) x all 16 queries; k-steps of 8 columns
+        {
+            const int g = lane >> 2, t = lane & 3;
+            float acc[2][4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+            const float *qa = qsb + g * XS + t, *qb8 = qa + 8 * XS;
+            const float *xb0 = xsb + (16 * warp + g) * XS + t, *xb1 = xb0 + 8 * XS;
+            const int ksteps = (dp4 + 1) >> 1;
+            for (int ks = 0; ks < ksteps; ++ks) {
+                const int k0 = ks * 8;
+                uint32_t ah[4], al[4];
+                tf32_split(qa[k0], ah[0], al[0]);
+                tf32_split(qb8[k0], ah[1], al[1]);
+                tf32_split(qa[k0 + 4], ah[2], al[2]);
+                tf32_split(qb8[k0 + 4], ah[3], al[3]);
+                uint32_t bh0, bl0, bh1, bl1;
+                tf32_split(xb0[k0], bh0, bl0);
+                tf32_split(xb0[k0 + 4], bh1, bl1);
+                mma_tf32_16x8x8(acc[0], ah, bh0, bh1);
+                mma_tf32_16x8x8(acc[0], ah, bl0, bl1);
+                mma_tf32_16x8x8(acc[0], al, bh0, bh1);
+                tf32_split(xb1[k0], bh0, bl0);
+                tf32_split(xb1[k0 + 4], bh1, bl1);
+                mma_tf32_16x8x8(acc[1], ah, bh0, bh1);
+                mma_tf32_16x8x8(acc[1], ah, bl0, bl1);
+                mma_tf32_16x8x8(acc[1], al, bh0, bh1);
+            }
+            // accumulator (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1) of each tile
+            const float qv0 = s_qn[qbuf][g], qv1 = s_qn[qbuf][g + 8];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int row = 16 * warp + 8 * j + 2 * t;
+                const float x0 = xnc[row], x1 = xnc[row + 1];
+                D[g * CM_R + row] = fmaf(-2.f, acc[j][0], x0 + qv0);
+                D[g * CM_R + row + 1] = fmaf(-2.f, acc[j][1], x1 + qv0);
+                D[(g + 8) * CM_R + row] = fmaf(-2.f, acc[j][2], x0 + qv1);
+                D[(g + 8) * CM_R + row + 1] = fmaf(-2.f, acc[j][3], x1 + qv1);
+            }
         }
         __syncthreads();
-        const int c = s_c;
-        const int64_t pb = s_pb;
-        const int nqb = (int)(s_pe - pb);
-        // queries of the item, transposed; missing ones are zero
-        for (int i = tid; i < CM_QB * dp4; i += CM_THREADS) {
-            const int qb = i % CM_QB, c4 = i / CM_QB;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (qb < nqb) v = Qp[(int64_t)(pairs[pb + qb] / P) * dp4 + c4];
-            qs[(c4 * 4 + 0) * CM_QB + qb] = v.x;
-            qs[(c4 * 4 + 1) * CM_QB + qb] = v.y;
-            qs[(c4 * 4 + 2) * CM_QB + qb] = v.z;
-            qs[(c4 * 4 + 3) * CM_QB + qb] = v.w;
-        }
-        for (int i = tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
-        if (tid < CM_QB) {
-            float qv = 0.f, tv = -1.f;  // missing queries: nothing passes the test
-            if (tid < nqb) {
-                const int64_t qq = pairs[pb + tid] / P;
-                qv = qn[qq];
-                tv = seed_d[qq * K + K - 1];  // +inf when the seed cluster has < K rows
-            }
-            s_qn[tid] = qv;
-            s_tq[tid] = tv;
-        }
-        const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
-        if (tid == 0)
-            atomicAdd(&g_cm_bytes, (unsigned long long)(re - rb) * (dp4 * 16ull + 4ull));
-        for (int64_t r0 = rb; r0 < re; r0 += CM_R) {
-            const int nr = (int)((re - r0) < (int64_t)CM_R ? (re - r0) : (int64_t)CM_R);
-            __syncthreads();
-            for (int i = tid; i < CM_R * dp4; i += CM_THREADS) {
-                const int rr = i % CM_R, c4 = i / CM_R;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (rr < nr) v = Xs[(r0 + rr) * dp4 + c4];
-                xs[(c4 * 4 + 0) * CM_R + rr] = v.x;
-                xs[(c4 * 4 + 1) * CM_R + rr] = v.y;
-                xs[(c4 * 4 + 2) * CM_R + rr] = v.z;
-                xs[(c4 * 4 + 3) * CM_R + rr] = v.w;
-            }
-            for (int i = tid; i < CM_R; i += CM_THREADS) {
-                ids[i] = i < nr ? xids[r0 + i] : -1;
-                s_xn[i] = i < nr ? xn[r0 + i] : 0.f;
-            }
-            __syncthreads();
-            // expanded-form distances: warp w -> queries 2w, 2w+1; lane -> rows 4*lane .. +3
-            {
-                float acc[2][4];
+        // merge the chunk into each query's K best: warp w owns queries 2w, 2w+1
+        for (int qi = 0; qi < 2; ++qi) {
+            const int qb = warp * 2 + qi;
+            if (qb >= nqb) break;
+            unsigned long long *tq = top + qb * K;
+            const unsigned long long th = tq[K - 1];
+            // distance bound a row must be able to reach (key of the list's K-th, or T_q)
+            const float lim = fminf(s_tq[qbuf][qb], th == kNoKey ? __int_as_float(0x7f800000)
+                                                                 : __uint_as_float((unsigned)(th >> 32)));
+            const float qv = s_qn[qbuf][qb];
+            const float4 *q4 = reinterpret_cast<const float4 *>(qsb) + qb * XS4;
+            unsigned long long cand[CM_R / 32];
+            int ncand = 0;
 #pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-                const int q0 = warp * 2;
-#pragma unroll 8
-                for (int t = 0; t < dp; ++t) {
-                    const float4 xv = *reinterpret_cast<const float4 *>(&xs[t * CM_R + lane * 4]);
-                    const float qa = qs[t * CM_QB + q0], qb2 = qs[t * CM_QB + q0 + 1];
-                    acc[0][0] = fmaf(xv.x, qa, acc[0][0]);
-                    acc[0][1] = fmaf(xv.y, qa, acc[0][1]);
-                    acc[0][2] = fmaf(xv.z, qa, acc[0][2]);
-                    acc[0][3] = fmaf(xv.w, qa, acc[0][3]);
-                    acc[1][0] = fmaf(xv.x, qb2, acc[1][0]);
-                    acc[1][1] = fmaf(xv.y, qb2, acc[1][1]);
-                    acc[1][2] = fmaf(xv.z, qb2, acc[1][2]);
-                    acc[1][3] = fmaf(xv.w, qb2, acc[1][3]);
-                }
-                const float4 xr = *reinterpret_cast<const float4 *>(&s_xn[lane * 4]);
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const float qv = s_qn[q0 + i];
-                    *reinterpret_cast<float4 *>(&D[(q0 + i) * CM_R + lane * 4]) =
-                        make_float4(fmaf(-2.f, acc[i][0], xr.x + qv), fmaf(-2.f, acc[i][1], xr.y + qv),
-                                    fmaf(-2.f, acc[i][2], xr.z + qv), fmaf(-2.f, acc[i][3], xr.w + qv));
+            for (int i = 0; i < CM_R / 32; ++i) {
+                const int rr = lane + 32 * i;
+                cand[i] = kNoKey;
+                if (rr < nr && D[qb * CM_R + rr] <= lim + mcoef * (xnc[rr] + qv)) {
+                    // exact key, the arithmetic of the per-query scan
+                    const float4 *x4 = reinterpret_cast<const float4 *>(xsb) + rr * XS4;
+                    float e2 = 0.f;
+#pragma unroll 4
+                    for (int t4 = 0; t4 < dp4; ++t4) {
+                        const float4 xv = x4[t4], qq = q4[t4];
+                        float e = xv.x - qq.x;
+                        e2 = fmaf(e, e, e2);
+                        e = xv.y - qq.y;
+                        e2 = fmaf(e, e, e2);
+                        e = xv.z - qq.z;
+                        e2 = fmaf(e, e, e2);
+                        e = xv.w - qq.w;
+                        e2 = fmaf(e, e, e2);
+                    }
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)xids[cur.r0 + rr];
+                    if (key < th) { cand[i] = key; ++ncand; }
                 }
             }
-            __syncthreads();
-            // merge the chunk into each query's K best: warp w owns queries 2w, 2w+1
-            for (int qi = 0; qi < 2; ++qi) {
-                const int qb = warp * 2 + qi;
-                if (qb >= nqb) break;
-                unsigned long long *tq = top + qb * K;
-                const unsigned long long th = tq[K - 1];
-                // distance bound a row must be able to reach (key of the list's K-th, or T_q)
-                const float lim = fminf(s_tq[qb], th == kNoKey ? __int_as_float(0x7f800000)
-                                                               : __uint_as_float((unsigned)(th >> 32)));
-                const float qv = s_qn[qb];
-                unsigned long long cand[CM_R / 32];
-                bool any = false;
+            // candidates of the whole warp
+            int total = ncand;
+            for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
+            if (total == 0) continue;
+            unsigned long long old = lane < K ? tq[lane] : kNoKey;
+            if (total <= 8) {
+                // few candidates: insert each into the sorted list held one
+                // entry per lane (keys are distinct: ids differ)
 #pragma unroll
                 for (int i = 0; i < CM_R / 32; ++i) {
-                    const int rr = lane + 32 * i;
-                    cand[i] = kNoKey;
-                    if (rr < nr && D[qb * CM_R + rr] <= lim + mcoef * (s_xn[rr] + qv)) {
-                        // exact key, the arithmetic of the per-query scan
-                        float e2 = 0.f;
-#pragma unroll 4
-                        for (int t = 0; t < dp; ++t) {
-                            const float e = xs[t * CM_R + rr] - qs[t * CM_QB + qb];
-                            e2 = fmaf(e, e, e2);
-                        }
-                        const unsigned long long key =
-                            ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)ids[rr];
-                        if (key < th) { cand[i] = key; any = true; }
+                    unsigned bal = __ballot_sync(kFull, cand[i] != kNoKey);
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const unsigned long long key = __shfl_sync(kFull, cand[i], src);
+                        const int pos = __popc(__ballot_sync(kFull, lane < K && old < key));
+                        const unsigned long long up = __shfl_up_sync(kFull, old, 1);
+                        if (pos < K) old = lane < pos ? old : (lane == pos ? key : up);
                     }
                 }
-                if (!__any_sync(kFull, any)) continue;
+                __syncwarp();
+                if (lane < K) tq[lane] = old;
+                __syncwarp();
+            } else {
                 // K rounds of warp-wide minimum over (current list, candidates)
-                unsigned long long old = lane < K ? tq[lane] : kNoKey;
                 unsigned long long out = kNoKey;
                 for (int r = 0; r < K; ++r) {
                     unsigned long long mine = old;
@@ -254,12 +400,24 @@ __global__ __launch_bounds__(CM_THREADS) void cm_scan_kernel(
                 __syncwarp();
             }
         }
-        __syncthreads();
-        for (int i = tid; i < nqb * K; i += CM_THREADS) {
-            const int qb = i / K, j = i % K;
-            pair_out[(int64_t)pairs[pb + qb] * K + j] = top[qb * K + j];
+        const bool last = nxt.item < 0 || nxt.first;
+        if (last) {
+            // the item is done: write its pair lists and clear them for the next item
+            if (tid == 0)
+                atomicAdd(&g_cm_bytes,
+                          (unsigned long long)(cur.re - leaf_off[cur.c]) * (dp4 * 16ull + 4ull));
+            __syncthreads();
+            for (int i = tid; i < nqb * K; i += CM_THREADS) {
+                const int qb = i / K, j = i % K;
+                pair_out[(int64_t)pairs[cur.pb + qb] * K + j] = top[i];
+                top[i] = kNoKey;
+            }
+            for (int i = nqb * K + tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
         }
-        __syncthreads();
+        if (nxt.item < 0) break;
+        cur = nxt;
+        buf = nbuf;
+        qbuf = nqbuf;
     }
 }
 
@@ -368,6 +526,13 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     // and the exact key's own dp FMAs over a distance <= 2 (||x||^2 + ||q||^2);
     // widened by 1/8
     const float mcoef = (float)((4.0 * dp + 8.0) * 0x1.0p-24 * 1.125);
+    // the tensor-core dot product (3xTF32) adds: the split (the dropped
+    // lo x lo products and the TF32 truncation of the lo parts, 2.5 * 2^-21
+    // relative to sum |x_t q_t|) and its FP32 accumulation over 3 ceil(dp/8)
+    // MMAs plus 8 in-MMA additions, counted at one ulp (2^-22) each; times 2
+    // for the factor -2 and sum |x_t q_t| <= (||x||^2 + ||q||^2) / 2
+    const float mcoef_tc =
+        mcoef + (float)((2.5 * 0x1.0p-21 + (3.0 * ((dp + 7) / 8) + 8.0) * 0x1.0p-22) * 1.125);
     Scratch<int32_t> pairs;
     Scratch<int64_t> poff, item_off;
     Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
@@ -375,16 +540,26 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     // no work item: their lists stay empty
     MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
     cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
+    Scratch<int32_t> item_c(npairs, s);   // work items <= pairs
+    item_cluster_kernel<<<(k0 + 255) / 256, 256, 0, s>>>(item_off.get(), k0, item_c.get());
+    MASK_LAUNCHED("item_cluster");
     {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
-        const size_t smem = ((size_t)dp * CM_R + (size_t)dp * CM_QB + CM_QB * CM_R) * 4 +
-                            CM_R * 4 + (size_t)CM_QB * K * 8 + 16;
+        const int XS = cm_stride(dp / 4);
+        const size_t smem = ((size_t)2 * CM_R * XS + (size_t)2 * CM_QB * XS + CM_QB * CM_R +
+                             2 * CM_R) * 4 + (size_t)CM_QB * K * 8 + 16;
         MASK_CUDA(cudaFuncSetAttribute(cm_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-        cm_scan_kernel<<<152 * 4, CM_THREADS, smem, s>>>(
+        int per_sm = 0;
+        MASK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cm_scan_kernel,
+                                                                CM_THREADS, smem));
+        int dev = 0, sms = 0;
+        MASK_CUDA(cudaGetDevice(&dev));
+        MASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        cm_scan_kernel<<<std::max(1, per_sm) * sms, CM_THREADS, smem, s>>>(
             reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids, leaf_off,
-            reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef, P, poff.get(),
-            pairs.get(), item_off.get(), k0, K, pair_out.get());
+            reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef_tc, P, poff.get(),
+            pairs.get(), item_off.get(), item_c.get(), k0, K, pair_out.get());
         MASK_LAUNCHED("cm_scan");
     }
     cm_merge(pair_out.get(), nq, P, K, ids, dists, s);

@@ -113,7 +113,8 @@ def main(argv=None) -> None:
     if a.profile:
         M.mask_profile_enable(False)
         for name in ("assign_tc", "assign_gemm", "assign_recheck", "kmeanspp", "label_sort",
-                     "centroid_update", "scan_topk_level", "scan_topk_leaf", "csr_assign",
+                     "centroid_update", "scan_topk_level", "scan_topk_leaf", "scan_leaf_cm",
+                     "leaf_group", "leaf_merge", "csr_scan_leaf_cm", "csr_assign",
                      "csr_spmm_assign", "csr_centroid_update", "csr_scan_level", "csr_scan_leaf"):
             r = M.mask_profile_read(name)
             if r:
