@@ -90,12 +90,35 @@ __global__ void __launch_bounds__(1024) item_scan_kernel(const int64_t *__restri
     if (tid == 1023) item_off[k0] = part[1023];
 }
 
-// item_c[i] = the cluster of work item i (items of cluster c are
-// item_off[c] .. item_off[c+1]-1).
-__global__ void item_cluster_kernel(const int64_t *__restrict__ item_off, int k0,
-                                    int32_t *__restrict__ item_c) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k0; c += gridDim.x * blockDim.x)
-        for (int64_t i = item_off[c]; i < item_off[c + 1]; ++i) item_c[i] = c;
+// Per work item i (cluster c, up to CM_QB of its pairs):
+//   meta[i] = {first row lo, first row hi, rows of c, pairs in the item}
+//   pid[i * CM_QB + q] = the item's q-th pair (-1 past the last),
+//   qid[i * CM_QB + q] = that pair's query.
+__global__ void item_meta_kernel(const int64_t *__restrict__ item_off, const int64_t *__restrict__ poff,
+                                 const int64_t *__restrict__ leaf_off,
+                                 const int32_t *__restrict__ pairs, int P, int k0,
+                                 int4 *__restrict__ meta, int32_t *__restrict__ pid,
+                                 int32_t *__restrict__ qid) {
+    // one warp per cluster; lanes over the cluster's (item, slot) entries
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < k0; c += gridDim.x * wpb) {
+        const int64_t rb = leaf_off[c], rows = leaf_off[c + 1] - rb;
+        const int64_t i0 = item_off[c], ni = item_off[c + 1] - i0;
+        const int64_t p0 = poff[c], np = poff[c + 1] - p0;
+        for (int64_t e = lane; e < ni * CM_QB; e += 32) {
+            const int64_t i = i0 + e / CM_QB;
+            const int q = (int)(e % CM_QB);
+            const int64_t pe = (e / CM_QB) * CM_QB + q;  // pair offset within the cluster
+            const int32_t pp = pe < np ? pairs[p0 + pe] : -1;
+            pid[i * CM_QB + q] = pp;
+            qid[i * CM_QB + q] = pp >= 0 ? pp / P : 0;
+            if (q == 0) {
+                const int nqb = (int)min((int64_t)CM_QB, np - pe);
+                meta[i] = make_int4((int)(rb & 0xffffffff), (int)(rb >> 32), (int)rows, nqb);
+            }
+        }
+    }
 }
 
 // Asynchronous global -> shared copies; a zero size writes zeros (the source
@@ -140,61 +163,25 @@ __device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&
 // columns hold zeros: the MMA's last k-step may read them.
 __host__ __device__ inline int cm_stride(int dp4) { return 4 * (dp4 + ((dp4 & 1) ? 2 : 1)); }
 
-// One chunk of a block's work: up to CM_R rows of the cluster of one item.
-struct CmChunk {
-    int64_t item;   // < 0: no more work
-    int c, nqb, nr;
-    int64_t pb, r0, re;
-    bool first;     // first chunk of its item
-};
-
-// The first chunk at or after item `it` (stepping by `step`) whose cluster
-// has rows; items of empty clusters have nothing to scan (their pair lists
-// stay empty).
-__device__ __forceinline__ CmChunk cm_first_chunk(int64_t it, int64_t step, int64_t n_items,
-                                                  const int32_t *__restrict__ item_c,
-                                                  const int64_t *__restrict__ item_off,
-                                                  const int64_t *__restrict__ poff,
-                                                  const int64_t *__restrict__ leaf_off) {
-    CmChunk ch;
-    ch.item = -1;
-    for (; it < n_items; it += step) {
-        const int c = item_c[it];
-        const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
-        if (re <= rb) continue;
-        const int64_t pb = poff[c] + (it - item_off[c]) * CM_QB;
-        const int64_t pe = min(poff[c + 1], pb + CM_QB);
-        ch.item = it;
-        ch.c = c;
-        ch.pb = pb;
-        ch.nqb = (int)(pe - pb);
-        ch.r0 = rb;
-        ch.re = re;
-        ch.nr = (int)min((int64_t)CM_R, re - rb);
-        ch.first = true;
-        break;
-    }
-    return ch;
-}
-
 // One work item = (cluster c, up to CM_QB of its pairs).  xn: row norms;
 // qn: query norms; seed_d [nq x K]: each query's K nearest distances within
 // its nearest kept cluster (the K-th is T_q); mcoef: rounding bound of
 // |expanded form - exact key| per unit of ||x||^2 + ||q||^2.
 //
-// A block walks its items' chunks in order; the rows and norms of the next
-// chunk (and the queries of the next item) are copied asynchronously into the
-// other half of double-buffered shared memory while the current chunk is
-// ranked.  Rows are staged row-major (stride cm_stride floats).  The
-// expanded-form dot products run on the tensor cores (mma.sync, 3xTF32:
-// x.q ~ x_hi.q_hi + x_hi.q_lo + x_lo.q_hi); mcoef covers their error.
+// A block walks its items' chunks (up to CM_R rows of the item's cluster) in
+// order; the rows and norms of the next chunk (and the queries of the next
+// item) are copied asynchronously into the other half of double-buffered
+// shared memory while the current chunk is ranked, and the next item's
+// metadata is read one item ahead.  Rows are staged row-major (stride
+// cm_stride floats).  The expanded-form dot products run on the tensor cores
+// (mma.sync, 3xTF32: x.q ~ x_hi.q_hi + x_hi.q_lo + x_lo.q_hi); mcoef covers
+// their error.  An item of an empty cluster is one chunk of no rows.
 __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
     const float4 *__restrict__ Xs, const float *__restrict__ xn, int dp4,
-    const int32_t *__restrict__ xids, const int64_t *__restrict__ leaf_off,
-    const float4 *__restrict__ Qp, const float *__restrict__ qn,
-    const float *__restrict__ seed_d, float mcoef, int P, const int64_t *__restrict__ poff,
-    const int32_t *__restrict__ pairs, const int64_t *__restrict__ item_off,
-    const int32_t *__restrict__ item_c, int k0, int K,
+    const int32_t *__restrict__ xids, const float4 *__restrict__ Qp,
+    const float *__restrict__ qn, const float *__restrict__ seed_d, float mcoef,
+    const int4 *__restrict__ meta, const int32_t *__restrict__ pid,
+    const int32_t *__restrict__ qid, const int64_t *__restrict__ item_off, int k0, int K,
     unsigned long long *__restrict__ pair_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int XS = cm_stride(dp4), XS4 = XS / 4;
@@ -204,85 +191,110 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
     float *xnb = D + CM_QB * CM_R;                               // [2][CM_R] row norms
     unsigned long long *top = reinterpret_cast<unsigned long long *>(xnb + 2 * CM_R);  // [CM_QB][K]
     __shared__ float s_qn[2][CM_QB], s_tq[2][CM_QB];
+    __shared__ int32_t s_pid[2][CM_QB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n_items = item_off[k0];
+    const int64_t G = gridDim.x;
+    int64_t item = blockIdx.x;
+    if (item >= n_items) return;
 
-    // stage chunk `ch` into row buffer b (and, for an item's first chunk,
-    // its queries into query buffer qb)
-    // thread -> (row offset, float4 column) of the staging copies
+    // thread -> (row offset, float4 column) of the staging copies; a copier
+    // stages queries rfirst and rfirst + rstep (rstep >= 8 since dp4 <= 32)
     const int rstep = CM_THREADS / dp4, rfirst = tid / dp4, c4 = tid - rfirst * dp4;
     const bool copier = rfirst < rstep;
-    auto prefetch = [&](const CmChunk ch, int b, int qb) {
+    const int q0c = rfirst, q1c = rfirst + rstep;
+    const int qt = tid < CM_QB ? tid : 0;
+
+    // an item's metadata and the query ids this thread stages
+    struct Item {
+        int64_t rb;
+        int rows, nqb, qa, qb, qn;
+    };
+    auto load_item = [&](int64_t it) {
+        Item r;
+        const int4 m = meta[it];
+        r.rb = (int64_t)(uint32_t)m.x | ((int64_t)m.y << 32);
+        r.rows = m.z;
+        r.nqb = m.w;
+        r.qa = (copier && q0c < CM_QB) ? qid[it * CM_QB + q0c] : 0;
+        r.qb = (copier && q1c < CM_QB) ? qid[it * CM_QB + q1c] : 0;
+        r.qn = qid[it * CM_QB + qt];
+        return r;
+    };
+    // stage rows [r0, r0 + nr) of the current cluster into row buffer b and,
+    // for an item's first chunk, its queries into query buffer qb
+    auto prefetch = [&](const Item &im, int64_t it, int64_t r0, int nr, bool first, int b, int qb) {
         float *xsb = xs + b * CM_R * XS;
         if (copier)
             for (int rr = rfirst; rr < CM_R; rr += rstep) {
-                const bool v = rr < ch.nr;
+                const bool v = rr < nr;
                 cp_async16(xsb + rr * XS + c4 * 4,
-                           v ? (const void *)(Xs + (ch.r0 + rr) * dp4 + c4) : (const void *)Xs, v);
+                           v ? (const void *)(Xs + (r0 + rr) * dp4 + c4) : (const void *)Xs, v);
             }
         if (tid < CM_R) {
-            const bool v = tid < ch.nr;
-            cp_async4(xnb + b * CM_R + tid, v ? xn + ch.r0 + tid : xn, v);
+            const bool v = tid < nr;
+            cp_async4(xnb + b * CM_R + tid, v ? xn + r0 + tid : xn, v);
         }
-        if (ch.first) {
+        if (first) {
             float *qsb = qs + qb * CM_QB * XS;
-            if (copier)
-                for (int q = rfirst; q < CM_QB; q += rstep) {
-                    const bool v = q < ch.nqb;
-                    const int64_t qq = v ? (int64_t)(pairs[ch.pb + q] / P) : 0;
-                    cp_async16(qsb + q * XS + c4 * 4, Qp + qq * dp4 + c4, v);
-                }
+            if (copier && q0c < CM_QB)
+                cp_async16(qsb + q0c * XS + c4 * 4, Qp + (int64_t)im.qa * dp4 + c4, q0c < im.nqb);
+            if (copier && q1c < CM_QB)
+                cp_async16(qsb + q1c * XS + c4 * 4, Qp + (int64_t)im.qb * dp4 + c4, q1c < im.nqb);
             if (tid < CM_QB) {
-                const bool v = tid < ch.nqb;
-                const int64_t qq = v ? (int64_t)(pairs[ch.pb + tid] / P) : 0;
-                cp_async4(&s_qn[qb][tid], qn + qq, v);
-                cp_async4(&s_tq[qb][tid], seed_d + qq * K + K - 1, v);  // +inf: seed cluster < K rows
+                const bool v = tid < im.nqb;
+                cp_async4(&s_qn[qb][tid], qn + im.qn, v);
+                cp_async4(&s_tq[qb][tid], seed_d + (int64_t)im.qn * K + K - 1, v);  // +inf: < K rows
+                cp_async4(&s_pid[qb][tid], pid + it * CM_QB + tid, true);
             }
         }
         cp_commit();
     };
 
-    CmChunk cur = cm_first_chunk(blockIdx.x, gridDim.x, n_items, item_c, item_off, poff, leaf_off);
-    if (cur.item < 0) return;
     for (int i = tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
     {
         const int padw = XS - 4 * dp4;  // zero padding columns of every staged row and query
         for (int i = tid; i < (2 * CM_R + 2 * CM_QB) * padw; i += CM_THREADS)
             xs[(i / padw) * XS + 4 * dp4 + i % padw] = 0.f;
     }
+    Item cur = load_item(item), nit;
+    const bool has_next0 = item + G < n_items;
+    if (has_next0) nit = load_item(item + G);
+    int64_t r0 = cur.rb;
+    int nr = min(CM_R, cur.rows);
     int buf = 0, qbuf = 0;
-    prefetch(cur, 0, 0);
+    prefetch(cur, item, r0, nr, true, 0, 0);
     for (;;) {
         cp_wait_all();
-        __syncthreads();  // cur is staged; every warp is done with the other buffers
+        __syncthreads();  // the chunk is staged; every warp is done with the other buffers
         // the next chunk: the rest of this cluster, else the block's next item
-        CmChunk nxt;
-        if (cur.r0 + CM_R < cur.re) {
-            nxt = cur;
-            nxt.r0 = cur.r0 + CM_R;
-            nxt.nr = (int)min((int64_t)CM_R, cur.re - nxt.r0);
-            nxt.first = false;
-        } else {
-            nxt = cm_first_chunk(cur.item + gridDim.x, gridDim.x, n_items, item_c, item_off, poff,
-                                 leaf_off);
+        const bool more = r0 + CM_R < cur.rb + cur.rows;
+        const bool has_next = more || item + G < n_items;
+        const int nbuf = buf ^ 1, nqbuf = more ? qbuf : (qbuf ^ 1);
+        if (more) {
+            const int64_t r1 = r0 + CM_R;
+            prefetch(cur, item, r1, (int)min((int64_t)CM_R, cur.rb + cur.rows - r1), false, nbuf,
+                     nqbuf);
+        } else if (has_next) {
+            prefetch(nit, item + G, nit.rb, min(CM_R, nit.rows), true, nbuf, nqbuf);
         }
-        const int nbuf = buf ^ 1, nqbuf = (nxt.item >= 0 && nxt.first) ? (qbuf ^ 1) : qbuf;
-        if (nxt.item >= 0) prefetch(nxt, nbuf, nqbuf);
 
         const float *xsb = xs + buf * CM_R * XS;
         const float *qsb = qs + qbuf * CM_QB * XS;
         const float *xnc = xnb + buf * CM_R;
-        const int nr = cur.nr, nqb = cur.nqb;
+        const int nqb = cur.nqb;
         // expanded-form distances on the tensor cores: warp w -> rows 16w ..
         // 16w+15 (two 8-row tiles) x all 16 queries; k-steps of 8 columns
         {
             const int g = lane >> 2, t = lane & 3;
-            float acc[2][4];
+            // hi.hi and the two cross terms accumulate separately (shorter
+            // dependent MMA chains); they are added once at the end
+            float acc[2][4], acx[2][4];
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+                for (int e = 0; e < 4; ++e) acc[j][e] = acx[j][e] = 0.f;
             const float *qa = qsb + g * XS + t, *qb8 = qa + 8 * XS;
             const float *xb0 = xsb + (16 * warp + g) * XS + t, *xb1 = xb0 + 8 * XS;
             const int ksteps = (dp4 + 1) >> 1;
@@ -297,14 +309,18 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
                 tf32_split(xb0[k0], bh0, bl0);
                 tf32_split(xb0[k0 + 4], bh1, bl1);
                 mma_tf32_16x8x8(acc[0], ah, bh0, bh1);
-                mma_tf32_16x8x8(acc[0], ah, bl0, bl1);
-                mma_tf32_16x8x8(acc[0], al, bh0, bh1);
+                mma_tf32_16x8x8(acx[0], ah, bl0, bl1);
+                mma_tf32_16x8x8(acx[0], al, bh0, bh1);
                 tf32_split(xb1[k0], bh0, bl0);
                 tf32_split(xb1[k0 + 4], bh1, bl1);
                 mma_tf32_16x8x8(acc[1], ah, bh0, bh1);
-                mma_tf32_16x8x8(acc[1], ah, bl0, bl1);
-                mma_tf32_16x8x8(acc[1], al, bh0, bh1);
+                mma_tf32_16x8x8(acx[1], ah, bl0, bl1);
+                mma_tf32_16x8x8(acx[1], al, bh0, bh1);
             }
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[j][e] += acx[j][e];
             // accumulator (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1) of each tile
             const float qv0 = s_qn[qbuf][g], qv1 = s_qn[qbuf][g + 8];
 #pragma unroll
@@ -352,7 +368,7 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
                         e2 = fmaf(e, e, e2);
                     }
                     const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)xids[cur.r0 + rr];
+                        ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)xids[r0 + rr];
                     if (key < th) { cand[i] = key; ++ncand; }
                 }
             }
@@ -400,22 +416,28 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
                 __syncwarp();
             }
         }
-        const bool last = nxt.item < 0 || nxt.first;
-        if (last) {
+        if (!more) {
             // the item is done: write its pair lists and clear them for the next item
             if (tid == 0)
-                atomicAdd(&g_cm_bytes,
-                          (unsigned long long)(cur.re - leaf_off[cur.c]) * (dp4 * 16ull + 4ull));
+                atomicAdd(&g_cm_bytes, (unsigned long long)cur.rows * (dp4 * 16ull + 4ull));
             __syncthreads();
             for (int i = tid; i < nqb * K; i += CM_THREADS) {
                 const int qb = i / K, j = i % K;
-                pair_out[(int64_t)pairs[cur.pb + qb] * K + j] = top[i];
+                pair_out[(int64_t)s_pid[qbuf][qb] * K + j] = top[i];
                 top[i] = kNoKey;
             }
             for (int i = nqb * K + tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
         }
-        if (nxt.item < 0) break;
-        cur = nxt;
+        if (!has_next) break;
+        if (more) {
+            r0 += CM_R;
+        } else {
+            item += G;
+            cur = nit;
+            r0 = cur.rb;
+            if (item + G < n_items) nit = load_item(item + G);  // read one item ahead
+        }
+        nr = (int)min((int64_t)CM_R, cur.rb + cur.rows - r0);
         buf = nbuf;
         qbuf = nqbuf;
     }
@@ -529,8 +551,9 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     // the tensor-core dot product (3xTF32) adds: the split (the dropped
     // lo x lo products and the TF32 truncation of the lo parts, 2.5 * 2^-21
     // relative to sum |x_t q_t|) and its FP32 accumulation over 3 ceil(dp/8)
-    // MMAs plus 8 in-MMA additions, counted at one ulp (2^-22) each; times 2
-    // for the factor -2 and sum |x_t q_t| <= (||x||^2 + ||q||^2) / 2
+    // MMAs (in two chains, added once) plus 8 in-MMA additions, counted at one
+    // ulp (2^-22) each; times 2 for the factor -2 and
+    // sum |x_t q_t| <= (||x||^2 + ||q||^2) / 2
     const float mcoef_tc =
         mcoef + (float)((2.5 * 0x1.0p-21 + (3.0 * ((dp + 7) / 8) + 8.0) * 0x1.0p-22) * 1.125);
     Scratch<int32_t> pairs;
@@ -540,9 +563,14 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     // no work item: their lists stay empty
     MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
     cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
-    Scratch<int32_t> item_c(npairs, s);   // work items <= pairs
-    item_cluster_kernel<<<(k0 + 255) / 256, 256, 0, s>>>(item_off.get(), k0, item_c.get());
-    MASK_LAUNCHED("item_cluster");
+    // per work item: metadata, pair ids, query ids (a cluster with m pairs
+    // has ceil(m / CM_QB) <= m / CM_QB + 1 items, and at most m)
+    const int64_t max_items = std::min(npairs, (npairs + CM_QB - 1) / CM_QB + (int64_t)k0);
+    Scratch<int4> meta(max_items, s);
+    Scratch<int32_t> ipid((size_t)max_items * CM_QB, s), iqid((size_t)max_items * CM_QB, s);
+    item_meta_kernel<<<(k0 + 7) / 8, 256, 0, s>>>(item_off.get(), poff.get(), leaf_off, pairs.get(),
+                                                      P, k0, meta.get(), ipid.get(), iqid.get());
+    MASK_LAUNCHED("item_meta");
     {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         const int XS = cm_stride(dp / 4);
@@ -557,9 +585,9 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
         MASK_CUDA(cudaGetDevice(&dev));
         MASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         cm_scan_kernel<<<std::max(1, per_sm) * sms, CM_THREADS, smem, s>>>(
-            reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids, leaf_off,
-            reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef_tc, P, poff.get(),
-            pairs.get(), item_off.get(), item_c.get(), k0, K, pair_out.get());
+            reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids,
+            reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef_tc, meta.get(),
+            ipid.get(), iqid.get(), item_off.get(), k0, K, pair_out.get());
         MASK_LAUNCHED("cm_scan");
     }
     cm_merge(pair_out.get(), nq, P, K, ids, dists, s);
