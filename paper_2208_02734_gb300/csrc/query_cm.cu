@@ -187,11 +187,13 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
     const int XS = cm_stride(dp4), XS4 = XS / 4;
     float *xs = reinterpret_cast<float *>(smem);                 // [2][CM_R][XS] rows
     float *qs = xs + 2 * CM_R * XS;                              // [2][CM_QB][XS] queries
-    float *D = qs + 2 * CM_QB * XS;                              // [CM_QB][CM_R] expanded form
-    float *xnb = D + CM_QB * CM_R;                               // [2][CM_R] row norms
+    float *xnb = qs + 2 * CM_QB * XS;                            // [2][CM_R] row norms
     unsigned long long *top = reinterpret_cast<unsigned long long *>(xnb + 2 * CM_R);  // [CM_QB][K]
+    unsigned long long *cbuf = top + CM_QB * K;                  // [CM_QB][CM_R] chunk candidates
     __shared__ float s_qn[2][CM_QB], s_tq[2][CM_QB];
     __shared__ int32_t s_pid[2][CM_QB];
+    __shared__ int s_ncand[CM_QB];                  // candidates of the chunk, per query
+    __shared__ unsigned long long s_th[CM_QB];      // each list's K-th key (kNoKey: not full)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n_items = item_off[k0];
@@ -253,6 +255,10 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
     };
 
     for (int i = tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
+    if (tid < CM_QB) {
+        s_ncand[tid] = 0;
+        s_th[tid] = kNoKey;
+    }
     {
         const int padw = XS - 4 * dp4;  // zero padding columns of every staged row and query
         for (int i = tid; i < (2 * CM_R + 2 * CM_QB) * padw; i += CM_THREADS)
@@ -321,82 +327,72 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
             for (int j = 0; j < 2; ++j)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[j][e] += acx[j][e];
-            // accumulator (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1) of each tile
-            const float qv0 = s_qn[qbuf][g], qv1 = s_qn[qbuf][g + 8];
+            // accumulator (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1) of each
+            // tile.  A (query, row) whose expanded form, less its rounding
+            // bound, can reach the smaller of the list's K-th and T_q gets its
+            // exact key (the arithmetic of the per-query scan); keys below the
+            // list's K-th at the start of the chunk become candidates.
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int row = 16 * warp + 8 * j + 2 * t;
-                const float x0 = xnc[row], x1 = xnc[row + 1];
-                D[g * CM_R + row] = fmaf(-2.f, acc[j][0], x0 + qv0);
-                D[g * CM_R + row + 1] = fmaf(-2.f, acc[j][1], x1 + qv0);
-                D[(g + 8) * CM_R + row] = fmaf(-2.f, acc[j][2], x0 + qv1);
-                D[(g + 8) * CM_R + row + 1] = fmaf(-2.f, acc[j][3], x1 + qv1);
+            for (int h = 0; h < 2; ++h) {
+                const int q = g + 8 * h;
+                if (q >= nqb) continue;
+                const unsigned long long th = s_th[q];
+                const float qv = s_qn[qbuf][q];
+                const float lim = fminf(s_tq[qbuf][q], th == kNoKey ? __int_as_float(0x7f800000)
+                                                                    : __uint_as_float((unsigned)(th >> 32)));
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int row = 16 * warp + 8 * j + 2 * t + e;
+                        if (row >= nr) continue;
+                        const float xv = xnc[row];
+                        const float dv = fmaf(-2.f, acc[j][2 * h + e], xv + qv);
+                        if (!(dv <= lim + mcoef * (xv + qv))) continue;
+                        const float4 *x4 = reinterpret_cast<const float4 *>(xsb) + row * XS4;
+                        const float4 *q4 = reinterpret_cast<const float4 *>(qsb) + q * XS4;
+                        float e2 = 0.f;
+                        for (int t4 = 0; t4 < dp4; ++t4) {
+                            const float4 a4 = x4[t4], b4 = q4[t4];
+                            float d = a4.x - b4.x;
+                            e2 = fmaf(d, d, e2);
+                            d = a4.y - b4.y;
+                            e2 = fmaf(d, d, e2);
+                            d = a4.z - b4.z;
+                            e2 = fmaf(d, d, e2);
+                            d = a4.w - b4.w;
+                            e2 = fmaf(d, d, e2);
+                        }
+                        const unsigned long long key =
+                            ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)xids[r0 + row];
+                        if (key < th) cbuf[q * CM_R + atomicAdd(&s_ncand[q], 1)] = key;
+                    }
             }
         }
         __syncthreads();
-        // merge the chunk into each query's K best: warp w owns queries 2w, 2w+1
+        // merge each query's candidates into its K best: warp w owns queries 2w, 2w+1
         for (int qi = 0; qi < 2; ++qi) {
             const int qb = warp * 2 + qi;
-            if (qb >= nqb) break;
-            unsigned long long *tq = top + qb * K;
-            const unsigned long long th = tq[K - 1];
-            // distance bound a row must be able to reach (key of the list's K-th, or T_q)
-            const float lim = fminf(s_tq[qbuf][qb], th == kNoKey ? __int_as_float(0x7f800000)
-                                                                 : __uint_as_float((unsigned)(th >> 32)));
-            const float qv = s_qn[qbuf][qb];
-            const float4 *q4 = reinterpret_cast<const float4 *>(qsb) + qb * XS4;
-            unsigned long long cand[CM_R / 32];
-            int ncand = 0;
-#pragma unroll
-            for (int i = 0; i < CM_R / 32; ++i) {
-                const int rr = lane + 32 * i;
-                cand[i] = kNoKey;
-                if (rr < nr && D[qb * CM_R + rr] <= lim + mcoef * (xnc[rr] + qv)) {
-                    // exact key, the arithmetic of the per-query scan
-                    const float4 *x4 = reinterpret_cast<const float4 *>(xsb) + rr * XS4;
-                    float e2 = 0.f;
-#pragma unroll 4
-                    for (int t4 = 0; t4 < dp4; ++t4) {
-                        const float4 xv = x4[t4], qq = q4[t4];
-                        float e = xv.x - qq.x;
-                        e2 = fmaf(e, e, e2);
-                        e = xv.y - qq.y;
-                        e2 = fmaf(e, e, e2);
-                        e = xv.z - qq.z;
-                        e2 = fmaf(e, e, e2);
-                        e = xv.w - qq.w;
-                        e2 = fmaf(e, e, e2);
-                    }
-                    const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)xids[r0 + rr];
-                    if (key < th) { cand[i] = key; ++ncand; }
-                }
-            }
-            // candidates of the whole warp
-            int total = ncand;
-            for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
+            const int total = qb < nqb ? s_ncand[qb] : 0;
             if (total == 0) continue;
+            unsigned long long *tq = top + qb * K;
+            const unsigned long long *cq = cbuf + qb * CM_R;
             unsigned long long old = lane < K ? tq[lane] : kNoKey;
             if (total <= 8) {
                 // few candidates: insert each into the sorted list held one
                 // entry per lane (keys are distinct: ids differ)
-#pragma unroll
-                for (int i = 0; i < CM_R / 32; ++i) {
-                    unsigned bal = __ballot_sync(kFull, cand[i] != kNoKey);
-                    while (bal) {
-                        const int src = __ffs(bal) - 1;
-                        bal &= bal - 1;
-                        const unsigned long long key = __shfl_sync(kFull, cand[i], src);
-                        const int pos = __popc(__ballot_sync(kFull, lane < K && old < key));
-                        const unsigned long long up = __shfl_up_sync(kFull, old, 1);
-                        if (pos < K) old = lane < pos ? old : (lane == pos ? key : up);
-                    }
+                for (int i = 0; i < total; ++i) {
+                    const unsigned long long key = cq[i];
+                    const int pos = __popc(__ballot_sync(kFull, lane < K && old < key));
+                    const unsigned long long up = __shfl_up_sync(kFull, old, 1);
+                    if (pos < K) old = lane < pos ? old : (lane == pos ? key : up);
                 }
-                __syncwarp();
-                if (lane < K) tq[lane] = old;
-                __syncwarp();
             } else {
                 // K rounds of warp-wide minimum over (current list, candidates)
+                unsigned long long cand[CM_R / 32];
+#pragma unroll
+                for (int i = 0; i < CM_R / 32; ++i)
+                    cand[i] = lane + 32 * i < total ? cq[lane + 32 * i] : kNoKey;
                 unsigned long long out = kNoKey;
                 for (int r = 0; r < K; ++r) {
                     unsigned long long mine = old;
@@ -411,9 +407,13 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
                     for (int i = 0; i < CM_R / 32; ++i)
                         if (cand[i] == w) cand[i] = kNoKey;
                 }
-                __syncwarp();
-                if (lane < K) tq[lane] = out;
-                __syncwarp();
+                old = out;
+            }
+            if (lane < K) tq[lane] = old;
+            const unsigned long long kth = __shfl_sync(kFull, old, K - 1);
+            if (lane == 0) {
+                s_th[qb] = kth;
+                s_ncand[qb] = 0;
             }
         }
         if (!more) {
@@ -427,6 +427,7 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
                 top[i] = kNoKey;
             }
             for (int i = nqb * K + tid; i < CM_QB * K; i += CM_THREADS) top[i] = kNoKey;
+            if (tid < CM_QB) s_th[tid] = kNoKey;
         }
         if (!has_next) break;
         if (more) {
@@ -574,8 +575,8 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         const int XS = cm_stride(dp / 4);
-        const size_t smem = ((size_t)2 * CM_R * XS + (size_t)2 * CM_QB * XS + CM_QB * CM_R +
-                             2 * CM_R) * 4 + (size_t)CM_QB * K * 8 + 16;
+        const size_t smem = ((size_t)2 * CM_R * XS + (size_t)2 * CM_QB * XS + 2 * CM_R) * 4 +
+                            (size_t)CM_QB * K * 8 + (size_t)CM_QB * CM_R * 8 + 16;
         MASK_CUDA(cudaFuncSetAttribute(cm_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         int per_sm = 0;
