@@ -305,6 +305,32 @@ void cm_bytes_reset();
 // groups the (query, kept leaf) pairs by leaf cluster; item_off[k0] = work items
 void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
                     Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s);
+// queries per work item of the cluster-major scans
+constexpr int kCmItemQueries = 16;
+// per work item i of cm_group_pairs (cluster c, up to kCmItemQueries of its
+// pairs): meta[i] = {first row (lo, hi), rows of c, pairs in the item};
+// pid/qid[i * kCmItemQueries + q] = the item's q-th pair (-1 past the last)
+// and its query (0 past the last)
+void cm_item_meta(const int32_t *pairs, const int64_t *poff, const int64_t *item_off,
+                  const int64_t *leaf_off, int64_t npairs, int P, int k0, Scratch<int4> &meta,
+                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s);
+
+// Asynchronous global -> shared copies (cp.async); a false `valid` writes
+// zeros (the source is then not read, but must still be a valid address).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // query_lp.cu -- BF16 / FP8 leaf scan with exact FP32 re-rank of a 4k shortlist
 int lp_padded_dim(int dp);

@@ -33,7 +33,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int CM_THREADS = 256;
-constexpr int CM_QB = 16;   // queries per work item
+constexpr int CM_QB = kCmItemQueries;   // queries per work item
 constexpr int CM_R = 128;   // cluster rows per shared-memory chunk
 
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a,
@@ -120,23 +120,6 @@ __global__ void item_meta_kernel(const int64_t *__restrict__ item_off, const int
         }
     }
 }
-
-// Asynchronous global -> shared copies; a zero size writes zeros (the source
-// is then not read, but is still a valid address).
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
-                 "r"(valid ? 16 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
-                 "r"(valid ? 4 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // hi = x rounded to TF32, lo = x - hi (exact in FP32; the MMA reads its TF32 part)
 __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
@@ -504,6 +487,20 @@ void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32
     MASK_LAUNCHED("item_scan");
 }
 
+void cm_item_meta(const int32_t *pairs, const int64_t *poff, const int64_t *item_off,
+                  const int64_t *leaf_off, int64_t npairs, int P, int k0, Scratch<int4> &meta,
+                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s) {
+    // a cluster with m pairs has ceil(m / CM_QB) <= m / CM_QB + 1 items, and at most m
+    const int64_t max_items = std::max<int64_t>(
+        1, std::min(npairs, (npairs + CM_QB - 1) / CM_QB + (int64_t)k0));
+    meta.alloc(max_items, s);
+    pid.alloc((size_t)max_items * CM_QB, s);
+    qid.alloc((size_t)max_items * CM_QB, s);
+    item_meta_kernel<<<(k0 + 7) / 8, 256, 0, s>>>(item_off, poff, leaf_off, pairs, P, k0,
+                                                  meta.get(), pid.get(), qid.get());
+    MASK_LAUNCHED("item_meta");
+}
+
 void cm_merge(const unsigned long long *pair_out, int64_t nq, int P, int K, int64_t *ids,
               float *dists, cudaStream_t s) {
     if (nq == 0) return;
@@ -564,14 +561,10 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     // no work item: their lists stay empty
     MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
     cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
-    // per work item: metadata, pair ids, query ids (a cluster with m pairs
-    // has ceil(m / CM_QB) <= m / CM_QB + 1 items, and at most m)
-    const int64_t max_items = std::min(npairs, (npairs + CM_QB - 1) / CM_QB + (int64_t)k0);
-    Scratch<int4> meta(max_items, s);
-    Scratch<int32_t> ipid((size_t)max_items * CM_QB, s), iqid((size_t)max_items * CM_QB, s);
-    item_meta_kernel<<<(k0 + 7) / 8, 256, 0, s>>>(item_off.get(), poff.get(), leaf_off, pairs.get(),
-                                                      P, k0, meta.get(), ipid.get(), iqid.get());
-    MASK_LAUNCHED("item_meta");
+    Scratch<int4> meta;
+    Scratch<int32_t> ipid, iqid;
+    cm_item_meta(pairs.get(), poff.get(), item_off.get(), leaf_off, npairs, P, k0, meta, ipid, iqid,
+                 s);
     {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         const int XS = cm_stride(dp / 4);

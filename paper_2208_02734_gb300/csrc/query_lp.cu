@@ -26,7 +26,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int LP_THREADS = 256;
-constexpr int LP_QB = 16;   // queries per work item (two n8 MMA tiles)
+constexpr int LP_QB = kCmItemQueries;   // queries per work item (two n8 MMA tiles)
 constexpr int LP_R = 128;   // rows per chunk (eight m16 MMA tiles, one per warp)
 constexpr int LP_KMAX = 64; // shortlist length limit
 
@@ -114,172 +114,247 @@ __device__ __forceinline__ void mma_e4m3_16832(float (&d)[4], const uint32_t (&a
 
 // One work item = (leaf cluster c, up to LP_QB of its (query, cluster) pairs).
 // FP8 = false: BF16 elements (2 bytes), MMA k = 16; true: e4m3 (1 byte), k = 32.
+//
+// A block walks its items' chunks (up to LP_R rows of the item's cluster) in
+// order; the next chunk's rows, norms and scales (and the next item's
+// queries) are copied asynchronously into the other half of double-buffered
+// shared memory while the current chunk is ranked, and the next item's
+// metadata is read one item ahead (cm_item_meta).  Each thread tests the
+// quantised distances it holds in MMA accumulators against the seed bound and
+// the pair's current list and appends the passing keys to per-query candidate
+// lists, which each query's warp merges.  An item of an empty cluster is one
+// chunk of no rows.
 template <bool FP8>
-__global__ __launch_bounds__(LP_THREADS) void lp_scan_kernel(
+__global__ __launch_bounds__(LP_THREADS, 2) void lp_scan_kernel(
     const uint8_t *__restrict__ Xl, int dpl, const float *__restrict__ xn2,
-    const float *__restrict__ xscale, const int64_t *__restrict__ leaf_off,
-    const uint8_t *__restrict__ Ql, const float *__restrict__ qn2, const float *__restrict__ qscale,
-    const float *__restrict__ seed_d, int kseed, float eta, float rslack, int P,
-    const int64_t *__restrict__ poff, const int32_t *__restrict__ pairs,
+    const float *__restrict__ xscale, const uint8_t *__restrict__ Ql,
+    const float *__restrict__ qn2, const float *__restrict__ qscale,
+    const float *__restrict__ seed_d, int kseed, float eta, float rslack,
+    const int4 *__restrict__ meta, const int32_t *__restrict__ pid, const int32_t *__restrict__ qid,
     const int64_t *__restrict__ item_off, int k0, int K, unsigned long long *__restrict__ pair_out) {
     constexpr int ES = FP8 ? 1 : 2;                   // bytes per element
     constexpr int KSTEP = FP8 ? 32 : 16;              // elements per MMA k-step
     extern __shared__ __align__(16) unsigned char smem[];
     const int rowb = dpl * ES + 16;                   // padded row stride in bytes
-    unsigned char *rows = smem;                       // [LP_R][rowb]
-    unsigned char *qs = rows + (size_t)LP_R * rowb;   // [LP_QB][rowb]
-    float *D = reinterpret_cast<float *>(qs + (size_t)LP_QB * rowb);  // [LP_QB][LP_R]
-    float *rn = D + LP_QB * LP_R;                     // [LP_R] row norms
-    float *rs = rn + LP_R;                            // [LP_R] row scales
-    int32_t *pos = reinterpret_cast<int32_t *>(rs + LP_R);            // [LP_R] row positions
-    float *qn = reinterpret_cast<float *>(pos + LP_R);                // [LP_QB]
-    float *qsc = qn + LP_QB;                                          // [LP_QB]
-    unsigned long long *top = reinterpret_cast<unsigned long long *>(qsc + LP_QB);  // [LP_QB][K]
-    __shared__ int s_c;
-    __shared__ int64_t s_pb, s_pe;
-    __shared__ float s_rt[LP_QB];  // sqrt(T_q): the seed's k-th exact distance, as a length
+    unsigned char *rows = smem;                                        // [2][LP_R][rowb]
+    unsigned char *qs = rows + 2 * (size_t)LP_R * rowb;                // [2][LP_QB][rowb]
+    float *rn = reinterpret_cast<float *>(qs + 2 * (size_t)LP_QB * rowb);  // [2][LP_R] norms
+    float *rsc = rn + 2 * LP_R;                                        // [2][LP_R] scales (FP8)
+    unsigned long long *top = reinterpret_cast<unsigned long long *>(rsc + 2 * LP_R);  // [LP_QB][K]
+    unsigned long long *cbuf = top + LP_QB * K;                        // [LP_QB][LP_R] candidates
+    __shared__ float s_qn[2][LP_QB], s_qsc[2][LP_QB], s_sd[2][LP_QB];
+    __shared__ int32_t s_pid[2][LP_QB];
+    __shared__ int s_ncand[LP_QB];
+    __shared__ unsigned long long s_th[LP_QB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, tig = lane & 3;
     const int c16 = dpl * ES / 16;                    // 16-byte chunks per row
     const int64_t n_items = item_off[k0];
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        if (tid == 0) {
-            int lo = 0, hi = k0 - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
+    const int64_t G = gridDim.x;
+    int64_t item = blockIdx.x;
+    if (item >= n_items) return;
+
+    // thread -> (row offset, 16-byte chunk) of the staging copies; a copier
+    // stages queries rfirst and rfirst + rstep (rstep >= 8 since c16 <= 32)
+    const int rstep = LP_THREADS / c16, rfirst = tid / c16, cc = tid - rfirst * c16;
+    const bool copier = rfirst < rstep;
+    const int q0c = rfirst, q1c = rfirst + rstep;
+    const int qt = tid < LP_QB ? tid : 0;
+    struct Item {
+        int64_t rb;
+        int rows, nqb, qa, qb, qn;
+    };
+    auto load_item = [&](int64_t it) {
+        Item r;
+        const int4 m = meta[it];
+        r.rb = (int64_t)(uint32_t)m.x | ((int64_t)m.y << 32);
+        r.rows = m.z;
+        r.nqb = m.w;
+        r.qa = (copier && q0c < LP_QB) ? qid[it * LP_QB + q0c] : 0;
+        r.qb = (copier && q1c < LP_QB) ? qid[it * LP_QB + q1c] : 0;
+        r.qn = qid[it * LP_QB + qt];
+        return r;
+    };
+    auto prefetch = [&](const Item &im, int64_t it, int64_t r0, int nr, bool first, int b, int qb) {
+        unsigned char *rb_ = rows + (size_t)b * LP_R * rowb;
+        if (copier)
+            for (int rr = rfirst; rr < LP_R; rr += rstep) {
+                const bool v = rr < nr;
+                cp_async16(rb_ + rr * rowb + cc * 16,
+                           v ? (const void *)(Xl + (r0 + rr) * dpl * ES + cc * 16) : (const void *)Xl,
+                           v);
             }
-            s_c = lo;
-            s_pb = poff[lo] + (item - item_off[lo]) * LP_QB;
-            s_pe = min(poff[lo + 1], s_pb + LP_QB);
+        if (tid < LP_R) {
+            const bool v = tid < nr;
+            cp_async4(rn + b * LP_R + tid, v ? xn2 + r0 + tid : xn2, v);
+            if (FP8) cp_async4(rsc + b * LP_R + tid, v ? xscale + r0 + tid : xscale, v);
+        }
+        if (first) {
+            unsigned char *qb_ = qs + (size_t)qb * LP_QB * rowb;
+            if (copier && q0c < LP_QB)
+                cp_async16(qb_ + q0c * rowb + cc * 16, Ql + (int64_t)im.qa * dpl * ES + cc * 16,
+                           q0c < im.nqb);
+            if (copier && q1c < LP_QB)
+                cp_async16(qb_ + q1c * rowb + cc * 16, Ql + (int64_t)im.qb * dpl * ES + cc * 16,
+                           q1c < im.nqb);
+            if (tid < LP_QB) {
+                const bool v = tid < im.nqb;
+                cp_async4(&s_qn[qb][tid], qn2 + im.qn, v);
+                if (FP8) cp_async4(&s_qsc[qb][tid], qscale + im.qn, v);
+                cp_async4(&s_sd[qb][tid], seed_d + (int64_t)im.qn * kseed + kseed - 1, v);
+                cp_async4(&s_pid[qb][tid], pid + it * LP_QB + tid, true);
+            }
+        }
+        cp_commit();
+    };
+
+    for (int i = tid; i < LP_QB * K; i += LP_THREADS) top[i] = kNoKey;
+    if (tid < LP_QB) {
+        s_ncand[tid] = 0;
+        s_th[tid] = kNoKey;
+        if (!FP8) s_qsc[0][tid] = s_qsc[1][tid] = 1.f;
+    }
+    if (!FP8)
+        for (int i = tid; i < 2 * LP_R; i += LP_THREADS) rsc[i] = 1.f;
+    Item cur = load_item(item), nit;
+    if (item + G < n_items) nit = load_item(item + G);
+    int64_t r0 = cur.rb;
+    int nr = min(LP_R, cur.rows);
+    int buf = 0, qbuf = 0;
+    prefetch(cur, item, r0, nr, true, 0, 0);
+    for (;;) {
+        cp_wait_all();
+        __syncthreads();  // the chunk is staged; every warp is done with the other buffers
+        const bool more = r0 + LP_R < cur.rb + cur.rows;
+        const bool has_next = more || item + G < n_items;
+        const int nbuf = buf ^ 1, nqbuf = more ? qbuf : (qbuf ^ 1);
+        if (more) {
+            const int64_t r1 = r0 + LP_R;
+            prefetch(cur, item, r1, (int)min((int64_t)LP_R, cur.rb + cur.rows - r1), false, nbuf,
+                     nqbuf);
+        } else if (has_next) {
+            prefetch(nit, item + G, nit.rb, min(LP_R, nit.rows), true, nbuf, nqbuf);
+        }
+        const unsigned char *rws = rows + (size_t)buf * LP_R * rowb;
+        const unsigned char *qss = qs + (size_t)qbuf * LP_QB * rowb;
+        const float *rnc = rn + buf * LP_R, *rsc_c = rsc + buf * LP_R;
+        const int nqb = cur.nqb;
+        // warp w: rows 16w .. 16w+15 against the 16 queries (two n8 tiles)
+        {
+            float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            const unsigned char *ra = rws + (16 * warp + g) * rowb;
+            const unsigned char *rb8 = ra + 8 * rowb;
+            for (int kk = 0; kk < dpl / KSTEP; ++kk) {
+                const int e0 = kk * KSTEP + tig * (FP8 ? 4 : 2);   // first element, low half
+                const int e1 = e0 + KSTEP / 2;                       // high half
+                uint32_t a[4];
+                a[0] = *reinterpret_cast<const uint32_t *>(ra + e0 * ES);
+                a[1] = *reinterpret_cast<const uint32_t *>(rb8 + e0 * ES);
+                a[2] = *reinterpret_cast<const uint32_t *>(ra + e1 * ES);
+                a[3] = *reinterpret_cast<const uint32_t *>(rb8 + e1 * ES);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const unsigned char *qb = qss + (nt * 8 + g) * rowb;
+                    uint32_t b[2];
+                    b[0] = *reinterpret_cast<const uint32_t *>(qb + e0 * ES);
+                    b[1] = *reinterpret_cast<const uint32_t *>(qb + e1 * ES);
+                    if (FP8) mma_e4m3_16832(acc[nt], a, b);
+                    else mma_bf16_16816(acc[nt], a, b);
+                }
+            }
+            // accumulator h of tile nt: row 16w + g (+8 for h >= 2), query
+            // nt * 8 + 2 tig + (h & 1).  A row whose quantised distance
+            // exceeds sqrt(T_q) + eta (|x| + |q|) is farther than T_q exactly
+            // and cannot be among the k nearest; rslack covers the rounding
+            // of the FP32 expanded form itself.
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int rr = 16 * warp + g + (h >= 2 ? 8 : 0);
+                    const int qb = nt * 8 + tig * 2 + (h & 1);
+                    if (rr >= nr || qb >= nqb) continue;
+                    const float rnv = rnc[rr], qnv = s_qn[qbuf][qb];
+                    const float dot = acc[nt][h] * rsc_c[rr] * s_qsc[qbuf][qb];
+                    const float dq = fmaxf(rnv + qnv - 2.f * dot, 0.f);
+                    const float lim = sqrtf(s_sd[qbuf][qb]) + eta * (sqrtf(rnv) + sqrtf(qnv));
+                    const float slack = rslack * (rnv + qnv);
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(dq) << 32) | (unsigned)(r0 + rr);
+                    if (key < s_th[qb] && dq <= fmaf(lim, lim, slack))
+                        cbuf[qb * LP_R + atomicAdd(&s_ncand[qb], 1)] = key;
+                }
         }
         __syncthreads();
-        const int c = s_c;
-        const int64_t pb = s_pb;
-        const int nqb = (int)(s_pe - pb);
-        for (int i = tid; i < LP_QB * c16; i += LP_THREADS) {
-            const int qb = i / c16, cc = i % c16;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (qb < nqb) {
-                const int64_t q = pairs[pb + qb] / P;
-                v = reinterpret_cast<const uint4 *>(Ql + q * dpl * ES)[cc];
-            }
-            *reinterpret_cast<uint4 *>(qs + qb * rowb + cc * 16) = v;
-        }
-        if (tid < LP_QB) {
-            const bool ok = tid < nqb;
-            const int64_t q = ok ? pairs[pb + tid] / P : 0;
-            qn[tid] = ok ? qn2[q] : 0.f;
-            qsc[tid] = (ok && FP8) ? qscale[q] : 1.f;
-            s_rt[tid] = ok ? sqrtf(seed_d[q * kseed + kseed - 1]) : 0.f;
-        }
-        for (int i = tid; i < LP_QB * K; i += LP_THREADS) top[i] = kNoKey;
-        const int64_t rb = leaf_off[c], re = leaf_off[c + 1];
-        for (int64_t r0 = rb; r0 < re; r0 += LP_R) {
-            const int nr = (int)((re - r0) < (int64_t)LP_R ? (re - r0) : (int64_t)LP_R);
-            __syncthreads();
-            for (int i = tid; i < LP_R * c16; i += LP_THREADS) {
-                const int rr = i / c16, cc = i % c16;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (rr < nr) v = reinterpret_cast<const uint4 *>(Xl + (r0 + rr) * dpl * ES)[cc];
-                *reinterpret_cast<uint4 *>(rows + rr * rowb + cc * 16) = v;
-            }
-            for (int i = tid; i < LP_R; i += LP_THREADS) {
-                const bool ok = i < nr;
-                rn[i] = ok ? xn2[r0 + i] : 0.f;
-                rs[i] = (ok && FP8) ? xscale[r0 + i] : 1.f;
-                pos[i] = ok ? (int32_t)(r0 + i) : -1;
-            }
-            __syncthreads();
-            // warp w: rows 16w .. 16w+15 against the 16 queries (two n8 tiles)
-            {
-                float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-                const unsigned char *ra = rows + (16 * warp + g) * rowb;
-                const unsigned char *rb8 = ra + 8 * rowb;
-                for (int kk = 0; kk < dpl / KSTEP; ++kk) {
-                    const int e0 = kk * KSTEP + tig * (FP8 ? 4 : 2);   // first element, low half
-                    const int e1 = e0 + KSTEP / 2;                       // high half
-                    uint32_t a[4];
-                    a[0] = *reinterpret_cast<const uint32_t *>(ra + e0 * ES);
-                    a[1] = *reinterpret_cast<const uint32_t *>(rb8 + e0 * ES);
-                    a[2] = *reinterpret_cast<const uint32_t *>(ra + e1 * ES);
-                    a[3] = *reinterpret_cast<const uint32_t *>(rb8 + e1 * ES);
-#pragma unroll
-                    for (int nt = 0; nt < 2; ++nt) {
-                        const unsigned char *qb = qs + (nt * 8 + g) * rowb;
-                        uint32_t b[2];
-                        b[0] = *reinterpret_cast<const uint32_t *>(qb + e0 * ES);
-                        b[1] = *reinterpret_cast<const uint32_t *>(qb + e1 * ES);
-                        if (FP8) mma_e4m3_16832(acc[nt], a, b);
-                        else mma_bf16_16816(acc[nt], a, b);
-                    }
+        // merge each query's candidates into its list: warp w owns queries 2w, 2w+1
+        for (int qi = 0; qi < 2; ++qi) {
+            const int qb = warp * 2 + qi;
+            const int total = qb < nqb ? s_ncand[qb] : 0;
+            if (total == 0) continue;
+            unsigned long long *tq = top + qb * K;
+            const unsigned long long *cq = cbuf + qb * LP_R;
+            unsigned long long old = lane < K ? tq[lane] : kNoKey;
+            if (total <= 8) {
+                // few candidates: insert each into the sorted list held one
+                // entry per lane (keys are distinct: positions differ)
+                for (int i = 0; i < total; ++i) {
+                    const unsigned long long key = cq[i];
+                    const int pos = __popc(__ballot_sync(kFull, lane < K && old < key));
+                    const unsigned long long up = __shfl_up_sync(kFull, old, 1);
+                    if (pos < K) old = lane < pos ? old : (lane == pos ? key : up);
                 }
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int rr = 16 * warp + g + (h >= 2 ? 8 : 0);
-                        const int qb = nt * 8 + tig * 2 + (h & 1);
-                        const float dot = acc[nt][h] * rs[rr] * qsc[qb];
-                        D[qb * LP_R + rr] = fmaxf(rn[rr] + qn[qb] - 2.f * dot, 0.f);
-                    }
-            }
-            __syncthreads();
-            // merge the chunk into each query's shortlist: warp w owns queries 2w, 2w+1
-            for (int qi = 0; qi < 2; ++qi) {
-                const int qb = warp * 2 + qi;
-                if (qb >= nqb) break;
-                unsigned long long *tq = top + qb * K;
-                const unsigned long long th = tq[K - 1];
-                // a row whose quantised distance exceeds sqrt(T_q) + eta (|x| + |q|)
-                // is farther than T_q exactly: it cannot be among the k nearest
-                const float rt = s_rt[qb], qlen = sqrtf(qn[qb]);
+            } else {
+                // K rounds of warp-wide minimum over (current list, candidates)
                 unsigned long long cand[LP_R / 32];
-                bool any = false;
 #pragma unroll
-                for (int i = 0; i < LP_R / 32; ++i) {
-                    const int rr = lane + 32 * i;
-                    cand[i] = kNoKey;
-                    if (rr < nr) {
-                        const float dq = D[qb * LP_R + rr];
-                        const float lim = rt + eta * (sqrtf(rn[rr]) + qlen);
-                        // plus the rounding of the FP32 expanded form dq itself
-                        const float slack = rslack * (rn[rr] + qn[qb]);
-                        const unsigned long long key =
-                            ((unsigned long long)__float_as_uint(dq) << 32) | (unsigned)pos[rr];
-                        if (key < th && dq <= fmaf(lim, lim, slack)) { cand[i] = key; any = true; }
-                    }
-                }
-                if (!__any_sync(kFull, any)) continue;
-                unsigned long long old0 = lane < K ? tq[lane] : kNoKey;
-                unsigned long long old1 = lane + 32 < K ? tq[lane + 32] : kNoKey;
-                unsigned long long out0 = kNoKey, out1 = kNoKey;
+                for (int i = 0; i < LP_R / 32; ++i)
+                    cand[i] = lane + 32 * i < total ? cq[lane + 32 * i] : kNoKey;
+                unsigned long long out = kNoKey;
                 for (int r = 0; r < K; ++r) {
-                    unsigned long long mine = umin64(old0, old1);
+                    unsigned long long mine = old;
 #pragma unroll
                     for (int i = 0; i < LP_R / 32; ++i) mine = umin64(mine, cand[i]);
                     const unsigned long long w = warp_min64(mine);
+                    if (lane == r) out = w;
                     if (w == kNoKey) break;
-                    if (lane == (r & 31)) { if (r < 32) out0 = w; else out1 = w; }
-                    if (old0 == w) old0 = kNoKey;
-                    if (old1 == w) old1 = kNoKey;
+                    if (old == w) old = kNoKey;
 #pragma unroll
                     for (int i = 0; i < LP_R / 32; ++i)
                         if (cand[i] == w) cand[i] = kNoKey;
                 }
-                __syncwarp();
-                if (lane < K) tq[lane] = out0;
-                if (lane + 32 < K) tq[lane + 32] = out1;
-                __syncwarp();
+                old = out;
+            }
+            if (lane < K) tq[lane] = old;
+            const unsigned long long kth = __shfl_sync(kFull, old, K - 1);
+            if (lane == 0) {
+                s_th[qb] = kth;
+                s_ncand[qb] = 0;
             }
         }
-        __syncthreads();
-        for (int i = tid; i < nqb * K; i += LP_THREADS) {
-            const int qb = i / K, j = i % K;
-            pair_out[(int64_t)pairs[pb + qb] * K + j] = top[qb * K + j];
+        if (!more) {
+            // the item is done: write its pair lists and clear them for the next item
+            __syncthreads();
+            for (int i = tid; i < nqb * K; i += LP_THREADS) {
+                const int qb = i / K, j = i % K;
+                pair_out[(int64_t)s_pid[qbuf][qb] * K + j] = top[i];
+                top[i] = kNoKey;
+            }
+            for (int i = nqb * K + tid; i < LP_QB * K; i += LP_THREADS) top[i] = kNoKey;
+            if (tid < LP_QB) s_th[tid] = kNoKey;
         }
-        __syncthreads();
+        if (!has_next) break;
+        if (more) {
+            r0 += LP_R;
+        } else {
+            item += G;
+            cur = nit;
+            r0 = cur.rb;
+            if (item + G < n_items) nit = load_item(item + G);  // read one item ahead
+        }
+        nr = (int)min((int64_t)LP_R, cur.rb + cur.rows - r0);
+        buf = nbuf;
+        qbuf = nqbuf;
     }
 }
 
@@ -440,24 +515,37 @@ void lp_leaf_scan(bool fp8, const void *Xl, const float *xn2, const float *xscal
     // no work item: their lists stay empty
     MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * nq * P * Kpair, s));
     Scratch<int32_t> shortlist((size_t)nq * Kp, s);
+    Scratch<int4> meta;
+    Scratch<int32_t> ipid, iqid;
+    cm_item_meta(pairs.get(), poff.get(), item_off.get(), leaf_off, nq * (int64_t)P, P, k0, meta,
+                 ipid, iqid, s);
     {
         ProfRegion pr(fp8 ? "scan_leaf_fp8" : "scan_leaf_bf16", s, 0.0);
+        MASK_REQUIRE(Kpair <= 32, "per-pair list longer than a warp");
         const int rowb = dpl * (fp8 ? 1 : 2) + 16;
-        const size_t smem = (size_t)(LP_R + LP_QB) * rowb + (size_t)LP_QB * LP_R * 4 +
-                            (size_t)LP_R * 12 + LP_QB * 8 + (size_t)LP_QB * Kpair * 8 + 16;
+        const size_t smem = 2 * (size_t)(LP_R + LP_QB) * rowb + (size_t)4 * LP_R * 4 +
+                            (size_t)LP_QB * Kpair * 8 + (size_t)LP_QB * LP_R * 8 + 16;
+        int dev = 0, sms = 0;
+        MASK_CUDA(cudaGetDevice(&dev));
+        MASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int per_sm = 0;
         if (fp8) {
             MASK_CUDA(cudaFuncSetAttribute(lp_scan_kernel<true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            lp_scan_kernel<true><<<152 * 4, LP_THREADS, smem, s>>>(
-                static_cast<const uint8_t *>(Xl), dpl, xn2, xscale, leaf_off, Ql.get(), qn2.get(),
-                qsc.get(), seed_d.get(), k, eta, rslack, P, poff.get(), pairs.get(), item_off.get(), k0,
+            MASK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lp_scan_kernel<true>,
+                                                                    LP_THREADS, smem));
+            lp_scan_kernel<true><<<std::max(1, per_sm) * sms, LP_THREADS, smem, s>>>(
+                static_cast<const uint8_t *>(Xl), dpl, xn2, xscale, Ql.get(), qn2.get(), qsc.get(),
+                seed_d.get(), k, eta, rslack, meta.get(), ipid.get(), iqid.get(), item_off.get(), k0,
                 Kpair, pair_out.get());
         } else {
             MASK_CUDA(cudaFuncSetAttribute(lp_scan_kernel<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            lp_scan_kernel<false><<<152 * 4, LP_THREADS, smem, s>>>(
-                static_cast<const uint8_t *>(Xl), dpl, xn2, nullptr, leaf_off, Ql.get(), qn2.get(),
-                nullptr, seed_d.get(), k, eta, rslack, P, poff.get(), pairs.get(), item_off.get(), k0,
+            MASK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lp_scan_kernel<false>,
+                                                                    LP_THREADS, smem));
+            lp_scan_kernel<false><<<std::max(1, per_sm) * sms, LP_THREADS, smem, s>>>(
+                static_cast<const uint8_t *>(Xl), dpl, xn2, nullptr, Ql.get(), qn2.get(), nullptr,
+                seed_d.get(), k, eta, rslack, meta.get(), ipid.get(), iqid.get(), item_off.get(), k0,
                 Kpair, pair_out.get());
         }
         MASK_LAUNCHED("lp_scan");
