@@ -226,12 +226,52 @@ __global__ void kpp_centre_dist_kernel(const float *__restrict__ X, int64_t m, i
     cc2[j] = acc;
 }
 
-// Shared memory of the draw: staged block sums and the selected block's D^2.
+// Shared memory of the draw (all kKppThreads threads of the last block).
 template <int ROWS>
 struct KppDrawSmem {
-    double s_b[kKppSelMax];
-    float s_r[ROWS];
+    double wsum[kKppThreads / 32];   // per-warp totals of a block scan
+    double excl, target;
+    long long fb, pick;
+    int first;
 };
+
+// Inclusive prefix sum of v over the kKppThreads threads of the block (FP64,
+// a warp scan then a scan of the warp totals); *total = the block's sum.
+__device__ double kpp_block_scan(double v, double *wsum, double *total) {
+    constexpr int W = kKppThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double n = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += n;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < W ? wsum[lane] : 0.0;
+        for (int o = 1; o < W; o <<= 1) {
+            const double n = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += n;
+        }
+        if (lane < W) wsum[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) v += wsum[warp - 1];
+    *total = wsum[W - 1];
+    __syncthreads();  // wsum may be reused by the next scan
+    return v;
+}
+
+// Smallest thread index of the block for which `flag` holds (INT_MAX if none).
+__device__ int kpp_block_first(bool flag, int *slot) {
+    if (threadIdx.x == 0) *slot = INT_MAX;
+    __syncthreads();
+    const unsigned bal = __ballot_sync(kFull, flag);
+    if ((threadIdx.x & 31) == 0 && bal) atomicMin(slot, (int)(threadIdx.x + __ffs(bal) - 1));
+    __syncthreads();
+    const int r = *slot;
+    __syncthreads();
+    return r;
+}
 
 // Block total of the D^2 fold -> bsum[blockIdx.x]; true in the last block to
 // finish (which then draws).
@@ -248,143 +288,120 @@ __device__ bool kpp_block_done(double local, double *red, double *__restrict__ b
     return last;
 }
 
-// The draw of centre t, by warp 0 of the last block (blocks of ROWS rows).
+// The draw of centre t by all threads of the last block (blocks of ROWS
+// rows): the smallest row whose inclusive prefix of D^2 exceeds u_t * S.
+// Thread i owns a contiguous run of block sums, then of the selected block's
+// rows; block scans give each run's prefix, the first run that crosses the
+// target is walked by its owner.
 template <int ROWS>
 __device__ void kpp_draw(int t, int64_t m, const double *__restrict__ u,
                          const float *__restrict__ D2, const double *__restrict__ bsum,
                          unsigned *__restrict__ counter, int *__restrict__ t_dev,
                          int64_t *__restrict__ chosen, unsigned char *__restrict__ taken,
                          KppDrawSmem<ROWS> &sm) {
-    static_assert(ROWS % 32 == 0, "rows per block must be a multiple of 32");
-    if (threadIdx.x >= 32) return;
-    double *s_b = sm.s_b;
-    float *s_r = sm.s_r;
-    const int lane = threadIdx.x;
+    constexpr int RPT = ROWS >= kKppThreads ? ROWS / kKppThreads : 1;  // rows per thread
+    static_assert(ROWS % kKppThreads == 0 || ROWS < kKppThreads, "rows per block");
+    const int tid = threadIdx.x;
     const int nb = gridDim.x;
-    if (t == 1 && lane == 0) taken[chosen[0]] = 1;
-    long long pick = -1;
-    double S = 0.0, target = 0.0;
-    long long fb = -1;
-    double excl = 0.0;
-    // pass over the block sums in chunks of kKppSelMax staged in shared memory
-    // (one chunk -- every launch of at most kKppSelMax blocks -- is loaded once)
-    const bool staged = nb <= kKppSelMax;
-    double carry = 0.0;
-    for (int c0 = 0; c0 < nb; c0 += kKppSelMax) {
-        const int cn = min(kKppSelMax, nb - c0);
-        for (int b = lane; b < cn; b += 32) s_b[b] = __ldcg(bsum + c0 + b);
-        __syncwarp();
-        double ls = 0.0;
-        const int per = (cn + 31) / 32;
-        for (int q = 0; q < per; ++q) {
-            const int b = lane * per + q;
-            if (b < cn) ls += s_b[b];
-        }
-        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(kFull, ls, o);
-        carry += ls;
-        __syncwarp();
-    }
-    S = carry;
+    if (t == 1 && tid == 0) taken[chosen[0]] = 1;
+    if (tid == 0) sm.pick = -1;
+    const double ut = u[t];
+    // block sums: thread tid owns [tid * per, (tid + 1) * per)
+    const int per = (nb + kKppThreads - 1) / kKppThreads;
+    const int b0 = tid * per;
+    double ls = 0.0;
+    for (int q = 0; q < per; ++q)
+        if (b0 + q < nb) ls += __ldcg(bsum + b0 + q);
+    double S;
+    const double inc = kpp_block_scan(ls, sm.wsum, &S);
     if (S > 0.0) {
-        target = u[t] * S;
-        carry = 0.0;
-        for (int c0 = 0; c0 < nb && fb < 0; c0 += kKppSelMax) {
-            const int cn = min(kKppSelMax, nb - c0);
-            if (!staged)
-                for (int b = lane; b < cn; b += 32) s_b[b] = __ldcg(bsum + c0 + b);
-            __syncwarp();
-            const int per = (cn + 31) / 32;
-            double ls = 0.0;
-            for (int q = 0; q < per; ++q) {
-                const int b = lane * per + q;
-                if (b < cn) ls += s_b[b];
-            }
-            double inc = ls;
-            for (int o = 1; o < 32; o <<= 1) {
-                const double v = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o) inc += v;
-            }
-            inc += carry;
-            const unsigned bal = __ballot_sync(kFull, inc > target && ls > 0.0);
-            if (bal) {
-                const int src = __ffs(bal) - 1;
-                long long f = -1;
-                double ex = 0.0;
-                if (lane == src) {
-                    double run = inc - ls, lastrun = 0.0;
-                    long long lastb = -1;
-                    for (int q = 0; q < per; ++q) {
-                        const int b = lane * per + q;
-                        if (b >= cn) break;
-                        const double v = s_b[b];
-                        if (v > 0.0) {
-                            lastb = c0 + b;
-                            lastrun = run;
-                            if (run + v > target) { f = c0 + b; ex = run; break; }
-                        }
-                        run += v;
-                    }
-                    if (f < 0) { f = lastb; ex = lastrun; }
+        const double target = ut * S;
+        const int src = kpp_block_first(inc > target && ls > 0.0, &sm.first);
+        if (tid == src) {
+            // walk the run; rounding may leave no crossing: its last block with mass
+            double run = inc - ls, lastrun = 0.0;
+            long long f = -1, lastb = -1;
+            double ex = 0.0;
+            for (int q = 0; q < per && b0 + q < nb; ++q) {
+                const double v = __ldcg(bsum + b0 + q);
+                if (v > 0.0) {
+                    lastb = b0 + q;
+                    lastrun = run;
+                    if (run + v > target) { f = b0 + q; ex = run; break; }
                 }
-                fb = __shfl_sync(kFull, f, src);
-                excl = __shfl_sync(kFull, ex, src);
+                run += v;
             }
-            carry = __shfl_sync(kFull, inc, 31);
-            __syncwarp();
+            if (f < 0) { f = lastb; ex = lastrun; }
+            sm.fb = f;
+            sm.excl = ex;
         }
+        if (tid == 0 && src == INT_MAX) sm.fb = -1;
+        if (tid == 0) sm.target = target;
+        __syncthreads();
+        const long long fb = sm.fb;
         if (fb >= 0) {
-            // stage the block's rows, then lane l walks rows [l*RPL, (l+1)*RPL)
-            for (int q = lane; q < ROWS; q += 32) {
-                const int64_t i = fb * ROWS + q;
-                s_r[q] = i < m ? __ldcg(D2 + i) : 0.f;
-            }
-            __syncwarp();
-            constexpr int RPL = ROWS / 32;
+            // the block's rows: thread tid owns rows [tid * RPT, (tid + 1) * RPT)
+            const int64_t r0 = fb * ROWS + (int64_t)tid * RPT;
+            float v[RPT];
             double rs = 0.0;
-            for (int q = 0; q < RPL; ++q) rs += (double)s_r[lane * RPL + q];
-            double rinc = rs;
-            for (int o = 1; o < 32; o <<= 1) {
-                const double v = __shfl_up_sync(kFull, rinc, o);
-                if (lane >= o) rinc += v;
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int64_t i = r0 + q;
+                v[q] = (tid * RPT + q < ROWS && i < m) ? __ldcg(D2 + i) : 0.f;
+                rs += (double)v[q];
             }
-            rinc += excl;
-            const unsigned b2 = __ballot_sync(kFull, rinc > target && rs > 0.0);
-            const unsigned pos = __ballot_sync(kFull, rs > 0.0);
-            // the crossing lane, or (rounding) the last lane holding mass
-            const int src2 = b2 ? __ffs(b2) - 1 : (pos ? 31 - __clz(pos) : -1);
-            if (src2 >= 0) {
+            double tot;
+            const double rinc = kpp_block_scan(rs, sm.wsum, &tot) + sm.excl;
+            const int src2 = kpp_block_first(rinc > target && rs > 0.0, &sm.first);
+            // no crossing (rounding): the last thread holding mass
+            int who = src2;
+            if (src2 == INT_MAX) {
+                if (tid == 0) sm.first = -1;
+                __syncthreads();
+                if (rs > 0.0) atomicMax(&sm.first, tid);
+                __syncthreads();
+                who = sm.first;
+            }
+            if (tid == who) {
+                double run = rinc - rs;
                 long long p = -1;
-                if (lane == src2) {
-                    double run = rinc - rs;
-                    for (int q = 0; q < RPL; ++q) {
-                        const double v = (double)s_r[lane * RPL + q];
-                        if (v > 0.0) {
-                            p = fb * ROWS + lane * RPL + q;
-                            if (run + v > target) break;
-                        }
-                        run += v;
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) {
+                    const double w = (double)v[q];
+                    if (w > 0.0) {
+                        p = r0 + q;
+                        if (run + w > target) break;
                     }
+                    run += w;
                 }
-                pick = __shfl_sync(kFull, p, src2);
+                sm.pick = p;
             }
+            __syncthreads();
         }
-        if (pick < 0 && lane == 0) {
+        if (tid == 0 && sm.pick < 0) {
             // rounding left the target past the end: the last row with D^2 > 0
+            long long pick = -1;
             for (long long b = nb - 1; b >= 0 && pick < 0; --b) {
                 if (!(__ldcg(bsum + b) > 0.0)) continue;
                 for (long long i = b * ROWS + ROWS - 1; i >= b * ROWS; --i)
                     if (i < m && __ldcg(D2 + i) > 0.f) { pick = i; break; }
             }
+            sm.pick = pick;
         }
     } else {
         // all remaining points coincide with chosen centres: lowest unchosen index
-        for (int64_t c0 = 0; c0 < m; c0 += 32) {
-            const int64_t i = c0 + lane;
-            const unsigned b = __ballot_sync(kFull, i < m && !taken[i]);
-            if (b) { pick = c0 + __ffs(b) - 1; break; }
+        for (int64_t c0 = 0; c0 < m; c0 += kKppThreads) {
+            const int64_t i = c0 + tid;
+            const int f = kpp_block_first(i < m && !taken[i], &sm.first);
+            if (f != INT_MAX) {
+                if (tid == 0) sm.pick = c0 + f;
+                break;
+            }
         }
     }
-    if (lane == 0) {
+    __syncthreads();
+    if (tid == 0) {
+        const long long pick = sm.pick;
         chosen[t] = pick;
         if (pick >= 0 && pick < m) taken[pick] = 1;
         *counter = 0u;
