@@ -272,6 +272,41 @@ def test_leaf_scan_paths_agree_bitwise(monkeypatch, loaded):
     assert torch.equal(out["query"][1], out["cluster"][1])
 
 
+def test_empty_leaf_clusters(monkeypatch, c1):
+    # every 7th leaf cluster hands its members to the next one: queries still
+    # keep the empty clusters' centroids, whose work items scan no rows
+    X, Q, idx_o = c1
+    _, cs = oracle_index_fp32(idx_o)
+    k0 = len(cs[0])
+    remap = np.arange(k0)
+    empty = np.arange(0, k0, 7)
+    remap[empty] = (empty + 1) % k0
+    lab0 = remap[idx_o.labels[0]].astype(np.int32)
+    labels = [lab0, idx_o.labels[1]]
+    ref = O.Index(idx_o.X, [c.astype(np.float64) for c in cs], labels)
+    idx = M.mask_index_load(cuda(X), [cuda(c) for c in cs], [cuda(lb) for lb in labels])
+    try:
+        out = {}
+        for leaf in ["query", "cluster"]:
+            monkeypatch.setenv("MASK_LEAF_SCAN", leaf)
+            out[leaf] = M.mask_query(idx, cuda(Q), 10, [12, 6])
+        assert torch.equal(out["query"][0], out["cluster"][0])
+        assert torch.equal(out["query"][1], out["cluster"][1])
+        ids_o, d_o, clear = ref.query(Q, 10, [12, 6])
+        loose = check_knn(X, Q, out["cluster"][0], out["cluster"][1], ids_o, d_o, clear)
+        assert loose <= 0.01 * len(Q)
+        for prec in (M.MASK_BF16, M.MASK_FP8E4M3):
+            ids_l, d_l = M.mask_query(idx, cuda(Q), 10, [12, 6], precision=prec)
+            ids_l, d_l = arr(ids_l), arr(d_l)
+            assert ids_l.min() >= -1 and ids_l.max() < len(X)
+            for q in range(0, len(Q), 25):
+                ok = ids_l[q] >= 0
+                check_close(d_l[q][ok], O.sqdist_rows(X, ids_l[q][ok], Q[q]), rtol=RTOL,
+                            atol=1e-30, what=f"re-ranked distances q={q}")
+    finally:
+        idx.free()
+
+
 def test_probing_everything_is_exact_knn(loaded):
     X, Q, ref, idx = loaded
     ids_b, d_b = O.bruteforce_knn(X, Q[:200], 10)
