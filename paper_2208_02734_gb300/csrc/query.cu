@@ -95,21 +95,34 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     if (tid == 0) {
         cnt = 0;
         thresh = kNoKey;
-        int64_t tot = 0;
+        cum[0] = 0;
         if (sel == nullptr) {
             rb[0] = 0;
-            cum[0] = 0;
-            tot = root_end;
-            cum[1] = tot;
-        } else {
-            cum[0] = 0;
-            for (int s = 0; s < P; ++s) {
-                const int32_t p = sel[q * P + s];
-                int64_t b = 0, e = 0;
-                if (p >= 0) { b = off[p]; e = off[p + 1]; }
-                rb[s] = b;
-                tot += e - b;
-                cum[s + 1] = tot;
+            cum[1] = root_end;
+        }
+    }
+    if (sel != nullptr) {
+        // the kept parents' row ranges, one thread each (loads in parallel);
+        // cum[s + 1] holds range s's length until warp 0 turns it into a prefix
+        for (int s = tid; s < P; s += kThreads) {
+            const int32_t p = sel[q * P + s];
+            int64_t b = 0, e = 0;
+            if (p >= 0) { b = off[p]; e = off[p + 1]; }
+            rb[s] = b;
+            cum[s + 1] = e - b;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            long long carry = 0;
+            for (int c0 = 0; c0 < P; c0 += 32) {
+                const int s = c0 + tid;
+                long long v = s < P ? cum[s + 1] : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long n = __shfl_up_sync(kFull, v, o);
+                    if (tid >= o) v += n;
+                }
+                if (s < P) cum[s + 1] = carry + v;
+                carry += __shfl_sync(kFull, v, 31);
             }
         }
     }
