@@ -48,6 +48,74 @@ __device__ __forceinline__ void bitonic_sort_keys(unsigned long long *buf, int S
         }
 }
 
+// The key of 0-based rank `rank` among keys[0..n) (distinct keys), by a
+// most-significant-digit-first radix select over 8-bit digits: each pass
+// histograms the digit of the keys that share the digits fixed so far, and
+// the select stops as soon as the rank falls on a digit held by one key.
+__device__ unsigned long long radix_kth(const unsigned long long *keys, int n, int rank) {
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_prefix, s_mask, s_kth;
+    __shared__ int s_rank, s_done;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        s_prefix = 0;
+        s_mask = 0;
+        s_rank = rank;
+        s_done = 0;
+    }
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int i = tid; i < 256; i += kThreads) hist[i] = 0;
+        __syncthreads();
+        const unsigned long long pre = s_prefix, msk = s_mask;
+        for (int i = tid; i < n; i += kThreads) {
+            const unsigned long long k = keys[i];
+            if ((k & msk) == pre) atomicAdd(&hist[(unsigned)(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            unsigned c[8], ls = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j] = hist[lane * 8 + j];
+                ls += c[j];
+            }
+            unsigned inc = ls;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const unsigned r = (unsigned)s_rank;
+            unsigned run = inc - ls;
+            if (run <= r && r < inc) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (r < run + c[j]) {
+                        s_prefix = pre | ((unsigned long long)(lane * 8 + j) << shift);
+                        s_mask = msk | (255ull << shift);
+                        s_rank = (int)(r - run);
+                        s_done = c[j] == 1;
+                        break;
+                    }
+                    run += c[j];
+                }
+            }
+        }
+        __syncthreads();
+        if (s_done) break;
+    }
+    if (s_done) {
+        const unsigned long long pre = s_prefix, msk = s_mask;
+        for (int i = tid; i < n; i += kThreads)
+            if ((keys[i] & msk) == pre) s_kth = keys[i];
+    } else if (tid == 0) {
+        s_kth = s_prefix;
+    }
+    __syncthreads();
+    const unsigned long long r = s_kth;
+    __syncthreads();
+    return r;
+}
+
 // Squared distance of one row to the query, t ascending (FMA per term).
 __device__ __forceinline__ float row_sqdist(const float4 *__restrict__ row, const float4 *qs,
                                             int dp4) {
@@ -79,7 +147,10 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     int64_t *__restrict__ out64, float *__restrict__ out_d) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem);  // S keys
-    int64_t *rb = reinterpret_cast<int64_t *>(buf + S);                      // P range begins
+    // KP keys, padded to an even count so the float4 query chunks below stay
+    // 16-byte aligned (S is even; rb and cum together hold an even count)
+    unsigned long long *pick = buf + S;
+    int64_t *rb = reinterpret_cast<int64_t *>(pick + (KP + (KP & 1)));       // P range begins
     int64_t *cum = rb + P;                                                   // P+1 prefix sizes
     float4 *qs = reinterpret_cast<float4 *>(cum + P + 2);                    // dp4 query chunks
     __shared__ int cnt;
@@ -130,6 +201,9 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     const int nr = sel == nullptr ? 1 : P;
     const int64_t T = cum[nr];
     const int lim = S - KP - ROUND;
+    // centroid levels whose candidates all fit: every key is kept (candidate
+    // t at buf[t]) and the K smallest are selected once at the end
+    const bool direct = !ROWWISE && T <= S;
     if (tid == 0)
         atomicAdd(&g_scan_bytes[out64 ? 1 : 0], (unsigned long long)T * (dp4 * 16ull + 4ull));
 
@@ -161,11 +235,12 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
             const int g = tid / LPR, gl = tid % LPR;
 #pragma unroll 1
             for (int u0 = 0; u0 < PER; u0 += 4) {
-                int64_t row[4];
+                int64_t row[4], tt[4];
                 float acc[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int64_t t = base + g + (int64_t)(u0 + i) * G;
+                    tt[i] = t;
                     row[i] = -1;
                     acc[i] = 0.f;
                     if (u0 + i < PER && t < T) {
@@ -203,11 +278,13 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
                         const unsigned long long key =
                             ((unsigned long long)__float_as_uint(acc[i]) << 32) |
                             (unsigned)rid[row[i]];
-                        if (key < th) buf[KP + atomicAdd(&cnt, 1)] = key;
+                        if (direct) buf[tt[i]] = key;
+                        else if (key < th) buf[KP + atomicAdd(&cnt, 1)] = key;
                     }
                 }
             }
         }
+        if (direct) continue;
         __syncthreads();
         const int c_now = cnt;
         __syncthreads();
@@ -226,6 +303,36 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
             }
             __syncthreads();
         }
+    }
+    if (direct) {
+        // the K smallest of the T keys: radix-select the K-th, gather the keys
+        // up to it (distinct keys: exactly K), sort only those
+        __syncthreads();
+        const int Ti = (int)T;
+        int nsel = Ti;
+        if (Ti <= K) {
+            for (int i = tid; i < Ti; i += kThreads) pick[i] = buf[i];
+        } else {
+            const unsigned long long kth = radix_kth(buf, Ti, K - 1);
+            if (tid == 0) cnt = 0;
+            __syncthreads();
+            for (int i = tid; i < Ti; i += kThreads) {
+                const unsigned long long k = buf[i];
+                if (k <= kth) {
+                    const int slot = atomicAdd(&cnt, 1);
+                    if (slot < KP) pick[slot] = k;
+                }
+            }
+            __syncthreads();
+            nsel = min(cnt, K);
+        }
+        int L = 1;
+        while (L < nsel) L <<= 1;
+        for (int i = nsel + tid; i < L; i += kThreads) pick[i] = kNoKey;
+        __syncthreads();
+        bitonic_sort_keys(pick, L);
+        for (int i = tid; i < K; i += kThreads) buf[i] = i < nsel ? pick[i] : kNoKey;
+        __syncthreads();
     }
     for (int r = tid; r < K; r += kThreads) {
         const unsigned long long key = buf[r];
@@ -251,9 +358,10 @@ void scan_topk(const ScanArgs &a, cudaStream_t s) {
     MASK_REQUIRE(a.K >= 1 && a.K <= 4096, "scan_topk: K out of range");
     const int round = a.out_ids64 ? kThreads * kUnroll : (kThreads / lanes_per_row(a.dp)) * 4;
     const int KP = next_pow2(a.K);
-    const int S = next_pow2(KP + 2 * round > 4 * KP ? KP + 2 * round : 4 * KP);
+    int S = next_pow2(KP + 2 * round > 4 * KP ? KP + 2 * round : 4 * KP);
+    if (!a.out_ids64 && S < 2048) S = 2048;  // centroid levels: room to keep every candidate
     const int P = a.sel ? a.P : 1;
-    const size_t smem = (size_t)S * 8 + (size_t)(2 * P + 2) * 8 + (size_t)a.dp * 4;
+    const size_t smem = (size_t)(S + KP + (KP & 1)) * 8 + (size_t)(2 * P + 2) * 8 + (size_t)a.dp * 4;
     MASK_REQUIRE(smem <= 220 * 1024, "scan_topk: K, probes or dimension too large");
     ProfRegion pr(a.out_ids64 ? "scan_topk_leaf" : "scan_topk_level", s, 0.0);
     const float4 *R = reinterpret_cast<const float4 *>(a.R);
