@@ -13,12 +13,13 @@
 // query.cu (one thread per (row, query) pair, sum_t (r_t - q_t)^2 in
 // increasing t with FMAs), so a query's result is the same whichever kernel
 // served it and whatever else is in the batch.  The scan first ranks rows by
-// the cheaper expanded form ||x||^2 + ||q||^2 - 2 x.q (one FMA per dimension)
-// and evaluates a row exactly only where that value, less its rounding bound,
-// can reach the smaller of the pair's current K-th distance and T_q -- the K-th
-// exact distance within the query's nearest kept cluster (a seed pass), which
-// bounds the query's final K-th from above.  Rows the test drops cannot be
-// among the query's K nearest, so the result equals the full exact scan's.
+// the cheaper expanded form ||x||^2 + ||q||^2 - 2 x.q (the dot products on the
+// tensor cores, 3xTF32) and evaluates a row exactly only where that value,
+// less its rounding bound, can reach the smaller of the pair's current K-th
+// distance and T_q -- the K-th exact distance within the query's nearest kept
+// cluster (a seed pass), which bounds the query's final K-th from above.  Rows
+// the test drops cannot be among the query's K nearest, so the result equals
+// the full exact scan's.
 #include <algorithm>
 #include <climits>
 
