@@ -186,7 +186,6 @@ __global__ void sum_f32_to_f64_kernel(const float *__restrict__ v, int64_t n, do
 constexpr int kKppThreads = 512;
 constexpr int kKppRows = 1024;   // rows per block; one D^2 block sum each
 constexpr int kKppRpt = kKppRows / kKppThreads;  // rows per thread
-constexpr int kKppSelMax = 2048; // block sums the selecting warp stages in shared memory
 
 // One k-means++ step (§3.2).  The step number t >= 1 is read from *t_dev.
 // Fold the centre picked at step t-1 into D^2, then the last block to finish
