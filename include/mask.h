@@ -295,6 +295,17 @@ int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,
 /* Kernel launches the library has issued since it was loaded. */
 int64_t mask_launch_count(void);
 
+/*
+ * Test of the failure-detection contract of the library's device-side waits
+ * (every spin on a flag or barrier is bounded and reports instead of hanging):
+ * one GPU thread polls a device flag, set before the launch when flag_set is
+ * nonzero and never otherwise, for at most limit_us microseconds of GPU timer
+ * time.  Returns MASK_OK if it saw the flag, MASK_ETIMEOUT if the wait ran out
+ * (the context stays usable), MASK_EINVAL if limit_us is outside
+ * [0, 10,000,000].  Synchronises `stream`.
+ */
+mask_status mask_test_bounded_wait(int32_t flag_set, int32_t limit_us, mask_stream stream);
+
 /* ---- serving: continuous batching over a resident index ----------------
  *
  * The paper answers queries one at a time (§3.3); a service takes a stream

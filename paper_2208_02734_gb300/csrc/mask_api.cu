@@ -857,6 +857,47 @@ mask_status mask_kmeans_assign(const float *X, int64_t n, int32_t d, const float
     });
 }
 
+namespace mask {
+namespace {
+// One thread polls *flag until it is nonzero or limit_ns of GPU timer time
+// have passed (a cap on the number of polls bounds it even without the
+// timer); *seen = 1 if the flag was seen, 0 if the wait ran out.
+__global__ void bounded_wait_kernel(const int *flag, unsigned long long limit_ns, int *seen) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long t0, now;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+    for (unsigned i = 0; i < (1u << 26); ++i) {
+        if (*(const volatile int *)flag != 0) {
+            *seen = 1;
+            return;
+        }
+        if ((i & 63u) == 63u) {
+            asm volatile("mov.u64 %0, %globaltimer;" : "=l"(now));
+            if (now - t0 > limit_ns) break;
+        }
+    }
+    *seen = 0;
+}
+}  // namespace
+}  // namespace mask
+
+mask_status mask_test_bounded_wait(int32_t flag_set, int32_t limit_us, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(limit_us >= 0 && limit_us <= 10000000, "limit_us out of range");
+        cudaStream_t s = (cudaStream_t)stream;
+        Scratch<int> buf(2, s);  // [0] the flag, [1] what the wait saw
+        const int init[2] = {flag_set ? 1 : 0, -1};
+        MASK_CUDA(cudaMemcpyAsync(buf.get(), init, sizeof(init), cudaMemcpyHostToDevice, s));
+        mask::bounded_wait_kernel<<<1, 32, 0, s>>>(buf.get(), (unsigned long long)limit_us * 1000ull,
+                                                   buf.get() + 1);
+        MASK_LAUNCHED("bounded_wait");
+        int seen = -1;
+        MASK_CUDA(cudaMemcpyAsync(&seen, buf.get() + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MASK_CUDA(cudaStreamSynchronize(s));
+        if (seen != 1) fail(MASK_ETIMEOUT, "bounded device wait ran out (the flag was never set)");
+    });
+}
+
 mask_status mask_kmeans_update(const float *X, int64_t n, int32_t d, const int32_t *labels,
                                int32_t k, const float *C_prev, float *C_out,
                                int64_t *counts_out, mask_stream stream) {

@@ -33,7 +33,7 @@ EXPORTED = [
     "mask_profile_enable", "mask_profile_reset", "mask_profile_read", "mask_launch_count",
     "mask_kmeans_assign_noalloc", "mask_kmeanspp_csr", "mask_kmeans_assign_csr",
     "mask_kmeans_update_csr", "mask_server_open", "mask_server_submit", "mask_server_poll",
-    "mask_server_wait", "mask_server_stats", "mask_server_close",
+    "mask_server_wait", "mask_server_stats", "mask_server_close", "mask_test_bounded_wait",
 ]
 
 
@@ -102,6 +102,7 @@ def load(build_if_stale: bool = True):
             "mask_profile_read": (C.c_int32, [C.c_char_p, C.POINTER(C.c_int64),
                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mask_launch_count": (C.c_int64, []),
+            "mask_test_bounded_wait": (C.c_int, [_i32, _i32, _vp]),
             "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
             "mask_kmeanspp_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _u64, _i32, _vp,
                                             _vp, _vp]),
@@ -507,3 +508,18 @@ def mask_profile_read(name: str):
 
 def mask_launch_count() -> int:
     return int(load().mask_launch_count())
+
+
+def mask_test_bounded_wait(flag_set: bool, limit_us: int, stream=None) -> str:
+    """Run the library's bounded device wait on a flag that is set before the
+    launch (flag_set) or never; returns the status name ("MASK_OK" or
+    "MASK_ETIMEOUT") instead of raising for those two."""
+    import torch
+    if stream is None:
+        st = torch.cuda.current_stream().cuda_stream
+    else:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    r = int(load().mask_test_bounded_wait(1 if flag_set else 0, int(limit_us), st))
+    if r not in (0, -4):
+        _check(r, "mask_test_bounded_wait")
+    return _STATUS[r]
