@@ -251,11 +251,14 @@ mask_status mask_kmeans_update_csr(const int64_t *row_ptr, const int32_t *col, c
  * one file-scope device array of 2.36 MB that every GPU which loads the
  * library holds until the process exits.
  *   X [n x d], C [k x d] float32, labels_out [n] int32, dist_out [n] float32
- *   (may be NULL): all DEVICE memory; X and C 16-byte aligned.
+ *   (may be NULL): all DEVICE memory of the current device; X and C 16-byte
+ *   aligned.  The C side cannot see array lengths: the caller guarantees
+ *   that C has d columns and the outputs hold n elements.
  *   d must be a multiple of 8 (rows are used in place, not padded).
  *   1 <= k <= 65536 (the array holds at most 65536 centroid norms); any n
  *   (rows are processed 262,144 at a time).
- * Larger k, host pointers or other d return MASK_EINVAL with a message.
+ * Larger k, host pointers, another device's pointers or other d return
+ * MASK_EINVAL with a message.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the one array: calls whose
@@ -296,6 +299,13 @@ int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,
 int64_t mask_launch_count(void);
 
 /*
+ * Device and pinned-host allocations the library has made since it was
+ * loaded (stream-ordered scratch, index arrays, serving staging buffers).
+ * A test hook: it lets a caller check that a call allocated nothing.
+ */
+int64_t mask_test_alloc_count(void);
+
+/*
  * Test of the failure-detection contract of the library's device-side waits
  * (every spin on a flag or barrier is bounded and reports instead of hanging):
  * one GPU thread polls a device flag, set before the launch when flag_set is
@@ -323,6 +333,8 @@ mask_status mask_test_bounded_wait(int32_t flag_set, int32_t limit_us, mask_stre
  * result is the same as mask_query's on its queries alone (bit for bit).
  * For FP32 shapes where both leaf scans apply, the first batch of a shape
  * times both and keeps the faster (autotuning; results are identical).
+ * The graphs captured while autotuning hold buffers outside the mem_budget
+ * accounting (the budget covers the batches admitted to run).
  *
  * The index must stay alive until mask_server_close.  Queries and outputs
  * are HOST memory: queries are copied at submit; ids_out / dists_out are

@@ -286,13 +286,15 @@ uint32_t *noalloc_scratch() {
     return static_cast<uint32_t *>(g_noalloc_ptr[dev]);
 }
 
-bool is_device_memory(const void *p) {
+// True for device (or managed) memory of device `dev`: the scratch array
+// used with it is the one of the current device.
+bool is_device_memory(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 void assign_noalloc(const float *X, int64_t n, int d, const float *C, int k, int32_t *labels,
@@ -347,9 +349,13 @@ extern "C" mask_status mask_kmeans_assign_noalloc(const float *X, int64_t n, int
                      "k must be in [1, 65536]: the no-alloc scratch holds at most 65536 centroid norms");
         MASK_REQUIRE((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(C)) % 16 == 0,
                      "X and C must be 16-byte aligned");
-        MASK_REQUIRE(is_device_memory(X) && is_device_memory(C) && is_device_memory(labels_out) &&
-                         (dist_out == nullptr || is_device_memory(dist_out)),
-                     "all arrays must be device memory (host staging would allocate)");
+        int dev = 0;
+        MASK_CUDA(cudaGetDevice(&dev));
+        MASK_REQUIRE(is_device_memory(X, dev) && is_device_memory(C, dev) &&
+                         is_device_memory(labels_out, dev) &&
+                         (dist_out == nullptr || is_device_memory(dist_out, dev)),
+                     "all arrays must be device memory of the current device (host staging "
+                     "would allocate; another device's arrays cannot use this device's scratch)");
         if (n == 0) return MASK_OK;
         assign_noalloc(X, n, d, C, k, labels_out, dist_out, (cudaStream_t)stream);
         return MASK_OK;

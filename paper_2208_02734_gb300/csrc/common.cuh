@@ -28,8 +28,14 @@ void set_last_error(const std::string &msg);
 
 // Counts one kernel launch (called by MASK_LAUNCHED at every launch site).
 void count_launch();
+// True while mask_profile_enable(1) is in effect (kernels then also count
+// the bytes their scans read).
+bool profiling_enabled();
 // Counts n launches at once (the kernel nodes of a replayed graph).
 void count_launches(long long n);
+// Counts one device or pinned-host allocation (Scratch, DevArray, server
+// staging); read through mask_test_alloc_count().
+void count_alloc();
 
 // While profiling is enabled, brackets its scope with CUDA events on stream s
 // and books the elapsed device time and `work` (flop or bytes) under `name`.
@@ -90,7 +96,10 @@ struct Scratch {
         release();
         s = st;
         n = count;
-        if (count) MASK_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+        if (count) {
+            count_alloc();
+            MASK_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+        }
     }
     void release() {
         if (p) cudaFreeAsync(p, s);
@@ -117,7 +126,10 @@ struct DevArray {
     void alloc(size_t count) {
         release();
         n = count;
-        if (count) MASK_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+        if (count) {
+            count_alloc();
+            MASK_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+        }
     }
     void release() {
         if (p) cudaFree(p);

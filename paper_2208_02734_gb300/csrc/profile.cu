@@ -13,6 +13,7 @@ namespace mask {
 namespace {
 
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};
 std::atomic<bool> g_enabled{false};
 std::mutex g_mu;
 
@@ -47,7 +48,11 @@ void drain_locked(const std::string &name) {
 
 }  // namespace
 
+bool profiling_enabled() { return g_enabled.load(std::memory_order_relaxed); }
+
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -112,5 +117,7 @@ int32_t mask_profile_read(const char *name, int64_t *launches, double *total_ms,
 }
 
 int64_t mask_launch_count(void) { return mask::g_launches.load(); }
+
+int64_t mask_test_alloc_count(void) { return mask::g_allocs.load(); }
 
 }  // extern "C"

@@ -27,6 +27,18 @@ namespace mask {
 // Bytes the scan kernels stream (rows x (row + id)), [0] levels, [1] leaf.
 __device__ unsigned long long g_scan_bytes[2];
 
+// Device address of a byte counter while profiling is on; null otherwise, so
+// the kernels skip the count (one uniform test, no atomic) in normal runs.
+unsigned long long *scan_bytes_counter(int which) {
+    if (!profiling_enabled()) return nullptr;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scan_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<unsigned long long *>(p) + which;
+}
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -144,7 +156,8 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     const float4 *__restrict__ R, int dp4, const int32_t *__restrict__ rid,
     const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P, int64_t root_end,
     const float4 *__restrict__ Q, int K, int KP, int S, int32_t *__restrict__ out32,
-    int64_t *__restrict__ out64, float *__restrict__ out_d) {
+    int64_t *__restrict__ out64, float *__restrict__ out_d,
+    unsigned long long *__restrict__ bytes_ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem);  // S keys
     // KP keys, padded to an even count so the float4 query chunks below stay
@@ -204,8 +217,8 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     // centroid levels whose candidates all fit: every key is kept (candidate
     // t at buf[t]) and the K smallest are selected once at the end
     const bool direct = !ROWWISE && T <= S;
-    if (tid == 0)
-        atomicAdd(&g_scan_bytes[out64 ? 1 : 0], (unsigned long long)T * (dp4 * 16ull + 4ull));
+    if (bytes_ctr != nullptr && tid == 0)
+        atomicAdd(bytes_ctr, (unsigned long long)T * (dp4 * 16ull + 4ull));
 
     for (int64_t base = 0; base < T; base += ROUND) {
         const unsigned long long th = thresh;
@@ -373,7 +386,8 @@ void scan_topk(const ScanArgs &a, cudaStream_t s) {
                                        (int)smem));                                          \
         kfn<<<(unsigned)a.nq, kThreads, smem, s>>>(R, a.dp / 4, a.rid, a.off, a.sel, P,      \
                                                    a.root_end, Qv, a.K, KP, S, a.out_ids32,  \
-                                                   a.out_ids64, a.out_d);                    \
+                                                   a.out_ids64, a.out_d,                     \
+                                                   scan_bytes_counter(a.out_ids64 ? 1 : 0)); \
     } while (0)
     if (a.out_ids64) {
         MASK_SCAN(true, 1);  // the leaf: per-row arithmetic shared with the cluster-major scan

@@ -30,6 +30,18 @@ namespace mask {
 // Bytes the cluster-major scan streams (rows x (row + id), per work item).
 __device__ unsigned long long g_cm_bytes;
 
+// Device address of a byte counter while profiling is on; null otherwise, so
+// the kernels skip the count (one uniform test, no atomic) in normal runs.
+unsigned long long *cm_bytes_counter() {
+    if (!profiling_enabled()) return nullptr;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_cm_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<unsigned long long *>(p);
+}
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -166,7 +178,7 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
     const float *__restrict__ qn, const float *__restrict__ seed_d, float mcoef,
     const int4 *__restrict__ meta, const int32_t *__restrict__ pid,
     const int32_t *__restrict__ qid, const int64_t *__restrict__ item_off, int k0, int K,
-    unsigned long long *__restrict__ pair_out) {
+    unsigned long long *__restrict__ pair_out, unsigned long long *__restrict__ bytes_ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int XS = cm_stride(dp4), XS4 = XS / 4;
     float *xs = reinterpret_cast<float *>(smem);                 // [2][CM_R][XS] rows
@@ -402,8 +414,8 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
         }
         if (!more) {
             // the item is done: write its pair lists and clear them for the next item
-            if (tid == 0)
-                atomicAdd(&g_cm_bytes, (unsigned long long)cur.rows * (dp4 * 16ull + 4ull));
+            if (bytes_ctr != nullptr && tid == 0)
+                atomicAdd(bytes_ctr, (unsigned long long)cur.rows * (dp4 * 16ull + 4ull));
             __syncthreads();
             for (int i = tid; i < nqb * K; i += CM_THREADS) {
                 const int qb = i / K, j = i % K;
@@ -582,7 +594,7 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
         cm_scan_kernel<<<std::max(1, per_sm) * sms, CM_THREADS, smem, s>>>(
             reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids,
             reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef_tc, meta.get(),
-            ipid.get(), iqid.get(), item_off.get(), k0, K, pair_out.get());
+            ipid.get(), iqid.get(), item_off.get(), k0, K, pair_out.get(), cm_bytes_counter());
         MASK_LAUNCHED("cm_scan");
     }
     cm_merge(pair_out.get(), nq, P, K, ids, dists, s);

@@ -30,6 +30,18 @@ namespace mask {
 // per row), counted per block.
 __device__ unsigned long long g_csr_scan_bytes[2];
 
+// Device address of a byte counter while profiling is on; null otherwise, so
+// the kernels skip the count (one uniform test, no atomic) in normal runs.
+unsigned long long *csr_scan_bytes_counter(int which) {
+    if (!profiling_enabled()) return nullptr;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_csr_scan_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<unsigned long long *>(p) + which;
+}
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -131,7 +143,7 @@ __global__ __launch_bounds__(kThreads) void csr_level_scan_kernel(
     const int32_t *__restrict__ rid, const int64_t *__restrict__ off,
     const int32_t *__restrict__ sel, int P, int64_t root_end, const int64_t *__restrict__ qrp,
     const int32_t *__restrict__ qcol, const float *__restrict__ qval, int qcap, int K, int KP,
-    int S, int32_t *__restrict__ out32) {
+    int S, int32_t *__restrict__ out32, unsigned long long *__restrict__ bytes_ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     ScanSmem sm;
     sm.buf = reinterpret_cast<unsigned long long *>(smem);
@@ -162,8 +174,8 @@ __global__ __launch_bounds__(kThreads) void csr_level_scan_kernel(
     const int64_t T = sm.cum[nr];
     const int lim = S - KP - kRound;
     const int g = tid / kGroup, gl = tid % kGroup;
-    if (tid == 0)
-        atomicAdd(&g_csr_scan_bytes[0], (unsigned long long)T * (4ull * qn + 8ull));
+    if (bytes_ctr != nullptr && tid == 0)
+        atomicAdd(bytes_ctr, (unsigned long long)T * (4ull * qn + 8ull));
 
     for (int64_t base = 0; base < T; base += kRound) {
         const unsigned long long th = thresh;
@@ -231,7 +243,8 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P,
     const int64_t *__restrict__ qrp, const int32_t *__restrict__ qcol,
     const float *__restrict__ qval, int hslots, int64_t min_nnz, int K, int KP, int S,
-    int64_t *__restrict__ out64, float *__restrict__ out_d) {
+    int64_t *__restrict__ out64, float *__restrict__ out_d,
+    unsigned long long *__restrict__ bytes_ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     ScanSmem sm;
     sm.buf = reinterpret_cast<unsigned long long *>(smem);
@@ -333,7 +346,8 @@ __global__ __launch_bounds__(kThreads) void csr_leaf_scan_kernel(
         }
         maybe_merge(sm, S, K, KP, lim, base + kRound >= T, &cnt, &thresh);
     }
-    if (tid == 0) atomicAdd(&g_csr_scan_bytes[1], 8ull * s_nnz + 12ull * (unsigned long long)T);
+    if (bytes_ctr != nullptr && tid == 0)
+        atomicAdd(bytes_ctr, 8ull * s_nnz + 12ull * (unsigned long long)T);
     for (int r = tid; r < K; r += kThreads) {
         const unsigned long long key = sm.buf[r];
         const bool ok = key != kNoKey;
@@ -626,7 +640,7 @@ void csr_level_scan(const float *R, int dp, const float *rcn, const int32_t *rid
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     csr_level_scan_kernel<<<(unsigned)nq, kThreads, smem, s>>>(
         R, dp, rcn, rid, off, sel, Pn, root_end, qrp, qcol, qval, qcap, K, next_pow2(K),
-        list_size(K), out32);
+        list_size(K), out32, csr_scan_bytes_counter(0));
     MASK_LAUNCHED("csr_level_scan");
 }
 
@@ -697,7 +711,7 @@ void csr_leaf_scan(const int64_t *xrp, const int32_t *xcol, const float *xval,
                                                               qrp, qcol, qval,
                                                               csr_leaf_table_slots(longest), min_nnz, K,
                                                               next_pow2(K), list_size(K), out64,
-                                                              out_d);
+                                                              out_d, csr_scan_bytes_counter(1));
     MASK_LAUNCHED("csr_leaf_scan");
 }
 

@@ -242,8 +242,11 @@ std::unique_ptr<Instance> make_instance(mask_server *S, const Shape &sh) {
     inst->Qp.alloc(B * dp);
     inst->ids.alloc(B * K);
     inst->dists.alloc(B * K);
+    count_alloc();
     MASK_CUDA(cudaMallocHost((void **)&inst->hQ, B * dp * sizeof(float)));
+    count_alloc();
     MASK_CUDA(cudaMallocHost((void **)&inst->hids, B * K * sizeof(int64_t)));
+    count_alloc();
     MASK_CUDA(cudaMallocHost((void **)&inst->hd, B * K * sizeof(float)));
     std::memset(inst->hQ, 0, B * dp * sizeof(float));
     MASK_CUDA(cudaMemsetAsync(inst->Qp.get(), 0, B * dp * sizeof(float), S->cap_stream));
@@ -332,9 +335,17 @@ int tune_mode(mask_server *S, int slot, Batch &b, const Key &key, int64_t bucket
     cudaStream_t st = S->streams[(size_t)slot];
     float best_ms = 0.f;
     int best = (int)LeafMode::Query;
-    cudaEvent_t e0, e1;
-    MASK_CUDA(cudaEventCreate(&e0));
-    MASK_CUDA(cudaEventCreate(&e1));
+    // the events are released on every exit, including a failed CUDA call
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    MASK_CUDA(cudaEventCreate(&ev.a));
+    MASK_CUDA(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     for (int mode : {(int)LeafMode::Query, (int)LeafMode::Cluster}) {
         Shape sh{key, bucket, K, mode};
         b.inst = get_instance(S, sh);
@@ -355,8 +366,6 @@ int tune_mode(mask_server *S, int slot, Batch &b, const Key &key, int64_t bucket
             best = mode;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     S->tuned[tk] = best;
     std::lock_guard<std::mutex> lk(S->mu);
     S->autotuned += 1;

@@ -34,6 +34,7 @@ EXPORTED = [
     "mask_kmeans_assign_noalloc", "mask_kmeanspp_csr", "mask_kmeans_assign_csr",
     "mask_kmeans_update_csr", "mask_server_open", "mask_server_submit", "mask_server_poll",
     "mask_server_wait", "mask_server_stats", "mask_server_close", "mask_test_bounded_wait",
+    "mask_test_alloc_count",
 ]
 
 
@@ -102,6 +103,7 @@ def load(build_if_stale: bool = True):
             "mask_profile_read": (C.c_int32, [C.c_char_p, C.POINTER(C.c_int64),
                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mask_launch_count": (C.c_int64, []),
+            "mask_test_alloc_count": (C.c_int64, []),
             "mask_test_bounded_wait": (C.c_int, [_i32, _i32, _vp]),
             "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
             "mask_kmeanspp_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _u64, _i32, _vp,
@@ -342,14 +344,49 @@ def mask_kmeans_assign(X, Cc, with_dist: bool = True, stream=None):
     return lab, dist
 
 
+def _noalloc_args(X, Cc, labels_out, dist_out):
+    """Checks what the C side cannot see (shapes, dtypes, layout, device) and
+    raises ValueError instead of converting: a cast or a contiguous copy would
+    allocate, which is what this entry point exists to avoid."""
+    import torch
+
+    def need(cond, msg):
+        if not cond:
+            raise ValueError("mask_kmeans_assign_noalloc: " + msg)
+
+    arrays = {"X": X, "Cc": Cc, "labels_out": labels_out}
+    if dist_out is not None:
+        arrays["dist_out"] = dist_out
+    for name, t in arrays.items():
+        need(isinstance(t, torch.Tensor), f"{name} must be a torch tensor")
+        need(t.is_cuda, f"{name} must be a CUDA tensor")
+        need(t.is_contiguous(), f"{name} must be contiguous")
+    need(X.dtype == torch.float32 and Cc.dtype == torch.float32, "X and Cc must be float32")
+    need(X.dim() == 2 and Cc.dim() == 2, "X and Cc must be 2-D")
+    need(Cc.shape[1] == X.shape[1], f"Cc has {Cc.shape[1]} columns, X has {X.shape[1]}")
+    n = X.shape[0]
+    need(labels_out.dtype == torch.int32, "labels_out must be int32")
+    need(labels_out.numel() >= n, f"labels_out holds {labels_out.numel()} < {n} rows")
+    if dist_out is not None:
+        need(dist_out.dtype == torch.float32, "dist_out must be float32")
+        need(dist_out.numel() >= n, f"dist_out holds {dist_out.numel()} < {n} rows")
+    devs = {t.device for t in arrays.values()}
+    need(len(devs) == 1, f"all tensors must be on one device, got {sorted(map(str, devs))}")
+
+
 def mask_kmeans_assign_noalloc(X, Cc, labels_out, dist_out=None, stream=None):
     """Allocation-free assignment for callers that cannot let the library
     allocate: every array (inputs and the caller-provided outputs) must be a
-    CUDA tensor; d a multiple of 8; k <= 65536."""
-    _check(load().mask_kmeans_assign_noalloc(
-        X.data_ptr(), X.shape[0], X.shape[1], Cc.data_ptr(), Cc.shape[0], labels_out.data_ptr(),
-        None if dist_out is None else dist_out.data_ptr(), _stream(X, stream)),
-        "mask_kmeans_assign_noalloc")
+    contiguous CUDA tensor on one device (X, Cc float32 [n x d] / [k x d];
+    labels_out int32 [>= n]; dist_out float32 [>= n] or None); d a multiple of
+    8; k <= 65536.  Anything else raises ValueError before the C call."""
+    _noalloc_args(X, Cc, labels_out, dist_out)
+    import torch
+    with torch.cuda.device(X.device):
+        _check(load().mask_kmeans_assign_noalloc(
+            X.data_ptr(), X.shape[0], X.shape[1], Cc.data_ptr(), Cc.shape[0],
+            labels_out.data_ptr(), None if dist_out is None else dist_out.data_ptr(),
+            _stream(X, stream)), "mask_kmeans_assign_noalloc")
     return labels_out, dist_out
 
 
@@ -508,6 +545,10 @@ def mask_profile_read(name: str):
 
 def mask_launch_count() -> int:
     return int(load().mask_launch_count())
+
+
+def mask_test_alloc_count() -> int:
+    return int(load().mask_test_alloc_count())
 
 
 def mask_test_bounded_wait(flag_set: bool, limit_us: int, stream=None) -> str:

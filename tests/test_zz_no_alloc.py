@@ -58,6 +58,23 @@ def test_noalloc_assign_matches_the_allocating_entry_point_on_two_calls():
     _same_as_allocating_path(X2, C2)
 
 
+def test_noalloc_assign_makes_no_library_allocation():
+    X, Cc = _data(20_000, 32, 500, seed=4)
+    lab = torch.empty(20_000, dtype=torch.int32, device="cuda")
+    dist = torch.empty(20_000, dtype=torch.float32, device="cuda")
+    M.mask_kmeans_assign_noalloc(X, Cc, lab, dist)   # the first call may look up the scratch
+    torch.cuda.synchronize()
+    before = M.mask_test_alloc_count()
+    for _ in range(2):
+        M.mask_kmeans_assign_noalloc(X, Cc, lab, dist)
+    torch.cuda.synchronize()
+    assert M.mask_test_alloc_count() == before
+    # the allocating entry point does move the counter (the hook works)
+    M.mask_kmeans_assign(X, Cc)
+    torch.cuda.synchronize()
+    assert M.mask_test_alloc_count() > before
+
+
 def test_noalloc_assign_refuses_what_it_cannot_serve_without_allocating():
     X, Cc = _data(1000, 16, 10, seed=3)
     lab = torch.empty(1000, dtype=torch.int32, device="cuda")
@@ -65,7 +82,26 @@ def test_noalloc_assign_refuses_what_it_cannot_serve_without_allocating():
         big = torch.zeros((65537, 16), dtype=torch.float32, device="cuda")
         M.mask_kmeans_assign_noalloc(X, big, lab)
     assert e.value.status == M.MASK_EINVAL and "65536" in str(e.value)
-    with pytest.raises(M.MaskError):  # host memory would need staging buffers
-        M.mask_kmeans_assign_noalloc(X.cpu(), Cc.cpu(), lab.cpu())
+    # host memory would need staging buffers: the C side refuses it (the
+    # binding already refuses CPU tensors before the call)
+    Xh, Ch, lh = X.cpu(), Cc.cpu(), lab.cpu()
+    st = M.load().mask_kmeans_assign_noalloc(Xh.data_ptr(), 1000, 16, Ch.data_ptr(), 10,
+                                             lh.data_ptr(), None, None)
+    assert st == M.MASK_EINVAL and "device memory" in M.mask_last_error()
+    with pytest.raises(ValueError):
+        M.mask_kmeans_assign_noalloc(Xh, Ch, lh)
     with pytest.raises(M.MaskError):  # rows must be usable in place
         M.mask_kmeans_assign_noalloc(X[:, :12].contiguous(), Cc[:, :12].contiguous(), lab)
+    before = M.mask_test_alloc_count()
+    lab = torch.empty(1000, dtype=torch.int32, device="cuda")
+    for bad in (
+        lambda: M.mask_kmeans_assign_noalloc(X, Cc[:, :8].contiguous(), lab),   # d mismatch
+        lambda: M.mask_kmeans_assign_noalloc(X, Cc, lab[:999]),                # short labels
+        lambda: M.mask_kmeans_assign_noalloc(X, Cc, lab.long()),               # int64 labels
+        lambda: M.mask_kmeans_assign_noalloc(X, Cc, lab, lab.float()[:10]),    # short dist
+        lambda: M.mask_kmeans_assign_noalloc(X.double(), Cc, lab),             # float64 rows
+        lambda: M.mask_kmeans_assign_noalloc(X.t(), Cc, lab),                  # non-contiguous
+    ):
+        with pytest.raises(ValueError):
+            bad()
+    assert M.mask_test_alloc_count() == before
