@@ -17,18 +17,19 @@ def bench():
     return mod
 
 
-def test_tensor_roofline_counts_the_three_tf32_passes(bench):
+def test_tensor_roofline_reports_useful_flop_and_the_issued_passes_apart(bench):
     peaks, _ = bench.measured_peaks()
     kernels = {"assign_tc": {"ms": 2000.0, "work": 6.0e14, "launches": 48},
                "kmeanspp": {"ms": 600.0, "work": 2.0e12, "launches": 3}}
     r = bench.roofline_of(kernels, "dense10m", 3000.0)
     assert r["kernel"] == "assign_tc" and r["bound"] == "tensor"
     useful = 6.0e14 / 2.0 / 1e12                      # TFLOP/s of useful work
-    assert r["achieved_useful"] == pytest.approx(useful)
-    assert r["achieved"] == pytest.approx(3 * useful)
     peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25
     assert r["peak"] == pytest.approx(peak)
-    assert r["frac"] == pytest.approx(3 * useful / peak)
+    assert r["achieved"] == pytest.approx(useful)
+    assert r["frac"] == pytest.approx(useful / peak)
+    assert r["achieved_issued"] == pytest.approx(bench.TC_PASSES * useful)
+    assert r["frac_issued"] == pytest.approx(bench.TC_PASSES * useful / peak)
     assert r["work_per_launch"] == pytest.approx(6.0e14 / 48)
     assert r["ms_share_of_step"] == pytest.approx(2000.0 / 3000.0)
     # the traffic row is used only while the kernel's source is unchanged

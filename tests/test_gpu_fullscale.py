@@ -8,10 +8,15 @@ size:
   - the first k-means++ picks of level 0 equal the oracle's on the same
     seeded subsample (8k of the 10^7 points, partial Fisher-Yates);
   - each level's objective after every assignment never increases;
-  - sampled labels are the argmin over the built centroids (up to near-ties);
+  - sampled labels are the oracle's argmin over the built centroids (up to
+    near-ties);
+  - one update step of all 10^7 points under the built labels gives the
+    oracle's mean for sampled clusters (teacher-forced);
   - returned distances of sampled queries equal the oracle's exact distances
-    of the returned ids, results are ascending, and recall@10 against the
-    oracle's exact k-NN meets the operating point's level;
+    of the returned ids, results are ascending, the ids are those of the
+    oracle's descent over the GPU-built index (up to near-tie swaps), and
+    recall@10 against the oracle's exact k-NN meets the operating point's
+    level;
   - both leaf scans give bit-identical results at this size.
 """
 
@@ -22,7 +27,7 @@ import oracle as O
 from paper_2208_02734_gb300 import mask as M
 from paper_2208_02734_gb300 import synth
 
-from parity_util import RTOL, arr, check_close
+from parity_util import RTOL, arr, check_close, check_knn, check_labels, check_rows_close
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -67,24 +72,39 @@ def test_objective_never_increases(built):
         assert np.all(np.diff(J) <= 1e-5 * J[0]), (lv, J)
 
 
-def test_sampled_labels_are_the_argmin(built):
+def test_sampled_labels_are_the_oracle_argmin(built):
     X, _, _, _, idx = built
     e = M.mask_index_export_level(idx, 0)
-    C = arr(e["centroids"]).astype(np.float64)
+    C = arr(e["centroids"])
     lab = arr(e["labels"])
     rows = np.random.default_rng(0).choice(N, 2000, replace=False)
-    x = X[rows].astype(np.float64)
-    cn = (C * C).sum(1)
-    for s in range(0, len(rows), 250):
-        xs = x[s:s + 250]
-        d = (xs * xs).sum(1)[:, None] - 2.0 * xs @ C.T + cn[None, :]
-        best = d.min(1)
-        got = d[np.arange(len(xs)), lab[rows[s:s + 250]]]
-        assert np.all(got <= best + RTOL * np.abs(best) + 1e-9 * (xs * xs).sum(1)), s
+    lab_o, _ = O.assign(X[rows], C.astype(np.float64))
+    check_labels(X[rows], C, lab[rows], lab_o)
+
+
+def test_full_size_update_step_on_sampled_clusters(built):
+    # teacher-forced: the update of all 10^7 points under the built index's
+    # final labels, checked cluster by cluster against the oracle's mean
+    X, _, Xd, _, idx = built
+    e = M.mask_index_export_level(idx, 0, device="cuda")
+    C_new, cnt = M.mask_kmeans_update(Xd, e["labels"], e["centroids"])
+    C_new, cnt, lab = arr(C_new), arr(cnt), arr(e["labels"])
+    assert cnt.sum() == N and np.array_equal(cnt, np.bincount(lab, minlength=KPL[0]))
+    order = np.argsort(lab, kind="stable")
+    start = np.concatenate([[0], np.cumsum(cnt)])
+    rng = np.random.default_rng(1)
+    sample = np.concatenate([rng.choice(KPL[0], 60, replace=False),
+                             np.argsort(cnt)[-4:]])   # and the largest clusters
+    for j in sample:
+        members = order[start[j]:start[j + 1]]
+        C_o, _ = O.update(X[members], np.zeros(len(members), np.int32),
+                          arr(e["centroids"])[j:j + 1].astype(np.float64))
+        check_rows_close(C_new[j:j + 1], C_o, what=f"cluster {j} ({len(members)} members)")
 
 
 def test_sampled_queries_against_oracle(built):
-    X, Q, _, Qd, idx = built
+    X32, Q, _, Qd, idx = built
+    X = X32.astype(np.float64)   # once: the oracle helpers take FP64 rows
     ids, dists = M.mask_query(idx, Qd, 10, PROBES)
     ids, dists = arr(ids), arr(dists)
     sel = np.arange(0, len(Q), len(Q) // 40)[:40]
@@ -93,6 +113,14 @@ def test_sampled_queries_against_oracle(built):
         ok = ids[q] >= 0
         exact = O.sqdist_rows(X, ids[q][ok], Q[q])
         check_close(dists[q][ok], exact, rtol=RTOL, atol=1e-30, what=f"query {q}")
+    # the oracle's descent (Algorithm 2, p_l kept per level) over the very
+    # index the GPU built: same ids except near-tie swaps
+    levels = [M.mask_index_export_level(idx, lv) for lv in range(len(KPL))]
+    oidx = O.Index(X, [arr(lv["centroids"]).astype(np.float64) for lv in levels],
+                   [arr(lv["labels"]) for lv in levels])
+    ids_o, d_o, clear = oidx.query(Q[sel], 10, PROBES)
+    loose = check_knn(X, Q[sel], ids[sel], dists[sel], ids_o, d_o, clear)
+    assert loose <= len(sel) // 4, loose
     gt_ids, gt_d = O.bruteforce_knn(X, Q[sel], 10)
     hits = 0
     for i, q in enumerate(sel):

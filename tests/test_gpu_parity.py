@@ -128,6 +128,32 @@ def test_update_of_a_large_cluster_matches_oracle():
     assert torch.equal(C_g, C_g2)
 
 
+def _fp32_ulps(a_g, a_o):
+    """|a_g - fl32(a_o)| in units of the FP32 spacing at fl32(a_o)."""
+    ref = np.asarray(a_o, np.float64).astype(np.float32)
+    spacing = np.spacing(np.abs(ref)).astype(np.float64)
+    return np.abs(np.asarray(a_g, np.float64) - ref.astype(np.float64)) / spacing
+
+
+def test_update_of_clusters_beyond_2_20_members_sums_in_fp64():
+    # cluster 0 has 2^20 + 1 members (FP64 sums), cluster 1 exactly 2^20
+    # (FP32 sums), cluster 2 a handful.  Coordinates near 1000 make FP32
+    # running sums lose digits, so only FP64 sums land within one FP32 ulp of
+    # the oracle's mean rounded to FP32.
+    m0, m1, m2, d = (1 << 20) + 1, 1 << 20, 7, 8
+    n = m0 + m1 + m2
+    rng = np.random.default_rng(11)
+    X = (1000.0 + rng.random((n, d)) * np.linspace(0.5, 4.0, d)).astype(np.float32)
+    lab = np.concatenate([np.zeros(m0), np.ones(m1), np.full(m2, 2)]).astype(np.int32)
+    lab = lab[rng.permutation(n)]
+    C_prev = np.zeros((3, d), np.float32)
+    C_o, cnt_o = O.update(X, lab, C_prev)
+    C_g, cnt_g = M.mask_kmeans_update(cuda(X), cuda(lab), cuda(C_prev))
+    assert arr(cnt_g).tolist() == [m0, m1, m2] == cnt_o.tolist()
+    check_rows_close(C_g, C_o, what="centroids")
+    assert _fp32_ulps(arr(C_g)[0], C_o[0]).max() <= 1.0, arr(C_g)[0] - C_o[0]
+
+
 def test_update_rejects_out_of_range_labels():
     X = np.zeros((10, 4), np.float32)
     with pytest.raises(M.MaskError):

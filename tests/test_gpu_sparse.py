@@ -302,3 +302,33 @@ def test_csr_rejects_malformed_inputs(sparse_c):
     with pytest.raises(M.MaskError, match="mask_query"):
         M.mask_query_csr(dense, *dcsr(Qa.rows(np.arange(4))), 5, [4])
     dense.free()
+
+
+def test_csr_update_of_a_cluster_beyond_2_20_members_sums_in_fp64():
+    # 2^20 + 1 rows in cluster 0 (FP64 sums), the rest in cluster 1; every
+    # row has the same few columns, values near 100, so FP32 running sums
+    # would lose digits and only FP64 sums stay within one FP32 ulp of the
+    # oracle's mean rounded to FP32
+    m0, m1, d, per = (1 << 20) + 1, 5000, 40, 4
+    n = m0 + m1
+    rng = np.random.default_rng(12)
+    cols = np.sort(rng.choice(d, per, replace=False)).astype(np.int32)
+    rp = np.arange(0, (n + 1) * per, per, dtype=np.int64)
+    col = np.tile(cols, n)
+    val = (100.0 + rng.random(n * per)).astype(np.float32)
+    A = synth.CSR(rp, col, val, d)
+    lab = np.zeros(n, np.int32)
+    lab[rng.choice(n, m1, replace=False)] = 1
+    C_prev = np.zeros((2, d), np.float32)
+    # oracle on the densified columns only (the others are exact zeros)
+    Xc = val.reshape(n, per).astype(np.float64)
+    C_o_c, cnt_o = O.update(Xc, lab, np.zeros((2, per)))
+    C_g, cnt_g = M.mask_kmeans_update_csr(*dcsr(A), d, cuda(lab), cuda(C_prev))
+    C_g = arr(C_g)
+    assert arr(cnt_g).tolist() == cnt_o.tolist() == [m0, m1]
+    other = np.setdiff1d(np.arange(d), cols)
+    assert np.all(C_g[:, other] == 0.0)
+    check_rows_close(C_g[:, cols], C_o_c, what="centroids")
+    ref = C_o_c[0].astype(np.float32)
+    ulps = np.abs(C_g[0, cols].astype(np.float64) - ref) / np.spacing(np.abs(ref))
+    assert ulps.max() <= 1.0, (C_g[0, cols], C_o_c[0])
