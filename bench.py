@@ -47,9 +47,9 @@ METRIC = "queries/s at recall@10>=0.95, p50/p99 latency, build s; %roofline vs F
 WORKLOADS = {
     "dense10m": dict(n=10_000_000, d=64, blobs=1000, kind="anisotropic", k_per_level=[32768, 1024, 32],
                      iters=15, nq=10_000, k=10, probes=[8, 4, 2],
-                     ladder=[[8, 4, 2], [16, 4, 2], [32, 8, 2], [48, 8, 4], [64, 16, 4], [96, 16, 4],
-                             [128, 24, 6], [192, 32, 8], [256, 48, 12], [384, 64, 16],
-                             [512, 96, 24]],
+                     ladder=[[8, 4, 2], [16, 4, 2], [32, 8, 2], [48, 8, 4], [64, 16, 4], [80, 16, 4],
+                             [96, 16, 4], [112, 16, 4], [112, 20, 5], [128, 24, 6], [160, 24, 6],
+                             [192, 32, 8], [256, 48, 12], [384, 64, 16], [512, 96, 24]],
                      desc="10M x 64 fp32, 1000 anisotropic blobs (eig log-U[0.1,10], Zipf 1.1), "
                           "index 32768/1024/32, 15 Lloyd iters, 10k queries, k=10, probes 8/4/2"),
     "sparse1m": dict(n=1_000_000, d=20_000, nnz_mean=60.0, kind="sparse", k_per_level=[4096, 64],
@@ -95,6 +95,11 @@ REF_SAMPLE = {
     "serving": dict(n=20_000, k_per_level=[200, 20], nq=1000),
     "small": dict(n=20_000, k_per_level=[200, 20], nq=1000),
 }
+
+# Rung selection: the selection sample must clear 0.95 by about two standard
+# errors of a 1,000-query recall estimate, so that the held-out measurement of
+# the chosen rung is itself at or above 0.95.
+SELECT_RECALL = 0.955
 
 # FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (maximum SM clock).
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -795,10 +800,11 @@ def run_ours(args, w, wname):
     stream = torch.cuda.current_stream(dev)
     kpl, k = w["k_per_level"], w["k"]
 
-    # operating point: the cheapest probes of a fixed ladder with recall@10 >= 0.95
-    # (measured on an index built once, against FP64 exact k-NN of 200 queries)
+    # operating point: the cheapest probes of a fixed ladder with recall@10 >=
+    # SELECT_RECALL on a 1,000-query selection sample (index built once, FP64
+    # exact k-NN); the headline recall is then measured on 1,000 other queries
     t_op = time.perf_counter()
-    sel = recall_sample(Qd)
+    sel = recall_sample(Qd, 1000)
     Qs = Qd[sel]
     _, gt_d = exact_knn_fp64(Xd, Qs, k)
     dk = gt_d[:, -1:]
@@ -808,7 +814,7 @@ def run_ours(args, w, wname):
         ids_s, _ = M.mask_query(idx_eval, Qs, k, pr)
         ladder.append({"probes": pr, "recall_at_10": recall_at_k(Xd, Qs, ids_s, dk)})
     idx_eval.free()
-    ok = [e for e in ladder if e["recall_at_10"] >= 0.95]
+    ok = [e for e in ladder if e["recall_at_10"] >= SELECT_RECALL]
     op = ok[0] if ok else ladder[-1]
     probes = op["probes"]
     stated = ladder[0] if ladder[0]["probes"] == w["probes"] else None
@@ -880,7 +886,7 @@ def run_ours(args, w, wname):
             for pr in w["ladder"]:
                 ids_s, _ = M.mask_query(idx_lp, Qs, k, pr, precision=prec)
                 r = recall_at_k(Xd, Qs, ids_s, dk)
-                if r >= 0.95:
+                if r >= SELECT_RECALL:
                     rung = (pr, r)
                     break
             if rung is None:
@@ -946,13 +952,14 @@ def run_ours(args, w, wname):
         "config": {"workload": w["desc"], "n": w["n"], "d": w["d"], "k_per_level": kpl,
                    "iters": w["iters"], "queries": w["nq"], "k": k, "probes": probes,
                    "stated_probes": w["probes"],
-                   "probes_rule": "cheapest probes of a fixed ladder with recall@10 >= 0.95 "
-                                  "(200-query sample vs FP64 exact k-NN)",
+                   "probes_rule": "cheapest probes of a fixed ladder with recall@10 >= "
+                                  f"{SELECT_RECALL} on a 1,000-query selection sample (vs FP64 "
+                                  "exact k-NN); recall_at_10 is measured on 1,000 other queries",
                    "l2": "inputs larger than L2 (points 2.56 GB); no flush",
                    "parallelism": f"independent index per GPU x{world}"},
         "recall_at_10": recall, "recall_queries": n_rec,
-        "recall_note": "recall@10 of the timed results on queries held out from the 200-query "
-                       "rung-selection sample, against FP64 exact k-NN",
+        "recall_note": "recall@10 of the timed results on 1,000 queries held out from the "
+                       "1,000-query rung-selection sample, against FP64 exact k-NN",
         "recall_at_10_selection_sample": recall_sel,
         "recall_at_stated_probes": stated["recall_at_10"] if stated else None,
         "probe_ladder": ladder,

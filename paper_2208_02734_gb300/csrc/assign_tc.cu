@@ -2,12 +2,17 @@
 // tensor cores: labels[i] = argmin_j ||x_i - c_j||^2, ties to the smallest j.
 //
 // Distances in the expanded form ||x||^2 - 2 x.c + ||c||^2.  The cross term
-// x.c is a GEMM on tcgen05 (kind::tf32, FP32 accumulation in tensor memory)
-// made FP32-accurate with the 3xTF32 split: x = x_hi + x_lo with x_hi the
-// TF32-rounded value and x_lo = x - x_hi (exact), and
-//     x.c ~= x_hi.c_hi + x_hi.c_lo + x_lo.c_hi
-// (Ootomo & Yokota 2022, "Recovering single precision accuracy from Tensor
-// Cores while surpassing the FP32 theoretical peak performance").
+// x.c is a GEMM on tcgen05 (kind::f16: FP16 operands, FP32 accumulation in
+// tensor memory) made FP32-accurate by a three-product split (the scheme of
+// Ootomo & Yokota 2022, "Recovering single precision accuracy from Tensor
+// Cores while surpassing the FP32 theoretical peak performance", on FP16):
+// every row of X is scaled by a power of two s_i that puts its largest
+// coordinate in [2^14, 2^15), C by one power of two s_c for all of it, and a
+// scaled value v = x*s splits into v_hi = fp16(v) and v_lo = fp16(v - v_hi),
+//     (x.c) s_i s_c ~= x_hi.c_hi + x_hi.c_lo + x_lo.c_hi,
+// with each fp16 x fp16 product exact in FP32.  The scales are powers of two,
+// so undoing them in the epilogue is exact; FP16 runs the tensor pipe at
+// twice the TF32 rate, and the split keeps 22 bits of each operand.
 //
 // One CTA owns 128 rows of X.  Their hi/lo tiles stay in shared memory while
 // 128-centroid tiles of C stream through a TMA pipeline; the accumulator is
@@ -24,6 +29,7 @@
 // centroids.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <cfloat>
 #include <climits>
@@ -41,13 +47,13 @@ constexpr int TC_M = 128, TC_N = 128;   // MMA tile: 128 rows x 128 centroids
 constexpr int TC_EPI_WARPS = 8;         // two epilogue warps per TMEM lane quadrant
 constexpr int TC_THREADS = (4 + TC_EPI_WARPS) * 32;
 constexpr int TC_EPI_COLS = TC_N / (TC_EPI_WARPS / 4);   // columns per epilogue thread per tile
-constexpr int TC_BOX_K = 32;            // fp32 columns per TMA box (128 bytes)
-constexpr int TC_BOX_BYTES = TC_M * TC_BOX_K * 4;   // 16 KB
+constexpr int TC_DK = 64;               // fp16 columns of the split copies (dp <= 64)
+constexpr int TC_BOX_BYTES = TC_M * TC_DK * 2;      // one 128-byte row per item: 16 KB
 constexpr int TC_NRING = 8;             // slots of the centroid-norm ring
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
-                            ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+// instruction descriptor: D = F32, A = B = F16, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) |
+                            ((uint32_t)(TC_M >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -138,12 +144,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b,
-                                         uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                        uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
         : "memory");
 }
@@ -227,22 +233,25 @@ struct Top4 {
 
 // ------------------------------------------------------------- main kernel
 
-template <int KB, int S>
+// ksteps = K-steps of 16 fp16 columns (ceil(dp / 16)); xinv[i] = 1 / s_i,
+// cinv[0] = 1 / s_c (the scales of the split copies).
+template <int S>
 __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl,
     const __grid_constant__ CUtensorMap tmCh, const __grid_constant__ CUtensorMap tmCl,
-    const float *__restrict__ xn, int64_t n, int ksteps, const float *__restrict__ cn_pad, int k,
+    const float *__restrict__ xn, const float *__restrict__ xinv, const float *__restrict__ cinv,
+    int64_t n, int ksteps, const float *__restrict__ cn_pad, int k,
     const float *__restrict__ cn_max, float margin_coef, int32_t *__restrict__ labels,
     int4 *__restrict__ list3, int *__restrict__ n3, int32_t *__restrict__ listF,
     int *__restrict__ nF, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    constexpr uint32_t kStage = 2u * KB * TC_BOX_BYTES;  // hi + lo tiles of one C tile
+    constexpr uint32_t kStage = 2u * TC_BOX_BYTES;       // hi + lo tiles of one C tile
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;        // swizzled tiles need 1 KB alignment
     unsigned char *basep = smem_raw + (base - raw);
-    const uint32_t A_hi = base, A_lo = base + KB * TC_BOX_BYTES;
-    const uint32_t B0 = base + 2u * KB * TC_BOX_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(basep + 2u * KB * TC_BOX_BYTES + S * kStage);
+    const uint32_t A_hi = base, A_lo = base + TC_BOX_BYTES;
+    const uint32_t B0 = base + 2u * TC_BOX_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(basep + 2u * TC_BOX_BYTES + S * kStage);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5 + 2 * TC_NRING);
     __shared__ int s_err;
     __shared__ __align__(16) float s_cn[TC_NRING][TC_N];   // norms of the C tiles in flight
@@ -296,22 +305,18 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        mbar_expect_tx(a_full, 2u * KB * TC_BOX_BYTES);
-        for (int kb = 0; kb < KB; ++kb) {
-            tma_load_2d(A_hi + kb * TC_BOX_BYTES, &tmXh, kb * TC_BOX_K, (int)row0, a_full);
-            tma_load_2d(A_lo + kb * TC_BOX_BYTES, &tmXl, kb * TC_BOX_K, (int)row0, a_full);
-        }
+        mbar_expect_tx(a_full, 2u * TC_BOX_BYTES);
+        tma_load_2d(A_hi, &tmXh, 0, (int)row0, a_full);
+        tma_load_2d(A_lo, &tmXl, 0, (int)row0, a_full);
         int armed = 0, armedN = 0;
         bool ok = true;
         for (int j = 0; j < ntiles; ++j) {
             const int s = j % S, u = j / S;
             if (u > 0 && !mbar_wait(b_empty(s), (u - 1) & 1, err)) { ok = false; break; }
-            const uint32_t bh = B0 + s * kStage, bl = bh + KB * TC_BOX_BYTES;
+            const uint32_t bh = B0 + s * kStage, bl = bh + TC_BOX_BYTES;
             mbar_expect_tx(b_full(s), kStage);
-            for (int kb = 0; kb < KB; ++kb) {
-                tma_load_2d(bh + kb * TC_BOX_BYTES, &tmCh, kb * TC_BOX_K, j * TC_N, b_full(s));
-                tma_load_2d(bl + kb * TC_BOX_BYTES, &tmCl, kb * TC_BOX_K, j * TC_N, b_full(s));
-            }
+            tma_load_2d(bh, &tmCh, 0, j * TC_N, b_full(s));
+            tma_load_2d(bl, &tmCl, 0, j * TC_N, b_full(s));
             armed = j + 1;
             // the tile's 128 norms (the ring is 8 tiles deep, far ahead of the epilogue)
             const int q = j % TC_NRING, w = j / TC_NRING;
@@ -340,16 +345,17 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             if (!ok) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(a * TC_N);
-            const uint32_t bh = B0 + s * kStage, bl = bh + KB * TC_BOX_BYTES;
+            const uint32_t bh = B0 + s * kStage, bl = bh + TC_BOX_BYTES;
             const uint64_t dBh = sw128_desc(bh), dBl = sw128_desc(bl);
+            // K-step kk covers fp16 columns 16kk..16kk+15: 32 bytes into each
+            // 128-byte row, i.e. +2 in the descriptor's 16-byte address units
 #pragma unroll
-            for (int kk = 0; kk < 4 * KB; ++kk) {
+            for (int kk = 0; kk < TC_DK / 16; ++kk) {
                 if (kk < ksteps) {
-                    const uint64_t off =
-                        (uint64_t)((kk >> 2) * (TC_BOX_BYTES >> 4) + (kk & 3) * 2);
-                    mma_tf32(d, dAh + off, dBh + off, kk > 0 ? 1u : 0u);
-                    mma_tf32(d, dAh + off, dBl + off, 1u);
-                    mma_tf32(d, dAl + off, dBh + off, 1u);
+                    const uint64_t off = (uint64_t)(kk * 2);
+                    mma_f16(d, dAh + off, dBh + off, kk > 0 ? 1u : 0u);
+                    mma_f16(d, dAh + off, dBl + off, 1u);
+                    mma_f16(d, dAl + off, dBh + off, 1u);
                 }
             }
             mma_commit(b_empty(s));    // the C tile's stage is free once these MMAs finish
@@ -363,12 +369,15 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         // ---------------- epilogue: one row per thread, half the columns ----------------
         // Rows are ranked by key = ||c||^2 - 2 x.c (the row's ||x||^2 is
         // added back at the end); the norms of each C tile arrive in a ring
-        // of shared-memory slots filled by the producer.
+        // of shared-memory slots filled by the producer.  The accumulator
+        // holds (x.c) s_i s_c: the factor -2 / (s_i s_c) is a power of two,
+        // so the scaling costs no rounding.
         const int quad = warp & 3;                  // TMEM lane quadrant of this warp
         const int half = (warp - 4) >> 2;           // column half of each tile
         const int r = quad * 32 + lane;
         const int64_t row = row0 + r;
         const float xr = row < n ? xn[row] : 0.f;
+        const float mul = row < n ? -2.f * xinv[row] * cinv[0] : 0.f;
         Top4 t4;
         t4.init();
         bool ok = true;
@@ -401,14 +410,14 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
                 const int b = (g & 3) * 8;
                 const float4 c0v = cn4[2 * g], c1v = cn4[2 * g + 1];
                 float *kk = key + 8 * g;
-                kk[0] = fmaf(-2.f, __uint_as_float(uu[b + 0]), c0v.x);
-                kk[1] = fmaf(-2.f, __uint_as_float(uu[b + 1]), c0v.y);
-                kk[2] = fmaf(-2.f, __uint_as_float(uu[b + 2]), c0v.z);
-                kk[3] = fmaf(-2.f, __uint_as_float(uu[b + 3]), c0v.w);
-                kk[4] = fmaf(-2.f, __uint_as_float(uu[b + 4]), c1v.x);
-                kk[5] = fmaf(-2.f, __uint_as_float(uu[b + 5]), c1v.y);
-                kk[6] = fmaf(-2.f, __uint_as_float(uu[b + 6]), c1v.z);
-                kk[7] = fmaf(-2.f, __uint_as_float(uu[b + 7]), c1v.w);
+                kk[0] = fmaf(mul, __uint_as_float(uu[b + 0]), c0v.x);
+                kk[1] = fmaf(mul, __uint_as_float(uu[b + 1]), c0v.y);
+                kk[2] = fmaf(mul, __uint_as_float(uu[b + 2]), c0v.z);
+                kk[3] = fmaf(mul, __uint_as_float(uu[b + 3]), c0v.w);
+                kk[4] = fmaf(mul, __uint_as_float(uu[b + 4]), c1v.x);
+                kk[5] = fmaf(mul, __uint_as_float(uu[b + 5]), c1v.y);
+                kk[6] = fmaf(mul, __uint_as_float(uu[b + 6]), c1v.z);
+                kk[7] = fmaf(mul, __uint_as_float(uu[b + 7]), c1v.w);
                 gm[g] = fminf(fminf(fminf(kk[0], kk[1]), fminf(kk[2], kk[3])),
                               fminf(fminf(kk[4], kk[5]), fminf(kk[6], kk[7])));
             }
@@ -523,20 +532,74 @@ __global__ __launch_bounds__(256) void recheck3_kernel(const float4 *__restrict_
     }
 }
 
-// hi = x rounded to TF32 (10 explicit mantissa bits), lo = x - hi (exact);
-// columns dp..dpk-1 are zero.
-__global__ void split_tf32_kernel(const float *__restrict__ src, int64_t rows, int dp, int dpk,
-                                  float *__restrict__ hi, float *__restrict__ lo) {
-    const int64_t total = rows * dpk;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / dpk;
-        const int c = (int)(e - r * dpk);
-        const float x = c < dp ? src[r * dp + c] : 0.f;
-        const float h = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-        hi[e] = h;
-        lo[e] = x - h;
+// Exponent e of a positive finite float m with 2^e <= m < 2^(e+1); values
+// below the normal range count as 2^-127.
+__device__ __forceinline__ int exponent_of(float m) {
+    const int b = (int)((__float_as_uint(m) >> 23) & 0xffu);
+    return b == 0 ? -127 : b - 127;
+}
+
+// 2^e as a float, for e in [-126, 127].
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Split copies for the FP16 three-product scheme: v = x * s with s a power of
+// two that puts m (the row's largest |x|, or *global_max for all rows) in
+// [2^14, 2^15); hi = fp16(v), lo = fp16(v - hi) (v - hi is exact in FP32).
+// hi, lo are [rows x 64] (columns dp..63 zero); inv_scale[row] = 1 / s (one
+// value, inv_scale[0], when global_max is given).  Eight lanes per row, eight
+// columns each.
+__global__ void split_f16_kernel(const float *__restrict__ src, int64_t rows, int dp,
+                                 const unsigned *__restrict__ global_max, __half *__restrict__ hi,
+                                 __half *__restrict__ lo, float *__restrict__ inv_scale) {
+    const int l = threadIdx.x & 7;
+    // the loop runs warp-uniformly (the shuffles below need all 32 lanes);
+    // a warp covers 4 rows per pass, lanes past the last row idle
+    const int64_t warp_rows = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32 * 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x / 32 * 4;
+    for (int64_t rb = warp_rows; rb < rows; rb += stride) {
+        const int64_t r = rb + (threadIdx.x & 31) / 8;
+        const bool live = r < rows;
+        float v[8];
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int col = l * 8 + c;
+            v[c] = live && col < dp ? src[r * dp + col] : 0.f;
+            m = fmaxf(m, fabsf(v[c]));
+        }
+        if (global_max != nullptr) {
+            m = __uint_as_float(*global_max);
+        } else {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1, 8));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2, 8));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4, 8));
+        }
+        int e = m > 0.f ? 14 - exponent_of(m) : 0;
+        e = e < -126 ? -126 : (e > 126 ? 126 : e);
+        const float sc = pow2f(e);
+        alignas(16) __half h8[8], l8[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float x = v[c] * sc;
+            const __half h = __float2half_rn(x);
+            h8[c] = h;
+            l8[c] = __float2half_rn(x - __half2float(h));
+        }
+        if (!live) continue;
+        *reinterpret_cast<uint4 *>(hi + r * TC_DK + l * 8) = *reinterpret_cast<const uint4 *>(h8);
+        *reinterpret_cast<uint4 *>(lo + r * TC_DK + l * 8) = *reinterpret_cast<const uint4 *>(l8);
+        if (l == 0 && (global_max == nullptr || r == 0)) inv_scale[global_max ? 0 : r] = pow2f(-e);
     }
+}
+
+// *out = max |v| (as float bits; *out must start at 0).
+__global__ void absmax_kernel(const float *__restrict__ v, int64_t count, unsigned *out) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(v[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
 }
 
 // Norms of the padding columns of the last 128-centroid tile: +inf, so their
@@ -561,18 +624,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D tensor map of a [rows x dpk] fp32 array, boxes of 128 rows x 32 columns,
-// 128-byte swizzle, zero fill out of bounds.
-CUtensorMap make_map(const float *base, int64_t rows, int dpk) {
+// 2-D tensor map of a [rows x 64] fp16 array, boxes of 128 rows x 64 columns
+// (one 128-byte row each), 128-byte swizzle, zero fill out of bounds.
+CUtensorMap make_map(const __half *base, int64_t rows) {
     auto fn = encode_fn();
     if (fn == nullptr) fail(MASK_ECUDA, "cuTensorMapEncodeTiled is unavailable");
     CUtensorMap m;
     std::memset(&m, 0, sizeof(m));
-    const cuuint64_t dims[2] = {(cuuint64_t)dpk, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)dpk * 4u};
-    const cuuint32_t box[2] = {(cuuint32_t)TC_BOX_K, (cuuint32_t)TC_M};
+    const cuuint64_t dims[2] = {(cuuint64_t)TC_DK, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)TC_DK * 2u};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_DK, (cuuint32_t)TC_M};
     const cuuint32_t estr[2] = {1u, 1u};
-    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims,
+    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -585,11 +648,13 @@ int grid_cap(int64_t work) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
 }
 
-template <int KB, int S>
+template <int S>
 size_t tc_smem_bytes() {
-    return 1024 + 2u * KB * TC_BOX_BYTES + (size_t)S * 2u * KB * TC_BOX_BYTES +
+    return 1024 + 2u * TC_BOX_BYTES + (size_t)S * 2u * TC_BOX_BYTES +
            (2 * S + 5 + 2 * TC_NRING) * 8 + 16;
 }
+
+constexpr int TC_STAGES = 4;   // C tiles in flight (32 KB each)
 
 }  // namespace
 
@@ -597,9 +662,10 @@ size_t tc_smem_bytes() {
 
 struct TcAssign {
     int64_t n = 0;
-    int dp = 0, dpk = 0;
+    int dp = 0;
     const float *X = nullptr;      // padded points [n x dp]
-    Scratch<float> Xh, Xl;         // [n x dpk] TF32 hi / lo parts
+    Scratch<__half> Xh, Xl;        // [n x 64] scaled FP16 hi / lo parts
+    Scratch<float> xinv;           // [n] 1 / s_i (powers of two)
     CUtensorMap mXh, mXl;
     Scratch<int> err;              // set by a kernel whose bounded wait ran out
 };
@@ -615,38 +681,41 @@ std::shared_ptr<TcAssign> tc_assign_prepare(const float *X, int64_t n, int dp, c
     auto p = std::make_shared<TcAssign>();
     p->n = n;
     p->dp = dp;
-    p->dpk = dp <= 32 ? 32 : 64;
     p->X = X;
-    p->Xh.alloc((size_t)n * p->dpk, s);
-    p->Xl.alloc((size_t)n * p->dpk, s);
-    split_tf32_kernel<<<grid_cap(n * p->dpk), 256, 0, s>>>(X, n, dp, p->dpk, p->Xh.get(), p->Xl.get());
-    MASK_LAUNCHED("split_tf32");
-    p->mXh = make_map(p->Xh.get(), n, p->dpk);
-    p->mXl = make_map(p->Xl.get(), n, p->dpk);
+    p->Xh.alloc((size_t)n * TC_DK, s);
+    p->Xl.alloc((size_t)n * TC_DK, s);
+    p->xinv.alloc((size_t)n, s);
+    split_f16_kernel<<<grid_cap(n * 8), 256, 0, s>>>(X, n, dp, nullptr, p->Xh.get(), p->Xl.get(),
+                                                     p->xinv.get());
+    MASK_LAUNCHED("split_f16");
+    p->mXh = make_map(p->Xh.get(), n);
+    p->mXl = make_map(p->Xl.get(), n);
     p->err.alloc(1, s);
     MASK_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));
     return p;
 }
 
-template <int KB, int S>
+template <int S>
 void launch_tc(const TcAssign &p, const CUtensorMap &mCh, const CUtensorMap &mCl, const float *xn,
-               const float *cn, int k, const float *cmax, float coef, int32_t *labels,
-               int4 *list3, int *n3, int32_t *listF, int *nF, cudaStream_t s) {
-    const size_t smem = tc_smem_bytes<KB, S>();
-    auto kfn = assign_tc_kernel<KB, S>;
+               const float *cinv, const float *cn, int k, const float *cmax, float coef,
+               int32_t *labels, int4 *list3, int *n3, int32_t *listF, int *nF, cudaStream_t s) {
+    const size_t smem = tc_smem_bytes<S>();
+    auto kfn = assign_tc_kernel<S>;
     MASK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned blocks = (unsigned)((p.n + TC_M - 1) / TC_M);
-    kfn<<<blocks, TC_THREADS, smem, s>>>(p.mXh, p.mXl, mCh, mCl, xn, p.n, p.dp / 8, cn, k, cmax,
-                                        coef, labels, list3, n3, listF, nF, p.err.get());
+    kfn<<<blocks, TC_THREADS, smem, s>>>(p.mXh, p.mXl, mCh, mCl, xn, p.xinv.get(), cinv, p.n,
+                                        (p.dp + 15) / 16, cn, k, cmax, coef, labels, list3, n3,
+                                        listF, nF, p.err.get());
 }
 
 void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *labels,
                cudaStream_t s) {
-    const int dp = p.dp, dpk = p.dpk;
+    const int dp = p.dp;
     const int ntiles = (k + TC_N - 1) / TC_N;
     // centroid norms padded to whole 128-centroid tiles (+inf past k)
-    Scratch<float> cn((size_t)ntiles * TC_N, s), cmax(1, s), Ch((size_t)k * dpk, s),
-        Cl((size_t)k * dpk, s);
+    Scratch<float> cn((size_t)ntiles * TC_N, s), cmax(1, s), cinv(1, s);
+    Scratch<__half> Ch((size_t)k * TC_DK, s), Cl((size_t)k * TC_DK, s);
+    Scratch<unsigned> cabs(1, s);
     Scratch<int4> list3(p.n, s);
     Scratch<int32_t> listF(p.n, s);
     Scratch<int> counts(2, s);
@@ -656,28 +725,35 @@ void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *lab
         MASK_LAUNCHED("pad_inf");
     }
     max_reduce(cn.get(), k, cmax.get(), s);
-    split_tf32_kernel<<<grid_cap((int64_t)k * dpk), 256, 0, s>>>(C, k, dp, dpk, Ch.get(), Cl.get());
-    MASK_LAUNCHED("split_tf32");
-    const CUtensorMap mCh = make_map(Ch.get(), k, dpk), mCl = make_map(Cl.get(), k, dpk);
+    MASK_CUDA(cudaMemsetAsync(cabs.get(), 0, sizeof(unsigned), s));
+    absmax_kernel<<<grid_cap((int64_t)k * dp), 256, 0, s>>>(C, (int64_t)k * dp, cabs.get());
+    MASK_LAUNCHED("absmax");
+    split_f16_kernel<<<grid_cap((int64_t)k * 8), 256, 0, s>>>(C, k, dp, cabs.get(), Ch.get(),
+                                                              Cl.get(), cinv.get());
+    MASK_LAUNCHED("split_f16");
+    const CUtensorMap mCh = make_map(Ch.get(), k), mCl = make_map(Cl.get(), k);
     MASK_CUDA(cudaMemsetAsync(counts.get(), 0, 2 * sizeof(int), s));
-    // Error bound of one expanded-form distance, relative to ||x||^2 + ||c||^2:
-    // the 3xTF32 cross term (split error 2.5 * 2^-21 and FP32 accumulation
-    // over 3*dp/8 MMA steps plus 8 in-MMA additions, counted at 2^-23 each,
-    // times 2 for the factor -2 and sum|x_t c_t| <= (||x||^2 + ||c||^2) / 2),
-    // the FP32 norms (dp * 2^-24) and two final roundings (4 * 2^-24).
+    // Error bound of one expanded-form distance, relative to ||x||^2 + ||c||^2
+    // (the factor 2 of -2 x.c cancels against sum|x_t c_t| <= (||x||^2 +
+    // ||c||^2) / 2):
+    //  - the split: with u = 2^-11 (FP16 rounding), v - hi is within u|v| and
+    //    lo within u|v - hi| of it, so the dropped lo*lo product and the two
+    //    rounded lo factors leave (3 + 3u) * 2^-22 of sum |x_t c_t|; lo values
+    //    below the FP16 normal range add at most 2^-24 (scaled units) each,
+    //    which after unscaling is below 2^-27 of ||x||^2 + ||c||^2;
+    //  - FP32 accumulation in the tensor core: 3 * ceil(dp/16) MMAs into one
+    //    accumulator plus 16 additions inside an MMA, counted at 2^-23 each
+    //    (truncating adders);
+    //  - the FP32 norms (dp * 2^-24) and two final roundings (4 * 2^-24).
     // A label is certain when the best two differ by more than twice the
     // bound; the coefficient is widened 2x beyond that.
-    const double per = 2.5 * 0x1.0p-21 + (3.0 * dp / 8.0 + 8.0) * 0x1.0p-23 +
-                       (dp + 4.0) * 0x1.0p-24;
+    const double per = (3.0 + 3.0 * 0x1.0p-11) * 0x1.0p-22 + 0x1.0p-27 +
+                       (3.0 * ((dp + 15) / 16) + 16.0) * 0x1.0p-23 + (dp + 4.0) * 0x1.0p-24;
     const float coef = (float)(2.0 * 2.0 * per);
     {
         ProfRegion pr("assign_tc", s, 2.0 * (double)p.n * (double)k * (double)dp);
-        if (dpk == 32)
-            launch_tc<1, 4>(p, mCh, mCl, xn, cn.get(), k, cmax.get(), coef, labels, list3.get(),
-                            counts.get(), listF.get(), counts.get() + 1, s);
-        else
-            launch_tc<2, 2>(p, mCh, mCl, xn, cn.get(), k, cmax.get(), coef, labels, list3.get(),
-                            counts.get(), listF.get(), counts.get() + 1, s);
+        launch_tc<TC_STAGES>(p, mCh, mCl, xn, cinv.get(), cn.get(), k, cmax.get(), coef, labels,
+                             list3.get(), counts.get(), listF.get(), counts.get() + 1, s);
         MASK_LAUNCHED("assign_tc");
     }
     {
