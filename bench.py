@@ -105,7 +105,7 @@ SELECT_RECALL = 0.955
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Dense TF32 tensor peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1 / 2.25).
 TF32_PER_BF16 = 1.1 / 2.25
-# The FP32-accurate tensor-core assignment issues 3 TF32 MMAs per useful product.
+# The FP32-accurate tensor-core assignment issues 3 FP16 MMAs per useful product.
 TC_PASSES = 3
 
 
@@ -401,11 +401,16 @@ def roofline_of(kernels, wname, step_ms):
         # timed inside a long step: the sustained BF16 figure scaled to TF32
         peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
         ach = kv.get("achieved_tflops", 0.0)
+        peak16 = peaks["bf16_tflops_sustained"]
         roofline = {"kernel": dom, "bound": "tensor", "achieved": ach,
                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "work_note": "achieved = useful flop 2*n*k*d per launch / launch time",
-                    "achieved_issued": ach * TC_PASSES, "frac_issued": ach * TC_PASSES / peak,
-                    "issued_note": "3 TF32 MMAs per useful product (3xTF32 split)",
+                    "work_note": "achieved = useful flop 2*n*k*d per launch / launch time, "
+                                 "against the TF32 peak (the FP32-accurate product's "
+                                 "reference rate)",
+                    "achieved_issued": ach * TC_PASSES, "peak_issued": peak16,
+                    "frac_issued": ach * TC_PASSES / peak16,
+                    "issued_note": "3 FP16 MMAs per useful product (scaled FP16 hi/lo split) "
+                                   f"against the {peak_kind} sustained BF16 = FP16 peak",
                     "peak_source": (f"{peak_kind} sustained BF16 x 1.1/2.25 (TF32)")}
     elif KERNEL_KIND[dom] == "alu":
         peak = FP32_ALU_TFLOPS

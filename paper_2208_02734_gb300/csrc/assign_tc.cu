@@ -14,9 +14,11 @@
 // so undoing them in the epilogue is exact; FP16 runs the tensor pipe at
 // twice the TF32 rate, and the split keeps 22 bits of each operand.
 //
-// One CTA owns 128 rows of X.  Their hi/lo tiles stay in shared memory while
+// One CTA owns 128 rows of X.  Their hi/lo parts sit in tensor memory as
+// the MMAs' A operand (so shared memory feeds only the B operand) while
 // 128-centroid tiles of C stream through a TMA pipeline; the accumulator is
-// double-buffered in TMEM so the epilogue of tile j overlaps the MMAs of j+1.
+// triple-buffered in TMEM so the epilogue of tile j overlaps the MMAs of the
+// next ones.
 // Warp roles: warp 0 = TMA producer (C tiles and their norms), warp 1 = MMA
 // issuer, warp 2 = TMEM allocator, warps 4-11 = epilogue (one thread per row
 // and half of each tile's columns, TMEM lane = row), which keeps the four
@@ -44,12 +46,18 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int TC_M = 128, TC_N = 128;   // MMA tile: 128 rows x 128 centroids
-constexpr int TC_EPI_WARPS = 8;         // two epilogue warps per TMEM lane quadrant
+constexpr int TC_EPI_PARTS = 2;         // epilogue warps per TMEM lane quadrant (column parts)
+constexpr int TC_EPI_WARPS = 4 * TC_EPI_PARTS;
 constexpr int TC_THREADS = (4 + TC_EPI_WARPS) * 32;
-constexpr int TC_EPI_COLS = TC_N / (TC_EPI_WARPS / 4);   // columns per epilogue thread per tile
+constexpr int TC_EPI_COLS = TC_N / TC_EPI_PARTS;   // columns per epilogue thread per tile
+constexpr int TC_EPI_LD = TC_EPI_COLS / 32;        // 32-column TMEM loads per thread per tile
+constexpr int TC_EPI_G = TC_EPI_COLS / 8;          // groups of 8 columns per thread per tile
 constexpr int TC_DK = 64;               // fp16 columns of the split copies (dp <= 64)
 constexpr int TC_BOX_BYTES = TC_M * TC_DK * 2;      // one 128-byte row per item: 16 KB
 constexpr int TC_NRING = 8;             // slots of the centroid-norm ring
+constexpr int TC_NACC = 3;              // accumulator buffers in tensor memory
+constexpr uint32_t TC_ACOL = TC_NACC * TC_N;  // tensor-memory column of the rows' hi/lo parts
+static_assert(TC_ACOL + TC_DK <= 512, "accumulators and rows fit the 512 TMEM columns");
 
 // instruction descriptor: D = F32, A = B = F16, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) |
@@ -144,13 +152,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
-                                        uint32_t accumulate) {
+// D (+)= A.B^T on tcgen05 (kind::f16, FP32 accumulation in tensor memory),
+// with the A operand in tensor memory (row i in lane i, two fp16 values of
+// consecutive K per 32-bit column, lower K in the low half) and B in shared
+// memory (descriptor).
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                           uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(accumulate)
         : "memory");
 }
 
@@ -181,17 +193,37 @@ __device__ __forceinline__ void tmem_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Named barrier 1 over the 256 epilogue threads (warps 4-11) that also ANDs a
+// 32 consecutive fp32 columns of this thread's TMEM lane from registers
+// (complete after tmem_wait_st()).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+        "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Named barrier 1 over the epilogue threads (warps 4 and up) that also ANDs a
 // flag across them, so every epilogue warp takes the same exit decision.
 __device__ __forceinline__ bool epi_bar_and(bool v) {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 256, p;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(out)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(TC_EPI_WARPS * 32)
         : "memory");
     return out != 0;
 }
@@ -234,10 +266,13 @@ struct Top4 {
 // ------------------------------------------------------------- main kernel
 
 // ksteps = K-steps of 16 fp16 columns (ceil(dp / 16)); xinv[i] = 1 / s_i,
-// cinv[0] = 1 / s_c (the scales of the split copies).
+// cinv[0] = 1 / s_c (the scales of the split copies).  When `seeded`, labels
+// holds each row's previous label on entry (Xf, Cf: the padded FP32 rows and
+// centroids, dp4 float4s each).
 template <int S>
 __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
-    const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl,
+    const uint4 *__restrict__ Xh, const uint4 *__restrict__ Xl, const float4 *__restrict__ Xf,
+    const float4 *__restrict__ Cf, int dp4, int seeded,
     const __grid_constant__ CUtensorMap tmCh, const __grid_constant__ CUtensorMap tmCl,
     const float *__restrict__ xn, const float *__restrict__ xinv, const float *__restrict__ cinv,
     int64_t n, int ksteps, const float *__restrict__ cn_pad, int k,
@@ -249,25 +284,26 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;        // swizzled tiles need 1 KB alignment
     unsigned char *basep = smem_raw + (base - raw);
-    const uint32_t A_hi = base, A_lo = base + TC_BOX_BYTES;
-    const uint32_t B0 = base + 2u * TC_BOX_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(basep + 2u * TC_BOX_BYTES + S * kStage);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5 + 2 * TC_NRING);
+    const uint32_t B0 = base;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(basep + S * kStage);
+    uint32_t *tmem_slot =
+        reinterpret_cast<uint32_t *>(bars + 2 * S + 1 + 2 * TC_NACC + 2 * TC_NRING);
     __shared__ int s_err;
     __shared__ __align__(16) float s_cn[TC_NRING][TC_N];   // norms of the C tiles in flight
-    __shared__ float s_top[TC_M][4];      // second-half top-4 lists, merged at the end
-    __shared__ int s_topi[TC_M][3];
+    __shared__ float s_top[TC_EPI_PARTS - 1][TC_M][4];   // parts 1.. top-4 lists, merged at the end
+    __shared__ int s_topi[TC_EPI_PARTS - 1][TC_M][3];
+    __shared__ float s_thr[TC_EPI_PARTS][TC_M];          // each part's current fourth value
 
-    // barriers: a_full | b_full[S] | b_empty[S] | acc_full[2] | acc_empty[2] |
-    //           n_full[TC_NRING] | n_empty[TC_NRING]
+    // barriers: a_full | b_full[S] | b_empty[S] | acc_full[TC_NACC] |
+    //           acc_empty[TC_NACC] | n_full[TC_NRING] | n_empty[TC_NRING]
     const uint32_t bar0 = smem_u32(bars);
     const uint32_t a_full = bar0;
     auto b_full = [&](int s) { return bar0 + 8u * (1 + s); };
     auto b_empty = [&](int s) { return bar0 + 8u * (1 + S + s); };
     auto acc_full = [&](int a) { return bar0 + 8u * (1 + 2 * S + a); };
-    auto acc_empty = [&](int a) { return bar0 + 8u * (3 + 2 * S + a); };
-    auto n_full = [&](int q) { return bar0 + 8u * (5 + 2 * S + q); };
-    auto n_empty = [&](int q) { return bar0 + 8u * (5 + 2 * S + TC_NRING + q); };
+    auto acc_empty = [&](int a) { return bar0 + 8u * (1 + TC_NACC + 2 * S + a); };
+    auto n_full = [&](int q) { return bar0 + 8u * (1 + 2 * TC_NACC + 2 * S + q); };
+    auto n_empty = [&](int q) { return bar0 + 8u * (1 + 2 * TC_NACC + 2 * S + TC_NRING + q); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TC_M;
@@ -275,14 +311,16 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
 
     // a CTA that starts after the grid aborted does nothing
     if (*(volatile int *)err != 0) return;
+    for (int i = threadIdx.x; i < TC_EPI_PARTS * TC_M; i += TC_THREADS)
+        (&s_thr[0][0])[i] = FLT_MAX;
     if (threadIdx.x == 0) {
         s_err = 0;
-        mbar_init(a_full, 1);
+        mbar_init(a_full, 4);   // the four warps that write the rows into tensor memory
         for (int s = 0; s < S; ++s) {
             mbar_init(b_full(s), 1);
             mbar_init(b_empty(s), 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < TC_NACC; ++a) {
             mbar_init(acc_full(a), 1);
             mbar_init(acc_empty(a), TC_EPI_WARPS);
         }
@@ -293,7 +331,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 2) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                          smem_u32(tmem_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -305,9 +343,6 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        mbar_expect_tx(a_full, 2u * TC_BOX_BYTES);
-        tma_load_2d(A_hi, &tmXh, 0, (int)row0, a_full);
-        tma_load_2d(A_lo, &tmXl, 0, (int)row0, a_full);
         int armed = 0, armedN = 0;
         bool ok = true;
         for (int j = 0; j < ntiles; ++j) {
@@ -326,7 +361,6 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             armedN = j + 1;
         }
         // every load this thread issued must land before the CTA may exit
-        mbar_wait(a_full, 0, err, true);
         for (int j = (armed > S ? armed - S : 0); j < armed; ++j)
             mbar_wait(b_full(j % S), (j / S) & 1, err, true);
         for (int j = (armedN > TC_NRING ? armedN - TC_NRING : 0); j < armedN; ++j)
@@ -334,12 +368,14 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         if (!ok) s_err = 1;
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
+        // the CTA's rows are in tensor memory (columns TC_ACOL..): hi parts
+        // first, then lo parts, 8 columns (16 fp16 values) per K-step
         bool ok = mbar_wait(a_full, 0, err);
-        // descriptors advance by (byte offset >> 4) in their address field
-        const uint64_t dAh = sw128_desc(A_hi), dAl = sw128_desc(A_lo);
+        tc_fence_after();
+        const uint32_t tAh = tmem + TC_ACOL, tAl = tmem + TC_ACOL + TC_DK / 2;
         int last = -1;
         for (int j = 0; ok && j < ntiles; ++j) {
-            const int s = j % S, u = j / S, a = j & 1, v = j >> 1;
+            const int s = j % S, u = j / S, a = j % TC_NACC, v = j / TC_NACC;
             ok = mbar_wait(b_full(s), u & 1, err);
             if (ok && v > 0) ok = mbar_wait(acc_empty(a), (v - 1) & 1, err);
             if (!ok) break;
@@ -353,9 +389,10 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             for (int kk = 0; kk < TC_DK / 16; ++kk) {
                 if (kk < ksteps) {
                     const uint64_t off = (uint64_t)(kk * 2);
-                    mma_f16(d, dAh + off, dBh + off, kk > 0 ? 1u : 0u);
-                    mma_f16(d, dAh + off, dBl + off, 1u);
-                    mma_f16(d, dAl + off, dBh + off, 1u);
+                    const uint32_t ta = (uint32_t)(kk * 8);
+                    mma_f16_ta(d, tAh + ta, dBh + off, kk > 0 ? 1u : 0u);
+                    mma_f16_ta(d, tAh + ta, dBl + off, 1u);
+                    mma_f16_ta(d, tAl + ta, dBh + off, 1u);
                 }
             }
             mma_commit(b_empty(s));    // the C tile's stage is free once these MMAs finish
@@ -363,50 +400,92 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             last = j;
         }
         // the MMAs must be complete before tensor memory is released
-        if (last >= 0) mbar_wait(acc_full(last & 1), (last >> 1) & 1, err, true);
+        if (last >= 0) mbar_wait(acc_full(last % TC_NACC), (last / TC_NACC) & 1, err, true);
         if (!ok) s_err = 1;
     } else if (warp >= 4) {
-        // ---------------- epilogue: one row per thread, half the columns ----------------
+        // ------------ epilogue: one row per thread, half of each tile's columns ------------
         // Rows are ranked by key = ||c||^2 - 2 x.c (the row's ||x||^2 is
         // added back at the end); the norms of each C tile arrive in a ring
         // of shared-memory slots filled by the producer.  The accumulator
         // holds (x.c) s_i s_c: the factor -2 / (s_i s_c) is a power of two,
         // so the scaling costs no rounding.
         const int quad = warp & 3;                  // TMEM lane quadrant of this warp
-        const int half = (warp - 4) >> 2;           // column half of each tile
+        const int part = (warp - 4) >> 2;           // column part of each tile
+        const int col = part * TC_EPI_COLS;
         const int r = quad * 32 + lane;
         const int64_t row = row0 + r;
         const float xr = row < n ? xn[row] : 0.f;
         const float mul = row < n ? -2.f * xinv[row] * cinv[0] : 0.f;
+        if (part == 0) {
+            // the row's hi and lo parts into its tensor-memory lane (rows
+            // past n are zero)
+            const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + TC_ACOL;
+            uint32_t hv[32];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint4 *src = (h == 0 ? Xh : Xl) + row * (TC_DK / 8);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint4 w = row < n ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+                    hv[4 * c] = w.x; hv[4 * c + 1] = w.y; hv[4 * c + 2] = w.z; hv[4 * c + 3] = w.w;
+                }
+                tmem_st32(lane_addr + (uint32_t)(h * (TC_DK / 2)), hv);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(a_full);
+        }
+        // Seed of the row's threshold from its previous label j': only keys
+        // below key(j') + 2 * margin can decide the label, its gap test or
+        // its re-decision list (a key above it is more than a margin behind
+        // the best, which is at most key(j')).  key(j') is taken in the exact
+        // difference form; its FP32 error and that of the tensor-core key are
+        // each within a quarter and three quarters of one margin.
+        float T0 = FLT_MAX;
+        if (seeded && row < n) {
+            const int jp = labels[row];
+            if (jp >= 0 && jp < k) {
+                const float4 *xa = Xf + row * dp4, *ca = Cf + (int64_t)jp * dp4;
+                float acc = 0.f;
+                for (int c = 0; c < dp4; ++c) {
+                    const float4 e = xa[c], f = ca[c];
+                    const float e0 = e.x - f.x, e1 = e.y - f.y, e2 = e.z - f.z, e3 = e.w - f.w;
+                    acc = fmaf(e0, e0, acc);
+                    acc = fmaf(e1, e1, acc);
+                    acc = fmaf(e2, e2, acc);
+                    acc = fmaf(e3, e3, acc);
+                }
+                T0 = (acc - xr) + 2.f * margin_coef * (xr + *cn_max);
+            }
+        }
         Top4 t4;
         t4.init();
         bool ok = true;
         for (int j = 0; j < ntiles; ++j) {
-            const int a = j & 1, v = j >> 1;
+            const int a = j % TC_NACC, v = j / TC_NACC;
             const int q = j % TC_NRING, w = j / TC_NRING;
-            const int c0 = j * TC_N;
             ok = mbar_wait(acc_full(a), v & 1, err) && mbar_wait(n_full(q), w & 1, err);
             if (!__all_sync(kFull, ok)) { ok = false; break; }  // the warp leaves as one
             tc_fence_after();
-            const int col = half * TC_EPI_COLS;
             const uint32_t taddr =
                 tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * TC_N + col);
-            uint32_t u0[32], u1[32];
-            tmem_ld32(taddr, u0);
-            tmem_ld32(taddr + 32, u1);
+            uint32_t u[TC_EPI_LD][32];
+#pragma unroll
+            for (int h = 0; h < TC_EPI_LD; ++h) tmem_ld32(taddr + 32 * h, u[h]);
             tmem_wait();
             // the accumulator is in registers: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty(a));
-            // keys of this thread's 64 columns, with the minimum of each
-            // group of 8; columns past k have norm +inf, so their keys never
-            // enter the list
+            // keys of this thread's columns, with the minimum of each group
+            // of 8; columns past k have norm +inf, so their keys never enter
+            // the list
             const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[q][col]);
-            float key[64], gm[8];
+            float key[TC_EPI_COLS], gm[TC_EPI_G];
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const uint32_t *uu = g < 4 ? u0 : u1;
+            for (int g = 0; g < TC_EPI_G; ++g) {
+                const uint32_t *uu = u[g >> 2];
                 const int b = (g & 3) * 8;
                 const float4 c0v = cn4[2 * g], c1v = cn4[2 * g + 1];
                 float *kk = key + 8 * g;
@@ -424,53 +503,69 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             // the norms are in registers: hand the ring slot back
             __syncwarp();
             if (lane == 0) mbar_arrive(n_empty(q));
-            const float mn = fminf(fminf(fminf(gm[0], gm[1]), fminf(gm[2], gm[3])),
-                                   fminf(fminf(gm[4], gm[5]), fminf(gm[6], gm[7])));
+            float mn = gm[0];
+#pragma unroll
+            for (int g = 1; g < TC_EPI_G; ++g) mn = fminf(mn, gm[g]);
+            // A key enters only below the row's threshold: the smallest of
+            // the parts' fourth values (each is at least the fourth smallest
+            // key over all columns seen, so no key of the final four is lost).
+            float T = fminf(T0, t4.v3);
+#pragma unroll
+            for (int pp = 0; pp < TC_EPI_PARTS; ++pp)
+                if (pp != part) T = fminf(T, s_thr[pp][r]);
             // insertions in column order (ties keep the earliest column),
             // under warp-uniform branches only.  A group is visited when some
-            // lane has a key in it below that lane's current fourth; when no
-            // lane has more than one such key, each lane inserts just its
-            // group minimum (a no-op where it is not below the fourth),
-            // otherwise all eight keys go through the branch-free insertion.
-            if (__any_sync(kFull, mn < t4.v3)) {
-                const int cb = c0 + col;
+            // lane has a key in it below that lane's threshold; when no lane
+            // has more than one such key, each lane inserts just its group
+            // minimum (a no-op where it is not below the fourth), otherwise
+            // all eight keys go through the branch-free insertion.
+            if (__any_sync(kFull, mn < T)) {
+                const int cb = j * TC_N + col;
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    if (__any_sync(kFull, gm[g] < t4.v3)) {
+                for (int g = 0; g < TC_EPI_G; ++g) {
+                    if (__any_sync(kFull, gm[g] < T)) {
                         int cnt = 0, first = 7;
 #pragma unroll
                         for (int e = 7; e >= 0; --e) {
-                            cnt += key[8 * g + e] < t4.v3 ? 1 : 0;
+                            cnt += key[8 * g + e] < T ? 1 : 0;
                             first = key[8 * g + e] == gm[g] ? e : first;
                         }
                         if (__any_sync(kFull, cnt > 1)) {
 #pragma unroll
                             for (int e = 0; e < 8; ++e)
-                                t4.push_nb(key[8 * g + e], cb + 8 * g + e);
-                        } else {
+                                if (key[8 * g + e] < T) t4.push_nb(key[8 * g + e], cb + 8 * g + e);
+                        } else if (gm[g] < T) {
                             t4.push_nb(gm[g], cb + 8 * g + first);
                         }
                     }
                 }
+                s_thr[part][r] = t4.v3;
             }
         }
-        // merge the two half-row lists: the second half hands its list over
-        if (half == 1) {
-            s_top[r][0] = t4.v0; s_top[r][1] = t4.v1; s_top[r][2] = t4.v2; s_top[r][3] = t4.v3;
-            s_topi[r][0] = t4.i0; s_topi[r][1] = t4.i1; s_topi[r][2] = t4.i2;
+        // merge the row's part lists: parts 1.. hand their lists to part 0.
+        // A part's fourth value enters after its first three, so it can only
+        // land in the fourth place (whose index is never used).
+        if (part > 0) {
+            float *t = s_top[part - 1][r];
+            int *ti = s_topi[part - 1][r];
+            t[0] = t4.v0; t[1] = t4.v1; t[2] = t4.v2; t[3] = t4.v3;
+            ti[0] = t4.i0; ti[1] = t4.i1; ti[2] = t4.i2;
         }
         ok = epi_bar_and(ok);
-        if (half == 1) {
+        if (part > 0) {
             // nothing more to do
         } else if (!ok) {
             s_err = 1;
         } else {
-            t4.push(s_top[r][0], s_topi[r][0]);
-            t4.push(s_top[r][1], s_topi[r][1]);
-            t4.push(s_top[r][2], s_topi[r][2]);
-            t4.push(s_top[r][3], -1);
+#pragma unroll
+            for (int pp = 0; pp < TC_EPI_PARTS - 1; ++pp) {
+                t4.push(s_top[pp][r][0], s_topi[pp][r][0]);
+                t4.push(s_top[pp][r][1], s_topi[pp][r][1]);
+                t4.push(s_top[pp][r][2], s_topi[pp][r][2]);
+                t4.push(s_top[pp][r][3], -1);
+            }
         }
-        if (half == 0 && ok && row < n) {
+        if (part == 0 && ok && row < n) {
             labels[row] = t4.i0;
             // gaps are the same in key and distance units
             const float margin = margin_coef * (xr + *cn_max);
@@ -488,7 +583,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     __syncthreads();
     if (warp == 2) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
     if (threadIdx.x == 0 && s_err) atomicExch(err, 1);
 }
@@ -650,11 +745,11 @@ int grid_cap(int64_t work) {
 
 template <int S>
 size_t tc_smem_bytes() {
-    return 1024 + 2u * TC_BOX_BYTES + (size_t)S * 2u * TC_BOX_BYTES +
-           (2 * S + 5 + 2 * TC_NRING) * 8 + 16;
+    return 1024 + (size_t)S * 2u * TC_BOX_BYTES + (2 * S + 1 + 2 * TC_NACC + 2 * TC_NRING) * 8 +
+           16;
 }
 
-constexpr int TC_STAGES = 4;   // C tiles in flight (32 KB each)
+constexpr int TC_STAGES = 5;   // C tiles in flight (32 KB each)
 
 }  // namespace
 
@@ -666,7 +761,6 @@ struct TcAssign {
     const float *X = nullptr;      // padded points [n x dp]
     Scratch<__half> Xh, Xl;        // [n x 64] scaled FP16 hi / lo parts
     Scratch<float> xinv;           // [n] 1 / s_i (powers of two)
-    CUtensorMap mXh, mXl;
     Scratch<int> err;              // set by a kernel whose bounded wait ran out
 };
 
@@ -688,28 +782,31 @@ std::shared_ptr<TcAssign> tc_assign_prepare(const float *X, int64_t n, int dp, c
     split_f16_kernel<<<grid_cap(n * 8), 256, 0, s>>>(X, n, dp, nullptr, p->Xh.get(), p->Xl.get(),
                                                      p->xinv.get());
     MASK_LAUNCHED("split_f16");
-    p->mXh = make_map(p->Xh.get(), n);
-    p->mXl = make_map(p->Xl.get(), n);
     p->err.alloc(1, s);
     MASK_CUDA(cudaMemsetAsync(p->err.get(), 0, sizeof(int), s));
     return p;
 }
 
 template <int S>
-void launch_tc(const TcAssign &p, const CUtensorMap &mCh, const CUtensorMap &mCl, const float *xn,
-               const float *cinv, const float *cn, int k, const float *cmax, float coef,
-               int32_t *labels, int4 *list3, int *n3, int32_t *listF, int *nF, cudaStream_t s) {
+void launch_tc(const TcAssign &p, const CUtensorMap &mCh, const CUtensorMap &mCl, const float *C,
+               bool seeded, const float *xn, const float *cinv, const float *cn, int k,
+               const float *cmax, float coef, int32_t *labels, int4 *list3, int *n3,
+               int32_t *listF, int *nF, cudaStream_t s) {
     const size_t smem = tc_smem_bytes<S>();
     auto kfn = assign_tc_kernel<S>;
     MASK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned blocks = (unsigned)((p.n + TC_M - 1) / TC_M);
-    kfn<<<blocks, TC_THREADS, smem, s>>>(p.mXh, p.mXl, mCh, mCl, xn, p.xinv.get(), cinv, p.n,
+    kfn<<<blocks, TC_THREADS, smem, s>>>(reinterpret_cast<const uint4 *>(p.Xh.get()),
+                                        reinterpret_cast<const uint4 *>(p.Xl.get()),
+                                        reinterpret_cast<const float4 *>(p.X),
+                                        reinterpret_cast<const float4 *>(C), p.dp / 4,
+                                        seeded ? 1 : 0, mCh, mCl, xn, p.xinv.get(), cinv, p.n,
                                         (p.dp + 15) / 16, cn, k, cmax, coef, labels, list3, n3,
                                         listF, nF, p.err.get());
 }
 
 void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *labels,
-               cudaStream_t s) {
+               bool seeded, cudaStream_t s) {
     const int dp = p.dp;
     const int ntiles = (k + TC_N - 1) / TC_N;
     // centroid norms padded to whole 128-centroid tiles (+inf past k)
@@ -752,7 +849,8 @@ void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *lab
     const float coef = (float)(2.0 * 2.0 * per);
     {
         ProfRegion pr("assign_tc", s, 2.0 * (double)p.n * (double)k * (double)dp);
-        launch_tc<TC_STAGES>(p, mCh, mCl, xn, cinv.get(), cn.get(), k, cmax.get(), coef, labels,
+        launch_tc<TC_STAGES>(p, mCh, mCl, C, seeded, xn, cinv.get(), cn.get(), k, cmax.get(), coef,
+                             labels,
                              list3.get(), counts.get(), listF.get(), counts.get() + 1, s);
         MASK_LAUNCHED("assign_tc");
     }

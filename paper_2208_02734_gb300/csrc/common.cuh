@@ -264,13 +264,15 @@ void assign_labels(const float *X, const float *xn, int64_t n, int dp, const flo
 void assign_recheck_rows(const float *X, int dp, const float *C, int k, const int32_t *rows,
                          const int *count, int32_t *labels, cudaStream_t s);
 
-// assign_tc.cu -- the same assignment on tcgen05 (3xTF32), for dp <= 64
+// assign_tc.cu -- the same assignment on tcgen05 (FP16 three-product split), for dp <= 64
 struct TcAssign;
 bool tc_assign_enabled(int dp);
-// Splits X (padded, [n x dp]) into TF32 hi/lo parts once; null if unsupported.
+// Splits X (padded, [n x dp]) into scaled FP16 hi/lo parts once; null if unsupported.
 std::shared_ptr<TcAssign> tc_assign_prepare(const float *X, int64_t n, int dp, cudaStream_t s);
+// seeded: labels holds the previous assignment's labels on entry (the
+// kernel starts each row's search threshold from its previous centroid).
 void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *labels,
-               cudaStream_t s);
+               bool seeded, cudaStream_t s);
 // Raises MASK_ETIMEOUT if a kernel of this plan hit a wait limit (synchronises).
 void tc_assign_check(TcAssign &p, cudaStream_t s);
 

@@ -249,11 +249,15 @@ void lloyd(const float *X, int64_t n_in, int dp, int k, int iters, float *C, int
     Scratch<float> xn(n_in, s), Cn((size_t)k * dp, s), sse(k, s);
     Scratch<double> J(iters + 1, s);
     row_sqnorm(X, n_in, dp, xn.get(), s);
-    // tensor-core assignment when the row fits (X split into TF32 hi/lo once)
+    // tensor-core assignment when the row fits (X split into FP16 hi/lo
+    // parts once); from the second assignment on, each row's search starts
+    // from its previous label
     auto tc = tc_assign_prepare(X, n_in, dp, s);
+    bool have_labels = false;
     auto assign = [&](const float *Cc) {
-        if (tc) tc_assign(*tc, xn.get(), Cc, k, labels, s);
+        if (tc) tc_assign(*tc, xn.get(), Cc, k, labels, have_labels, s);
         else assign_labels(X, xn.get(), n_in, dp, Cc, k, labels, s);
+        have_labels = true;
     };
     float *cur = C, *nxt = Cn.get();
     for (int it = 0; it < iters; ++it) {
@@ -839,7 +843,7 @@ mask_status mask_kmeans_assign(const float *X, int64_t n, int32_t d, const float
         row_sqnorm(Xp.get(), n, dp, xn.get(), s);
         Out<int32_t> lb(labels_out, (size_t)n, s);
         if (auto tc = tc_assign_prepare(Xp.get(), n, dp, s)) {
-            tc_assign(*tc, xn.get(), Cp.get(), k, lb.p, s);
+            tc_assign(*tc, xn.get(), Cp.get(), k, lb.p, false, s);
             tc_assign_check(*tc, s);
         } else {
             assign_labels(Xp.get(), xn.get(), n, dp, Cp.get(), k, lb.p, s);

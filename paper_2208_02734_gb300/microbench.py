@@ -124,6 +124,9 @@ def main(argv=None) -> None:
         kms = out.get("assign_tc_ms") or out.get("assign_gemm_ms")
         if kms:
             out["kernel_tflops"] = 2.0 * a.n * a.k * a.d / (kms / 1e3) / 1e12
+    if a.profile and "assign_tc_ms" in out:
+        r = M.mask_profile_read("assign_tc")
+        out["assign_tc_useful_tflops"] = r[2] / max(1, r[0]) / (out["assign_tc_ms"] / 1e3) / 1e12
     if a.step == "csr_assign" and "csr_spmm_assign_ms" in out:
         r = M.mask_profile_read("csr_spmm_assign")
         out["spmm_tflops"] = r[2] / max(1, r[0]) / (out["csr_spmm_assign_ms"] / 1e3) / 1e12

@@ -29,7 +29,8 @@ def test_tensor_roofline_reports_useful_flop_and_the_issued_passes_apart(bench):
     assert r["achieved"] == pytest.approx(useful)
     assert r["frac"] == pytest.approx(useful / peak)
     assert r["achieved_issued"] == pytest.approx(bench.TC_PASSES * useful)
-    assert r["frac_issued"] == pytest.approx(bench.TC_PASSES * useful / peak)
+    assert r["frac_issued"] == pytest.approx(bench.TC_PASSES * useful /
+                                             peaks["bf16_tflops_sustained"])
     assert r["work_per_launch"] == pytest.approx(6.0e14 / 48)
     assert r["ms_share_of_step"] == pytest.approx(2000.0 / 3000.0)
     # the traffic row is used only while the kernel's source is unchanged
