@@ -170,13 +170,15 @@ void max_reduce(const float *v, int64_t n, float *out, cudaStream_t s);
 template <class I>
 void gather_rows(const float *src, int dp, const I *idx, int64_t m, float *dst, cudaStream_t s);
 void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
-// k-means++ over the m rows of Xs; chosen[0] must be set; fills chosen[1..k)
-void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_dev,
+// k-means++ over the m rows of Xs; chosen[0] must be set; fills chosen[1..k).
+// a53[t] (device) is the t-th draw as the generator's 53-bit integer
+// (u_t = a53[t] * 2^-53).
+void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const unsigned long long *a53,
                     int64_t *chosen, cudaStream_t s);
 // the same over CSR rows (dense row of dp <= kCsrMaxDim in shared memory)
 void kmeanspp_steps_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t m,
-                        int64_t nnz, int dp, int k, const double *u_dev, int64_t *chosen,
-                        cudaStream_t s);
+                        int64_t nnz, int dp, int k, const unsigned long long *a53,
+                        int64_t *chosen, cudaStream_t s);
 // counting sort of labels in [0,k): off[k+1] (int64), perm[n] (item ids by label)
 void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *perm,
                 cudaStream_t s);
@@ -187,7 +189,6 @@ void centroid_update(const float *X, int dp, const int32_t *perm, const int64_t 
 // dist[i] = ||x_i - c_{labels[i]}||^2, difference form
 void label_dist(const float *X, int64_t n, int dp, const float *C, const int32_t *labels,
                 float *dist, cudaStream_t s);
-void sum_reduce_f32_to_f64(const float *v, int64_t n, double *out, cudaStream_t s);
 void off_to_counts(const int64_t *off, int k, int64_t *counts, cudaStream_t s);
 void count_bad_labels(const int32_t *labels, int64_t n, int k, int *bad, cudaStream_t s);
 

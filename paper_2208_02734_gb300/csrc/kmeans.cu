@@ -12,60 +12,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// ------------------------------------------------------- block reductions
-
-template <int T>
-__device__ double block_sum_f64(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < T / 32; ++i) t += red[i];
-    return t;
-}
-
-template <int T>
-__device__ long long block_min_ll(long long v, long long *red) {
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    long long t = LLONG_MAX;
-    for (int i = 0; i < T / 32; ++i) t = min(t, red[i]);
-    return t;
-}
-
-template <int T>
-__device__ long long block_max_ll(long long v, long long *red) {
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    long long t = LLONG_MIN;
-    for (int i = 0; i < T / 32; ++i) t = max(t, red[i]);
-    return t;
-}
-
-// Inclusive scan of one double per thread (block of T threads, fixed tree).
-template <int T>
-__device__ double block_incl_scan_f64(double v, double *wsum) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        double t = __shfl_up_sync(kFull, v, o);
-        if (lane >= o) v += t;
-    }
-    __syncthreads();
-    if (lane == 31) wsum[w] = v;
-    __syncthreads();
-    double base = 0.0;
-    for (int i = 0; i < w; ++i) base += wsum[i];
-    return v + base;
-}
-
 // ------------------------------------------------------ elementwise kernels
 
 __global__ void pad_rows_kernel(const float *__restrict__ src, int64_t n, int d,
@@ -173,14 +119,6 @@ __global__ void max_reduce_kernel(const float *__restrict__ v, int64_t n, float 
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(out), __float_as_uint(m));
 }
 
-__global__ void sum_f32_to_f64_kernel(const float *__restrict__ v, int64_t n, double *out) {
-    __shared__ double red[8];
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) s += (double)v[i];
-    s = block_sum_f64<256>(s, red);
-    if (threadIdx.x == 0) *out = s;
-}
-
 // --------------------------------------------------------------- k-means++
 
 constexpr int kKppThreads = 512;
@@ -190,11 +128,20 @@ constexpr int kKppRpt = kKppRows / kKppThreads;  // rows per thread
 // One k-means++ step (§3.2).  The step number t >= 1 is read from *t_dev.
 // Fold the centre picked at step t-1 into D^2, then the last block to finish
 // draws centre t: the smallest row whose inclusive prefix of D^2 exceeds
-// u_t * sum(D^2) (all sums FP64); if that sum is 0, the lowest-index row not
-// chosen yet.  The last block then advances *t_dev, so identical launches can
-// be replayed step after step.  Three kernels fold D^2 (dense rows one per
-// thread with triangle-inequality pruning, wide dense rows one per warp, CSR
-// rows one per lane group); they share the draw.
+// u_t * sum(D^2); if that sum is 0, the lowest-index row not chosen yet.
+// The last block then advances *t_dev, so identical launches can be replayed
+// step after step.  Three kernels fold D^2 (dense rows one per thread with
+// triangle-inequality pruning, wide dense rows one per warp, CSR rows one per
+// lane group); they share the draw.
+//
+// The sums are exact integers: every D^2 (FP32) becomes the 64-bit integer
+// q_i = round(D^2_i * 2^sh), with one power of two 2^sh per seeding run that
+// keeps sum_i q_i below 2^62 (from the first step's total, which bounds every
+// later one: D^2 only decreases).  Integer sums do not depend on their
+// order, and u_t = a_t * 2^-53 (a_t the generator's 53-bit integer), so the
+// pick rule "prefix_i > u_t * S" is decided exactly as the 128-bit
+// comparison prefix_i * 2^53 > a_t * S.  q_i resolves 2^-61 of the first
+// total, far below the FP32 rounding of D^2 itself.
 //
 // cc2[j] = ||c_{t-1} - c_j||^2 for the centres j < t-1 chosen so far (FP32
 // difference form): the distances the narrow dense D^2 update prunes with.
@@ -225,30 +172,59 @@ __global__ void kpp_centre_dist_kernel(const float *__restrict__ X, int64_t m, i
     cc2[j] = acc;
 }
 
+// 64 x 64 -> 128-bit unsigned products and comparisons for the draw.
+struct U128 {
+    unsigned long long hi, lo;
+};
+__device__ __forceinline__ U128 mul_u128(unsigned long long a, unsigned long long b) {
+    return U128{__umul64hi(a, b), a * b};
+}
+// v * 2^53 for v < 2^64
+__device__ __forceinline__ U128 shl53(unsigned long long v) { return U128{v >> 11, v << 53}; }
+__device__ __forceinline__ bool gt_u128(U128 x, U128 y) {
+    return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo);
+}
+
+// q = round(d2 * qs), qs = 2^sh (exact scaling, then one rounding).
+__device__ __forceinline__ unsigned long long kpp_q(float d2, float qs) {
+    return __float2ull_rn(d2 * qs);
+}
+
+// 2^sh with sum(D^2) * 2^sh < 2^61, from a bound s1 >= sum(D^2) (FP32 bits
+// of s1 in *s1_bits; 0 gives 1).
+__device__ __forceinline__ float kpp_scale(const unsigned *s1_bits) {
+    const unsigned b = *s1_bits;
+    if (b == 0u) return 1.f;
+    const int e = (int)((b >> 23) & 0xffu) - 127;   // 2^e <= s1 < 2^(e+1)
+    int sh = 60 - e;
+    sh = sh < -126 ? -126 : (sh > 126 ? 126 : sh);
+    return __uint_as_float((uint32_t)(sh + 127) << 23);
+}
+
 // Shared memory of the draw (all kKppThreads threads of the last block).
-template <int ROWS>
 struct KppDrawSmem {
-    double wsum[kKppThreads / 32];   // per-warp totals of a block scan
-    double excl, target;
+    unsigned long long wsum[kKppThreads / 32];   // per-warp totals of a block scan
+    unsigned long long excl;
     long long fb, pick;
     int first;
 };
 
-// Inclusive prefix sum of v over the kKppThreads threads of the block (FP64,
-// a warp scan then a scan of the warp totals); *total = the block's sum.
-__device__ double kpp_block_scan(double v, double *wsum, double *total) {
+// Inclusive prefix sum of v over the kKppThreads threads of the block (a
+// warp scan then a scan of the warp totals); *total = the block's sum.
+__device__ unsigned long long kpp_block_scan(unsigned long long v, unsigned long long *wsum,
+                                             unsigned long long *total) {
     constexpr int W = kKppThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
-        const double n = __shfl_up_sync(kFull, v, o);
+        const unsigned long long n = __shfl_up_sync(kFull, v, o);
         if (lane >= o) v += n;
     }
     if (lane == 31) wsum[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        double w = lane < W ? wsum[lane] : 0.0;
+        unsigned long long w = lane < W ? wsum[lane] : 0ull;
         for (int o = 1; o < W; o <<= 1) {
-            const double n = __shfl_up_sync(kFull, w, o);
+            const unsigned long long n = __shfl_up_sync(kFull, w, o);
             if (lane >= o) w += n;
         }
         if (lane < W) wsum[lane] = w;
@@ -272,12 +248,20 @@ __device__ int kpp_block_first(bool flag, int *slot) {
     return r;
 }
 
-// Block total of the D^2 fold -> bsum[blockIdx.x]; true in the last block to
-// finish (which then draws).
-__device__ bool kpp_block_done(double local, double *red, double *__restrict__ bsum,
+// Block total of the quantised D^2 -> bsum[blockIdx.x]; true in the last
+// block to finish (which then draws).
+__device__ bool kpp_block_done(unsigned long long local, unsigned long long *red,
+                               unsigned long long *__restrict__ bsum,
                                unsigned *__restrict__ counter, int *s_last) {
-    const double bs = block_sum_f64<kKppThreads>(local, red);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = bs;
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long bs = 0;
+        for (int i = 0; i < kKppThreads / 32; ++i) bs += red[i];
+        bsum[blockIdx.x] = bs;
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) *s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
@@ -287,105 +271,94 @@ __device__ bool kpp_block_done(double local, double *red, double *__restrict__ b
     return last;
 }
 
+// The measuring launch (before the first step): each block adds its FP32 sum
+// of the first step's D^2 to *s1 (bits of a float, atomically as a float
+// add); twice that bounds every step's sum.
+__device__ void kpp_measure(float local, float *red, unsigned *__restrict__ s1_bits) {
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bs = 0.f;
+        for (int i = 0; i < kKppThreads / 32; ++i) bs += red[i];
+        atomicAdd(reinterpret_cast<float *>(s1_bits), 2.f * bs);
+    }
+}
+
 // The draw of centre t by all threads of the last block (blocks of ROWS
-// rows): the smallest row whose inclusive prefix of D^2 exceeds u_t * S.
-// Thread i owns a contiguous run of block sums, then of the selected block's
-// rows; block scans give each run's prefix, the first run that crosses the
-// target is walked by its owner.
+// rows): the smallest row i with (sum_{j<=i} q_j) * 2^53 > a_t * Q, Q the
+// total.  Thread i owns a contiguous run of block sums, then of the selected
+// block's rows; block scans give each run's prefix, and the first run that
+// crosses the target is walked by its owner.  The crossing always exists
+// when Q > 0 (the full prefix Q times 2^53 exceeds a_t * Q as a_t < 2^53).
 template <int ROWS>
-__device__ void kpp_draw(int t, int64_t m, const double *__restrict__ u,
-                         const float *__restrict__ D2, const double *__restrict__ bsum,
+__device__ void kpp_draw(int t, int64_t m, const unsigned long long *__restrict__ a53,
+                         const float *__restrict__ D2, float qs,
+                         const unsigned long long *__restrict__ bsum,
                          unsigned *__restrict__ counter, int *__restrict__ t_dev,
                          int64_t *__restrict__ chosen, unsigned char *__restrict__ taken,
-                         KppDrawSmem<ROWS> &sm) {
+                         KppDrawSmem &sm) {
     constexpr int RPT = ROWS >= kKppThreads ? ROWS / kKppThreads : 1;  // rows per thread
     static_assert(ROWS % kKppThreads == 0 || ROWS < kKppThreads, "rows per block");
     const int tid = threadIdx.x;
     const int nb = gridDim.x;
     if (t == 1 && tid == 0) taken[chosen[0]] = 1;
     if (tid == 0) sm.pick = -1;
-    const double ut = u[t];
+    const unsigned long long at = a53[t];
     // block sums: thread tid owns [tid * per, (tid + 1) * per)
     const int per = (nb + kKppThreads - 1) / kKppThreads;
     const int b0 = tid * per;
-    double ls = 0.0;
+    unsigned long long ls = 0;
     for (int q = 0; q < per; ++q)
         if (b0 + q < nb) ls += __ldcg(bsum + b0 + q);
-    double S;
-    const double inc = kpp_block_scan(ls, sm.wsum, &S);
-    if (S > 0.0) {
-        const double target = ut * S;
-        const int src = kpp_block_first(inc > target && ls > 0.0, &sm.first);
+    unsigned long long Q;
+    const unsigned long long inc = kpp_block_scan(ls, sm.wsum, &Q);
+    if (Q > 0) {
+        const U128 target = mul_u128(at, Q);
+        const int src = kpp_block_first(ls > 0 && gt_u128(shl53(inc), target), &sm.first);
         if (tid == src) {
-            // walk the run; rounding may leave no crossing: its last block with mass
-            double run = inc - ls, lastrun = 0.0;
-            long long f = -1, lastb = -1;
-            double ex = 0.0;
+            unsigned long long run = inc - ls;
+            long long f = -1;
             for (int q = 0; q < per && b0 + q < nb; ++q) {
-                const double v = __ldcg(bsum + b0 + q);
-                if (v > 0.0) {
-                    lastb = b0 + q;
-                    lastrun = run;
-                    if (run + v > target) { f = b0 + q; ex = run; break; }
+                const unsigned long long v = __ldcg(bsum + b0 + q);
+                if (v > 0 && gt_u128(shl53(run + v), target)) {
+                    f = b0 + q;
+                    break;
                 }
                 run += v;
             }
-            if (f < 0) { f = lastb; ex = lastrun; }
             sm.fb = f;
-            sm.excl = ex;
+            sm.excl = run;
         }
         if (tid == 0 && src == INT_MAX) sm.fb = -1;
-        if (tid == 0) sm.target = target;
         __syncthreads();
         const long long fb = sm.fb;
         if (fb >= 0) {
             // the block's rows: thread tid owns rows [tid * RPT, (tid + 1) * RPT)
             const int64_t r0 = fb * ROWS + (int64_t)tid * RPT;
-            float v[RPT];
-            double rs = 0.0;
+            unsigned long long v[RPT];
+            unsigned long long rs = 0;
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
                 const int64_t i = r0 + q;
-                v[q] = (tid * RPT + q < ROWS && i < m) ? __ldcg(D2 + i) : 0.f;
-                rs += (double)v[q];
+                v[q] = (tid * RPT + q < ROWS && i < m) ? kpp_q(__ldcg(D2 + i), qs) : 0ull;
+                rs += v[q];
             }
-            double tot;
-            const double rinc = kpp_block_scan(rs, sm.wsum, &tot) + sm.excl;
-            const int src2 = kpp_block_first(rinc > target && rs > 0.0, &sm.first);
-            // no crossing (rounding): the last thread holding mass
-            int who = src2;
-            if (src2 == INT_MAX) {
-                if (tid == 0) sm.first = -1;
-                __syncthreads();
-                if (rs > 0.0) atomicMax(&sm.first, tid);
-                __syncthreads();
-                who = sm.first;
-            }
-            if (tid == who) {
-                double run = rinc - rs;
+            unsigned long long tot;
+            const unsigned long long rinc = kpp_block_scan(rs, sm.wsum, &tot) + sm.excl;
+            const int src2 = kpp_block_first(rs > 0 && gt_u128(shl53(rinc), target), &sm.first);
+            if (tid == src2) {
+                unsigned long long run = rinc - rs;
                 long long p = -1;
 #pragma unroll
                 for (int q = 0; q < RPT; ++q) {
-                    const double w = (double)v[q];
-                    if (w > 0.0) {
-                        p = r0 + q;
-                        if (run + w > target) break;
-                    }
-                    run += w;
+                    if (p < 0 && v[q] > 0 && gt_u128(shl53(run + v[q]), target)) p = r0 + q;
+                    run += v[q];
                 }
                 sm.pick = p;
             }
             __syncthreads();
-        }
-        if (tid == 0 && sm.pick < 0) {
-            // rounding left the target past the end: the last row with D^2 > 0
-            long long pick = -1;
-            for (long long b = nb - 1; b >= 0 && pick < 0; --b) {
-                if (!(__ldcg(bsum + b) > 0.0)) continue;
-                for (long long i = b * ROWS + ROWS - 1; i >= b * ROWS; --i)
-                    if (i < m && __ldcg(D2 + i) > 0.f) { pick = i; break; }
-            }
-            sm.pick = pick;
         }
     } else {
         // all remaining points coincide with chosen centres: lowest unchosen index
@@ -411,16 +384,19 @@ __device__ void kpp_draw(int t, int64_t m, const double *__restrict__ u,
 // Narrow dense rows: one thread per row, FP32 difference form.
 __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
     const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
-    const double *__restrict__ u, float *__restrict__ D2, int32_t *__restrict__ asg,
-    const float *__restrict__ cc2, double *__restrict__ bsum, unsigned *__restrict__ counter,
-    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken) {
-    __shared__ double red[kKppThreads / 32];
+    const unsigned long long *__restrict__ a53, float *__restrict__ D2,
+    int32_t *__restrict__ asg, const float *__restrict__ cc2, unsigned long long *__restrict__ bsum,
+    unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
+    unsigned char *__restrict__ taken, unsigned *__restrict__ s1_bits, int measure) {
+    __shared__ unsigned long long red[kKppThreads / 32];
+    __shared__ float fred[kKppThreads / 32];
     __shared__ int s_last;
-    __shared__ KppDrawSmem<kKppRows> sm;
+    __shared__ KppDrawSmem sm;
 
     const int t = *t_dev;
     const int tid = threadIdx.x;
     const int dp4 = dp / 4;
+    const float qs = measure ? 0.f : kpp_scale(s1_bits);
     int64_t c = chosen[t - 1];
     if (c < 0 || c >= m) c = 0;  // never out of bounds (a valid pick is always in [0, m))
     const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
@@ -431,7 +407,8 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
     // rounding) from the new centre cannot get closer to it (triangle
     // inequality), so its distance is not evaluated: the result is the same
     // as evaluating it and keeping min(D^2, distance).
-    double local = 0.0;
+    unsigned long long local = 0;
+    float flocal = 0.f;
 #pragma unroll
     for (int q = 0; q < kKppRpt; ++q) {
         const int64_t i = r0 + tid + q * kKppThreads;
@@ -463,10 +440,15 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_kernel(
             D2[i] = d2;
             asg[i] = a;
         }
-        local += (double)d2;
+        local += kpp_q(d2, qs);
+        flocal += d2;
+    }
+    if (measure) {
+        kpp_measure(flocal, fred, s1_bits);
+        return;
     }
     if (!kpp_block_done(local, red, bsum, counter, &s_last)) return;
-    kpp_draw<kKppRows>(t, m, u, D2, bsum, counter, t_dev, chosen, taken, sm);
+    kpp_draw<kKppRows>(t, m, a53, D2, qs, bsum, counter, t_dev, chosen, taken, sm);
 }
 
 // Wide dense rows (dp > kKppWideDim): one warp per row with coalesced float4
@@ -477,18 +459,21 @@ constexpr int kKppWideDim = 256;
 constexpr int kKppWideRows = 64;
 __global__ __launch_bounds__(kKppThreads) void kpp_step_wide_kernel(
     const float *__restrict__ X, int64_t m, int dp, int *__restrict__ t_dev,
-    const double *__restrict__ u, float *__restrict__ D2, double *__restrict__ bsum,
-    unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
-    unsigned char *__restrict__ taken) {
-    __shared__ double red[kKppThreads / 32];
+    const unsigned long long *__restrict__ a53, float *__restrict__ D2,
+    unsigned long long *__restrict__ bsum, unsigned *__restrict__ counter,
+    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken,
+    unsigned *__restrict__ s1_bits, int measure) {
+    __shared__ unsigned long long red[kKppThreads / 32];
+    __shared__ float fred[kKppThreads / 32];
     __shared__ int s_last;
-    __shared__ KppDrawSmem<kKppWideRows> sm;
+    __shared__ KppDrawSmem sm;
     constexpr int W = kKppThreads / 32;       // warps
     constexpr int RPW = kKppWideRows / W;     // rows per warp, all in flight
 
     const int t = *t_dev;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int dp4 = dp / 4;
+    const float qs = measure ? 0.f : kpp_scale(s1_bits);
     int64_t c = chosen[t - 1];
     if (c < 0 || c >= m) c = 0;
     const float4 *crow = reinterpret_cast<const float4 *>(X + c * dp);
@@ -511,7 +496,8 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_wide_kernel(
             }
         }
     }
-    double local = 0.0;
+    unsigned long long local = 0;
+    float flocal = 0.f;
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
         float v = acc[q];
@@ -520,11 +506,16 @@ __global__ __launch_bounds__(kKppThreads) void kpp_step_wide_kernel(
         if (lane == 0 && i < m) {
             const float d2 = t > 1 ? fminf(D2[i], v) : v;
             D2[i] = d2;
-            local += (double)d2;
+            local += kpp_q(d2, qs);
+            flocal += d2;
         }
     }
+    if (measure) {
+        kpp_measure(flocal, fred, s1_bits);
+        return;
+    }
     if (!kpp_block_done(local, red, bsum, counter, &s_last)) return;
-    kpp_draw<kKppWideRows>(t, m, u, D2, bsum, counter, t_dev, chosen, taken, sm);
+    kpp_draw<kKppWideRows>(t, m, a53, D2, qs, bsum, counter, t_dev, chosen, taken, sm);
 }
 
 // CSR rows (§4.3 TF-IDF shape): the new centre (a CSR row) is scattered into a
@@ -556,19 +547,22 @@ __device__ __forceinline__ void csr_row_ab(const int64_t b, const int64_t e,
 __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_csr_kernel(
     const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
     const float *__restrict__ val, int64_t m, int dp, int *__restrict__ t_dev,
-    const double *__restrict__ u, float *__restrict__ D2, double *__restrict__ bsum,
-    unsigned *__restrict__ counter, int64_t *__restrict__ chosen,
-    unsigned char *__restrict__ taken) {
+    const unsigned long long *__restrict__ a53, float *__restrict__ D2,
+    unsigned long long *__restrict__ bsum, unsigned *__restrict__ counter,
+    int64_t *__restrict__ chosen, unsigned char *__restrict__ taken,
+    unsigned *__restrict__ s1_bits, int measure) {
     extern __shared__ __align__(16) float cden[];  // [dp] the new centre, dense
-    __shared__ double red[kKppThreads / 32];
+    __shared__ unsigned long long red[kKppThreads / 32];
+    __shared__ float fred[kKppThreads / 32];
     __shared__ int s_last;
     __shared__ float s_cn;
-    __shared__ KppDrawSmem<kKppRows> sm;
+    __shared__ KppDrawSmem sm;
     constexpr int G = kKppThreads / kKppGroup;  // lane groups (rows in flight per block)
 
     const int t = *t_dev;
     const int tid = threadIdx.x;
     const int g = tid / kKppGroup, gl = tid % kKppGroup;
+    const float qs = measure ? 0.f : kpp_scale(s1_bits);
     int64_t c = chosen[t - 1];
     if (c < 0 || c >= m) c = 0;
     const int64_t cb = rp[c], ce = rp[c + 1];
@@ -586,7 +580,8 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_csr_kernel(
     __syncthreads();
     const float cn = s_cn;
     const int64_t r0 = (int64_t)blockIdx.x * kKppRows;
-    double local = 0.0;
+    unsigned long long local = 0;
+    float flocal = 0.f;
 #pragma unroll 2
     for (int q = 0; q < kKppRows / G; ++q) {
         const int64_t i = r0 + g + (int64_t)q * G;
@@ -597,11 +592,16 @@ __global__ __launch_bounds__(kKppThreads, 2) void kpp_step_csr_kernel(
             const float v = A + fmaxf(cn - B, 0.f);
             const float d2 = t > 1 ? fminf(D2[i], v) : v;
             D2[i] = d2;
-            local += (double)d2;
+            local += kpp_q(d2, qs);
+            flocal += d2;
         }
     }
+    if (measure) {
+        kpp_measure(flocal, fred, s1_bits);
+        return;
+    }
     if (!kpp_block_done(local, red, bsum, counter, &s_last)) return;
-    kpp_draw<kKppRows>(t, m, u, D2, bsum, counter, t_dev, chosen, taken, sm);
+    kpp_draw<kKppRows>(t, m, a53, D2, qs, bsum, counter, t_dev, chosen, taken, sm);
 }
 
 // ------------------------------------------------------------ label sort
@@ -907,11 +907,6 @@ void max_reduce(const float *v, int64_t n, float *out, cudaStream_t s) {
     MASK_LAUNCHED("max_reduce");
 }
 
-void sum_reduce_f32_to_f64(const float *v, int64_t n, double *out, cudaStream_t s) {
-    sum_f32_to_f64_kernel<<<1, 256, 0, s>>>(v, n, out);
-    MASK_LAUNCHED("sum_reduce");
-}
-
 // Run `steps` identical k-means++ step launches (the step number lives on the
 // device): a captured graph of kBatch steps is replayed, the rest run directly.
 template <class F>
@@ -949,32 +944,39 @@ void replay_steps(int steps, int kernels_per_step, F &&launch, cudaStream_t s) {
 
 struct KppState {
     Scratch<float> D2;
-    Scratch<double> bsum;
-    Scratch<unsigned> counter;
+    Scratch<unsigned long long> bsum;
+    Scratch<unsigned> counter, s1;   // s1: bound of the first step's sum (FP32 bits)
     Scratch<int> t_dev;
     Scratch<unsigned char> taken;
     KppState(int64_t m, int nb, cudaStream_t s)
-        : D2(m, s), bsum(nb, s), counter(1, s), t_dev(1, s), taken(m, s) {
+        : D2(m, s), bsum(nb, s), counter(1, s), s1(1, s), t_dev(1, s), taken(m, s) {
         const int one = 1;
         MASK_CUDA(cudaMemsetAsync(counter.get(), 0, sizeof(unsigned), s));
+        MASK_CUDA(cudaMemsetAsync(s1.get(), 0, sizeof(unsigned), s));
         MASK_CUDA(cudaMemsetAsync(taken.get(), 0, m, s));
         MASK_CUDA(cudaMemcpyAsync(t_dev.get(), &one, sizeof(int), cudaMemcpyHostToDevice, s));
     }
 };
 
-void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_dev,
+// Each seeding run starts with one measuring launch of its step kernel (the
+// first step's D^2 and the bound of its sum that fixes the integer scale),
+// then replays the steps.
+void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const unsigned long long *a53,
                     int64_t *chosen, cudaStream_t s) {
     if (k <= 1) return;
     ProfRegion pr("kmeanspp", s, (double)(k - 1) * (double)m * dp * 4.0);
     if (dp > kKppWideDim) {
         const int nb = (int)((m + kKppWideRows - 1) / kKppWideRows);
         KppState st(m, nb, s);
-        replay_steps(k - 1, 1, [&](cudaStream_t cs) {
-            kpp_step_wide_kernel<<<nb, kKppThreads, 0, cs>>>(Xs, m, dp, st.t_dev.get(), u_dev,
+        auto launch = [&](cudaStream_t cs, int measure) {
+            kpp_step_wide_kernel<<<nb, kKppThreads, 0, cs>>>(Xs, m, dp, st.t_dev.get(), a53,
                                                              st.D2.get(), st.bsum.get(),
                                                              st.counter.get(), chosen,
-                                                             st.taken.get());
-        }, s);
+                                                             st.taken.get(), st.s1.get(), measure);
+        };
+        launch(s, 1);
+        MASK_LAUNCHED("kpp_measure");
+        replay_steps(k - 1, 1, [&](cudaStream_t cs) { launch(cs, 0); }, s);
         return;
     }
     const int nb = (int)((m + kKppRows - 1) / kKppRows);
@@ -982,17 +984,23 @@ void kmeanspp_steps(const float *Xs, int64_t m, int dp, int k, const double *u_d
     Scratch<float> cc2(k, s);
     Scratch<int32_t> asg(m, s);
     const int ccb = (k + 255) / 256;
+    auto step = [&](cudaStream_t cs, int measure) {
+        kpp_step_kernel<<<nb, kKppThreads, 0, cs>>>(Xs, m, dp, st.t_dev.get(), a53, st.D2.get(),
+                                                    asg.get(), cc2.get(), st.bsum.get(),
+                                                    st.counter.get(), chosen, st.taken.get(),
+                                                    st.s1.get(), measure);
+    };
+    step(s, 1);
+    MASK_LAUNCHED("kpp_measure");
     replay_steps(k - 1, 2, [&](cudaStream_t cs) {
         kpp_centre_dist_kernel<<<ccb, 256, 0, cs>>>(Xs, m, dp, st.t_dev.get(), chosen, cc2.get());
-        kpp_step_kernel<<<nb, kKppThreads, 0, cs>>>(Xs, m, dp, st.t_dev.get(), u_dev, st.D2.get(),
-                                                    asg.get(), cc2.get(), st.bsum.get(),
-                                                    st.counter.get(), chosen, st.taken.get());
+        step(cs, 0);
     }, s);
 }
 
 void kmeanspp_steps_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t m,
-                        int64_t nnz, int dp, int k, const double *u_dev, int64_t *chosen,
-                        cudaStream_t s) {
+                        int64_t nnz, int dp, int k, const unsigned long long *a53,
+                        int64_t *chosen, cudaStream_t s) {
     if (k <= 1) return;
     const size_t smem = (size_t)dp * sizeof(float);
     MASK_REQUIRE(smem <= (size_t)kCsrMaxDim * sizeof(float), "CSR dimension too large");
@@ -1002,12 +1010,15 @@ void kmeanspp_steps_csr(const int64_t *rp, const int32_t *col, const float *val,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nb = (int)((m + kKppRows - 1) / kKppRows);
     KppState st(m, nb, s);
-    replay_steps(k - 1, 1, [&](cudaStream_t cs) {
+    auto launch = [&](cudaStream_t cs, int measure) {
         kpp_step_csr_kernel<<<nb, kKppThreads, smem, cs>>>(rp, col, val, m, dp, st.t_dev.get(),
-                                                           u_dev, st.D2.get(), st.bsum.get(),
+                                                           a53, st.D2.get(), st.bsum.get(),
                                                            st.counter.get(), chosen,
-                                                           st.taken.get());
-    }, s);
+                                                           st.taken.get(), st.s1.get(), measure);
+    };
+    launch(s, 1);
+    MASK_LAUNCHED("kpp_measure");
+    replay_steps(k - 1, 1, [&](cudaStream_t cs) { launch(cs, 0); }, s);
 }
 
 void label_sort(const int32_t *labels, int64_t n, int k, int64_t *off, int32_t *perm,

@@ -158,18 +158,21 @@ std::vector<int64_t> draw_subsample(SplitMix64 &rng, int64_t n, int64_t m) {
     return idx;
 }
 
-// One draw per centre, on the device: ud [k] and chosen[0] = floor(u_0 m).
-void draw_centres(SplitMix64 &rng, int64_t m, int k, Scratch<double> &ud, Scratch<int64_t> &ch,
-                  cudaStream_t s) {
-    std::vector<double> u((size_t)k);
-    for (int t = 0; t < k; ++t) u[(size_t)t] = rng.uniform();
-    int64_t first = (int64_t)std::floor(u[0] * (double)m);
+// One draw per centre: a53 [k] on the device holds each draw as the
+// generator's 53-bit integer a (u = a * 2^-53, so the device decides the
+// pick rule in integers), and chosen[0] = floor(u_0 m).
+void draw_centres(SplitMix64 &rng, int64_t m, int k, Scratch<unsigned long long> &a53,
+                  Scratch<int64_t> &ch, cudaStream_t s) {
+    std::vector<unsigned long long> a((size_t)k);
+    for (int t = 0; t < k; ++t) a[(size_t)t] = rng.next() >> 11;
+    int64_t first = (int64_t)std::floor((double)a[0] * 0x1.0p-53 * (double)m);
     if (first > m - 1) first = m - 1;
-    ud.alloc(k, s);
+    a53.alloc(k, s);
     ch.alloc(k, s);
-    MASK_CUDA(cudaMemcpyAsync(ud.get(), u.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    MASK_CUDA(cudaMemcpyAsync(a53.get(), a.data(), k * sizeof(unsigned long long),
+                              cudaMemcpyHostToDevice, s));
     MASK_CUDA(cudaMemcpyAsync(ch.get(), &first, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    MASK_CUDA(cudaStreamSynchronize(s));  // u and first are host temporaries
+    MASK_CUDA(cudaStreamSynchronize(s));  // a and first are host temporaries
 }
 
 // k-means++ for one level: C_out [k x dp] = the chosen rows of X; `chosen`
@@ -192,7 +195,7 @@ void seed_level(const float *X, int64_t n, int dp, int k, uint64_t seed, int lv,
         S = Xsub.get();
         MASK_CUDA(cudaStreamSynchronize(s));  // sidx and sample are released below
     }
-    Scratch<double> ud;
+    Scratch<unsigned long long> ud;
     Scratch<int64_t> ch;
     draw_centres(rng, m, k, ud, ch, s);
     kmeanspp_steps(S, m, dp, k, ud.get(), ch.get(), s);
@@ -225,7 +228,7 @@ void seed_level_csr(const int64_t *rp, const int32_t *col, const float *val, int
         Cl = scol.get();
         Vl = sval.get();
     }
-    Scratch<double> ud;
+    Scratch<unsigned long long> ud;
     Scratch<int64_t> ch;
     draw_centres(rng, m, k, ud, ch, s);
     int64_t nnz = 0;
@@ -240,6 +243,26 @@ void seed_level_csr(const int64_t *rp, const int32_t *col, const float *val, int
 
 // ------------------------------------------------------- Lloyd (§2.4, R4)
 
+// The objective after each assignment: the k per-cluster sums of squared
+// distances (FP32, one row per assignment) are kept on the device and summed
+// on the host in FP64, in cluster order, once the iterations are done.
+struct ObjectiveTrace {
+    Scratch<float> rows;
+    int k = 0, count = 0;
+    ObjectiveTrace(int k_, int count_, cudaStream_t s) : rows((size_t)k_ * count_, s), k(k_), count(count_) {}
+    void record(int i, const float *sse, cudaStream_t s) {
+        MASK_CUDA(cudaMemcpyAsync(rows.get() + (size_t)i * k, sse, sizeof(float) * k,
+                                  cudaMemcpyDeviceToDevice, s));
+    }
+    void finish(std::vector<double> &out, cudaStream_t s) {
+        std::vector<float> h;
+        to_host(h, rows.get(), (size_t)k * count, s);
+        out.assign((size_t)count, 0.0);
+        for (int i = 0; i < count; ++i)
+            for (int j = 0; j < k; ++j) out[(size_t)i] += (double)h[(size_t)i * k + j];
+    }
+};
+
 // Lloyd iterations on the n_in rows of X (padded) from the centres in C
 // (k x dp, updated in place).  Writes the final labels, the membership list
 // of the final assignment (off [k+1], perm [n_in]) and the objective after
@@ -247,7 +270,7 @@ void seed_level_csr(const int64_t *rp, const int32_t *col, const float *val, int
 void lloyd(const float *X, int64_t n_in, int dp, int k, int iters, float *C, int32_t *labels,
            int64_t *off, int32_t *perm, std::vector<double> &objective, cudaStream_t s) {
     Scratch<float> xn(n_in, s), Cn((size_t)k * dp, s), sse(k, s);
-    Scratch<double> J(iters + 1, s);
+    ObjectiveTrace J(k, iters + 1, s);
     row_sqnorm(X, n_in, dp, xn.get(), s);
     // tensor-core assignment when the row fits (X split into FP16 hi/lo
     // parts once); from the second assignment on, each row's search starts
@@ -264,17 +287,17 @@ void lloyd(const float *X, int64_t n_in, int dp, int k, int iters, float *C, int
         assign(cur);
         label_sort(labels, n_in, k, off, perm, s);
         centroid_update(X, dp, perm, off, k, cur, nxt, sse.get(), true, s);
-        sum_reduce_f32_to_f64(sse.get(), k, J.get() + it, s);
+        J.record(it, sse.get(), s);
         std::swap(cur, nxt);
     }
     assign(cur);
     label_sort(labels, n_in, k, off, perm, s);
     centroid_update(X, dp, perm, off, k, cur, nullptr, sse.get(), false, s);
     if (tc) tc_assign_check(*tc, s);
-    sum_reduce_f32_to_f64(sse.get(), k, J.get() + iters, s);
+    J.record(iters, sse.get(), s);
     if (cur != C)
         MASK_CUDA(cudaMemcpyAsync(C, cur, sizeof(float) * k * dp, cudaMemcpyDeviceToDevice, s));
-    to_host(objective, J.get(), (size_t)iters + 1, s);
+    J.finish(objective, s);
 }
 
 // Lloyd iterations on CSR rows (dense centroids C [k x dp], updated in place);
@@ -283,23 +306,23 @@ void lloyd_csr(const int64_t *rp, const int32_t *col, const float *val, int64_t 
                int dp, int k, int iters, float *C, int32_t *labels, int64_t *off, int32_t *perm,
                std::vector<double> &objective, cudaStream_t s) {
     Scratch<float> xn(n, s), Cn((size_t)k * dp, s), sse(k, s), cn(k, s);
-    Scratch<double> J(iters + 1, s);
+    ObjectiveTrace J(k, iters + 1, s);
     csr_row_sqnorm(rp, val, n, xn.get(), s);
     float *cur = C, *nxt = Cn.get();
     for (int it = 0; it < iters; ++it) {
         csr_assign(rp, col, val, n, nnz, xn.get(), cur, k, dp, labels, cn.get(), s);
         label_sort(labels, n, k, off, perm, s);
         csr_centroid_update(rp, col, val, perm, off, n, k, dp, cur, cn.get(), nxt, sse.get(), s);
-        sum_reduce_f32_to_f64(sse.get(), k, J.get() + it, s);
+        J.record(it, sse.get(), s);
         std::swap(cur, nxt);
     }
     csr_assign(rp, col, val, n, nnz, xn.get(), cur, k, dp, labels, cn.get(), s);
     label_sort(labels, n, k, off, perm, s);
     csr_centroid_update(rp, col, val, perm, off, n, k, dp, cur, cn.get(), nullptr, sse.get(), s);
-    sum_reduce_f32_to_f64(sse.get(), k, J.get() + iters, s);
+    J.record(iters, sse.get(), s);
     if (cur != C)
         MASK_CUDA(cudaMemcpyAsync(C, cur, sizeof(float) * k * dp, cudaMemcpyDeviceToDevice, s));
-    to_host(objective, J.get(), (size_t)iters + 1, s);
+    J.finish(objective, s);
 }
 
 // ------------------------------------------------------------ index layout
