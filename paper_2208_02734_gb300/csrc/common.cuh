@@ -208,8 +208,9 @@ void csr_gather_rows(const int64_t *rp, const int32_t *col, const float *val, co
 // out [m x dp] = dense copies of rows rows[i] (rows == null: rows 0..m)
 void csr_densify_rows(const int64_t *rp, const int32_t *col, const float *val,
                       const int64_t *rows, int64_t m, int dp, float *out, cudaStream_t s);
-// cn [kp] = ||c_j||^2 (FP64 sum rounded; +inf for j >= k), cn64 [k] the FP64 values
-void centroid_norms(const float *C, int k, int dp, int kp, float *cn, double *cn64,
+// cn [kp] = ||c_j||^2 (float-float sum rounded; +inf for j >= k), cn_lo [k]
+// the remainders (cn + cn_lo = the float-float sums)
+void centroid_norms(const float *C, int k, int dp, int kp, float *cn, float *cn_lo,
                     cudaStream_t s);
 // labels = argmin_j ||x_i - c_j||^2 for CSR rows and dense C [k x dp] (ties to
 // the smallest j); cn_out (optional, [k]) receives ||c_j||^2

@@ -346,8 +346,8 @@ void finish_levels(mask_index &idx, cudaStream_t s) {
         }
         if (idx.sparse) {
             L.cns.alloc((size_t)L.k);
-            Scratch<double> n64(L.k, s);
-            centroid_norms(L.Cs.get(), L.k, dp, L.k, L.cns.get(), n64.get(), s);
+            Scratch<float> nlo(L.k, s);
+            centroid_norms(L.Cs.get(), L.k, dp, L.k, L.cns.get(), nlo.get(), s);
             MASK_CUDA(cudaStreamSynchronize(s));
         }
     }
@@ -1033,11 +1033,11 @@ mask_status mask_kmeans_update_csr(const int64_t *row_ptr, const int32_t *col, c
         MASK_CUDA(cudaStreamSynchronize(s));
         MASK_REQUIRE(nbad == 0, "labels out of range");
         Scratch<float> Cp((size_t)k * dp, s), Cn((size_t)k * dp, s), sse(k, s), cn(k, s);
-        Scratch<double> cn64(k, s);
+        Scratch<float> cn_lo(k, s);
         Scratch<int64_t> off((size_t)k + 1, s);
         Scratch<int32_t> perm((size_t)(n > 0 ? n : 1), s);
         pad_rows(Cin.p, k, d, Cp.get(), dp, s);
-        centroid_norms(Cp.get(), k, dp, k, cn.get(), cn64.get(), s);
+        centroid_norms(Cp.get(), k, dp, k, cn.get(), cn_lo.get(), s);
         label_sort(Lin.p, n, k, off.get(), perm.get(), s);
         csr_centroid_update(in.rp->p, in.col->p, in.val->p, perm.get(), off.get(), n, k, dp,
                             Cp.get(), cn.get(), Cn.get(), sse.get(), s);

@@ -71,21 +71,63 @@ __global__ void csr_check_cols_kernel(const int32_t *__restrict__ col, int64_t n
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(bad + 1, b);
 }
 
+// ------------------------------------------------- float-float arithmetic
+//
+// Long sums of squares (rows and centroids of up to tens of thousands of
+// coordinates) and the exact re-decision of near-tie rows are carried in
+// float-float form: a value is hi + lo with |lo| <= ulp(hi) / 2, kept by the
+// error-free transformations TwoSum (Knuth) and TwoProduct (one fma), which
+// give about 48 significant bits with FP32 instructions only.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return FF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return FF{s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
+// x + a * a
+__device__ __forceinline__ FF ff_add_sq(FF x, float a) {
+    const float p = a * a;
+    return ff_add(x, FF{p, fmaf(a, a, -p)});
+}
+// x + (a - b)^2 with a - b kept exactly as a float-float pair
+__device__ __forceinline__ FF ff_add_sq_diff(FF x, float a, float b) {
+    const FF d = two_sum(a, -b);
+    const float p = d.hi * d.hi, q = 2.f * d.hi * d.lo;
+    x = ff_add(x, FF{p, fmaf(d.hi, d.hi, -p)});
+    x = ff_add(x, FF{q, fmaf(2.f * d.hi, d.lo, -q)});
+    return ff_add(x, FF{d.lo * d.lo, 0.f});
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF x, int o) {
+    return FF{__shfl_xor_sync(kFull, x.hi, o), __shfl_xor_sync(kFull, x.lo, o)};
+}
+// strict order of normalised float-float values
+__device__ __forceinline__ bool ff_lt(FF x, FF y) {
+    return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo);
+}
+
 // ------------------------------------------------------------ row helpers
 
-// ||x_i||^2 (FP64 sum over the row, rounded once), one warp per row.
+// ||x_i||^2 (float-float sum over the row, rounded once), one warp per row.
 __global__ void csr_sqnorm_kernel(const int64_t *__restrict__ rp, const float *__restrict__ val,
                                   int64_t n, float *__restrict__ xn) {
     const int lane = threadIdx.x & 31;
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        double s = 0.0;
-        for (int64_t j = rp[i] + lane; j < rp[i + 1]; j += 32) {
-            const double v = val[j];
-            s += v * v;
-        }
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (lane == 0) xn[i] = (float)s;
+        FF s{0.f, 0.f};
+        for (int64_t j = rp[i] + lane; j < rp[i + 1]; j += 32) s = ff_add_sq(s, val[j]);
+        for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_xor(s, o));
+        if (lane == 0) xn[i] = s.hi + s.lo;
     }
 }
 
@@ -202,10 +244,11 @@ __global__ void csr_densify_kernel(const int64_t *__restrict__ rp, const int32_t
 
 // ------------------------------------------------------ centroid tables
 
-// cn[j] = ||c_j||^2 (FP64 sum, rounded once), cn64[j] the FP64 value; the
-// padding entries j in [k, kp) get +inf so they never win.
+// cn[j] = ||c_j||^2 (float-float sum, rounded once), cn_lo[j] its
+// remainder (cn + cn_lo is the float-float value); the padding entries j in
+// [k, kp) get +inf so they never win.
 __global__ void centroid_norms_kernel(const float *__restrict__ C, int k, int dp, int kp,
-                                      float *__restrict__ cn, double *__restrict__ cn64) {
+                                      float *__restrict__ cn, float *__restrict__ cn_lo) {
     const int lane = threadIdx.x & 31;
     for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; j < kp;
          j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -213,15 +256,12 @@ __global__ void centroid_norms_kernel(const float *__restrict__ C, int k, int dp
             if (lane == 0) cn[j] = __int_as_float(0x7f800000);
             continue;
         }
-        double s = 0.0;
-        for (int t = lane; t < dp; t += 32) {
-            const double v = C[j * dp + t];
-            s += v * v;
-        }
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        FF s{0.f, 0.f};
+        for (int t = lane; t < dp; t += 32) s = ff_add_sq(s, C[j * dp + t]);
+        for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_xor(s, o));
         if (lane == 0) {
-            cn[j] = (float)s;
-            cn64[j] = s;
+            cn[j] = s.hi;
+            cn_lo[j] = s.lo;
         }
     }
 }
@@ -385,19 +425,19 @@ __global__ void sp_combine_kernel(const float *__restrict__ pb1, const int32_t *
 
 // Listed rows, decided exactly: an FP32 pass over all k finds the smallest
 // distance; every centroid within the rounding bound of it is then evaluated
-// in FP64 as sum_{t in x} (x_t - c_t)^2 + (||c||^2 - sum_{t in x} c_t^2) (the
-// difference form over the row's support plus the centroid's mass outside
-// it), and the smallest (distance, j) wins.
+// in float-float as sum_{t in x} (x_t - c_t)^2 + (||c||^2 - sum_{t in x}
+// c_t^2) (the difference form over the row's support plus the centroid's
+// mass outside it), and the smallest (distance, j) wins.
 constexpr int kRcThreads = 256;
 __global__ __launch_bounds__(kRcThreads) void sp_recheck_kernel(
     const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ CT, int kp,
-    const float *__restrict__ cn, const double *__restrict__ cn64, int k,
+    const float *__restrict__ cn, const float *__restrict__ cn_lo, int k,
     const int32_t *__restrict__ flagged, const int *__restrict__ n_flagged,
     const float *__restrict__ xn, const float *__restrict__ cn_max,
     int32_t *__restrict__ labels) {
     __shared__ float red_f[kRcThreads / 32];
-    __shared__ double red_d[kRcThreads / 32];
+    __shared__ FF red_d[kRcThreads / 32];
     __shared__ int red_i[kRcThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int nf = *n_flagged;
@@ -418,27 +458,26 @@ __global__ __launch_bounds__(kRcThreads) void sp_recheck_kernel(
         mn = red_f[0];
         for (int v = 1; v < kRcThreads / 32; ++v) mn = fminf(mn, red_f[v]);
         const float thr = mn + sp_margin(e - b, xn[i], cmax);
-        double best = DBL_MAX;
+        FF best{FLT_MAX, 0.f};
         int bj = INT_MAX;
         for (int j = tid; j < k; j += kRcThreads) {
             if (!(d32(j) <= thr)) continue;
-            double A = 0.0, B = 0.0;
+            FF A{0.f, 0.f}, B{0.f, 0.f};
             for (int64_t t = b; t < e; ++t) {
-                const double c = CT[(int64_t)col[t] * kp + j];
-                const double x = val[t] - c;
-                A += x * x;
-                B += c * c;
+                const float c = CT[(int64_t)col[t] * kp + j];
+                A = ff_add_sq_diff(A, val[t], c);
+                B = ff_add_sq(B, c);
             }
-            const double D = A + (cn64[j] - B);
-            if (D < best || (D == best && j < bj)) {
+            const FF D = ff_add(A, ff_add(FF{cn[j], cn_lo[j]}, ff_neg(B)));
+            if (ff_lt(D, best) || (D.hi == best.hi && D.lo == best.lo && j < bj)) {
                 best = D;
                 bj = j;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(kFull, best, o);
+            const FF ob = ff_shfl_xor(best, o);
             const int oj = __shfl_xor_sync(kFull, bj, o);
-            if (ob < best || (ob == best && oj < bj)) {
+            if (ff_lt(ob, best) || (ob.hi == best.hi && ob.lo == best.lo && oj < bj)) {
                 best = ob;
                 bj = oj;
             }
@@ -450,7 +489,8 @@ __global__ __launch_bounds__(kRcThreads) void sp_recheck_kernel(
         __syncthreads();
         if (tid == 0) {
             for (int v = 1; v < kRcThreads / 32; ++v)
-                if (red_d[v] < best || (red_d[v] == best && red_i[v] < bj)) {
+                if (ff_lt(red_d[v], best) ||
+                    (red_d[v].hi == best.hi && red_d[v].lo == best.lo && red_i[v] < bj)) {
                     best = red_d[v];
                     bj = red_i[v];
                 }
@@ -642,9 +682,9 @@ void csr_densify_rows(const int64_t *rp, const int32_t *col, const float *val,
     MASK_LAUNCHED("csr_densify");
 }
 
-void centroid_norms(const float *C, int k, int dp, int kp, float *cn, double *cn64,
+void centroid_norms(const float *C, int k, int dp, int kp, float *cn, float *cn_lo,
                     cudaStream_t s) {
-    centroid_norms_kernel<<<grid_for((int64_t)kp * 32, 256), 256, 0, s>>>(C, k, dp, kp, cn, cn64);
+    centroid_norms_kernel<<<grid_for((int64_t)kp * 32, 256), 256, 0, s>>>(C, k, dp, kp, cn, cn_lo);
     MASK_LAUNCHED("centroid_norms");
 }
 
@@ -658,8 +698,8 @@ void csr_assign(const int64_t *rp, const int32_t *col, const float *val, int64_t
     const int nch = kp / kSpBN;
     ProfRegion pr("csr_assign", s, 0.0);
     Scratch<float> CT((size_t)dp * kp, s), cn(kp, s), cmax(1, s);
-    Scratch<double> cn64(k, s);
-    centroid_norms(C, k, dp, kp, cn.get(), cn64.get(), s);
+    Scratch<float> cn_lo(k, s);
+    centroid_norms(C, k, dp, kp, cn.get(), cn_lo.get(), s);
     max_reduce(cn.get(), k, cmax.get(), s);
     dim3 tg((dp + 31) / 32, kp / 32), tb(32, 8);
     transpose_ct_kernel<<<tg, tb, 0, s>>>(C, k, dp, kp, CT.get());
@@ -682,7 +722,7 @@ void csr_assign(const int64_t *rp, const int32_t *col, const float *val, int64_t
                                                        nflag.get());
     MASK_LAUNCHED("sp_combine");
     sp_recheck_kernel<<<152 * 4, kRcThreads, 0, s>>>(rp, col, val, CT.get(), kp, cn.get(),
-                                                     cn64.get(), k, flagged.get(), nflag.get(), xn,
+                                                     cn_lo.get(), k, flagged.get(), nflag.get(), xn,
                                                      cmax.get(), labels);
     MASK_LAUNCHED("sp_recheck");
     if (cn_out) MASK_CUDA(cudaMemcpyAsync(cn_out, cn.get(), sizeof(float) * k,
