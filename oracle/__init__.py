@@ -12,6 +12,11 @@ Functions follow the paper (Ortega et al., arXiv 2208.02734):
   build                  -- multilevel index, global form of Algorithm 1 (§3.1)
   query                  -- top-down k-NN descent (§3.3, Algorithm 2)
   bruteforce_knn         -- exact k-NN by full scan (ground truth)
+  grouped_sizes / build_grouped -- Algorithm 1 as printed: random split into
+                            groups of lengthGroup, nCentroids per group (§3.1)
+  descend                -- the kept leaf clusters of the descent
+  range_query            -- range search (§3.3, Algorithm 3)
+  relocate               -- one point-relocation pass of §4.1
 """
 
 from __future__ import annotations
@@ -86,6 +91,22 @@ def _load():
                                      _u8p]),
             "mo_bruteforce_knn": (C.c_int32, [_f64p, C.c_int64, C.c_int32, _f64p, C.c_int64,
                                               C.c_int32, _i64p, _f64p]),
+            "mo_grouped_sizes": (C.c_int32, [C.c_int64, C.c_int32, C.c_int32, _i64p, C.c_int32]),
+            "mo_group_state": (C.c_uint64, [C.c_uint64, C.c_int32, C.c_int64]),
+            "mo_split_groups": (C.c_int32, [C.c_int64, C.c_int64, _u64ref, _i32p]),
+            "mo_build_grouped": (C.c_int32, [_f64p, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                             C.c_int32, C.c_uint64, C.c_void_p, C.c_int32,
+                                             C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+            "mo_descend": (C.c_int32, [C.c_int64, C.c_int32, C.c_int32, _i32p,
+                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), _f64p,
+                                       C.c_int64, _i32p, _i32p]),
+            "mo_range_query": (C.c_int32, [_f64p, C.c_int64, C.c_int32, C.c_int32, _i32p,
+                                           C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), _f64p,
+                                           C.c_int64, C.c_double, _i64p, C.c_int64, C.c_void_p,
+                                           C.c_void_p]),
+            "mo_relocate": (C.c_int64, [_f64p, C.c_int64, C.c_int32, C.c_int32, _i32p,
+                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
+                                        _i32p, C.POINTER(C.c_int64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -265,3 +286,103 @@ def bruteforce_knn(X, Q, k: int):
     _check(_load().mo_bruteforce_knn(X, X.shape[0], X.shape[1], Q, Q.shape[0], k, ids,
                                      dists), "bruteforce_knn")
     return ids, dists
+
+
+# ------------------------------------------------ grouped build (Algorithm 1)
+
+def grouped_sizes(n: int, length_group: int, n_centroids: int):
+    """Centroids per level of the grouped build (finest first)."""
+    sizes = np.empty(64, dtype=np.int64)
+    L = _load().mo_grouped_sizes(n, length_group, n_centroids, sizes, 64)
+    _check(0 if L >= 0 else L, "grouped_sizes")
+    return [int(v) for v in sizes[:L]]
+
+
+def group_state(seed: int, level: int, group: int) -> int:
+    return int(_load().mo_group_state(C.c_uint64(seed), int(level), int(group)))
+
+
+def split_groups(m: int, G: int, state: int) -> np.ndarray:
+    """R16: the group of each of m items split at random into G groups."""
+    out = np.empty(m, dtype=np.int32)
+    s = C.c_uint64(state)
+    _check(_load().mo_split_groups(m, G, C.byref(s), out), "split_groups")
+    return out
+
+
+def build_grouped(X, length_group: int, n_centroids: int, iters: int, seed: int,
+                  group0=None) -> Index:
+    """Algorithm 1 as printed (readings R16-R18); group0 replaces the random
+    level-0 split (relocation, §4.1)."""
+    X = _f64(X)
+    n, d = X.shape
+    sizes = grouped_sizes(n, length_group, n_centroids)
+    L = len(sizes)
+    if L == 0:
+        raise ValueError("fewer points than lengthGroup: no level")
+    Cs = [np.empty((k, d)) for k in sizes]
+    n_in = [n] + sizes[:-1]
+    Ls = [np.empty(m, dtype=np.int32) for m in n_in]
+    ptrs = lambda arrs: (C.c_void_p * L)(*[a.ctypes.data for a in arrs])  # noqa: E731
+    g0 = None if group0 is None else np.ascontiguousarray(group0, dtype=np.int32)
+    _check(_load().mo_build_grouped(X, n, d, length_group, n_centroids, iters, C.c_uint64(seed),
+                                    None if g0 is None else g0.ctypes.data, L, ptrs(Cs),
+                                    ptrs(Ls)), "build_grouped")
+    return Index(X, Cs, Ls)
+
+
+def descend(index: Index, Q, probes) -> np.ndarray:
+    """The kept leaf clusters of the descent, [nq x probes[0]], nearest first."""
+    Q = _f64(Q)
+    L = len(index.centroids)
+    kp = np.ascontiguousarray(index.k_per_level, dtype=np.int32)
+    pr = np.ascontiguousarray(probes, dtype=np.int32)
+    out = np.empty((Q.shape[0], int(pr[0])), dtype=np.int32)
+    ptrs = lambda arrs: (C.c_void_p * L)(*[a.ctypes.data for a in arrs])  # noqa: E731
+    _check(_load().mo_descend(index.X.shape[0], index.X.shape[1], L, kp, ptrs(index.centroids),
+                              ptrs(index.labels), Q, Q.shape[0], pr, out), "descend")
+    return out
+
+
+def range_query(index: Index, Q, radius: float):
+    """Range search (Algorithm 3, reading R19): per query, (ids, squared
+    distances) of the points found within `radius`, ascending."""
+    Q = _f64(Q)
+    nq = Q.shape[0]
+    L = len(index.centroids)
+    kp = np.ascontiguousarray(index.k_per_level, dtype=np.int32)
+    counts = np.empty(nq, dtype=np.int64)
+    ptrs = lambda arrs: (C.c_void_p * L)(*[a.ctypes.data for a in arrs])  # noqa: E731
+    args = (index.X, index.X.shape[0], index.X.shape[1], L, kp, ptrs(index.centroids),
+            ptrs(index.labels), Q, nq, float(radius) ** 2, counts)
+    _check(_load().mo_range_query(*args, 0, None, None), "range_query")
+    total = int(counts.sum())
+    ids = np.empty(max(total, 1), dtype=np.int64)
+    dists = np.empty(max(total, 1))
+    _check(_load().mo_range_query(*args, total, ids.ctypes.data, dists.ctypes.data),
+           "range_query")
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    return [(ids[offs[q]:offs[q + 1]], dists[offs[q]:offs[q + 1]]) for q in range(nq)]
+
+
+def relocate(index: Index, n_centroids: int, group0):
+    """One relocation pass (§4.1, reading R20): returns (missed points, new
+    group0, moves)."""
+    L = len(index.centroids)
+    kp = np.ascontiguousarray(index.k_per_level, dtype=np.int32)
+    g = np.array(group0, dtype=np.int32, copy=True)
+    moved = C.c_int64(0)
+    ptrs = lambda arrs: (C.c_void_p * L)(*[a.ctypes.data for a in arrs])  # noqa: E731
+    missed = _load().mo_relocate(index.X, index.X.shape[0], index.X.shape[1], L, kp,
+                                 ptrs(index.centroids), ptrs(index.labels), n_centroids, g,
+                                 C.byref(moved))
+    if missed < 0:
+        raise RuntimeError(f"oracle relocate failed with status {missed}")
+    return int(missed), g, int(moved.value)
+
+
+def point_query_error(index: Index) -> float:
+    """Error rate of the exhaustive point query (§4.2): the fraction of the
+    indexed points whose greedy descent does not reach their own leaf cluster."""
+    leaf = descend(index, index.X, [1] * len(index.centroids))[:, 0]
+    return float(np.mean(leaf != index.labels[0]))

@@ -481,3 +481,353 @@ int32_t mo_bruteforce_knn(const double *X, int64_t n, int32_t d, const double *Q
     }
     return MO_OK;
 }
+
+/* ------------------------------------------ grouped build (Algorithm 1) */
+
+/*
+ * Algorithm 1 as printed (§3.1): the items of a level are split at random into
+ * ngroups = floor(items / lengthGroup) groups, each group is clustered into
+ * nCentroids centroids by its own k-means, and the centroids of all groups
+ * are the items of the next level; the loop stops when ngroups < 1.
+ *
+ * Readings (where the paper is silent):
+ *   R16 split: a full Fisher-Yates shuffle of the level's items with the
+ *       level stream of R1 (draws j = 0..m-2: r = j + floor(u (m - j))), then
+ *       consecutive parts of the shuffled order whose sizes differ by at
+ *       most one, the first (m mod G) parts one larger.  Within a group the
+ *       items are taken in ascending item index.
+ *   R17 group g of level lv seeds its k-means++ from the state
+ *       level_state(seed, lv) ^ (0xD1B54A32D192ED03 * (g + 1)); its k-means is
+ *       R2 + R4 with nCentroids centres and `iters` Lloyd iterations.
+ *   R18 centroid j of group g is item g * nCentroids + j of the next level;
+ *       the labels of a level map each item to that global centroid id.
+ * With those, the index is the same structure as the global form's, so the
+ * top-down search (mo_query) applies unchanged.
+ */
+
+/* Level sizes of the grouped build: sizes[lv] = centroids at level lv
+ * (finest first); returns the number of levels (0 if n < lengthGroup), or
+ * MO_EINVAL for bad parameters.  Integer arithmetic only. */
+int32_t mo_grouped_sizes(int64_t n, int32_t lg, int32_t nc, int64_t *sizes, int32_t max_levels) {
+    if (lg < 1 || nc < 1 || nc > lg || n < 0) return MO_EINVAL;
+    int32_t L = 0;
+    int64_t items = n;
+    int64_t groups = items / lg;
+    while (groups >= 1) {
+        if (L >= max_levels) return MO_EINVAL;
+        sizes[L++] = groups * nc;
+        items = groups * nc;
+        groups = items / lg;
+    }
+    return L;
+}
+
+uint64_t mo_group_state(uint64_t seed, int32_t level, int64_t group) {
+    return mo_level_state(seed, level) ^ (0xD1B54A32D192ED03ull * (uint64_t)(group + 1));
+}
+
+/* R16: group_of[item] for m items split into G groups with the stream state. */
+int32_t mo_split_groups(int64_t m, int64_t G, uint64_t *state, int32_t *group_of) {
+    if (G < 1 || m < G) return MO_EINVAL;
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    if (!perm) return MO_ENOMEM;
+    for (int64_t i = 0; i < m; ++i) perm[i] = i;
+    for (int64_t j = 0; j + 1 < m; ++j) {
+        int64_t r = j + (int64_t)floor(mo_uniform(state) * (double)(m - j));
+        if (r > m - 1) r = m - 1;
+        int64_t t = perm[j];
+        perm[j] = perm[r];
+        perm[r] = t;
+    }
+    const int64_t base = m / G, extra = m % G;
+    int64_t pos = 0;
+    for (int64_t g = 0; g < G; ++g) {
+        const int64_t len = base + (g < extra ? 1 : 0);
+        for (int64_t q = 0; q < len; ++q) group_of[perm[pos + q]] = (int32_t)g;
+        pos += len;
+    }
+    free(perm);
+    return MO_OK;
+}
+
+/*
+ * One level of the grouped build: items X (m x d), their groups group_of[m]
+ * (each group with at least nc items), G groups.  C (G*nc x d) and labels
+ * (m, global centroid ids) are written.
+ */
+static int32_t grouped_level(const double *X, int64_t m, int32_t d, const int32_t *group_of,
+                             int64_t G, int32_t nc, int32_t iters, uint64_t seed, int32_t lv,
+                             double *C, int32_t *labels) {
+    int64_t *off = NULL, *items = NULL;
+    int32_t rc = member_lists(group_of, m, (int32_t)G, &off, &items);
+    if (rc != MO_OK) return rc;
+    for (int64_t g = 0; g < G && rc == MO_OK; ++g) {
+        const int64_t mg = off[g + 1] - off[g];
+        if (mg < nc) { rc = MO_EINVAL; break; }
+        double *Xg = (double *)malloc(sizeof(double) * (size_t)mg * (size_t)d);
+        int32_t *lg_ = (int32_t *)malloc(sizeof(int32_t) * (size_t)mg);
+        int64_t *chosen = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+        if (!Xg || !lg_ || !chosen) { free(Xg); free(lg_); free(chosen); rc = MO_ENOMEM; break; }
+        for (int64_t q = 0; q < mg; ++q)   /* items in ascending index (member_lists order) */
+            memcpy(Xg + q * d, X + items[off[g] + q] * (int64_t)d, sizeof(double) * (size_t)d);
+        uint64_t st = mo_group_state(seed, lv, g);
+        double *Cg = C + g * (int64_t)nc * d;
+        rc = mo_kmeanspp(Xg, mg, d, nc, &st, chosen, Cg);
+        if (rc == MO_OK) rc = mo_lloyd(Xg, mg, d, nc, iters, Cg, lg_, NULL);
+        if (rc == MO_OK)
+            for (int64_t q = 0; q < mg; ++q)
+                labels[items[off[g] + q]] = (int32_t)(g * nc + lg_[q]);
+        free(Xg);
+        free(lg_);
+        free(chosen);
+    }
+    free(off);
+    free(items);
+    return rc;
+}
+
+/*
+ * Grouped multilevel build.  L = mo_grouped_sizes(n, lg, nc, ...) levels;
+ * C_levels[lv] (sizes[lv] x d) and labels_levels[lv] (items of level lv: n
+ * for lv = 0, else sizes[lv-1]) are caller-allocated.  group0 (may be NULL)
+ * gives the level-0 groups of the points (values in [0, floor(n/lg)), each
+ * group with at least nc points) instead of the random split; the levels
+ * above are always split at random.
+ */
+int32_t mo_build_grouped(const double *X, int64_t n, int32_t d, int32_t lg, int32_t nc,
+                         int32_t iters, uint64_t seed, const int32_t *group0, int32_t L,
+                         double *const *C_levels, int32_t *const *labels_levels) {
+    int64_t sizes[64];
+    int32_t Lc = mo_grouped_sizes(n, lg, nc, sizes, 64);
+    if (Lc < 0 || Lc != L || iters < 0) return MO_EINVAL;
+    const double *in = X;
+    int64_t m = n;
+    for (int32_t lv = 0; lv < L; ++lv) {
+        const int64_t G = m / lg;
+        int32_t *grp = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+        if (!grp) return MO_ENOMEM;
+        int32_t rc = MO_OK;
+        if (lv == 0 && group0) {
+            for (int64_t i = 0; i < m; ++i) {
+                if (group0[i] < 0 || group0[i] >= G) { rc = MO_EINVAL; break; }
+                grp[i] = group0[i];
+            }
+        } else {
+            uint64_t st = mo_level_state(seed, lv);
+            rc = mo_split_groups(m, G, &st, grp);
+        }
+        if (rc == MO_OK)
+            rc = grouped_level(in, m, d, grp, G, nc, iters, seed, lv, C_levels[lv], labels_levels[lv]);
+        free(grp);
+        if (rc != MO_OK) return rc;
+        in = C_levels[lv];
+        m = G * nc;
+    }
+    return MO_OK;
+}
+
+/* -------------------------------------------- descent to the leaf clusters */
+
+/*
+ * The kept leaf clusters of the top-down search (the kept set of level 0
+ * after the same descent as mo_query): leaf_out [nq x probes[0]], nearest
+ * first, padded with -1.
+ */
+int32_t mo_descend(int64_t n, int32_t d, int32_t L, const int32_t *k_per_level,
+                   const double *const *C_levels, const int32_t *const *labels_levels,
+                   const double *Q, int64_t nq, const int32_t *probes, int32_t *leaf_out) {
+    if (L < 1 || d < 1) return MO_EINVAL;
+    int64_t **off = (int64_t **)calloc((size_t)L, sizeof(int64_t *));
+    int64_t **items = (int64_t **)calloc((size_t)L, sizeof(int64_t *));
+    if (!off || !items) { free(off); free(items); return MO_ENOMEM; }
+    int32_t rc = MO_OK;
+    for (int32_t lv = 1; lv < L && rc == MO_OK; ++lv)
+        rc = member_lists(labels_levels[lv], (int64_t)k_per_level[lv - 1], k_per_level[lv],
+                          &off[lv], &items[lv]);
+    int64_t max_n = 1;
+    for (int32_t lv = 0; lv < L; ++lv)
+        if ((int64_t)k_per_level[lv] > max_n) max_n = k_per_level[lv];
+    (void)n;
+    if (rc == MO_OK) {
+#pragma omp parallel
+        {
+            mo_pair *cand = (mo_pair *)malloc(sizeof(mo_pair) * (size_t)max_n);
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t qi = 0; qi < nq; ++qi) {
+                const double *q = Q + qi * (int64_t)d;
+                int64_t ncand = 0;
+                const int32_t top = L - 1;
+                for (int64_t j = 0; j < k_per_level[top]; ++j) {
+                    cand[ncand].d = sqdist(q, C_levels[top] + j * (int64_t)d, d);
+                    cand[ncand].id = j;
+                    ++ncand;
+                }
+                for (int32_t lv = top; lv >= 0; --lv) {
+                    qsort(cand, (size_t)ncand, sizeof(mo_pair), pair_cmp);
+                    int64_t p = probes[lv] < ncand ? probes[lv] : ncand;
+                    if (lv == 0) {
+                        for (int32_t s = 0; s < probes[0]; ++s)
+                            leaf_out[qi * probes[0] + s] = s < p ? (int32_t)cand[s].id : -1;
+                        break;
+                    }
+                    int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)(p > 0 ? p : 1));
+                    for (int64_t s = 0; s < p; ++s) kept[s] = cand[s].id;
+                    ncand = 0;
+                    for (int64_t s = 0; s < p; ++s) {
+                        const int64_t c = kept[s];
+                        for (int64_t mm = off[lv][c]; mm < off[lv][c + 1]; ++mm) {
+                            const int64_t it = items[lv][mm];
+                            cand[ncand].d = sqdist(q, C_levels[lv - 1] + it * (int64_t)d, d);
+                            cand[ncand].id = it;
+                            ++ncand;
+                        }
+                    }
+                    free(kept);
+                }
+            }
+            free(cand);
+        }
+    }
+    for (int32_t lv = 0; lv < L; ++lv) { free(off[lv]); free(items[lv]); }
+    free(off);
+    free(items);
+    return rc;
+}
+
+/* --------------------------------------------------- range query (A3) */
+
+/*
+ * Range search (§3.3, Algorithm 3), reading R19: at every level, from the top
+ * centroids down, keep the candidate centroids within the ball of squared
+ * radius r2 around q (||q - c||^2 <= r2) and descend into their children;
+ * return the points of the kept leaf clusters within the ball, ascending by
+ * (distance, id).  counts_out[q] receives each query's result count; when
+ * ids_out is not NULL the results are written query after query (the first
+ * counts_out[0] entries for query 0, ...), at most cap entries in all
+ * (MO_EINVAL if they do not fit; counts_out is filled either way).
+ */
+int32_t mo_range_query(const double *X, int64_t n, int32_t d, int32_t L,
+                       const int32_t *k_per_level, const double *const *C_levels,
+                       const int32_t *const *labels_levels, const double *Q, int64_t nq,
+                       double r2, int64_t *counts_out, int64_t cap, int64_t *ids_out,
+                       double *dists_out) {
+    if (L < 1 || d < 1) return MO_EINVAL;
+    int64_t **off = (int64_t **)calloc((size_t)L, sizeof(int64_t *));
+    int64_t **items = (int64_t **)calloc((size_t)L, sizeof(int64_t *));
+    mo_pair **res = (mo_pair **)calloc((size_t)(nq > 0 ? nq : 1), sizeof(mo_pair *));
+    if (!off || !items || !res) { free(off); free(items); free(res); return MO_ENOMEM; }
+    int32_t rc = MO_OK;
+    for (int32_t lv = 0; lv < L && rc == MO_OK; ++lv) {
+        int64_t n_below = lv == 0 ? n : (int64_t)k_per_level[lv - 1];
+        rc = member_lists(labels_levels[lv], n_below, k_per_level[lv], &off[lv], &items[lv]);
+    }
+    int64_t max_n = n;
+    for (int32_t lv = 0; lv < L; ++lv)
+        if ((int64_t)k_per_level[lv] > max_n) max_n = k_per_level[lv];
+    if (rc == MO_OK) {
+#pragma omp parallel
+        {
+            int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)max_n);
+            int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)max_n);
+            mo_pair *pts = (mo_pair *)malloc(sizeof(mo_pair) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 8)
+            for (int64_t qi = 0; qi < nq; ++qi) {
+                const double *q = Q + qi * (int64_t)d;
+                const int32_t top = L - 1;
+                int64_t nk = 0;
+                for (int64_t j = 0; j < k_per_level[top]; ++j)
+                    if (sqdist(q, C_levels[top] + j * (int64_t)d, d) <= r2) kept[nk++] = j;
+                for (int32_t lv = top; lv >= 1; --lv) {
+                    int64_t nn = 0;
+                    for (int64_t s = 0; s < nk; ++s)
+                        for (int64_t mm = off[lv][kept[s]]; mm < off[lv][kept[s] + 1]; ++mm) {
+                            const int64_t it = items[lv][mm];
+                            if (sqdist(q, C_levels[lv - 1] + it * (int64_t)d, d) <= r2)
+                                next[nn++] = it;
+                        }
+                    for (int64_t s = 0; s < nn; ++s) kept[s] = next[s];
+                    nk = nn;
+                }
+                int64_t np = 0;
+                for (int64_t s = 0; s < nk; ++s)
+                    for (int64_t mm = off[0][kept[s]]; mm < off[0][kept[s] + 1]; ++mm) {
+                        const int64_t it = items[0][mm];
+                        const double e = sqdist(q, X + it * (int64_t)d, d);
+                        if (e <= r2) { pts[np].d = e; pts[np].id = it; ++np; }
+                    }
+                qsort(pts, (size_t)np, sizeof(mo_pair), pair_cmp);
+                counts_out[qi] = np;
+                res[qi] = (mo_pair *)malloc(sizeof(mo_pair) * (size_t)(np > 0 ? np : 1));
+                if (res[qi]) memcpy(res[qi], pts, sizeof(mo_pair) * (size_t)np);
+            }
+            free(kept);
+            free(next);
+            free(pts);
+        }
+        int64_t total = 0;
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            if (!res[qi]) rc = MO_ENOMEM;
+            total += counts_out[qi];
+        }
+        if (rc == MO_OK && ids_out) {
+            if (total > cap) rc = MO_EINVAL;
+            else {
+                int64_t pos = 0;
+                for (int64_t qi = 0; qi < nq; ++qi)
+                    for (int64_t s = 0; s < counts_out[qi]; ++s, ++pos) {
+                        ids_out[pos] = res[qi][s].id;
+                        dists_out[pos] = res[qi][s].d;
+                    }
+            }
+        }
+    }
+    for (int64_t qi = 0; qi < nq; ++qi) free(res[qi]);
+    free(res);
+    for (int32_t lv = 0; lv < L; ++lv) { free(off[lv]); free(items[lv]); }
+    free(off);
+    free(items);
+    return rc;
+}
+
+/* ------------------------------------------ relocation (§4.1), reading R20 */
+
+/*
+ * One relocation pass of the grouped build (§4.1): every point is searched
+ * for by the greedy descent (one kept centroid per level, as the point query
+ * of §3.3); a point is missed when the reached leaf cluster is not its own.
+ * A missed point moves to the level-0 group of the reached leaf cluster
+ * (leaf / nc), in ascending point order, unless its own group would drop
+ * below nc points.  group0 [n] is updated in place; *moved receives the
+ * number of moves.  Returns the number of missed points (< 0 on error).
+ */
+int64_t mo_relocate(const double *X, int64_t n, int32_t d, int32_t L, const int32_t *k_per_level,
+                    const double *const *C_levels, const int32_t *const *labels_levels,
+                    int32_t nc, int32_t *group0, int64_t *moved) {
+    int32_t *leaf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *probes = (int32_t *)malloc(sizeof(int32_t) * (size_t)L);
+    if (!leaf || !probes) { free(leaf); free(probes); return MO_ENOMEM; }
+    for (int32_t lv = 0; lv < L; ++lv) probes[lv] = 1;
+    int32_t rc = mo_descend(n, d, L, k_per_level, C_levels, labels_levels, X, n, probes, leaf);
+    free(probes);
+    if (rc != MO_OK) { free(leaf); return rc; }
+    int64_t G = 0;
+    for (int64_t i = 0; i < n; ++i) if (group0[i] + 1 > G) G = group0[i] + 1;
+    int64_t *size = (int64_t *)calloc((size_t)(G > 0 ? G : 1), sizeof(int64_t));
+    if (!size) { free(leaf); return MO_ENOMEM; }
+    for (int64_t i = 0; i < n; ++i) size[group0[i]] += 1;
+    int64_t missed = 0, mv = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (leaf[i] == labels_levels[0][i]) continue;
+        ++missed;
+        const int32_t tgt = leaf[i] / nc, src = group0[i];
+        if (leaf[i] < 0 || tgt == src || size[src] <= nc) continue;
+        size[src] -= 1;
+        size[tgt] += 1;
+        group0[i] = tgt;
+        ++mv;
+    }
+    if (moved) *moved = mv;
+    free(size);
+    free(leaf);
+    return missed;
+}
