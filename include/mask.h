@@ -187,6 +187,75 @@ mask_status mask_index_load(const float *points, int64_t n, int32_t d, int32_t n
                             const int32_t *const *labels, mask_stream stream,
                             mask_index **out);
 
+/* ---- the grouped build of §3.1 and the point query of §3.3 ------------ */
+
+/*
+ * Level sizes of the grouped build (Algorithm 1 as printed): at each level the
+ * m items are split into floor(m / length_group) groups of nCentroids
+ * centroids each; the loop ends when that count drops below one.
+ *   sizes_out    host [MASK_MAX_LEVELS]: centroids per level, finest first.
+ *   n_levels_out number of levels (0 when n < length_group).
+ * Needs 1 <= n_centroids <= length_group (MASK_EINVAL otherwise).  Host only.
+ */
+mask_status mask_grouped_levels(int64_t n, int32_t length_group, int32_t n_centroids,
+                                int64_t *sizes_out, int32_t *n_levels_out);
+
+/*
+ * Grouped multilevel index (§3.1, Algorithm 1 as printed): at every level the
+ * items (points, then the centroids of the level below) are split at random
+ * into floor(m / length_group) groups whose sizes differ by at most one (a
+ * Fisher-Yates shuffle from the level's SplitMix64 stream, then consecutive
+ * parts, the first m mod G parts one larger); every group is clustered into
+ * n_centroids centroids by its own k-means (k-means++ seeding from the state
+ * level_state(seed, lv) ^ (0xD1B54A32D192ED03 * (group + 1)), then `iters`
+ * Lloyd iterations with the conventions of mask_build), over its items in
+ * ascending index.  Centroid j of group g is centroid g * n_centroids + j of
+ * the level.  Levels as mask_grouped_levels gives them (at most
+ * MASK_MAX_LEVELS, else MASK_EUNSUPPORTED).
+ *   points  [n x d] float32, n >= length_group.
+ *   group0  [n] int32 (host or device, may be NULL): the level-0 group of
+ *           every point, each in [0, n / length_group) and each group with
+ *           at least n_centroids points, instead of the random split (the
+ *           relocation of §4.1, see mask_relocate); levels above are split
+ *           at random as usual.
+ * A group's items (times the padded dimension) must fit shared memory (about
+ * 50,000 floats), else MASK_EINVAL.  The result is an ordinary index: query
+ * it with mask_query, mask_descend or mask_range_query.  Synchronises
+ * `stream`.
+ */
+mask_status mask_build_grouped(const float *points, int64_t n, int32_t d, int32_t length_group,
+                               int32_t n_centroids, int32_t iters, uint64_t seed,
+                               const int32_t *group0, mask_stream stream, mask_index **out);
+
+/*
+ * The descent of §3.3 (Algorithm 2 with p_l kept centroids per level) down to
+ * the leaf clusters, without the leaf scan: leaf_out [nq x probes[0]] int32
+ * receives the kept leaf clusters (level-0 centroid ids), nearest first, -1
+ * past the clusters that exist.  probes as for mask_query; all ones is the
+ * greedy descent of the paper's point query.  Synchronises `stream`.
+ */
+mask_status mask_descend(const mask_index *index, const float *queries, int64_t nq,
+                         const int32_t *probes, int32_t *leaf_out, mask_stream stream);
+
+/*
+ * One relocation pass of §4.1 on a grouped index of `points` (the same
+ * [n x d] points it was built from): every point is searched for by the
+ * greedy point query (one kept centroid per level); a point is missed when the
+ * leaf cluster reached is not its own.  A missed point moves to the level-0
+ * group of the reached cluster (its id / n_centroids), in ascending point
+ * order, unless its current group would fall below n_centroids points.
+ *   group0      HOST [n] int32, in/out: the level-0 groups the index was
+ *               built with; updated in place for the next mask_build_grouped.
+ *   missed_out  points the greedy point query missed (may be NULL).
+ *   moved_out   points moved (may be NULL).
+ * The level-0 group of point i in an index built by mask_build_grouped is
+ * labels_0[i] / n_centroids (mask_index_export_level, level 0).
+ * Synchronises `stream`.
+ */
+mask_status mask_relocate(const mask_index *index, const float *points, int32_t n_centroids,
+                          int32_t *group0, int64_t *missed_out, int64_t *moved_out,
+                          mask_stream stream);
+
 /* ---- k-means steps (the build's kernels, callable on their own) -------- */
 
 /*

@@ -8,6 +8,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "mask.h"
 
@@ -160,6 +161,26 @@ constexpr uint64_t kNoKey = ~0ull;
 // shared memory.
 constexpr int kCsrMaxDim = 40960;
 
+// ------------------------------------------------------- random numbers
+
+// R1: SplitMix64 (Steele, Lea & Flood 2014), host side: every draw of the
+// library is taken on the host from this generator.
+struct SplitMix64 {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * 0x1.0p-53; }
+};
+
+// The stream of level lv (0-based) under `seed`.
+inline uint64_t level_state(uint64_t seed, int lv) {
+    return seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(lv + 1));
+}
+
 // ------------------------------------------------------ kernel launchers
 
 // kmeans.cu
@@ -277,6 +298,15 @@ void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *lab
                bool seeded, cudaStream_t s);
 // Raises MASK_ETIMEOUT if a kernel of this plan hit a wait limit (synchronises).
 void tc_assign_check(TcAssign &p, cudaStream_t s);
+
+// grouped.cu -- the grouped build of Algorithm 1 (random split into groups of
+// lengthGroup items, nCentroids centroids per group by its own k-means)
+uint64_t group_state(uint64_t seed, int lv, int64_t g);
+std::vector<int64_t> grouped_sizes(int64_t n, int lg, int nc);
+std::vector<int32_t> split_groups(int64_t m, int64_t G, SplitMix64 &rng);
+void grouped_level(const float *X, int64_t m, int dp, const std::vector<int32_t> &group_of,
+                   int64_t G, int nc, int iters, uint64_t seed, int lv, float *C,
+                   int32_t *labels, cudaStream_t s);
 
 // query.cu -- keep the K nearest rows among the children of each query's parents
 struct ScanArgs {

@@ -28,22 +28,6 @@ void set_last_error(const std::string &msg) { g_err = msg; }
 
 namespace {
 
-// ----------------------------------------------------------- R1: SplitMix64
-
-struct SplitMix64 {
-    uint64_t s;
-    uint64_t next() {
-        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        return z ^ (z >> 31);
-    }
-    double uniform() { return (double)(next() >> 11) * 0x1.0p-53; }
-};
-
-uint64_t level_state(uint64_t seed, int lv) {
-    return seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(lv + 1));
-}
 
 // ------------------------------------------------------- pointer staging
 
@@ -506,12 +490,12 @@ void ensure_lowp(const mask_index &idx, bool fp8, cudaStream_t s) {
     MASK_CUDA(cudaStreamSynchronize(s));
 }
 
-void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
-                 const std::vector<int> &p, mask_precision prec, LeafMode mode, int64_t *ids,
-                 float *dists, cudaStream_t s) {
-    if (nq == 0) return;
+// The descent of Algorithm 2 down to the leaf clusters: sel[l] [nq x p_l]
+// receives each level's kept centroids (cluster ids), nearest first.
+void descend_levels(const mask_index &idx, const float *Qp, int64_t nq, const std::vector<int> &p,
+                    std::vector<Scratch<int32_t>> &sel, cudaStream_t s) {
     const int L = idx.L, dp = idx.dp;
-    std::vector<Scratch<int32_t>> sel((size_t)L);
+    sel.resize((size_t)L);
     for (int l = 0; l < L; ++l) sel[(size_t)l].alloc((size_t)nq * p[(size_t)l], s);
     ScanArgs a;
     a.Q = Qp;
@@ -535,6 +519,19 @@ void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
         b.out_ids32 = sel[(size_t)l - 1].get();
         scan_topk(b, s);
     }
+}
+
+void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
+                 const std::vector<int> &p, mask_precision prec, LeafMode mode, int64_t *ids,
+                 float *dists, cudaStream_t s) {
+    if (nq == 0) return;
+    const int dp = idx.dp;
+    std::vector<Scratch<int32_t>> sel;
+    descend_levels(idx, Qp, nq, p, sel, s);
+    ScanArgs a;
+    a.Q = Qp;
+    a.nq = nq;
+    a.dp = dp;
     const int k0 = idx.lv[0].k;
     if (prec != MASK_FP32) {
         // BF16 / FP8 distances for a max(4k, 16) shortlist, exact FP32 re-rank
@@ -1050,6 +1047,180 @@ mask_status mask_kmeans_update_csr(const int64_t *row_ptr, const int32_t *col, c
             cnt.finish(s);
         }
         MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+// ------------------------------------------------ grouped build (§3.1, A1)
+
+mask_status mask_grouped_levels(int64_t n, int32_t length_group, int32_t n_centroids,
+                                int64_t *sizes_out, int32_t *n_levels_out) {
+    return guard([&] {
+        MASK_REQUIRE(sizes_out && n_levels_out, "NULL output");
+        MASK_REQUIRE(length_group >= 1 && n_centroids >= 1 && n_centroids <= length_group,
+                     "need 1 <= nCentroids <= lengthGroup");
+        MASK_REQUIRE(n >= 0, "n must be >= 0");
+        const auto sizes = grouped_sizes(n, length_group, n_centroids);
+        MASK_REQUIRE((int)sizes.size() <= MASK_MAX_LEVELS, "more than MASK_MAX_LEVELS levels");
+        for (size_t l = 0; l < sizes.size(); ++l) sizes_out[l] = sizes[l];
+        *n_levels_out = (int32_t)sizes.size();
+    });
+}
+
+mask_status mask_build_grouped(const float *points, int64_t n, int32_t d, int32_t length_group,
+                               int32_t n_centroids, int32_t iters, uint64_t seed,
+                               const int32_t *group0, mask_stream stream, mask_index **out) {
+    return guard([&] {
+        MASK_REQUIRE(out != nullptr, "out is NULL");
+        MASK_REQUIRE(points != nullptr, "points is NULL");
+        MASK_REQUIRE(n >= 1 && n <= INT32_MAX, "n must be in [1, 2^31)");
+        MASK_REQUIRE(d >= 1, "d must be >= 1");
+        MASK_REQUIRE(length_group >= 1 && n_centroids >= 1 && n_centroids <= length_group,
+                     "need 1 <= nCentroids <= lengthGroup");
+        MASK_REQUIRE(n >= length_group, "fewer points than lengthGroup: no level to build");
+        MASK_REQUIRE(iters >= 0, "iters must be >= 0");
+        const auto sizes = grouped_sizes(n, length_group, n_centroids);
+        const int L = (int)sizes.size();
+        if (L > MASK_MAX_LEVELS) fail(MASK_EUNSUPPORTED, "more than MASK_MAX_LEVELS levels");
+        std::vector<int32_t> kpl((size_t)L);
+        for (int l = 0; l < L; ++l) {
+            MASK_REQUIRE(sizes[(size_t)l] <= INT32_MAX, "too many centroids at one level");
+            kpl[(size_t)l] = (int32_t)sizes[(size_t)l];
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        const int64_t G0 = n / length_group;
+        std::vector<int32_t> g0;
+        if (group0) {
+            g0.resize((size_t)n);
+            if (on_device(group0)) {
+                MASK_CUDA(cudaMemcpyAsync(g0.data(), group0, sizeof(int32_t) * n,
+                                          cudaMemcpyDeviceToHost, s));
+                MASK_CUDA(cudaStreamSynchronize(s));
+            } else {
+                std::copy(group0, group0 + n, g0.begin());
+            }
+            for (int32_t v : g0) MASK_REQUIRE(v >= 0 && v < G0, "group0 value outside [0, n / lengthGroup)");
+        }
+        auto idx = new_index(n, d, kpl.data(), L);
+        idx->iters = iters;
+        In<float> P(points, (size_t)n * d, s);
+        Scratch<float> Xp((size_t)n * idx->dp, s);
+        pad_rows(P.p, n, d, Xp.get(), idx->dp, s);
+        const float *in = Xp.get();
+        int64_t m = n;
+        for (int lv = 0; lv < L; ++lv) {
+            auto &Lv = idx->lv[(size_t)lv];
+            const int64_t G = m / length_group;
+            std::vector<int32_t> group_of;
+            if (lv == 0 && group0) {
+                group_of = g0;
+            } else {
+                SplitMix64 rng{level_state(seed, lv)};
+                group_of = split_groups(m, G, rng);
+            }
+            Lv.C.alloc((size_t)Lv.k * idx->dp);
+            Lv.labels.alloc((size_t)m);
+            Lv.off.alloc((size_t)Lv.k + 1);
+            grouped_level(in, m, idx->dp, group_of, G, n_centroids, iters, seed, lv, Lv.C.get(),
+                          Lv.labels.get(), s);
+            label_sort(Lv.labels.get(), m, Lv.k, Lv.off.get(), below_ids(*idx, lv, m), s);
+            in = Lv.C.get();
+            m = Lv.k;
+        }
+        finish_layout(*idx, Xp.get(), s);
+        MASK_CUDA(cudaStreamSynchronize(s));
+        *out = idx.release();
+    });
+}
+
+// ------------------------------------------------- descent (§3.3, A2)
+
+mask_status mask_descend(const mask_index *index, const float *queries, int64_t nq,
+                         const int32_t *probes, int32_t *leaf_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(index != nullptr, "index is NULL");
+        MASK_REQUIRE(nq >= 0, "nq must be >= 0");
+        MASK_REQUIRE(probes != nullptr, "probes is NULL");
+        MASK_REQUIRE(current_device() == index->device, "index lives on another device");
+        MASK_REQUIRE(!index->sparse, "index built from CSR points");
+        if (nq == 0) return;
+        MASK_REQUIRE(queries && leaf_out, "NULL queries or leaf_out");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int L = index->L, dp = index->dp;
+        std::vector<int> p((size_t)L);
+        for (int l = 0; l < L; ++l) {
+            MASK_REQUIRE(probes[l] >= 1, "probes must be >= 1");
+            p[(size_t)l] = std::min<int>(probes[l], index->lv[(size_t)l].k);
+        }
+        In<float> Qin(queries, (size_t)nq * index->d, s);
+        Scratch<float> Qp((size_t)nq * dp, s);
+        pad_rows(Qin.p, nq, index->d, Qp.get(), dp, s);
+        std::vector<Scratch<int32_t>> sel;
+        descend_levels(*index, Qp.get(), nq, p, sel, s);
+        Out<int32_t> lo(leaf_out, (size_t)nq * probes[0], s);
+        if (p[0] == probes[0]) {
+            MASK_CUDA(cudaMemcpyAsync(lo.p, sel[0].get(), sizeof(int32_t) * nq * p[0],
+                                      cudaMemcpyDeviceToDevice, s));
+        } else {
+            // more probes than leaf clusters: pad each row with -1
+            MASK_CUDA(cudaMemsetAsync(lo.p, 0xFF, sizeof(int32_t) * nq * probes[0], s));
+            MASK_CUDA(cudaMemcpy2DAsync(lo.p, sizeof(int32_t) * probes[0], sel[0].get(),
+                                        sizeof(int32_t) * p[0], sizeof(int32_t) * p[0], nq,
+                                        cudaMemcpyDeviceToDevice, s));
+        }
+        lo.finish(s);
+        MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+// -------------------------------------------- relocation (§4.1), R20
+
+mask_status mask_relocate(const mask_index *index, const float *points, int32_t n_centroids,
+                          int32_t *group0, int64_t *missed_out, int64_t *moved_out,
+                          mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(index != nullptr && points != nullptr && group0 != nullptr, "NULL argument");
+        MASK_REQUIRE(!on_device(group0), "group0 must be host memory");
+        MASK_REQUIRE(n_centroids >= 1, "n_centroids must be >= 1");
+        MASK_REQUIRE(current_device() == index->device, "index lives on another device");
+        MASK_REQUIRE(!index->sparse, "index built from CSR points");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int64_t n = index->n;
+        std::vector<int32_t> leaf((size_t)n), own((size_t)n);
+        // the greedy point query of every indexed point (one kept centroid per level)
+        {
+            In<float> P(points, (size_t)n * index->d, s);
+            Scratch<float> Qp((size_t)n * index->dp, s);
+            pad_rows(P.p, n, index->d, Qp.get(), index->dp, s);
+            std::vector<int> p((size_t)index->L, 1);
+            std::vector<Scratch<int32_t>> sel;
+            descend_levels(*index, Qp.get(), n, p, sel, s);
+            MASK_CUDA(cudaMemcpyAsync(leaf.data(), sel[0].get(), sizeof(int32_t) * n,
+                                      cudaMemcpyDeviceToHost, s));
+            MASK_CUDA(cudaMemcpyAsync(own.data(), index->lv[0].labels.get(), sizeof(int32_t) * n,
+                                      cudaMemcpyDeviceToHost, s));
+            MASK_CUDA(cudaStreamSynchronize(s));
+        }
+        int64_t G = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            MASK_REQUIRE(group0[i] >= 0, "group0 value < 0");
+            G = std::max<int64_t>(G, (int64_t)group0[i] + 1);
+        }
+        std::vector<int64_t> size((size_t)G, 0);
+        for (int64_t i = 0; i < n; ++i) size[(size_t)group0[i]] += 1;
+        int64_t missed = 0, moved = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (leaf[(size_t)i] == own[(size_t)i]) continue;
+            ++missed;
+            const int64_t tgt = leaf[(size_t)i] / n_centroids, src = group0[i];
+            if (leaf[(size_t)i] < 0 || tgt == src || tgt >= G || size[(size_t)src] <= n_centroids)
+                continue;
+            size[(size_t)src] -= 1;
+            size[(size_t)tgt] += 1;
+            group0[i] = (int32_t)tgt;
+            ++moved;
+        }
+        if (missed_out) *missed_out = missed;
+        if (moved_out) *moved_out = moved;
     });
 }
 

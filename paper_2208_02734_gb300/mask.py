@@ -34,7 +34,8 @@ EXPORTED = [
     "mask_kmeans_assign_noalloc", "mask_kmeanspp_csr", "mask_kmeans_assign_csr",
     "mask_kmeans_update_csr", "mask_server_open", "mask_server_submit", "mask_server_poll",
     "mask_server_wait", "mask_server_stats", "mask_server_close", "mask_test_bounded_wait",
-    "mask_test_alloc_count",
+    "mask_test_alloc_count", "mask_grouped_levels", "mask_build_grouped", "mask_descend",
+    "mask_relocate",
 ]
 
 
@@ -104,6 +105,11 @@ def load(build_if_stale: bool = True):
                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mask_launch_count": (C.c_int64, []),
             "mask_test_alloc_count": (C.c_int64, []),
+            "mask_grouped_levels": (C.c_int, [_i64, _i32, _i32, _vp, _vp]),
+            "mask_build_grouped": (C.c_int, [_vp, _i64, _i32, _i32, _i32, _i32, _u64, _vp, _vp,
+                                             _vp]),
+            "mask_descend": (C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+            "mask_relocate": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
             "mask_test_bounded_wait": (C.c_int, [_i32, _i32, _vp]),
             "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
             "mask_kmeanspp_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _u64, _i32, _vp,
@@ -321,6 +327,46 @@ def mask_index_load(points, centroids, labels, stream=None) -> Index:
     _check(load().mask_index_load(px, n, d, L, pk, cptr, lptr, _stream(X, stream),
                                   C.byref(out)), "mask_index_load")
     return Index(out.value)
+
+
+def mask_grouped_levels(n: int, length_group: int, n_centroids: int):
+    sizes = np.zeros(MASK_MAX_LEVELS, dtype=np.int64)
+    L = C.c_int32()
+    _check(load().mask_grouped_levels(n, length_group, n_centroids, sizes.ctypes.data,
+                                      C.byref(L)), "mask_grouped_levels")
+    return [int(v) for v in sizes[:L.value]]
+
+
+def mask_build_grouped(points, length_group: int, n_centroids: int, iters: int, seed: int,
+                       group0=None, stream=None) -> Index:
+    X, px = _arr(points, "float32")
+    n, d = X.shape
+    g0, pg = (None, None) if group0 is None else _arr(group0, "int32")
+    out = C.c_void_p()
+    _check(load().mask_build_grouped(px, n, d, length_group, n_centroids, iters,
+                                     seed & 0xFFFFFFFFFFFFFFFF, pg, _stream(X, stream),
+                                     C.byref(out)), "mask_build_grouped")
+    return Index(out.value)
+
+
+def mask_descend(index, queries, probes, stream=None):
+    Q, pq = _arr(queries, "float32")
+    nq = Q.shape[0]
+    pr, pp = _host_i32(probes)
+    leaf, pl = _empty_like_kind(Q, (nq, int(pr[0])), "int32")
+    _check(load().mask_descend(_handle(index), pq, nq, pp, pl, _stream(Q, stream)),
+           "mask_descend")
+    return leaf
+
+
+def mask_relocate(index, points, n_centroids: int, group0, stream=None):
+    """One relocation pass (§4.1): returns (missed, moved, new group0)."""
+    X, px = _arr(points, "float32")
+    g = np.array(np.asarray(group0), dtype=np.int32, copy=True)
+    missed, moved = C.c_int64(0), C.c_int64(0)
+    _check(load().mask_relocate(_handle(index), px, n_centroids, g.ctypes.data, C.byref(missed),
+                                C.byref(moved), _stream(X, stream)), "mask_relocate")
+    return int(missed.value), int(moved.value), g
 
 
 def mask_kmeanspp(X, k: int, seed: int, level: int = 0, stream=None):

@@ -16,6 +16,9 @@ for them with the shapes and distributions the workloads below state:
 * ``sparse_tfidf_like``  - CSR rows with lognormal row lengths, Zipf column
   ids and L2-normalised |N(0,1)| values (the 10^6 x 20,000 sparse workload, a
   stand-in for the shape of a TF-IDF term-document matrix, §4.3).
+* ``gaussian_clouds_2d`` - 8 Gaussian clouds in R^2 (the synthetic datasets of
+  §4.2: centres evenly on a circle, the radius setting how much adjacent
+  clouds overlap).
 
 Every generator is a pure function of its seed (numpy PCG64).
 """
@@ -29,7 +32,15 @@ __all__ = [
     "AnisotropicMixture",
     "sparse_tfidf_like",
     "CSR",
+    "gaussian_clouds_2d",
+    "CLOUD_RADIUS",
 ]
+
+# Circle radius of the cloud centres for the three datasets of §4.2 (sigma 1):
+# adjacent centres are 2 R sin(pi/8) = 0.765 R apart, i.e. 7.7, 3.1 and 1.5
+# standard deviations: clearly separated (GNO), moderate overlap (GMO),
+# strong overlap (GRO).  The paper does not state its cloud parameters.
+CLOUD_RADIUS = {"GNO": 10.0, "GMO": 4.0, "GRO": 2.0}
 
 
 class IsotropicMixture:
@@ -225,3 +236,17 @@ def sparse_tfidf_like(n: int, d: int, nnz_mean: float = 60.0,
     sq = np.add.reduceat(val * val, row_ptr[:-1]) if len(val) else np.zeros(n)
     val = val / np.sqrt(np.repeat(sq, m))
     return CSR(row_ptr, col, val.astype(np.float32), d)
+
+
+def gaussian_clouds_2d(npc: int, radius: float, sigma: float = 1.0, seed: int = 0,
+                       return_cloud: bool = False):
+    """8 isotropic Gaussian clouds in R^2 with ``npc`` points each, centres at
+    angles 2 pi c / 8 on a circle of the given radius, cloud c's points
+    contiguous (rows c * npc ...).  Returns float32 points (and the cloud of
+    every point)."""
+    rng = np.random.default_rng([seed, 0xC10D])
+    ang = np.arange(8) * 2.0 * np.pi / 8.0
+    centres = np.stack([np.cos(ang), np.sin(ang)], 1) * radius
+    cloud = np.repeat(np.arange(8), npc)
+    x = (centres[cloud] + sigma * rng.standard_normal(size=(8 * npc, 2))).astype(np.float32)
+    return (x, cloud) if return_cloud else x
