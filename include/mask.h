@@ -256,6 +256,39 @@ mask_status mask_relocate(const mask_index *index, const float *points, int32_t 
                           int32_t *group0, int64_t *missed_out, int64_t *moved_out,
                           mask_stream stream);
 
+/*
+ * Range search (§3.3, Algorithm 3): from the top level down, the candidate
+ * centroids within distance `radius` of the query are kept and their
+ * children become the next candidates; the result is the points of the kept
+ * leaf clusters within `radius`, ascending by (squared distance, id).  A
+ * point whose ancestors lie outside the ball is not found: the search is
+ * approximate, as the paper's.  Distances are FP32 sums of squared
+ * differences and are returned squared.
+ *   counts_out [nq] int64: results per query (always written).
+ *   ids_out / dists_out: [capacity] int64 / float32 (may be NULL: counts
+ *   only); results are written query after query (the first counts_out[0]
+ *   entries belong to query 0, ...).  When their total exceeds `capacity`
+ *   nothing else is written and MASK_EINVAL is returned with counts_out
+ *   filled, so the caller can retry with a larger buffer.
+ * Synchronises `stream`.
+ */
+mask_status mask_range_query(const mask_index *index, const float *queries, int64_t nq,
+                             float radius, int64_t *counts_out, int64_t capacity,
+                             int64_t *ids_out, float *dists_out, mask_stream stream);
+
+/*
+ * Insertion (§3.3, last paragraph): each new point descends greedily (one
+ * kept centroid per level) and joins the leaf cluster it reaches; the
+ * centroids are not changed.  The new points get the ids index->n .. n +
+ * n_new - 1 in order; leaf_out [n_new] int32 (may be NULL) receives the leaf
+ * cluster each joined.  Dense indexes only (MASK_EUNSUPPORTED for CSR).  The
+ * BF16/FP8 copies of the points are dropped and made again on their next use.
+ * Not safe while a server or another call uses the index.  Synchronises
+ * `stream`.
+ */
+mask_status mask_insert(mask_index *index, const float *points, int64_t n_new,
+                        int32_t *leaf_out, mask_stream stream);
+
 /* ---- k-means steps (the build's kernels, callable on their own) -------- */
 
 /*

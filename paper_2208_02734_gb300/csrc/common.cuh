@@ -308,6 +308,14 @@ void grouped_level(const float *X, int64_t m, int dp, const std::vector<int32_t>
                    int64_t G, int nc, int iters, uint64_t seed, int lv, float *C,
                    int32_t *labels, cudaStream_t s);
 
+// range.cu -- range search (Algorithm 3) over a dense index: counts_out
+// (host) [nq] = results per query; when ids_out is given and the total fits
+// `capacity`, the results (ascending by (distance, id), query after query)
+// go to ids_out / dists_out (device).  Returns the total.
+int64_t range_search(const mask_index &idx, const float *Qp, int64_t nq, float radius,
+                     int64_t *counts_out, int64_t capacity, int64_t *ids_out, float *dists_out,
+                     cudaStream_t s);
+
 // query.cu -- keep the K nearest rows among the children of each query's parents
 struct ScanArgs {
     const float *R = nullptr;     // [M x dp] rows (parent-major)

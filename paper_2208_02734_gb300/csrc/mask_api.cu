@@ -490,6 +490,14 @@ void ensure_lowp(const mask_index &idx, bool fp8, cudaStream_t s) {
     MASK_CUDA(cudaStreamSynchronize(s));
 }
 
+// inv[perm[i]] = i for a permutation of [0, n).
+__global__ void invert_perm_kernel(const int32_t *__restrict__ perm, int64_t n,
+                                   int32_t *__restrict__ inv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[i]] = (int32_t)i;
+}
+
 // The descent of Algorithm 2 down to the leaf clusters: sel[l] [nq x p_l]
 // receives each level's kept centroids (cluster ids), nearest first.
 void descend_levels(const mask_index &idx, const float *Qp, int64_t nq, const std::vector<int> &p,
@@ -1221,6 +1229,115 @@ mask_status mask_relocate(const mask_index *index, const float *points, int32_t 
         }
         if (missed_out) *missed_out = missed;
         if (moved_out) *moved_out = moved;
+    });
+}
+
+// ------------------------------------------------ range search (§3.3, A3)
+
+mask_status mask_range_query(const mask_index *index, const float *queries, int64_t nq,
+                             float radius, int64_t *counts_out, int64_t capacity,
+                             int64_t *ids_out, float *dists_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(index != nullptr, "index is NULL");
+        MASK_REQUIRE(nq >= 0 && nq <= INT32_MAX, "nq must be in [0, 2^31)");
+        MASK_REQUIRE(radius >= 0.f && std::isfinite(radius), "radius must be finite and >= 0");
+        MASK_REQUIRE(capacity >= 0, "capacity must be >= 0");
+        MASK_REQUIRE(current_device() == index->device, "index lives on another device");
+        MASK_REQUIRE(!index->sparse, "index built from CSR points");
+        if (nq == 0) return;
+        MASK_REQUIRE(queries && counts_out, "NULL queries or counts_out");
+        cudaStream_t s = (cudaStream_t)stream;
+        In<float> Qin(queries, (size_t)nq * index->d, s);
+        Scratch<float> Qp((size_t)nq * index->dp, s);
+        pad_rows(Qin.p, nq, index->d, Qp.get(), index->dp, s);
+        std::vector<int64_t> counts((size_t)nq);
+        Out<int64_t> ids(ids_out, (size_t)(ids_out ? capacity : 0), s);
+        Out<float> dd(dists_out, (size_t)(dists_out ? capacity : 0), s);
+        const int64_t total = range_search(*index, Qp.get(), nq, radius, counts.data(), capacity,
+                                           ids_out ? ids.p : nullptr, dists_out ? dd.p : nullptr,
+                                           s);
+        copy_out_host_vec(counts, counts_out, s);
+        if (ids_out && total > capacity)
+            fail(MASK_EINVAL, "capacity " + std::to_string(capacity) + " < " +
+                                  std::to_string(total) + " results (counts_out is filled)");
+        if (ids_out) {
+            // only the first `total` entries are results
+            if (ids.host)
+                MASK_CUDA(cudaMemcpyAsync(ids_out, ids.p, sizeof(int64_t) * total,
+                                          cudaMemcpyDeviceToHost, s));
+            if (dists_out && dd.host)
+                MASK_CUDA(cudaMemcpyAsync(dists_out, dd.p, sizeof(float) * total,
+                                          cudaMemcpyDeviceToHost, s));
+        }
+        MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+// ---------------------------------------------- insertion (§3.3, end)
+
+mask_status mask_insert(mask_index *index, const float *points, int64_t n_new,
+                        int32_t *leaf_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(index != nullptr, "index is NULL");
+        MASK_REQUIRE(n_new >= 0, "n_new must be >= 0");
+        MASK_REQUIRE(current_device() == index->device, "index lives on another device");
+        if (index->sparse) fail(MASK_EUNSUPPORTED, "insertion into a CSR index is not built");
+        if (n_new == 0) return;
+        MASK_REQUIRE(points != nullptr, "points is NULL");
+        MASK_REQUIRE(index->n + n_new <= INT32_MAX, "index would exceed 2^31 points");
+        cudaStream_t s = (cudaStream_t)stream;
+        mask_index &idx = *index;
+        const int dp = idx.dp;
+        const int64_t n0 = idx.n, n1 = n0 + n_new;
+        auto &L0 = idx.lv[0];
+        // the greedy descent of each new point (one kept centroid per level)
+        In<float> P(points, (size_t)n_new * idx.d, s);
+        Scratch<float> Xall((size_t)n1 * dp, s);
+        pad_rows(P.p, n_new, idx.d, Xall.get() + (size_t)n0 * dp, dp, s);
+        std::vector<int> p((size_t)idx.L, 1);
+        std::vector<Scratch<int32_t>> sel;
+        descend_levels(idx, Xall.get() + (size_t)n0 * dp, n_new, p, sel, s);
+        // the points in id order (old ones back out of the cluster-major
+        // layout), then every point's leaf cluster: the old labels and the
+        // reached clusters of the new points
+        Scratch<int32_t> inv((size_t)n0, s);
+        invert_perm_kernel<<<(unsigned)std::min<int64_t>((n0 + 255) / 256, 152 * 16), 256, 0, s>>>(
+            idx.xids.get(), n0, inv.get());
+        MASK_LAUNCHED("invert_perm");
+        gather_rows<int32_t>(idx.Xs.get(), dp, inv.get(), n0, Xall.get(), s);
+        DevArray<int32_t> labels;
+        labels.alloc((size_t)n1);
+        MASK_CUDA(cudaMemcpyAsync(labels.get(), L0.labels.get(), sizeof(int32_t) * n0,
+                                  cudaMemcpyDeviceToDevice, s));
+        MASK_CUDA(cudaMemcpyAsync(labels.get() + n0, sel[0].get(), sizeof(int32_t) * n_new,
+                                  cudaMemcpyDeviceToDevice, s));
+        if (leaf_out) {
+            Out<int32_t> lo(leaf_out, (size_t)n_new, s);
+            MASK_CUDA(cudaMemcpyAsync(lo.p, sel[0].get(), sizeof(int32_t) * n_new,
+                                      cudaMemcpyDeviceToDevice, s));
+            lo.finish(s);
+        }
+        // the new leaf layout: membership lists, points cluster-major, norms;
+        // the centroids stay as they are (the paper assigns the point to the
+        // reached group)
+        L0.labels = std::move(labels);
+        idx.xids.alloc((size_t)n1);
+        label_sort(L0.labels.get(), n1, L0.k, L0.off.get(), idx.xids.get(), s);
+        idx.n = n1;
+        idx.Xs.alloc((size_t)n1 * dp);
+        gather_rows<int32_t>(Xall.get(), dp, idx.xids.get(), n1, idx.Xs.get(), s);
+        idx.xn.alloc((size_t)n1);
+        row_sqnorm(idx.Xs.get(), n1, dp, idx.xn.get(), s);
+        {
+            // the low-precision copies describe the old layout: made again on use
+            std::lock_guard<std::mutex> lk(idx.lp_mu);
+            for (int i = 0; i < 2; ++i) {
+                idx.Xlp[i].release();
+                idx.xn_lp[i].release();
+            }
+            idx.xscale_fp8.release();
+        }
+        MASK_CUDA(cudaStreamSynchronize(s));
     });
 }
 

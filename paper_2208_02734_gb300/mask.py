@@ -35,7 +35,7 @@ EXPORTED = [
     "mask_kmeans_update_csr", "mask_server_open", "mask_server_submit", "mask_server_poll",
     "mask_server_wait", "mask_server_stats", "mask_server_close", "mask_test_bounded_wait",
     "mask_test_alloc_count", "mask_grouped_levels", "mask_build_grouped", "mask_descend",
-    "mask_relocate",
+    "mask_relocate", "mask_range_query", "mask_insert",
 ]
 
 
@@ -110,6 +110,8 @@ def load(build_if_stale: bool = True):
                                              _vp]),
             "mask_descend": (C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
             "mask_relocate": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+            "mask_range_query": (C.c_int, [_vp, _vp, _i64, C.c_float, _vp, _i64, _vp, _vp, _vp]),
+            "mask_insert": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
             "mask_test_bounded_wait": (C.c_int, [_i32, _i32, _vp]),
             "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
             "mask_kmeanspp_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _u64, _i32, _vp,
@@ -367,6 +369,35 @@ def mask_relocate(index, points, n_centroids: int, group0, stream=None):
     _check(load().mask_relocate(_handle(index), px, n_centroids, g.ctypes.data, C.byref(missed),
                                 C.byref(moved), _stream(X, stream)), "mask_relocate")
     return int(missed.value), int(moved.value), g
+
+
+def mask_range_query(index, queries, radius: float, stream=None):
+    """Range search (Algorithm 3): per query, (ids, squared distances) of the
+    points found within `radius`, ascending.  Sizes the output with a first
+    counting call, then fills it."""
+    Q, pq = _arr(queries, "float32")
+    nq = Q.shape[0]
+    counts = np.zeros(nq, dtype=np.int64)
+    lib = load()
+    st = _stream(Q, stream)
+    _check(lib.mask_range_query(_handle(index), pq, nq, float(radius), counts.ctypes.data, 0,
+                                None, None, st), "mask_range_query")
+    total = int(counts.sum())
+    ids, pids = _empty_like_kind(Q, (max(total, 1),), "int64")
+    dists, pd = _empty_like_kind(Q, (max(total, 1),), "float32")
+    _check(lib.mask_range_query(_handle(index), pq, nq, float(radius), counts.ctypes.data,
+                                total, pids, pd, st), "mask_range_query")
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    return [(ids[offs[q]:offs[q + 1]], dists[offs[q]:offs[q + 1]]) for q in range(nq)]
+
+
+def mask_insert(index, points, stream=None):
+    """Insert points (§3.3): returns the leaf cluster each new point joined."""
+    X, px = _arr(points, "float32")
+    n_new = X.shape[0]
+    leaf, pl = _empty_like_kind(X, (n_new,), "int32")
+    _check(load().mask_insert(_handle(index), px, n_new, pl, _stream(X, stream)), "mask_insert")
+    return leaf
 
 
 def mask_kmeanspp(X, k: int, seed: int, level: int = 0, stream=None):

@@ -122,3 +122,93 @@ def test_grouped_build_rejects_bad_parameters():
             M.mask_build_grouped(X, lg, nc, 3, 0)
     with pytest.raises(M.MaskError):   # group0 outside [0, n / lengthGroup)
         M.mask_build_grouped(X, 5, 2, 3, 0, group0=np.full(10, 2, np.int32))
+
+
+# ------------------------------------------------------ range search (A3)
+
+def _radius_clear_of_ties(index_o, Q, r):
+    """Nudge r so that no centroid of any level and no point lies within a
+    relative 2e-6 of the ball's boundary for any query (well beyond the FP32
+    rounding of a 2-D squared distance, so FP32 and FP64 decide every
+    membership alike)."""
+    rows = [index_o.X] + list(index_o.centroids)
+    for _ in range(50):
+        r2, ok = r * r, True
+        for R in rows:
+            d = ((R[None, :, :] - Q[:, None, :]) ** 2).sum(-1)
+            if np.any(np.abs(d - r2) <= 2e-6 * r2):
+                ok = False
+                break
+        if ok:
+            return r
+        r *= 1.0137
+    raise AssertionError("no tie-free radius found")
+
+
+@pytest.mark.parametrize("build", ["global", "grouped"])
+def test_range_query_matches_oracle(build):
+    X = clouds(150, 6.0, 1.2, seed=7).astype(np.float32)
+    Q = clouds(6, 6.0, 1.2, seed=8).astype(np.float32)
+    if build == "global":
+        ref = O.build(X, [120, 12], 6, 0)
+    else:
+        ref = O.build_grouped(X, 16, 8, 6, 1)
+    cs = [c.astype(np.float32) for c in ref.centroids]
+    oref = O.Index(X, [c.astype(np.float64) for c in cs], ref.labels)
+    loaded = M.mask_index_load(cuda(X), [cuda(c) for c in cs], [cuda(lb) for lb in ref.labels])
+    for r in (0.7, 2.0, 5.0, 40.0):
+        r = _radius_clear_of_ties(oref, Q.astype(np.float64), r)
+        got = M.mask_range_query(loaded, cuda(Q), r)
+        want = O.range_query(oref, Q, r)
+        for q in range(len(Q)):
+            gi, gd = arr(got[q][0]), arr(got[q][1])
+            wi, wd = want[q]
+            # the same points (the radius is clear of ties); the order is by
+            # (distance, id) on each side, so it may differ only where FP32
+            # and FP64 distances of two points nearly tie
+            assert sorted(gi.tolist()) == sorted(wi.tolist()), (r, q)
+            assert np.all(np.diff(gd) >= 0)
+            exact = O.sqdist_rows(X, gi, Q[q])
+            assert np.allclose(gd, exact, rtol=RTOL, atol=1e-6)
+            for a in np.flatnonzero(gi != wi):
+                da, db = O.sqdist_rows(X, [gi[a], wi[a]], Q[q])
+                assert abs(da - db) <= RTOL * max(da, db) + 1e-12, (r, q, a)
+    # host buffers, an empty batch and a too-small buffer
+    got_h = M.mask_range_query(loaded, Q, 40.0)
+    assert sum(len(i) for i, _ in got_h) == sum(len(i) for i, _ in O.range_query(oref, Q, 40.0))
+    assert M.mask_range_query(loaded, Q[:0], 1.0) == []
+    counts = np.zeros(len(Q), np.int64)
+    st = M.load().mask_range_query(loaded.handle, Q.ctypes.data, len(Q), 40.0, counts.ctypes.data,
+                                   1, np.zeros(1, np.int64).ctypes.data, None, None)
+    assert st == M.MASK_EINVAL and counts.sum() > 1
+    loaded.free()
+
+
+# ---------------------------------------------------------- insertion
+
+def test_insertion_joins_the_reached_leaf_and_queries_see_it():
+    X = clouds(150, 6.0, 1.2, seed=9).astype(np.float32)
+    n0 = 1000
+    idx = M.mask_build(cuda(X[:n0]), [100, 10], 6, seed=0)
+    levels = [M.mask_index_export_level(idx, lv) for lv in range(2)]
+    cs = [arr(e["centroids"]).astype(np.float64) for e in levels]
+    labs = [arr(e["labels"]) for e in levels]
+    leaf = arr(M.mask_insert(idx, cuda(X[n0:])))
+    assert idx.info.n == len(X)
+    oref0 = O.Index(X[:n0], cs, labs)
+    want = O.descend(oref0, X[n0:], [1, 1])[:, 0]
+    _, _, clear = oref0.query(X[n0:], 1, [1, 1])
+    assert np.array_equal(leaf[clear], want[clear])
+    # the updated index is the oracle's index with the new labels appended
+    lab0 = arr(M.mask_index_export_level(idx, 0)["labels"])
+    assert np.array_equal(lab0[:n0], labs[0]) and np.array_equal(lab0[n0:], leaf)
+    oref = O.Index(X, cs, [lab0, labs[1]])
+    Q = clouds(10, 6.0, 1.2, seed=10).astype(np.float32)
+    ids, d = M.mask_query(idx, cuda(Q), 5, [4, 3])
+    ids_o, d_o, clear = oref.query(Q, 5, [4, 3])
+    from parity_util import check_knn
+    check_knn(X, Q, arr(ids), arr(d), ids_o, d_o, clear)
+    # each new point finds itself (it sits in the leaf it joined)
+    ids_s, d_s = M.mask_query(idx, cuda(X[n0:]), 1, [1, 1])
+    assert np.all(arr(d_s)[:, 0] == 0.0)
+    idx.free()
