@@ -772,6 +772,105 @@ def run_serving(args, w, wname):
     return 0
 
 
+# ------------------------------------------- the paper's point-query experiment
+
+# §4.2: exhaustive point query of every indexed point on 8 Gaussian clouds in
+# R^2, grouped build (Algorithm 1) with lengthGroup 16 and nCentroids 8.
+POINTQ_SIZES = (200, 1_000, 10_000, 100_000)      # points per cloud (Tables 3-4)
+POINTQ_ORACLE_MAX = 10_000                        # the oracle runs up to 80,000 points
+POINTQ_LG, POINTQ_NC, POINTQ_ITERS = 16, 8, 10
+POINTQ_RELOCATIONS = 8                            # Table 2: iterations 0..8 on GRO
+
+
+def point_query_errors(ids, cloud):
+    """(self miss rate, class error) of the exhaustive point query: the
+    returned nearest point is not the query point itself / lies in another
+    cloud."""
+    ids = np.asarray(ids).reshape(-1)
+    n = len(cloud)
+    miss = float(np.mean(ids != np.arange(n)))
+    cls = float(np.mean((ids < 0) | (cloud[np.maximum(ids, 0)] != cloud)))
+    return miss, cls
+
+
+def point_query_experiment(dev):
+    """GPU grouped build + exhaustive point query (greedy descent, k = 1) for
+    GNO / GMO clouds at every size, and the relocation iterations of §4.1 on
+    GRO (1,600 points)."""
+    import torch
+    from paper_2208_02734_gb300 import mask as M
+    from paper_2208_02734_gb300 import synth
+    rows = []
+    for name in ("GNO", "GMO"):
+        for npc in POINTQ_SIZES:
+            X, cloud = synth.gaussian_clouds_2d(npc, synth.CLOUD_RADIUS[name], 1.0, seed=0,
+                                                return_cloud=True)
+            n = len(X)
+            Xd = torch.from_numpy(X).to(dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            idx = M.mask_build_grouped(Xd, POINTQ_LG, POINTQ_NC, POINTQ_ITERS, 0)
+            t1 = time.perf_counter()
+            L = idx.info.n_levels
+            ids, _ = M.mask_query(idx, Xd, 1, [1] * L)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            miss, cls = point_query_errors(ids.cpu().numpy(), cloud)
+            row = {"dataset": name, "n": n, "depth": L, "gpu_build_s": t1 - t0,
+                   "gpu_search_s": t2 - t1, "gpu_queries_per_s": n / (t2 - t1),
+                   "gpu_self_miss": miss, "gpu_class_error": cls}
+            idx.free()
+            rows.append(row)
+            log(f"[pointq] {name} n={n}: depth {L}, miss {miss:.4f}, class error {cls:.4f}")
+    # relocation iterations (§4.1, Table 2) on GRO with 200 points per cloud
+    X, cloud = synth.gaussian_clouds_2d(200, synth.CLOUD_RADIUS["GRO"], 1.0, seed=0,
+                                        return_cloud=True)
+    Xd = torch.from_numpy(X).to(dev)
+    g0, trace = None, []
+    for it in range(POINTQ_RELOCATIONS + 1):
+        idx = M.mask_build_grouped(Xd, POINTQ_LG, POINTQ_NC, POINTQ_ITERS, 0, group0=g0)
+        L = idx.info.n_levels
+        ids, _ = M.mask_query(idx, Xd, 1, [1] * L)
+        miss, cls = point_query_errors(ids.cpu().numpy(), cloud)
+        if g0 is None:
+            g0 = M.mask_index_export_level(idx, 0)["labels"] // POINTQ_NC
+        _, moved, g0 = M.mask_relocate(idx, Xd, POINTQ_NC, g0)
+        trace.append({"iteration": it, "self_miss": miss, "class_error": cls, "moved": moved})
+        idx.free()
+    return {"setup": "8 Gaussian clouds in R^2 (centres on a circle, radius GNO 10 / GMO 4 / "
+                     "GRO 2, sigma 1), grouped build lengthGroup 16, nCentroids 8, "
+                     f"{POINTQ_ITERS} Lloyd iterations; every point queried with the greedy "
+                     "descent (k = 1)",
+            "errors_note": "self_miss: the point query does not return the point itself; "
+                           "class_error: it returns a point of another cloud",
+            "sizes": rows, "relocation_GRO_1600": trace}
+
+
+def point_query_cpu_baseline():
+    """The FP64 oracle on the same point-query experiment (sizes up to 80,000
+    points), timed on the host cores."""
+    import oracle as O
+    from paper_2208_02734_gb300 import synth
+    rows = []
+    for name in ("GNO", "GMO"):
+        for npc in POINTQ_SIZES:
+            if npc > POINTQ_ORACLE_MAX:
+                continue
+            X, cloud = synth.gaussian_clouds_2d(npc, synth.CLOUD_RADIUS[name], 1.0, seed=0,
+                                                return_cloud=True)
+            t0 = time.perf_counter()
+            oidx = O.build_grouped(X, POINTQ_LG, POINTQ_NC, POINTQ_ITERS, 0)
+            t1 = time.perf_counter()
+            ids_o, _, _ = oidx.query(X, 1, [1] * len(oidx.centroids))
+            t2 = time.perf_counter()
+            miss_o, cls_o = point_query_errors(ids_o[:, 0], cloud)
+            rows.append({"dataset": name, "n": len(X), "depth": len(oidx.centroids),
+                         "build_s": t1 - t0, "search_s": t2 - t1,
+                         "queries_per_s": len(X) / (t2 - t1), "self_miss": miss_o,
+                         "class_error": cls_o})
+    return {"kind": "oracle", "cores": O.max_threads(), "sizes": rows}
+
+
 def run_ours(args, w, wname):
     if w["kind"] == "sparse":
         return run_ours_sparse(args, w, wname)
@@ -975,9 +1074,13 @@ def run_ours(args, w, wname):
         "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
         "clocks": clocks, "e2e": e2e,
     }
+    if world == 1 and not args.no_pointq:
+        line["point_query"] = point_query_experiment(dev)
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(X, Q, w, wname)
+            if not args.no_pointq:
+                line["cpu_baseline"]["point_query"] = point_query_cpu_baseline()
         except Exception as ex:  # report, do not hide, a baseline failure
             line["cpu_baseline"] = {"error": repr(ex)}
     print(json.dumps(line), flush=True)
@@ -996,6 +1099,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowp", action="store_true", help="skip the BF16/FP8 query modes")
+    ap.add_argument("--no-pointq", action="store_true",
+                    help="skip the exhaustive point-query experiment of the paper (section 4.2)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="serving workload: seconds of arrivals per rate")
     args = ap.parse_args()

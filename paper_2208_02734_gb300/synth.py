@@ -37,10 +37,13 @@ __all__ = [
 ]
 
 # Circle radius of the cloud centres for the three datasets of §4.2 (sigma 1):
-# adjacent centres are 2 R sin(pi/8) = 0.765 R apart, i.e. 7.7, 3.1 and 1.5
+# adjacent centres are 2 R sin(pi/8) = 0.765 R apart, i.e. 7.7, 3.6 and 2.1
 # standard deviations: clearly separated (GNO), moderate overlap (GMO),
-# strong overlap (GRO).  The paper does not state its cloud parameters.
-CLOUD_RADIUS = {"GNO": 10.0, "GMO": 4.0, "GRO": 2.0}
+# strong overlap (GRO).  The paper does not state its cloud parameters; GMO
+# and GRO are set so that, at 200 points per cloud, the share of points whose
+# point query lands on another cloud is near the first values the paper
+# reports for them (about 12% and 40%).
+CLOUD_RADIUS = {"GNO": 10.0, "GMO": 4.75, "GRO": 2.8}
 
 
 class IsotropicMixture:
