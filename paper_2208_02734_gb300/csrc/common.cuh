@@ -316,6 +316,21 @@ int64_t range_search(const mask_index &idx, const float *Qp, int64_t nq, float r
                      int64_t *counts_out, int64_t capacity, int64_t *ids_out, float *dists_out,
                      cudaStream_t s);
 
+// query.cu -- the greedy descent (one kept centroid per level) for a whole
+// batch in one launch: per level, the parent-major centroid rows, their ids
+// and off[l] = the child ranges of level l's centroids in level l-1's rows
+// (level 0: in the points).  leaf (may be null) gets the reached leaf cluster;
+// ids/dists (may be null) the nearest point of that cluster.
+struct GreedyLevels {
+    const float4 *Cs[MASK_MAX_LEVELS];
+    const int32_t *ids[MASK_MAX_LEVELS];
+    const int64_t *off[MASK_MAX_LEVELS];
+    int64_t k_top;
+};
+void greedy_descent(const GreedyLevels &lv, int L, const float *Xs, const int32_t *xids, int dp,
+                    const float *Qp, int64_t nq, int32_t *leaf, int64_t *ids, float *dists,
+                    cudaStream_t s);
+
 // query.cu -- keep the K nearest rows among the children of each query's parents
 struct ScanArgs {
     const float *R = nullptr;     // [M x dp] rows (parent-major)

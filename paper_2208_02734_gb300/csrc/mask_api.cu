@@ -498,6 +498,24 @@ __global__ void invert_perm_kernel(const int32_t *__restrict__ perm, int64_t n,
         inv[perm[i]] = (int32_t)i;
 }
 
+// The index's levels for the one-launch greedy descent.
+GreedyLevels greedy_levels(const mask_index &idx) {
+    GreedyLevels g{};
+    for (int l = 0; l < idx.L; ++l) {
+        g.Cs[l] = reinterpret_cast<const float4 *>(idx.lv[(size_t)l].Cs.get());
+        g.ids[l] = idx.lv[(size_t)l].ids.get();
+        g.off[l] = idx.lv[(size_t)l].off.get();
+    }
+    g.k_top = idx.lv[(size_t)idx.L - 1].k;
+    return g;
+}
+
+bool all_ones(const std::vector<int> &p) {
+    for (int v : p)
+        if (v != 1) return false;
+    return true;
+}
+
 // The descent of Algorithm 2 down to the leaf clusters: sel[l] [nq x p_l]
 // receives each level's kept centroids (cluster ids), nearest first.
 void descend_levels(const mask_index &idx, const float *Qp, int64_t nq, const std::vector<int> &p,
@@ -534,6 +552,13 @@ void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
                  float *dists, cudaStream_t s) {
     if (nq == 0) return;
     const int dp = idx.dp;
+    if (k == 1 && prec == MASK_FP32 && all_ones(p)) {
+        // the paper's point query / nearest neighbour: one launch for the
+        // whole descent (same results as the general path)
+        greedy_descent(greedy_levels(idx), idx.L, idx.Xs.get(), idx.xids.get(), dp, Qp, nq,
+                       nullptr, ids, dists, s);
+        return;
+    }
     std::vector<Scratch<int32_t>> sel;
     descend_levels(idx, Qp, nq, p, sel, s);
     ScanArgs a;
@@ -1162,13 +1187,18 @@ mask_status mask_descend(const mask_index *index, const float *queries, int64_t 
         In<float> Qin(queries, (size_t)nq * index->d, s);
         Scratch<float> Qp((size_t)nq * dp, s);
         pad_rows(Qin.p, nq, index->d, Qp.get(), dp, s);
-        std::vector<Scratch<int32_t>> sel;
-        descend_levels(*index, Qp.get(), nq, p, sel, s);
         Out<int32_t> lo(leaf_out, (size_t)nq * probes[0], s);
-        if (p[0] == probes[0]) {
+        std::vector<Scratch<int32_t>> sel;
+        if (all_ones(p) && probes[0] == 1) {
+            greedy_descent(greedy_levels(*index), L, index->Xs.get(), index->xids.get(), dp,
+                           Qp.get(), nq, lo.p, nullptr, nullptr, s);
+        } else {
+            descend_levels(*index, Qp.get(), nq, p, sel, s);
+        }
+        if (!sel.empty() && p[0] == probes[0]) {
             MASK_CUDA(cudaMemcpyAsync(lo.p, sel[0].get(), sizeof(int32_t) * nq * p[0],
                                       cudaMemcpyDeviceToDevice, s));
-        } else {
+        } else if (!sel.empty()) {
             // more probes than leaf clusters: pad each row with -1
             MASK_CUDA(cudaMemsetAsync(lo.p, 0xFF, sizeof(int32_t) * nq * probes[0], s));
             MASK_CUDA(cudaMemcpy2DAsync(lo.p, sizeof(int32_t) * probes[0], sel[0].get(),
@@ -1199,10 +1229,10 @@ mask_status mask_relocate(const mask_index *index, const float *points, int32_t 
             In<float> P(points, (size_t)n * index->d, s);
             Scratch<float> Qp((size_t)n * index->dp, s);
             pad_rows(P.p, n, index->d, Qp.get(), index->dp, s);
-            std::vector<int> p((size_t)index->L, 1);
-            std::vector<Scratch<int32_t>> sel;
-            descend_levels(*index, Qp.get(), n, p, sel, s);
-            MASK_CUDA(cudaMemcpyAsync(leaf.data(), sel[0].get(), sizeof(int32_t) * n,
+            Scratch<int32_t> dleaf((size_t)n, s);
+            greedy_descent(greedy_levels(*index), index->L, index->Xs.get(), index->xids.get(),
+                           index->dp, Qp.get(), n, dleaf.get(), nullptr, nullptr, s);
+            MASK_CUDA(cudaMemcpyAsync(leaf.data(), dleaf.get(), sizeof(int32_t) * n,
                                       cudaMemcpyDeviceToHost, s));
             MASK_CUDA(cudaMemcpyAsync(own.data(), index->lv[0].labels.get(), sizeof(int32_t) * n,
                                       cudaMemcpyDeviceToHost, s));
@@ -1294,9 +1324,10 @@ mask_status mask_insert(mask_index *index, const float *points, int64_t n_new,
         In<float> P(points, (size_t)n_new * idx.d, s);
         Scratch<float> Xall((size_t)n1 * dp, s);
         pad_rows(P.p, n_new, idx.d, Xall.get() + (size_t)n0 * dp, dp, s);
-        std::vector<int> p((size_t)idx.L, 1);
-        std::vector<Scratch<int32_t>> sel;
-        descend_levels(idx, Xall.get() + (size_t)n0 * dp, n_new, p, sel, s);
+        std::vector<Scratch<int32_t>> sel(1);
+        sel[0].alloc((size_t)n_new, s);
+        greedy_descent(greedy_levels(idx), idx.L, idx.Xs.get(), idx.xids.get(), dp,
+                       Xall.get() + (size_t)n0 * dp, n_new, sel[0].get(), nullptr, nullptr, s);
         // the points in id order (old ones back out of the cluster-major
         // layout), then every point's leaf cluster: the old labels and the
         // reached clusters of the new points

@@ -364,6 +364,77 @@ int next_pow2(int v) {
     return p;
 }
 
+
+// The greedy descent of the paper's point query (§3.3: one kept centroid per
+// level, then the nearest point of the reached leaf cluster), one warp per
+// query through all levels in one launch.  Level rows are evaluated by groups
+// of LPR lanes and leaf rows one per lane, with exactly the arithmetic of the
+// level and leaf scans above, and every choice is the smallest (distance, id)
+// key, so the results are those of the general descent with all probes 1.
+template <int LPR>
+__global__ __launch_bounds__(kThreads) void greedy_descent_kernel(GreedyLevels lv, int L,
+                                                                  const float4 *__restrict__ Xs,
+                                                                  const int32_t *__restrict__ xids,
+                                                                  const float4 *__restrict__ Q,
+                                                                  int64_t nq, int dp4,
+                                                                  int32_t *__restrict__ leaf_out,
+                                                                  int64_t *__restrict__ id_out,
+                                                                  float *__restrict__ d_out) {
+    constexpr int G = 32 / LPR;   // rows per warp step
+    const int lane = threadIdx.x & 31, g = lane / LPR, gl = lane % LPR;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;   // whole warps leave together
+    const float4 *qv = Q + q * dp4;
+    int64_t b = 0, e = lv.k_top;
+    int32_t c = -1;
+    for (int l = L - 1; l >= 0; --l) {
+        const float4 *R = lv.Cs[l];
+        const int32_t *rid = lv.ids[l];
+        unsigned long long best = kNoKey;
+        for (int64_t r0 = b; r0 < e; r0 += G) {
+            const int64_t row = r0 + g;
+            float acc = 0.f;
+            if (row < e) {
+                for (int ch = gl; ch < dp4; ch += LPR) {
+                    const float4 v = R[row * dp4 + ch], x = qv[ch];
+                    const float e0 = v.x - x.x, e1 = v.y - x.y, e2 = v.z - x.z, e3 = v.w - x.w;
+                    acc = fmaf(e0, e0, acc);
+                    acc = fmaf(e1, e1, acc);
+                    acc = fmaf(e2, e2, acc);
+                    acc = fmaf(e3, e3, acc);
+                }
+            }
+            for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if (row < e && gl == 0)
+                best = min(best, ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)rid[row]);
+        }
+        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
+        if (best == kNoKey) { c = -1; break; }   // a kept centroid with no children
+        c = (int32_t)(best & 0xffffffffull);
+        b = lv.off[l][c];
+        e = lv.off[l][c + 1];
+    }
+    if (leaf_out && lane == 0) leaf_out[q] = c;
+    if (!id_out) return;
+    unsigned long long best = kNoKey;
+    if (c >= 0) {
+        __shared__ __align__(16) float4 qsh[kThreads / 32][32];
+        const int w = threadIdx.x >> 5;
+        for (int ch = lane; ch < dp4 && ch < 32; ch += 32) qsh[w][ch] = qv[ch];
+        __syncwarp();
+        const float4 *qs = dp4 <= 32 ? qsh[w] : qv;
+        for (int64_t row = b + lane; row < e; row += 32) {
+            const float dist = row_sqdist(Xs + row * dp4, qs, dp4);
+            best = min(best, ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)xids[row]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
+    if (lane == 0) {
+        id_out[q] = best == kNoKey ? -1 : (int64_t)(best & 0xffffffffull);
+        if (d_out) d_out[q] = best == kNoKey ? __int_as_float(0x7f800000)
+                                             : __uint_as_float((unsigned)(best >> 32));
+    }
+}
 }  // namespace
 
 void scan_topk(const ScanArgs &a, cudaStream_t s) {
@@ -403,6 +474,29 @@ void scan_topk(const ScanArgs &a, cudaStream_t s) {
     }
 #undef MASK_SCAN
     MASK_LAUNCHED("scan_topk");
+}
+
+void greedy_descent(const GreedyLevels &lv, int L, const float *Xs, const int32_t *xids, int dp,
+                    const float *Qp, int64_t nq, int32_t *leaf, int64_t *ids, float *dists,
+                    cudaStream_t s) {
+    if (nq == 0) return;
+    ProfRegion pr("greedy_descent", s, 0.0);
+    const unsigned blocks = (unsigned)((nq * 32 + kThreads - 1) / kThreads);
+    const float4 *X4 = reinterpret_cast<const float4 *>(Xs);
+    const float4 *Q4 = reinterpret_cast<const float4 *>(Qp);
+#define MASK_GREEDY(LPRV)                                                                    \
+    greedy_descent_kernel<LPRV><<<blocks, kThreads, 0, s>>>(lv, L, X4, xids, Q4, nq, dp / 4, \
+                                                           leaf, ids, dists)
+    switch (lanes_per_row(dp)) {
+    case 1: MASK_GREEDY(1); break;
+    case 2: MASK_GREEDY(2); break;
+    case 4: MASK_GREEDY(4); break;
+    case 8: MASK_GREEDY(8); break;
+    case 16: MASK_GREEDY(16); break;
+    default: MASK_GREEDY(32); break;
+    }
+#undef MASK_GREEDY
+    MASK_LAUNCHED("greedy_descent");
 }
 
 double scan_bytes(int which) {

@@ -212,3 +212,24 @@ def test_insertion_joins_the_reached_leaf_and_queries_see_it():
     ids_s, d_s = M.mask_query(idx, cuda(X[n0:]), 1, [1, 1])
     assert np.all(arr(d_s)[:, 0] == 0.0)
     idx.free()
+
+
+# ---------------------------------------- one-launch greedy descent
+
+@pytest.mark.parametrize("d", [2, 16, 64, 130])
+def test_greedy_point_query_equals_the_general_descent(d):
+    if d == 2:
+        X = clouds(500, 6.0, 1.5, seed=11).astype(np.float32)
+        idx = M.mask_build_grouped(cuda(X), 16, 8, 5, 3)
+    else:
+        X = synth.IsotropicMixture(d=d, n_blobs=6, seed=2).sample(6000, seed=3)
+        idx = M.mask_build(cuda(X), [300, 30, 4], 5, seed=1)
+    L = idx.info.n_levels
+    Q = cuda(np.concatenate([X[:300], X[:300] + 0.01]))
+    ids1, d1 = M.mask_query(idx, Q, 1, [1] * L)           # one launch
+    ids2, d2 = M.mask_query(idx, Q, 2, [1] * L)           # the level-by-level scans
+    assert torch.equal(ids1[:, 0], ids2[:, 0]) and torch.equal(d1[:, 0], d2[:, 0])
+    leaf1 = M.mask_descend(idx, Q, [1] * L)
+    leaf2 = M.mask_descend(idx, Q, [2] + [1] * (L - 1))
+    assert torch.equal(leaf1[:, 0], leaf2[:, 0])
+    idx.free()
