@@ -1041,6 +1041,26 @@ def run_ours(args, w, wname):
                        "(those copies inside the wall-clock region); build_s: mask_build from "
                        "host-pinned points (its upload, build_h2d_bytes, inside its own region)"}
 
+    # §3.4 across the ranks: one common query batch answered over the union
+    # of all ranks' partitions (local search, one all-gather, the merge)
+    dquery = None
+    if world > 1:
+        from paper_2208_02734_gb300 import dist as D
+        Qc = torch.from_numpy(make_data(w, 0)[1]).to(dev)
+        idx_d = M.mask_build(Xd, kpl, w["iters"], seed=0)
+        D.query_partitioned(idx_d, Qc, k, probes, rank * w["n"])       # warm
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids_d, _ = D.query_partitioned(idx_d, Qc, k, probes, rank * w["n"])
+        torch.cuda.synchronize()
+        dt, = max_over_ranks([time.perf_counter() - t0])
+        idx_d.free()
+        dquery = {"queries_per_s": w["nq"] / dt, "points_in_union": world * w["n"],
+                  "note": "the same query batch on every rank, answered over the union of "
+                          "the ranks' partitions (local search + all-gather + merge), wall "
+                          "clock of the slowest rank"}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -1074,6 +1094,8 @@ def run_ours(args, w, wname):
         "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
         "clocks": clocks, "e2e": e2e,
     }
+    if dquery is not None:
+        line["distributed_query"] = dquery
     if world == 1 and not args.no_pointq:
         line["point_query"] = point_query_experiment(dev)
     if world == 1 and not args.no_cpu_baseline:

@@ -289,6 +289,24 @@ mask_status mask_range_query(const mask_index *index, const float *queries, int6
 mask_status mask_insert(mask_index *index, const float *points, int64_t n_new,
                         int32_t *leaf_out, mask_stream stream);
 
+/*
+ * The exchange step of the distributed design (§3.4): each of n_parts nodes
+ * answers the same queries on its own partition with its own index; their
+ * results, gathered, are merged into the k nearest over all partitions.
+ *   ids, dists  [n_parts x nq x k] int64 / float32, partition-major (the
+ *               layout of an all-gather of each node's [nq x k] mask_query
+ *               output); ids -1 (with dists +inf) are padding.
+ *   id_offset   [n_parts] int64 (may be NULL): added to partition g's ids,
+ *               turning partition-local ids into global ones.
+ *   ids_out, dists_out [nq x k]: ascending by (distance, global id), padded
+ *               with (-1, +inf).
+ * n_parts * k <= 16384 (one block sorts a query's candidates in shared
+ * memory), else MASK_EUNSUPPORTED.  Synchronises `stream`.
+ */
+mask_status mask_merge_topk(const int64_t *ids, const float *dists, int32_t n_parts, int64_t nq,
+                            int32_t k, const int64_t *id_offset, int64_t *ids_out,
+                            float *dists_out, mask_stream stream);
+
 /* ---- k-means steps (the build's kernels, callable on their own) -------- */
 
 /*

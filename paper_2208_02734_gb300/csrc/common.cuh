@@ -316,6 +316,12 @@ int64_t range_search(const mask_index &idx, const float *Qp, int64_t nq, float r
                      int64_t *counts_out, int64_t capacity, int64_t *ids_out, float *dists_out,
                      cudaStream_t s);
 
+// merge.cu -- the distributed exchange (§3.4): ids/dists [G x nq x k] from G
+// partitions -> the k smallest (distance, global id) per query
+size_t merge_topk_smem(int G, int k);
+void merge_topk(const int64_t *ids, const float *dists, int G, int64_t nq, int k,
+                const int64_t *id_offset, int64_t *ids_out, float *dists_out, cudaStream_t s);
+
 // query.cu -- the greedy descent (one kept centroid per level) for a whole
 // batch in one launch: per level, the parent-major centroid rows, their ids
 // and off[l] = the child ranges of level l's centroids in level l-1's rows

@@ -1372,4 +1372,29 @@ mask_status mask_insert(mask_index *index, const float *points, int64_t n_new,
     });
 }
 
+// ------------------------------------------ distributed merge (§3.4)
+
+mask_status mask_merge_topk(const int64_t *ids, const float *dists, int32_t n_parts, int64_t nq,
+                            int32_t k, const int64_t *id_offset, int64_t *ids_out,
+                            float *dists_out, mask_stream stream) {
+    return guard([&] {
+        MASK_REQUIRE(n_parts >= 1 && k >= 1 && nq >= 0, "need n_parts >= 1, k >= 1, nq >= 0");
+        if ((size_t)merge_topk_smem(n_parts, k) > 200 * 1024)
+            fail(MASK_EUNSUPPORTED, "n_parts * k too large for one block (at most 16384)");
+        if (nq == 0) return;
+        MASK_REQUIRE(ids && dists && ids_out && dists_out, "NULL array");
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t total = (size_t)n_parts * nq * k;
+        In<int64_t> I(ids, total, s);
+        In<float> D(dists, total, s);
+        In<int64_t> off(id_offset, id_offset ? (size_t)n_parts : 0, s);
+        Out<int64_t> io(ids_out, (size_t)nq * k, s);
+        Out<float> dout(dists_out, (size_t)nq * k, s);
+        merge_topk(I.p, D.p, n_parts, nq, k, id_offset ? off.p : nullptr, io.p, dout.p, s);
+        io.finish(s);
+        dout.finish(s);
+        MASK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
 }  // extern "C"

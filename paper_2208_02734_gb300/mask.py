@@ -35,7 +35,7 @@ EXPORTED = [
     "mask_kmeans_update_csr", "mask_server_open", "mask_server_submit", "mask_server_poll",
     "mask_server_wait", "mask_server_stats", "mask_server_close", "mask_test_bounded_wait",
     "mask_test_alloc_count", "mask_grouped_levels", "mask_build_grouped", "mask_descend",
-    "mask_relocate", "mask_range_query", "mask_insert",
+    "mask_relocate", "mask_range_query", "mask_insert", "mask_merge_topk",
 ]
 
 
@@ -112,6 +112,7 @@ def load(build_if_stale: bool = True):
             "mask_relocate": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
             "mask_range_query": (C.c_int, [_vp, _vp, _i64, C.c_float, _vp, _i64, _vp, _vp, _vp]),
             "mask_insert": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
+            "mask_merge_topk": (C.c_int, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _vp, _vp]),
             "mask_test_bounded_wait": (C.c_int, [_i32, _i32, _vp]),
             "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
             "mask_kmeanspp_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _u64, _i32, _vp,
@@ -398,6 +399,20 @@ def mask_insert(index, points, stream=None):
     leaf, pl = _empty_like_kind(X, (n_new,), "int32")
     _check(load().mask_insert(_handle(index), px, n_new, pl, _stream(X, stream)), "mask_insert")
     return leaf
+
+
+def mask_merge_topk(ids, dists, id_offset=None, stream=None):
+    """Merge per-partition k-NN lists ([G x nq x k]) into the k nearest over
+    all partitions (§3.4); id_offset [G] turns local ids into global ones."""
+    I, pi = _arr(ids, "int64")
+    D, pd = _arr(dists, "float32")
+    G, nq, k = I.shape
+    off, po = (None, None) if id_offset is None else _arr(id_offset, "int64")
+    out_i, poi = _empty_like_kind(I, (nq, k), "int64")
+    out_d, pod = _empty_like_kind(I, (nq, k), "float32")
+    _check(load().mask_merge_topk(pi, pd, G, nq, k, po, poi, pod, _stream(I, stream)),
+           "mask_merge_topk")
+    return out_i, out_d
 
 
 def mask_kmeanspp(X, k: int, seed: int, level: int = 0, stream=None):
