@@ -78,7 +78,14 @@ class ProfRegion {
 
 // --------------------------------------------------------- device buffers
 
-// Stream-ordered scratch (cudaMallocAsync / cudaFreeAsync on one stream).
+// Stream-ordered allocation from the library's memory pool of the current
+// device (kept warm between calls: up to kScratchKeepBytes stay reserved
+// after a synchronisation instead of going back to the driver); inside a
+// stream capture, from the device's default pool (graph memory nodes).
+void *scratch_alloc(size_t bytes, cudaStream_t s);
+constexpr unsigned long long kScratchKeepBytes = 4ull << 30;
+
+// Stream-ordered scratch (scratch_alloc / cudaFreeAsync on one stream).
 template <class T>
 struct Scratch {
     T *p = nullptr;
@@ -99,7 +106,7 @@ struct Scratch {
         n = count;
         if (count) {
             count_alloc();
-            MASK_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+            p = static_cast<T *>(scratch_alloc(count * sizeof(T), st));
         }
     }
     void release() {

@@ -54,6 +54,43 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+void *scratch_alloc(size_t bytes, cudaStream_t s) {
+    void *p = nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cudaGetLastError();
+    if (cs != cudaStreamCaptureStatusNone) {
+        MASK_CUDA(cudaMallocAsync(&p, bytes, s));
+        return p;
+    }
+    int dev = 0;
+    MASK_CUDA(cudaGetDevice(&dev));
+    MASK_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (g_pools[dev] == nullptr) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t created = nullptr;
+            MASK_CUDA(cudaMemPoolCreate(&created, &props));
+            unsigned long long keep = kScratchKeepBytes;
+            MASK_CUDA(cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep));
+            g_pools[dev] = created;
+        }
+        pool = g_pools[dev];
+    }
+    MASK_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool, s));
+    return p;
+}
+
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfRegion::ProfRegion(const char *name, cudaStream_t s, double work)
