@@ -190,6 +190,9 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
     __shared__ int32_t s_pid[2][CM_QB];
     __shared__ int s_ncand[CM_QB];                  // candidates of the chunk, per query
     __shared__ unsigned long long s_th[CM_QB];      // each list's K-th key (kNoKey: not full)
+    // per warp: the (query, row) pairs of its tile that pass the filter,
+    // query << 8 | row (a warp's tile holds 16 rows x 16 queries)
+    __shared__ unsigned short s_pass[CM_THREADS / 32][256];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n_items = item_off[k0];
@@ -328,41 +331,57 @@ __global__ __launch_bounds__(CM_THREADS, 2) void cm_scan_kernel(
             // bound, can reach the smaller of the list's K-th and T_q gets its
             // exact key (the arithmetic of the per-query scan); keys below the
             // list's K-th at the start of the chunk become candidates.
+            // The pairs that pass are first collected (ballots give each its
+            // slot), then evaluated one per lane, so the exact loop runs once
+            // per 32 survivors instead of once per slot any lane needs.
+            int npass = 0;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q = g + 8 * h;
-                if (q >= nqb) continue;
-                const unsigned long long th = s_th[q];
-                const float qv = s_qn[qbuf][q];
-                const float lim = fminf(s_tq[qbuf][q], th == kNoKey ? __int_as_float(0x7f800000)
-                                                                    : __uint_as_float((unsigned)(th >> 32)));
+                const unsigned long long th = q < nqb ? s_th[q] : kNoKey;
+                const float qv = q < nqb ? s_qn[qbuf][q] : 0.f;
+                const float lim = fminf(q < nqb ? s_tq[qbuf][q] : 0.f,
+                                        th == kNoKey ? __int_as_float(0x7f800000)
+                                                     : __uint_as_float((unsigned)(th >> 32)));
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int row = 16 * warp + 8 * j + 2 * t + e;
-                        if (row >= nr) continue;
-                        const float xv = xnc[row];
-                        const float dv = fmaf(-2.f, acc[j][2 * h + e], xv + qv);
-                        if (!(dv <= lim + mcoef * (xv + qv))) continue;
-                        const float4 *x4 = reinterpret_cast<const float4 *>(xsb) + row * XS4;
-                        const float4 *q4 = reinterpret_cast<const float4 *>(qsb) + q * XS4;
-                        float e2 = 0.f;
-                        for (int t4 = 0; t4 < dp4; ++t4) {
-                            const float4 a4 = x4[t4], b4 = q4[t4];
-                            float d = a4.x - b4.x;
-                            e2 = fmaf(d, d, e2);
-                            d = a4.y - b4.y;
-                            e2 = fmaf(d, d, e2);
-                            d = a4.z - b4.z;
-                            e2 = fmaf(d, d, e2);
-                            d = a4.w - b4.w;
-                            e2 = fmaf(d, d, e2);
+                        bool pass = false;
+                        if (q < nqb && row < nr) {
+                            const float xv = xnc[row];
+                            const float dv = fmaf(-2.f, acc[j][2 * h + e], xv + qv);
+                            pass = dv <= lim + mcoef * (xv + qv);
                         }
-                        const unsigned long long key =
-                            ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)xids[r0 + row];
-                        if (key < th) cbuf[q * CM_R + atomicAdd(&s_ncand[q], 1)] = key;
+                        const unsigned bal = __ballot_sync(kFull, pass);
+                        if (pass)
+                            s_pass[warp][npass + __popc(bal & ((1u << lane) - 1u))] =
+                                (unsigned short)((q << 8) | row);
+                        npass += __popc(bal);
                     }
+            }
+            __syncwarp();
+            for (int i = lane; i < npass; i += 32) {
+                const int pr = s_pass[warp][i];
+                const int q = pr >> 8, row = pr & 255;
+                const float4 *x4 = reinterpret_cast<const float4 *>(xsb) + row * XS4;
+                const float4 *q4 = reinterpret_cast<const float4 *>(qsb) + q * XS4;
+                float e2 = 0.f;
+                for (int t4 = 0; t4 < dp4; ++t4) {
+                    const float4 a4 = x4[t4], b4 = q4[t4];
+                    float d = a4.x - b4.x;
+                    e2 = fmaf(d, d, e2);
+                    d = a4.y - b4.y;
+                    e2 = fmaf(d, d, e2);
+                    d = a4.z - b4.z;
+                    e2 = fmaf(d, d, e2);
+                    d = a4.w - b4.w;
+                    e2 = fmaf(d, d, e2);
+                }
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(e2) << 32) | (unsigned)xids[r0 + row];
+                if (key < s_th[q]) cbuf[q * CM_R + atomicAdd(&s_ncand[q], 1)] = key;
             }
         }
         __syncthreads();
