@@ -56,7 +56,7 @@ WORKLOADS = {
                      iters=10, nq=5_000, k=10, probes=[16, 4],
                      ladder=[[16, 4], [24, 6], [32, 8], [48, 8], [64, 12], [96, 16], [128, 24],
                              [192, 32], [256, 48], [384, 64], [512, 64], [768, 64], [1024, 64],
-                             [1536, 64], [2048, 64]],
+                             [1536, 64], [2048, 64], [3072, 64]],
                      desc="1M CSR rows x 20000 (nnz log-normal mean 60 sigma 0.8, Zipf(1.0) "
                           "columns, |N(0,1)| values, rows L2-normalised), index 4096/64, 10 Lloyd "
                           "iters, 5k CSR queries, k=10, probes 16/4"),
@@ -624,16 +624,17 @@ def serving_requests(rng, Q, n, P, lowp):
     return out
 
 
-def run_serving(args, w, wname):
-    """Serving workload: continuous batching (mask_server_*) on the resident
-    small index; saturation throughput, then open-loop Poisson arrivals at
-    five fractions of it, per precision mode."""
+SERVE_FRACTIONS = (0.1, 0.25, 0.5, 0.75, 0.95)
+
+
+def serving_modes(w, dev, secs, fractions=SERVE_FRACTIONS, warm_n=400, backlog_n=2000):
+    """Continuous batching (mask_server_*) on the resident small index, per
+    precision mode: saturation throughput on a backlog, then open-loop
+    Poisson arrivals at `fractions` of it for `secs` seconds each.  Returns
+    (per-mode results, P, calibration recall, kernel launches, X, Q)."""
     import torch
     from paper_2208_02734_gb300 import mask as M
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    M.load()
     X, Q = make_data(w, 0)
     Xd, Qd = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
     idx = M.mask_build(Xd, w["k_per_level"], w["iters"], seed=0)
@@ -655,7 +656,6 @@ def run_serving(args, w, wname):
     if P is None:
         P = 64
     log(f"[serving] probes U{{{P}..{P + 2}}} x U{{3..5}}: recall@10 {rec:.4f}")
-    secs = args.serve_seconds
     modes = {"fp32": M.MASK_FP32, "bf16": M.MASK_BF16, "fp8": M.MASK_FP8E4M3}
     out = {}
     lc0 = M.mask_launch_count()
@@ -667,7 +667,7 @@ def run_serving(args, w, wname):
             return srv.submit(Q[q0:q0 + nq], k, probes, pr), r
 
         # warm-up: capture the graphs of the shapes the stream will use
-        warm = serving_requests(rng, Q, 400, P, prec)
+        warm = serving_requests(rng, Q, warm_n, P, prec)
         for t, _ in [submit(r) for r in warm]:
             t.result()
         # saturation: a backlog of 2,000 requests submitted by 4 threads at once,
@@ -675,7 +675,7 @@ def run_serving(args, w, wname):
         sub_s = [0.0] * SUBMITTERS
         for rep in range(2):
             srv.stats(reset=True)
-            sat = serving_requests(rng, Q, 2000, P, prec)
+            sat = serving_requests(rng, Q, backlog_n, P, prec)
             done = [None] * len(sat)
 
             def backlog(c):
@@ -708,7 +708,7 @@ def run_serving(args, w, wname):
             hits += recall_at_k(Xd, qq, ids, g[:, -1:]) * ids.numel()
             tot += ids.numel()
         rates = []
-        for frac in (0.1, 0.25, 0.5, 0.75, 0.95):
+        for frac in fractions:
             lam = frac * sat_qps / mean_q       # requests per second, SUBMITTERS streams
             streams = []
             for c in range(SUBMITTERS):
@@ -754,6 +754,92 @@ def run_serving(args, w, wname):
                       "k100_requests_in_fp32": mname != "fp32"}
     launches = M.mask_launch_count() - lc0
     idx.free()
+    return out, P, rec, launches, X, Q
+
+
+def serving_summary(dev, secs=3.0, fractions=(0.5, 0.95)):
+    """Compact serving report for the headline line (the serving workload at
+    two arrival rates, `secs` seconds each): per precision mode the saturation
+    q/s, the served recall@10, and p50/p99 request latency per rate."""
+    t0 = time.perf_counter()
+    out, P, rec, launches, _, _ = serving_modes(WORKLOADS["serving"], dev, secs, fractions,
+                                                warm_n=200, backlog_n=1000)
+    summ = {"workload": WORKLOADS["serving"]["desc"], "probes_P": P,
+            "recall_at_10_calibration": rec, "seconds_per_rate": secs,
+            "gpu_launches": int(launches)}
+    for m, r in out.items():
+        summ[m] = {"saturation_qps": r["saturation_qps"], "recall_at_10": r["recall_at_10"],
+                   "autotuned_shapes": r["autotuned_shapes"]}
+        for x in r["rates"]:
+            summ[m][f"at_{x['offered_fraction']}"] = {
+                k: x[k] for k in ("achieved_qps", "p50_ms", "p99_ms", "mean_batch_queries")}
+    summ["wall_s"] = time.perf_counter() - t0
+    return summ
+
+
+def sparse_summary(dev, reps=2):
+    """Compact report of the sparse workload for the headline line: build
+    time, and q/s with p50/p99 over `reps` 5k-query batches at the cheapest
+    ladder probes reaching recall@10 >= 0.95 (200-query sample vs FP64 exact
+    k-NN)."""
+    import torch
+    from paper_2208_02734_gb300 import mask as M
+    t0 = time.perf_counter()
+    w = WORKLOADS["sparse1m"]
+    A, Qa = make_data(w, 0)
+    rp, cl, vl = (torch.from_numpy(a).to(dev) for a in (A.row_ptr, A.col, A.val))
+    qrp, qcl, qvl = (torch.from_numpy(a).to(dev) for a in (Qa.row_ptr, Qa.col, Qa.val))
+    stream = torch.cuda.current_stream(dev)
+    kpl, k, d = w["k_per_level"], w["k"], w["d"]
+    sel = recall_sample(qrp[:-1])
+    Qsub = Qa.rows(sel.cpu().numpy())
+    sq = tuple(torch.from_numpy(a).to(dev) for a in (Qsub.row_ptr, Qsub.col, Qsub.val))
+    _, gt_d, Dfull = exact_knn_csr_fp64(rp, cl, vl, A.n_rows, d,
+                                         torch.from_numpy(Qsub.to_dense(np.float64)).to(dev), k)
+    dk = gt_d[:, -1:]
+    M.mask_build_csr(rp, cl, vl, d, kpl, w["iters"], seed=0).free()      # warm
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    idx = M.mask_build_csr(rp, cl, vl, d, kpl, w["iters"], seed=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_s = e0.elapsed_time(e1) / 1e3
+    rung = None
+    for pr in w["ladder"]:
+        ids_s, _ = M.mask_query_csr(idx, *sq, k, pr)
+        r = recall_from_matrix(Dfull, ids_s, dk)
+        rung = (pr, r)
+        if r >= 0.95:
+            break
+    qms = []
+    for i in range(1 + reps):
+        e0.record(stream)
+        ids, _ = M.mask_query_csr(idx, qrp, qcl, qvl, k, rung[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            qms.append(e0.elapsed_time(e1))
+    recall = recall_from_matrix(Dfull, ids[sel], dk)
+    idx.free()
+    return {"workload": w["desc"], "probes": rung[0], "recall_at_10": recall,
+            "recall_queries": int(len(sel)), "reached_0.95": rung[1] >= 0.95,
+            "value": reps * w["nq"] / (sum(qms) / 1e3), "unit": "queries/s",
+            "p50_ms": float(np.percentile(qms, 50)), "p99_ms": float(np.percentile(qms, 99)),
+            "latency_note": f"device time of one {w['nq']}-query batch",
+            "build_s": build_s, "wall_s": time.perf_counter() - t0}
+
+
+def run_serving(args, w, wname):
+    """Serving workload: saturation throughput, then open-loop Poisson
+    arrivals at five fractions of it, per precision mode."""
+    import torch
+    from paper_2208_02734_gb300 import mask as M
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    M.load()
+    secs = args.serve_seconds
+    out, P, rec, launches, X, Q = serving_modes(w, dev, secs)
     fp = out["fp32"]
     line = {"metric": METRIC, "value": fp["saturation_qps"], "unit": "queries/s", "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
@@ -1005,9 +1091,14 @@ def run_ours(args, w, wname):
                 torch.cuda.synchronize()
                 if i >= args.warmup:
                     qms.append(e0.elapsed_time(e1))
-            ids_h, _ = M.mask_query(idx_lp, Qd[hold], k, rung[0], precision=prec)
+            ids_h, d_h = M.mask_query(idx_lp, Qd[hold], k, rung[0], precision=prec)
+            # returned distances against FP64 distances of the returned points
+            ok = ids_h >= 0
+            d64 = ((Xd[ids_h.clamp_min(0)].double() - Qd[hold].double()[:, None, :]) ** 2).sum(-1)
+            rel = ((d_h.double() - d64).abs() / d64.clamp_min(1e-300))[ok]
             lowp[mode] = {"probes": rung[0],
                           "recall_at_10": recall_at_k(Xd, Qd[hold], ids_h, dk_h),
+                          "max_rel_dist_err_vs_fp64": float(rel.max().item()),
                           "recall_queries": int(len(hold)),
                           "recall_at_10_selection_sample": rung[1],
                           "value": args.steps * w["nq"] / (sum(qms) / 1e3), "unit": "queries/s",
@@ -1096,6 +1187,10 @@ def run_ours(args, w, wname):
     }
     if dquery is not None:
         line["distributed_query"] = dquery
+    if world == 1 and not args.no_serving:
+        line["serving"] = serving_summary(dev)
+    if world == 1 and not args.no_sparse:
+        line["sparse"] = sparse_summary(dev)
     if world == 1 and not args.no_pointq:
         line["point_query"] = point_query_experiment(dev)
     if world == 1 and not args.no_cpu_baseline:
@@ -1123,6 +1218,10 @@ def main():
     ap.add_argument("--no-lowp", action="store_true", help="skip the BF16/FP8 query modes")
     ap.add_argument("--no-pointq", action="store_true",
                     help="skip the exhaustive point-query experiment of the paper (section 4.2)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the compact serving report of the dense workload's line")
+    ap.add_argument("--no-sparse", action="store_true",
+                    help="skip the compact sparse report of the dense workload's line")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="serving workload: seconds of arrivals per rate")
     args = ap.parse_args()

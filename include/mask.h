@@ -452,9 +452,12 @@ mask_status mask_test_bounded_wait(int32_t flag_set, int32_t limit_us, mask_stre
  * others run join the next batch as slots and memory free up.  A request's
  * result is the same as mask_query's on its queries alone (bit for bit).
  * For FP32 shapes where both leaf scans apply, the first batch of a shape
- * times both and keeps the faster (autotuning; results are identical).
- * The graphs captured while autotuning hold buffers outside the mem_budget
- * accounting (the budget covers the batches admitted to run).
+ * (probes, precision, batch bucket, k) times five captured graphs: the
+ * query-major scan, and the cluster-major scan with 16 or 8 queries per work
+ * item at all the blocks per SM that fit or at one.  It keeps the fastest
+ * and releases the others (autotuning; results are identical).  The graphs
+ * captured while autotuning hold buffers outside the mem_budget accounting
+ * (the budget covers the batches admitted to run).
  *
  * The index must stay alive until mask_server_close.  Queries and outputs
  * are HOST memory: queries are copied at submit; ids_out / dists_out are

@@ -379,14 +379,23 @@ void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, in
                cudaStream_t s);
 // xn [rows] = ||row of Xs||^2 (FP32); the scan evaluates a row exactly only
 // where its expanded-form distance can reach the query's current K-th
+// Work-item shape of the cluster-major scans, chosen by the serving loop's
+// autotuner: queries per item (<= kCmItemQueries) and blocks per SM (0: as
+// many as fit).
+struct CmTile {
+    int qpi = 16;
+    int bps = 0;
+};
 void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
                   const int64_t *leaf_off, int k0, const float *Qp, int64_t nq,
-                  const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s);
+                  const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s,
+                  CmTile tile = CmTile{});
 double cm_bytes();
 void cm_bytes_reset();
 // groups the (query, kept leaf) pairs by leaf cluster; item_off[k0] = work items
 void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
-                    Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s);
+                    Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s,
+                    int qpi = 16);
 // queries per work item of the cluster-major scans
 constexpr int kCmItemQueries = 16;
 // per work item i of cm_group_pairs (cluster c, up to kCmItemQueries of its
@@ -395,7 +404,8 @@ constexpr int kCmItemQueries = 16;
 // and its query (0 past the last)
 void cm_item_meta(const int32_t *pairs, const int64_t *poff, const int64_t *item_off,
                   const int64_t *leaf_off, int64_t npairs, int P, int k0, Scratch<int4> &meta,
-                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s);
+                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s,
+                  int qpi = 16);
 
 // Asynchronous global -> shared copies (cp.async); a false `valid` writes
 // zeros (the source is then not read, but must still be a valid address).

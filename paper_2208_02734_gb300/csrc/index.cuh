@@ -55,6 +55,7 @@ void ensure_lowp(const mask_index &idx, bool fp8, cudaStream_t s);
 // synchronisation (capturable once ensure_lowp has run for lowp modes).
 void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
                  const std::vector<int> &p, mask_precision prec, LeafMode mode, int64_t *ids,
-                 float *dists, cudaStream_t s);
+                 float *dists, cudaStream_t s,
+                 CmTile tile = CmTile{});
 
 }  // namespace mask

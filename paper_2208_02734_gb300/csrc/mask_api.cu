@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -549,7 +550,7 @@ void descend_levels(const mask_index &idx, const float *Qp, int64_t nq, const st
 
 void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
                  const std::vector<int> &p, mask_precision prec, LeafMode mode, int64_t *ids,
-                 float *dists, cudaStream_t s) {
+                 float *dists, cudaStream_t s, CmTile tile) {
     if (nq == 0) return;
     const int dp = idx.dp;
     if (k == 1 && prec == MASK_FP32 && all_ones(p)) {
@@ -583,7 +584,7 @@ void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
     if (mode == LeafMode::Query) cluster_major = false;
     if (cluster_major) {
         cm_leaf_scan(idx.Xs.get(), idx.xn.get(), dp, idx.xids.get(), idx.lv[0].off.get(), k0, Qp,
-                     nq, sel[0].get(), p[0], k, ids, dists, s);
+                     nq, sel[0].get(), p[0], k, ids, dists, s, tile);
     } else {
         ScanArgs c = a;
         c.R = idx.Xs.get();
@@ -769,9 +770,20 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
             p[(size_t)l] = std::min<int>(probes[l], index->lv[(size_t)l].k);
         }
         if (lowp) ensure_lowp(*index, precision == MASK_FP8E4M3, s);
+        // MASK_LEAF_SCAN = query | cluster[:queries per item:blocks per SM]
+        // pins the leaf scan (and the cluster-major tile) for tests
         LeafMode mode = LeafMode::Auto;
+        CmTile tile;
         if (const char *m = std::getenv("MASK_LEAF_SCAN")) {
-            if (std::strcmp(m, "cluster") == 0) mode = LeafMode::Cluster;
+            if (std::strncmp(m, "cluster", 7) == 0) {
+                mode = LeafMode::Cluster;
+                int qpi = 0, bps = 0;
+                if (std::sscanf(m + 7, ":%d:%d", &qpi, &bps) == 2) {
+                    MASK_REQUIRE(qpi >= 1 && qpi <= kCmItemQueries && bps >= 0,
+                                 "MASK_LEAF_SCAN tile out of range");
+                    tile = CmTile{qpi, bps};
+                }
+            }
             if (std::strcmp(m, "query") == 0) mode = LeafMode::Query;
         }
         In<float> Qin(queries, (size_t)nq * index->d, s);
@@ -779,7 +791,7 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
         pad_rows(Qin.p, nq, index->d, Qp.get(), dp, s);
         Out<int64_t> ids(ids_out, (size_t)nq * k, s);
         Out<float> dd(dists_out, (size_t)nq * k, s);
-        query_dense(*index, Qp.get(), nq, k, p, precision, mode, ids.p, dd.p, s);
+        query_dense(*index, Qp.get(), nq, k, p, precision, mode, ids.p, dd.p, s, tile);
         ids.finish(s);
         dd.finish(s);
         if (ids.host || dd.host) MASK_CUDA(cudaStreamSynchronize(s));

@@ -77,16 +77,16 @@ __global__ void pair_labels_kernel(const int32_t *__restrict__ sel, int64_t npai
     }
 }
 
-// item_off[c] = sum over clusters < c of ceil(pairs_c / CM_QB); item_off[k0]
+// item_off[c] = sum over clusters < c of ceil(pairs_c / qpi); item_off[k0]
 // is the number of work items (one block of 1024 threads).
 __global__ void __launch_bounds__(1024) item_scan_kernel(const int64_t *__restrict__ poff, int k0,
-                                                         int64_t *__restrict__ item_off) {
+                                                         int qpi, int64_t *__restrict__ item_off) {
     __shared__ long long part[1024];
     const int tid = threadIdx.x;
     const int per = (k0 + 1023) / 1024;
     const int b = tid * per, e = min(k0, b + per);
     long long s = 0;
-    for (int c = b; c < e; ++c) s += (poff[c + 1] - poff[c] + CM_QB - 1) / CM_QB;
+    for (int c = b; c < e; ++c) s += (poff[c + 1] - poff[c] + qpi - 1) / qpi;
     part[tid] = s;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
@@ -98,18 +98,18 @@ __global__ void __launch_bounds__(1024) item_scan_kernel(const int64_t *__restri
     long long run = part[tid] - s;
     for (int c = b; c < e; ++c) {
         item_off[c] = run;
-        run += (poff[c + 1] - poff[c] + CM_QB - 1) / CM_QB;
+        run += (poff[c + 1] - poff[c] + qpi - 1) / qpi;
     }
     if (tid == 1023) item_off[k0] = part[1023];
 }
 
-// Per work item i (cluster c, up to CM_QB of its pairs):
+// Per work item i (cluster c, up to qpi <= CM_QB of its pairs):
 //   meta[i] = {first row lo, first row hi, rows of c, pairs in the item}
 //   pid[i * CM_QB + q] = the item's q-th pair (-1 past the last),
 //   qid[i * CM_QB + q] = that pair's query.
 __global__ void item_meta_kernel(const int64_t *__restrict__ item_off, const int64_t *__restrict__ poff,
                                  const int64_t *__restrict__ leaf_off,
-                                 const int32_t *__restrict__ pairs, int P, int k0,
+                                 const int32_t *__restrict__ pairs, int P, int k0, int qpi,
                                  int4 *__restrict__ meta, int32_t *__restrict__ pid,
                                  int32_t *__restrict__ qid) {
     // one warp per cluster; lanes over the cluster's (item, slot) entries
@@ -122,12 +122,12 @@ __global__ void item_meta_kernel(const int64_t *__restrict__ item_off, const int
         for (int64_t e = lane; e < ni * CM_QB; e += 32) {
             const int64_t i = i0 + e / CM_QB;
             const int q = (int)(e % CM_QB);
-            const int64_t pe = (e / CM_QB) * CM_QB + q;  // pair offset within the cluster
-            const int32_t pp = pe < np ? pairs[p0 + pe] : -1;
+            const int64_t pe = (e / CM_QB) * qpi + q;  // pair offset within the cluster
+            const int32_t pp = (q < qpi && pe < np) ? pairs[p0 + pe] : -1;
             pid[i * CM_QB + q] = pp;
             qid[i * CM_QB + q] = pp >= 0 ? pp / P : 0;
             if (q == 0) {
-                const int nqb = (int)min((int64_t)CM_QB, np - pe);
+                const int nqb = (int)min((int64_t)qpi, np - pe);
                 meta[i] = make_int4((int)(rb & 0xffffffff), (int)(rb >> 32), (int)rows, nqb);
             }
         }
@@ -505,7 +505,9 @@ int grid_cap(int64_t work, int threads) {
 bool cm_leaf_supported(int dp, int K) { return dp <= 128 && K >= 1 && K <= 32; }
 
 void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
-                    Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s) {
+                    Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s,
+                    int qpi) {
+    MASK_REQUIRE(qpi >= 1 && qpi <= CM_QB, "queries per item out of range");
     const int64_t npairs = nq * P;
     ProfRegion pr("leaf_group", s, 0.0);
     Scratch<int32_t> lab(npairs, s);
@@ -515,20 +517,20 @@ void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32
     pair_labels_kernel<<<grid_cap(npairs, 256), 256, 0, s>>>(sel, npairs, k0, lab.get());
     MASK_LAUNCHED("pair_labels");
     label_sort(lab.get(), npairs, k0 + 1, poff.get(), pairs.get(), s);
-    item_scan_kernel<<<1, 1024, 0, s>>>(poff.get(), k0, item_off.get());
+    item_scan_kernel<<<1, 1024, 0, s>>>(poff.get(), k0, qpi, item_off.get());
     MASK_LAUNCHED("item_scan");
 }
 
 void cm_item_meta(const int32_t *pairs, const int64_t *poff, const int64_t *item_off,
                   const int64_t *leaf_off, int64_t npairs, int P, int k0, Scratch<int4> &meta,
-                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s) {
-    // a cluster with m pairs has ceil(m / CM_QB) <= m / CM_QB + 1 items, and at most m
+                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s, int qpi) {
+    // a cluster with m pairs has ceil(m / qpi) <= m / qpi + 1 items, and at most m
     const int64_t max_items = std::max<int64_t>(
-        1, std::min(npairs, (npairs + CM_QB - 1) / CM_QB + (int64_t)k0));
+        1, std::min(npairs, (npairs + qpi - 1) / qpi + (int64_t)k0));
     meta.alloc(max_items, s);
     pid.alloc((size_t)max_items * CM_QB, s);
     qid.alloc((size_t)max_items * CM_QB, s);
-    item_meta_kernel<<<(k0 + 7) / 8, 256, 0, s>>>(item_off, poff, leaf_off, pairs, P, k0,
+    item_meta_kernel<<<(k0 + 7) / 8, 256, 0, s>>>(item_off, poff, leaf_off, pairs, P, k0, qpi,
                                                   meta.get(), pid.get(), qid.get());
     MASK_LAUNCHED("item_meta");
 }
@@ -566,7 +568,8 @@ void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, in
 
 void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
                   const int64_t *leaf_off, int k0, const float *Qp, int64_t nq,
-                  const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s) {
+                  const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s,
+                  CmTile tile) {
     if (nq == 0) return;
     const int64_t npairs = nq * P;
     Scratch<float> qn(nq, s), seed_d((size_t)nq * K, s);
@@ -592,11 +595,11 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     // pairs of an absent parent (sel = -1, fewer children than probes) are in
     // no work item: their lists stay empty
     MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
-    cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s);
+    cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s, tile.qpi);
     Scratch<int4> meta;
     Scratch<int32_t> ipid, iqid;
     cm_item_meta(pairs.get(), poff.get(), item_off.get(), leaf_off, npairs, P, k0, meta, ipid, iqid,
-                 s);
+                 s, tile.qpi);
     {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         const int XS = cm_stride(dp / 4);
@@ -610,6 +613,7 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
         int dev = 0, sms = 0;
         MASK_CUDA(cudaGetDevice(&dev));
         MASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (tile.bps > 0) per_sm = std::min(per_sm, tile.bps);
         cm_scan_kernel<<<std::max(1, per_sm) * sms, CM_THREADS, smem, s>>>(
             reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids,
             reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef_tc, meta.get(),

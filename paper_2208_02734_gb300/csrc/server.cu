@@ -82,11 +82,26 @@ struct Key {
     }
 };
 
+// The leaf-scan configurations the autotuner times for an FP32 shape: the
+// query-major scan, and the cluster-major scan at each (queries per work
+// item, blocks per SM) pair (0 blocks per SM: as many as fit).  All give
+// bit-identical results.
+struct LeafConfig {
+    LeafMode mode;
+    CmTile tile;
+};
+const LeafConfig kLeafConfigs[] = {
+    {LeafMode::Query, CmTile{16, 0}},  {LeafMode::Cluster, CmTile{16, 0}},
+    {LeafMode::Cluster, CmTile{16, 1}}, {LeafMode::Cluster, CmTile{8, 0}},
+    {LeafMode::Cluster, CmTile{8, 1}},
+};
+constexpr int kNumLeafConfigs = (int)(sizeof(kLeafConfigs) / sizeof(kLeafConfigs[0]));
+
 struct Shape {
     Key key;
     int64_t bucket = 0;
     int K = 0;
-    int mode = 0;  // LeafMode
+    int mode = 0;  // index into kLeafConfigs
     bool operator<(const Shape &o) const {
         return std::tie(key, bucket, K, mode) < std::tie(o.key, o.bucket, o.K, o.mode);
     }
@@ -152,7 +167,7 @@ struct mask_server {
 
     // worker-owned
     std::multimap<Shape, std::unique_ptr<Instance>> cache;
-    std::map<std::tuple<Key, int64_t, int>, int> tuned;  // (key, bucket, K) -> leaf mode
+    std::map<std::tuple<Key, int64_t, int>, int> tuned;  // (key, bucket, K) -> leaf config
     size_t inflight_bytes = 0;
 
     // statistics (under mu)
@@ -255,9 +270,10 @@ std::unique_ptr<Instance> make_instance(mask_server *S, const Shape &sh) {
     cudaGraph_t g = nullptr;
     MASK_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
     try {
+        const LeafConfig &lc = kLeafConfigs[sh.mode];
         query_dense(idx, inst->Qp.get(), sh.bucket, sh.K, sh.key.probes,
-                    (mask_precision)sh.key.prec, (LeafMode)sh.mode, inst->ids.get(),
-                    inst->dists.get(), S->cap_stream);
+                    (mask_precision)sh.key.prec, lc.mode, inst->ids.get(), inst->dists.get(),
+                    S->cap_stream, lc.tile);
     } catch (...) {
         cudaStreamEndCapture(S->cap_stream, &g);
         if (g) cudaGraphDestroy(g);
@@ -325,16 +341,17 @@ void launch(mask_server *S, int slot, Batch &b) {
     MASK_CUDA(cudaEventRecord(S->events[(size_t)slot], st));
 }
 
-// Leaf scan for an FP32 shape: the faster of the two captured graphs, timed
-// once on the batch at hand (both give bit-identical results).
+// Leaf scan for an FP32 shape: the fastest of the configurations' captured
+// graphs, each timed once on the batch at hand; other shapes take the
+// query-major scan (configuration 0).
 int tune_mode(mask_server *S, int slot, Batch &b, const Key &key, int64_t bucket, int K) {
-    if (key.prec != MASK_FP32 || !cm_leaf_supported(S->idx->dp, K)) return (int)LeafMode::Query;
+    if (key.prec != MASK_FP32 || !cm_leaf_supported(S->idx->dp, K)) return 0;
     const auto tk = std::make_tuple(key, bucket, K);
     auto it = S->tuned.find(tk);
     if (it != S->tuned.end()) return it->second;
     cudaStream_t st = S->streams[(size_t)slot];
     float best_ms = 0.f;
-    int best = (int)LeafMode::Query;
+    int best = 0;
     // the events are released on every exit, including a failed CUDA call
     struct Events {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -346,7 +363,7 @@ int tune_mode(mask_server *S, int slot, Batch &b, const Key &key, int64_t bucket
     MASK_CUDA(cudaEventCreate(&ev.a));
     MASK_CUDA(cudaEventCreate(&ev.b));
     cudaEvent_t e0 = ev.a, e1 = ev.b;
-    for (int mode : {(int)LeafMode::Query, (int)LeafMode::Cluster}) {
+    for (int mode = 0; mode < kNumLeafConfigs; ++mode) {
         Shape sh{key, bucket, K, mode};
         b.inst = get_instance(S, sh);
         stage(S, b);
@@ -361,12 +378,16 @@ int tune_mode(mask_server *S, int slot, Batch &b, const Key &key, int64_t bucket
         count_launches(4 * b.inst->kernels);
         float ms = 0.f;
         MASK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (mode == (int)LeafMode::Query || ms < best_ms) {
+        if (mode == 0 || ms < best_ms) {
             best_ms = ms;
             best = mode;
         }
     }
     S->tuned[tk] = best;
+    // the losing configurations' graphs and buffers are not needed again
+    for (int mode = 0; mode < kNumLeafConfigs; ++mode)
+        if (mode != best) S->cache.erase(Shape{key, bucket, K, mode});
+    b.inst = nullptr;
     std::lock_guard<std::mutex> lk(S->mu);
     S->autotuned += 1;
     return best;

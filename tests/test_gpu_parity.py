@@ -287,15 +287,18 @@ def test_low_precision_probes_beyond_the_children_kept(loaded, prec):
     assert overlap >= 0.9, overlap
 
 
-def test_leaf_scan_paths_agree_bitwise(monkeypatch, loaded):
-    # both leaf scans evaluate sum_t (x_t - q_t)^2 in the same order
+@pytest.mark.parametrize("tile", ["", ":16:1", ":8:0", ":8:1", ":3:2", ":1:0"])
+def test_leaf_scan_paths_agree_bitwise(monkeypatch, loaded, tile):
+    # both leaf scans evaluate sum_t (x_t - q_t)^2 in the same order, at every
+    # cluster-major tile the serving autotuner may pick (queries per work
+    # item, blocks per SM)
     X, Q, ref, idx = loaded
     out = {}
-    for leaf in ["query", "cluster"]:
+    for leaf in ["query", "cluster" + tile]:
         monkeypatch.setenv("MASK_LEAF_SCAN", leaf)
         out[leaf] = M.mask_query(idx, cuda(Q), 10, [12, 6])
-    assert torch.equal(out["query"][0], out["cluster"][0])
-    assert torch.equal(out["query"][1], out["cluster"][1])
+    assert torch.equal(out["query"][0], out["cluster" + tile][0])
+    assert torch.equal(out["query"][1], out["cluster" + tile][1])
 
 
 def test_empty_leaf_clusters(monkeypatch, c1):
