@@ -40,9 +40,12 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace mask {
 namespace {
+
+using namespace tc;
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int TC_M = 128, TC_N = 128;   // MMA tile: 128 rows x 128 centroids
@@ -63,95 +66,6 @@ static_assert(TC_ACOL + TC_DK <= 512, "accumulators and rows fit the 512 TMEM co
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) |
                             ((uint32_t)(TC_M >> 4) << 24);
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait for the phase with the given parity to complete.  Gives up
-// after kWaitNs of wall time, or as soon as any CTA of the grid has raised the
-// abort word, and then raises it itself so the rest of the grid stops early.
-// A drain (waiting for this thread's own copies before the CTA exits) ignores
-// the abort word and is bounded by time only.
-constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s; a healthy wait takes microseconds
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *abort_word,
-                                          bool drain = false) {
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t i = 0;; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((i & 255u) == 255u) {
-            if ((!drain && *(volatile int *)abort_word != 0) || globaltimer_ns() - t0 > kWaitNs) {
-                atomicExch(abort_word, 1);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16).
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
-                                          uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (SBO); the leading offset is unused in this mode.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
-    d |= (uint64_t)1u << 46;
-    d |= (uint64_t)2u << 61;
-    return d;
-}
-
 // D (+)= A.B^T on tcgen05 (kind::f16, FP32 accumulation in tensor memory),
 // with the A operand in tensor memory (row i in lane i, two fp16 values of
 // consecutive K per 32-bit column, lower K in the low half) and B in shared
@@ -164,53 +78,6 @@ __device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uin
         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(accumulate)
         : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-// 32 consecutive fp32 columns of this thread's TMEM lane (issue only; the
-// registers are valid after tmem_wait()).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-        "[%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// 32 consecutive fp32 columns of this thread's TMEM lane from registers
-// (complete after tmem_wait_st()).
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
-            taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
-        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
-        "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Named barrier 1 over the epilogue threads (warps 4 and up) that also ANDs a
@@ -336,9 +203,9 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
@@ -371,7 +238,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         // the CTA's rows are in tensor memory (columns TC_ACOL..): hi parts
         // first, then lo parts, 8 columns (16 fp16 values) per K-step
         bool ok = mbar_wait(a_full, 0, err);
-        tc_fence_after();
+        fence_after();
         const uint32_t tAh = tmem + TC_ACOL, tAl = tmem + TC_ACOL + TC_DK / 2;
         int last = -1;
         for (int j = 0; ok && j < ntiles; ++j) {
@@ -379,7 +246,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             ok = mbar_wait(b_full(s), u & 1, err);
             if (ok && v > 0) ok = mbar_wait(acc_empty(a), (v - 1) & 1, err);
             if (!ok) break;
-            tc_fence_after();
+            fence_after();
             const uint32_t d = tmem + (uint32_t)(a * TC_N);
             const uint32_t bh = B0 + s * kStage, bl = bh + TC_BOX_BYTES;
             const uint64_t dBh = sw128_desc(bh), dBl = sw128_desc(bl);
@@ -432,7 +299,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
                 tmem_st32(lane_addr + (uint32_t)(h * (TC_DK / 2)), hv);
             }
             tmem_wait_st();
-            tc_fence_before();
+            fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(a_full);
         }
@@ -467,7 +334,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             const int q = j % TC_NRING, w = j / TC_NRING;
             ok = mbar_wait(acc_full(a), v & 1, err) && mbar_wait(n_full(q), w & 1, err);
             if (!__all_sync(kFull, ok)) { ok = false; break; }  // the warp leaves as one
-            tc_fence_after();
+            fence_after();
             const uint32_t taddr =
                 tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * TC_N + col);
             uint32_t u[TC_EPI_LD][32];
@@ -475,7 +342,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             for (int h = 0; h < TC_EPI_LD; ++h) tmem_ld32(taddr + 32 * h, u[h]);
             tmem_wait();
             // the accumulator is in registers: hand the buffer back to the MMA warp
-            tc_fence_before();
+            fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty(a));
             // keys of this thread's columns, with the minimum of each group
@@ -579,10 +446,10 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             }
         }
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 2) {
-        tc_fence_after();
+        fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
     if (threadIdx.x == 0 && s_err) atomicExch(err, 1);
@@ -704,38 +571,10 @@ __global__ void pad_inf_kernel(float *__restrict__ cn, int k, int total) {
     if (i < total) cn[i] = __int_as_float(0x7f800000);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-        cudaGetLastError();
-    });
-    return fn;
-}
-
 // 2-D tensor map of a [rows x 64] fp16 array, boxes of 128 rows x 64 columns
 // (one 128-byte row each), 128-byte swizzle, zero fill out of bounds.
 CUtensorMap make_map(const __half *base, int64_t rows) {
-    auto fn = encode_fn();
-    if (fn == nullptr) fail(MASK_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-    CUtensorMap m;
-    std::memset(&m, 0, sizeof(m));
-    const cuuint64_t dims[2] = {(cuuint64_t)TC_DK, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)TC_DK * 2u};
-    const cuuint32_t box[2] = {(cuuint32_t)TC_DK, (cuuint32_t)TC_M};
-    const cuuint32_t estr[2] = {1u, 1u};
-    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims,
-                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) fail(MASK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-    return m;
+    return tc::make_map_2d(base, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, rows, TC_DK, TC_M, TC_DK);
 }
 
 int grid_cap(int64_t work) {

@@ -380,13 +380,30 @@ void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, in
 // xn [rows] = ||row of Xs||^2 (FP32); the scan evaluates a row exactly only
 // where its expanded-form distance can reach the query's current K-th
 // Work-item shape of the cluster-major scans, chosen by the serving loop's
-// autotuner: queries per item (<= kCmItemQueries) and blocks per SM (0: as
-// many as fit).
+// autotuner: queries per item (<= kCmItemQueries), the kernel (the
+// tensor-core scan where it applies, or the mma.sync scan), and for the
+// latter blocks per SM (0: as many as fit).
 struct CmTile {
     int qpi = 16;
     int bps = 0;
+    bool legacy = false;
 };
-void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
+
+// The tensor-core cluster-major scan (query_cm_tc.cu): rows of 32 or 64
+// floats, K <= 32.  A bounded pipeline wait that ran out raises a device
+// error word; cm_tc_check (synchronising) reports it as MASK_ETIMEOUT and
+// clears it, cm_tc_error_word gives its device address.
+bool cm_tc_supported(int dp, int K);
+void cm_tc_scan(const float *Xs, int64_t n, const float *xn, int dp, const int32_t *xids,
+                const float *Qp, const float *qn, const float *seed_d, float mcoef,
+                const int4 *meta, const int32_t *pid, const int32_t *qid, const int64_t *item_off,
+                int k0, int K, unsigned long long *pair_out, unsigned long long *bytes_ctr,
+                cudaStream_t s);
+int *cm_tc_error_word();
+void cm_tc_check(cudaStream_t s);
+// Whether cm_tc_scan was called on this thread since the last call (clears).
+bool cm_tc_take_launched();
+void cm_leaf_scan(const float *Xs, int64_t n, const float *xn, int dp, const int32_t *xids,
                   const int64_t *leaf_off, int k0, const float *Qp, int64_t nq,
                   const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s,
                   CmTile tile = CmTile{});

@@ -583,8 +583,8 @@ void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
     if (mode == LeafMode::Cluster) cluster_major = cm_leaf_supported(dp, k);
     if (mode == LeafMode::Query) cluster_major = false;
     if (cluster_major) {
-        cm_leaf_scan(idx.Xs.get(), idx.xn.get(), dp, idx.xids.get(), idx.lv[0].off.get(), k0, Qp,
-                     nq, sel[0].get(), p[0], k, ids, dists, s, tile);
+        cm_leaf_scan(idx.Xs.get(), idx.n, idx.xn.get(), dp, idx.xids.get(), idx.lv[0].off.get(),
+                     k0, Qp, nq, sel[0].get(), p[0], k, ids, dists, s, tile);
     } else {
         ScanArgs c = a;
         c.R = idx.Xs.get();
@@ -791,9 +791,11 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
         pad_rows(Qin.p, nq, index->d, Qp.get(), dp, s);
         Out<int64_t> ids(ids_out, (size_t)nq * k, s);
         Out<float> dd(dists_out, (size_t)nq * k, s);
+        cm_tc_take_launched();
         query_dense(*index, Qp.get(), nq, k, p, precision, mode, ids.p, dd.p, s, tile);
         ids.finish(s);
         dd.finish(s);
+        if (cm_tc_take_launched()) cm_tc_check(s);   // synchronises; MASK_ETIMEOUT on a stall
         if (ids.host || dd.host) MASK_CUDA(cudaStreamSynchronize(s));
     });
 }

@@ -566,7 +566,7 @@ void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, in
     scan_topk(a, s);
 }
 
-void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
+void cm_leaf_scan(const float *Xs, int64_t n, const float *xn, int dp, const int32_t *xids,
                   const int64_t *leaf_off, int k0, const float *Qp, int64_t nq,
                   const int32_t *sel, int P, int K, int64_t *ids, float *dists, cudaStream_t s,
                   CmTile tile) {
@@ -600,7 +600,20 @@ void cm_leaf_scan(const float *Xs, const float *xn, int dp, const int32_t *xids,
     Scratch<int32_t> ipid, iqid;
     cm_item_meta(pairs.get(), poff.get(), item_off.get(), leaf_off, npairs, P, k0, meta, ipid, iqid,
                  s, tile.qpi);
-    {
+    if (!tile.legacy && cm_tc_supported(dp, K)) {
+        // the tensor-core scan (kind::tf32): the rows are read as TF32
+        // (|x - x_tf32| <= 2^-10 |x|), the queries split into an exact TF32
+        // part and a remainder read as TF32 (2^-20 |q|), which leaves
+        // (2^-10 + 2^-20 + 2^-30) of sum |x_t q_t| in the units above;
+        // accumulation: 2 ceil(dp/8) MMAs plus 8 in-MMA additions at 2^-22
+        const float mcoef_t =
+            mcoef + (float)((0x1.0p-10 + 0x1.0p-20 + 0x1.0p-30 + (2.0 * ((dp + 7) / 8) + 8.0) *
+                                                                    0x1.0p-22) * 1.125);
+        ProfRegion pr("scan_leaf_cm", s, 0.0);
+        cm_tc_scan(Xs, n, xn, dp, xids, Qp, qn.get(), seed_d.get(), mcoef_t, meta.get(),
+                   ipid.get(), iqid.get(), item_off.get(), k0, K, pair_out.get(),
+                   cm_bytes_counter(), s);
+    } else {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         const int XS = cm_stride(dp / 4);
         const size_t smem = ((size_t)2 * CM_R * XS + (size_t)2 * CM_QB * XS + 2 * CM_R) * 4 +

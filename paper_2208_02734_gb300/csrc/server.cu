@@ -115,6 +115,8 @@ struct Instance {
     float *hQ = nullptr;
     int64_t *hids = nullptr;
     float *hd = nullptr;
+    int *herr = nullptr;      // pinned copy of the tensor-core scan's error word
+    bool check_tc = false;    // the graph holds the tensor-core leaf scan
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
     bool busy = false;
@@ -125,6 +127,7 @@ struct Instance {
         if (hQ) cudaFreeHost(hQ);
         if (hids) cudaFreeHost(hids);
         if (hd) cudaFreeHost(hd);
+        if (herr) cudaFreeHost(herr);
     }
 };
 
@@ -263,11 +266,15 @@ std::unique_ptr<Instance> make_instance(mask_server *S, const Shape &sh) {
     MASK_CUDA(cudaMallocHost((void **)&inst->hids, B * K * sizeof(int64_t)));
     count_alloc();
     MASK_CUDA(cudaMallocHost((void **)&inst->hd, B * K * sizeof(float)));
+    count_alloc();
+    MASK_CUDA(cudaMallocHost((void **)&inst->herr, sizeof(int)));
+    *inst->herr = 0;
     std::memset(inst->hQ, 0, B * dp * sizeof(float));
     MASK_CUDA(cudaMemsetAsync(inst->Qp.get(), 0, B * dp * sizeof(float), S->cap_stream));
     if (sh.key.prec != MASK_FP32) ensure_lowp(idx, sh.key.prec == MASK_FP8E4M3, S->cap_stream);
     MASK_CUDA(cudaStreamSynchronize(S->cap_stream));
     cudaGraph_t g = nullptr;
+    cm_tc_take_launched();
     MASK_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
     try {
         const LeafConfig &lc = kLeafConfigs[sh.mode];
@@ -281,6 +288,7 @@ std::unique_ptr<Instance> make_instance(mask_server *S, const Shape &sh) {
         throw;
     }
     MASK_CUDA(cudaStreamEndCapture(S->cap_stream, &g));
+    inst->check_tc = cm_tc_take_launched();
     cudaError_t e = cudaGraphInstantiate(&inst->exec, g, 0);
     size_t nn = 0;
     if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &nn);
@@ -338,6 +346,9 @@ void launch(mask_server *S, int slot, Batch &b) {
                               cudaMemcpyDeviceToHost, st));
     MASK_CUDA(cudaMemcpyAsync(in->hd, in->dists.get(), (size_t)b.nq * K * sizeof(float),
                               cudaMemcpyDeviceToHost, st));
+    if (in->check_tc)
+        MASK_CUDA(cudaMemcpyAsync(in->herr, cm_tc_error_word(), sizeof(int),
+                                  cudaMemcpyDeviceToHost, st));
     MASK_CUDA(cudaEventRecord(S->events[(size_t)slot], st));
 }
 
@@ -444,7 +455,13 @@ bool retire(mask_server *S) {
         const cudaError_t e = cudaEventQuery(S->events[s]);
         if (e == cudaErrorNotReady) continue;
         const size_t K = (size_t)b.inst->shape.K;
-        if (e == cudaSuccess) {
+        // a leaf scan whose bounded wait ran out fails the batch's requests
+        const bool stalled = e == cudaSuccess && b.inst->check_tc && *b.inst->herr != 0;
+        if (stalled) {
+            *b.inst->herr = 0;
+            MASK_CUDA(cudaMemsetAsync(cm_tc_error_word(), 0, sizeof(int), S->streams[s]));
+        }
+        if (e == cudaSuccess && !stalled) {
             int64_t row = 0;
             for (const Piece &p : b.pieces) {
                 Request &r = *p.r;
@@ -468,6 +485,10 @@ bool retire(mask_server *S) {
                 p.r->failed = true;
                 p.r->status = MASK_ECUDA;
                 p.r->err = std::string("query batch: ") + cudaGetErrorString(e);
+            } else if (stalled && !p.r->failed) {
+                p.r->failed = true;
+                p.r->status = MASK_ETIMEOUT;
+                p.r->err = "query batch: a bounded pipeline wait of the leaf scan ran out";
             }
             p.r->left -= p.q1 - p.q0;
             if (p.r->left == 0) finish_locked(S, *p.r);
