@@ -42,6 +42,8 @@ def main(argv=None) -> None:
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
+                    help="query step: the leaf scan's precision")
     ap.add_argument("--profile", action="store_true",
                     help="also report the library's per-kernel device times")
     a = ap.parse_args(argv)
@@ -84,7 +86,8 @@ def main(argv=None) -> None:
         elif a.step == "kmeanspp":
             M.mask_kmeanspp(X, a.k, seed=0)
         elif a.step == "query":
-            M.mask_query(state["index"], state["Q"], a.topk, probes)
+            prec = {"fp32": M.MASK_FP32, "bf16": M.MASK_BF16, "fp8": M.MASK_FP8E4M3}[a.precision]
+            M.mask_query(state["index"], state["Q"], a.topk, probes, precision=prec)
         elif a.step == "csr_assign":
             M.mask_kmeans_assign_csr(*csr, a.d, C, with_dist=False)
         elif a.step == "csr_kmeanspp":
@@ -114,7 +117,8 @@ def main(argv=None) -> None:
         M.mask_profile_enable(False)
         for name in ("assign_tc", "assign_gemm", "assign_recheck", "kmeanspp", "label_sort",
                      "centroid_update", "scan_topk_level", "scan_topk_leaf", "scan_leaf_cm",
-                     "leaf_group", "leaf_merge", "csr_scan_leaf_cm", "csr_assign",
+                     "leaf_group", "leaf_merge", "scan_leaf_bf16", "scan_leaf_fp8", "leaf_rerank",
+                     "csr_scan_leaf_cm", "csr_assign",
                      "csr_spmm_assign", "csr_centroid_update", "csr_scan_level", "csr_scan_leaf"):
             r = M.mask_profile_read(name)
             if r:
