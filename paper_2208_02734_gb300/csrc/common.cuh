@@ -359,6 +359,9 @@ struct ScanArgs {
     int32_t *out_ids32 = nullptr; // [nq x K] (levels) ...
     int64_t *out_ids64 = nullptr; // ... or int64 (leaf)
     float *out_d = nullptr;       // [nq x K] (may be null)
+    // centroid levels: false when only the first (nearest) key's place
+    // matters to the caller, who reads the rest as a set
+    bool sorted = true;
 };
 void scan_topk(const ScanArgs &a, cudaStream_t s);
 // bytes streamed by the scans since the last reset ([0] levels, [1] leaf)

@@ -520,7 +520,7 @@ bool all_ones(const std::vector<int> &p) {
 // The descent of Algorithm 2 down to the leaf clusters: sel[l] [nq x p_l]
 // receives each level's kept centroids (cluster ids), nearest first.
 void descend_levels(const mask_index &idx, const float *Qp, int64_t nq, const std::vector<int> &p,
-                    std::vector<Scratch<int32_t>> &sel, cudaStream_t s) {
+                    std::vector<Scratch<int32_t>> &sel, cudaStream_t s, bool sorted_last) {
     const int L = idx.L, dp = idx.dp;
     sel.resize((size_t)L);
     for (int l = 0; l < L; ++l) sel[(size_t)l].alloc((size_t)nq * p[(size_t)l], s);
@@ -534,6 +534,9 @@ void descend_levels(const mask_index &idx, const float *Qp, int64_t nq, const st
     a.root_end = idx.lv[(size_t)top].k;
     a.K = p[(size_t)top];
     a.out_ids32 = sel[(size_t)top].get();
+    // the kept parents of a level are read as a set; the last level's list
+    // only needs its nearest entry first, unless the caller wants it sorted
+    a.sorted = top == 0 ? sorted_last : false;
     scan_topk(a, s);
     for (int l = top; l >= 1; --l) {
         ScanArgs b = a;
@@ -544,6 +547,7 @@ void descend_levels(const mask_index &idx, const float *Qp, int64_t nq, const st
         b.P = p[(size_t)l];
         b.K = p[(size_t)l - 1];
         b.out_ids32 = sel[(size_t)l - 1].get();
+        b.sorted = l == 1 ? sorted_last : false;
         scan_topk(b, s);
     }
 }
@@ -561,7 +565,7 @@ void query_dense(const mask_index &idx, const float *Qp, int64_t nq, int k,
         return;
     }
     std::vector<Scratch<int32_t>> sel;
-    descend_levels(idx, Qp, nq, p, sel, s);
+    descend_levels(idx, Qp, nq, p, sel, s, false);
     ScanArgs a;
     a.Q = Qp;
     a.nq = nq;
@@ -1207,7 +1211,7 @@ mask_status mask_descend(const mask_index *index, const float *queries, int64_t 
             greedy_descent(greedy_levels(*index), L, index->Xs.get(), index->xids.get(), dp,
                            Qp.get(), nq, lo.p, nullptr, nullptr, s);
         } else {
-            descend_levels(*index, Qp.get(), nq, p, sel, s);
+            descend_levels(*index, Qp.get(), nq, p, sel, s, true);
         }
         if (!sel.empty() && p[0] == probes[0]) {
             MASK_CUDA(cudaMemcpyAsync(lo.p, sel[0].get(), sizeof(int32_t) * nq * p[0],

@@ -157,7 +157,7 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     const int64_t *__restrict__ off, const int32_t *__restrict__ sel, int P, int64_t root_end,
     const float4 *__restrict__ Q, int K, int KP, int S, int32_t *__restrict__ out32,
     int64_t *__restrict__ out64, float *__restrict__ out_d,
-    unsigned long long *__restrict__ bytes_ctr) {
+    unsigned long long *__restrict__ bytes_ctr, int sorted) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem);  // S keys
     // KP keys, padded to an even count so the float4 query chunks below stay
@@ -339,11 +339,38 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
             __syncthreads();
             nsel = min(cnt, K);
         }
-        int L = 1;
-        while (L < nsel) L <<= 1;
-        for (int i = nsel + tid; i < L; i += kThreads) pick[i] = kNoKey;
-        __syncthreads();
-        bitonic_sort_keys(pick, L);
+        if (sorted) {
+            int L = 1;
+            while (L < nsel) L <<= 1;
+            for (int i = nsel + tid; i < L; i += kThreads) pick[i] = kNoKey;
+            __syncthreads();
+            bitonic_sort_keys(pick, L);
+        } else {
+            // the caller reads the keys as a set, except that the smallest
+            // comes first: find it (block reduction) and swap it to the front
+            __shared__ unsigned long long s_min[kThreads / 32];
+            __shared__ int s_at[kThreads / 32];
+            unsigned long long mn = kNoKey;
+            int at = 0;
+            for (int i = tid; i < nsel; i += kThreads)
+                if (pick[i] < mn) { mn = pick[i]; at = i; }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long v = __shfl_xor_sync(kFull, mn, o);
+                const int ai = __shfl_xor_sync(kFull, at, o);
+                if (v < mn) { mn = v; at = ai; }
+            }
+            if ((tid & 31) == 0) { s_min[tid >> 5] = mn; s_at[tid >> 5] = at; }
+            __syncthreads();
+            if (tid == 0 && nsel > 0) {
+                int a0 = s_at[0];
+                unsigned long long m0 = s_min[0];
+                for (int w = 1; w < kThreads / 32; ++w)
+                    if (s_min[w] < m0) { m0 = s_min[w]; a0 = s_at[w]; }
+                pick[a0] = pick[0];
+                pick[0] = m0;
+            }
+            __syncthreads();
+        }
         for (int i = tid; i < K; i += kThreads) buf[i] = i < nsel ? pick[i] : kNoKey;
         __syncthreads();
     }
@@ -458,7 +485,8 @@ void scan_topk(const ScanArgs &a, cudaStream_t s) {
         kfn<<<(unsigned)a.nq, kThreads, smem, s>>>(R, a.dp / 4, a.rid, a.off, a.sel, P,      \
                                                    a.root_end, Qv, a.K, KP, S, a.out_ids32,  \
                                                    a.out_ids64, a.out_d,                     \
-                                                   scan_bytes_counter(a.out_ids64 ? 1 : 0)); \
+                                                   scan_bytes_counter(a.out_ids64 ? 1 : 0),  \
+                                                   a.sorted ? 1 : 0);                        \
     } while (0)
     if (a.out_ids64) {
         MASK_SCAN(true, 1);  // the leaf: per-row arithmetic shared with the cluster-major scan
