@@ -18,6 +18,7 @@
 // Candidates below the current K-th key are appended to a shared-memory
 // buffer, which is bitonic-sorted together with the current top list whenever
 // it could overflow.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -385,6 +386,11 @@ __global__ __launch_bounds__(kThreads) void scan_topk_kernel(
     }
 }
 
+// Lanes per row of the centroid-level distances (scan_topk_kernel's lane
+// groups and the greedy descent, which must agree): at most 4, so a row of
+// up to 64 floats takes at most two shuffle steps to reduce.
+int level_lanes_per_row(int dp) { return std::min(lanes_per_row(dp), 4); }
+
 int next_pow2(int v) {
     int p = 1;
     while (p < v) p <<= 1;
@@ -467,7 +473,8 @@ __global__ __launch_bounds__(kThreads) void greedy_descent_kernel(GreedyLevels l
 void scan_topk(const ScanArgs &a, cudaStream_t s) {
     if (a.nq == 0) return;
     MASK_REQUIRE(a.K >= 1 && a.K <= 4096, "scan_topk: K out of range");
-    const int round = a.out_ids64 ? kThreads * kUnroll : (kThreads / lanes_per_row(a.dp)) * 4;
+    const int round =
+        a.out_ids64 ? kThreads * kUnroll : (kThreads / level_lanes_per_row(a.dp)) * 4;
     const int KP = next_pow2(a.K);
     int S = next_pow2(KP + 2 * round > 4 * KP ? KP + 2 * round : 4 * KP);
     if (!a.out_ids64 && S < 2048) S = 2048;  // centroid levels: room to keep every candidate
@@ -491,7 +498,7 @@ void scan_topk(const ScanArgs &a, cudaStream_t s) {
     if (a.out_ids64) {
         MASK_SCAN(true, 1);  // the leaf: per-row arithmetic shared with the cluster-major scan
     } else {
-        switch (lanes_per_row(a.dp)) {
+        switch (level_lanes_per_row(a.dp)) {
         case 1: MASK_SCAN(false, 1); break;
         case 2: MASK_SCAN(false, 2); break;
         case 4: MASK_SCAN(false, 4); break;
@@ -515,7 +522,7 @@ void greedy_descent(const GreedyLevels &lv, int L, const float *Xs, const int32_
 #define MASK_GREEDY(LPRV)                                                                    \
     greedy_descent_kernel<LPRV><<<blocks, kThreads, 0, s>>>(lv, L, X4, xids, Q4, nq, dp / 4, \
                                                            leaf, ids, dists)
-    switch (lanes_per_row(dp)) {
+    switch (level_lanes_per_row(dp)) {
     case 1: MASK_GREEDY(1); break;
     case 2: MASK_GREEDY(2); break;
     case 4: MASK_GREEDY(4); break;
