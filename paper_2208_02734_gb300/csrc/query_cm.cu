@@ -67,6 +67,68 @@ __global__ void first_col_kernel(const int32_t *__restrict__ sel, int64_t nq, in
         out[q] = sel[q * P];
 }
 
+// The seed of the leaf scans, one warp per query: the K smallest exact
+// distances among the rows of the query's nearest kept cluster sel[q * P]
+// (ascending, +inf past the cluster's rows).  Rows one per lane with the
+// arithmetic of the per-query leaf scan (sum over t of (x_t - q_t)^2, FMAs, t
+// ascending); each lane keeps its 32 smallest in registers (an insertion
+// network), and K rounds of warp minimum take the K smallest of all lanes.
+constexpr int kSeedK = 32;
+__global__ __launch_bounds__(256) void leaf_seed_warp_kernel(
+    const float4 *__restrict__ Xs, int dp4, const int64_t *__restrict__ leaf_off,
+    const float4 *__restrict__ Q, int64_t nq, const int32_t *__restrict__ sel, int P, int K,
+    float *__restrict__ seed_d) {
+    __shared__ __align__(16) float4 qs[8][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * 8 + w;
+    if (q >= nq) return;   // whole warps leave together
+    for (int c = lane; c < dp4; c += 32) qs[w][c] = Q[q * dp4 + c];
+    __syncwarp();
+    const int32_t c0 = sel[q * P];
+    int64_t b = 0, e = 0;
+    if (c0 >= 0) {
+        b = leaf_off[c0];
+        e = leaf_off[c0 + 1];
+    }
+    const float inf = __int_as_float(0x7f800000);
+    float t[kSeedK];
+#pragma unroll
+    for (int j = 0; j < kSeedK; ++j) t[j] = inf;
+    for (int64_t row = b + lane; row < e; row += 32) {
+        const float4 *r = Xs + row * dp4;
+        float acc = 0.f;
+#pragma unroll 4
+        for (int c = 0; c < dp4; ++c) {
+            const float4 v = r[c], x = qs[w][c];
+            float d = v.x - x.x;
+            acc = fmaf(d, d, acc);
+            d = v.y - x.y;
+            acc = fmaf(d, d, acc);
+            d = v.z - x.z;
+            acc = fmaf(d, d, acc);
+            d = v.w - x.w;
+            acc = fmaf(d, d, acc);
+        }
+#pragma unroll
+        for (int j = kSeedK - 1; j > 0; --j)
+            t[j] = t[j - 1] > acc ? t[j - 1] : (t[j] > acc ? acc : t[j]);
+        t[0] = fminf(t[0], acc);
+    }
+    for (int rd = 0; rd < K; ++rd) {
+        float m = t[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(kFull, m, o));
+        // one lane holding the minimum at its head pops it
+        const unsigned bal = __ballot_sync(kFull, t[0] == m);
+        if (lane == __ffs(bal) - 1) {
+#pragma unroll
+            for (int j = 0; j < kSeedK - 1; ++j) t[j] = t[j + 1];
+            t[kSeedK - 1] = inf;
+        }
+        if (lane == 0) seed_d[q * K + rd] = m;
+    }
+}
+
 // labels for grouping: the kept cluster of each pair, or k0 for "none"
 __global__ void pair_labels_kernel(const int32_t *__restrict__ sel, int64_t npairs, int k0,
                                    int32_t *__restrict__ lab) {
@@ -547,6 +609,14 @@ void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, in
                const float *Qp, int64_t nq, const int32_t *sel, int P, int K, float *seed_d,
                cudaStream_t s) {
     if (nq == 0) return;
+    if (K <= kSeedK && dp <= 128) {
+        ProfRegion pr("scan_topk_leaf", s, 0.0);
+        leaf_seed_warp_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(
+            reinterpret_cast<const float4 *>(Xs), dp / 4, leaf_off,
+            reinterpret_cast<const float4 *>(Qp), nq, sel, P, K, seed_d);
+        MASK_LAUNCHED("leaf_seed");
+        return;
+    }
     Scratch<int64_t> seed_i((size_t)nq * K, s);
     Scratch<int32_t> sel0(nq, s);
     first_col_kernel<<<grid_cap(nq, 256), 256, 0, s>>>(sel, nq, P, sel0.get());
