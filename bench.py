@@ -625,6 +625,7 @@ def serving_requests(rng, Q, n, P, lowp):
 
 
 SERVE_FRACTIONS = (0.1, 0.25, 0.5, 0.75, 0.95)
+SAT_MAX_PASSES = 8  # backlog passes at most before the saturation measurement
 
 
 def serving_modes(w, dev, secs, fractions=SERVE_FRACTIONS, warm_n=400, backlog_n=2000):
@@ -670,11 +671,15 @@ def serving_modes(w, dev, secs, fractions=SERVE_FRACTIONS, warm_n=400, backlog_n
         warm = serving_requests(rng, Q, warm_n, P, prec)
         for t, _ in [submit(r) for r in warm]:
             t.result()
-        # saturation: a backlog of 2,000 requests submitted by 4 threads at once,
-        # twice (the first pass captures the graphs of the large merged batches)
+        # saturation: a backlog of 2,000 requests submitted by 4 threads at
+        # once, repeated until a pass meets no shape it has not seen (a pass is
+        # ~0.1 s, so one graph capture or tile autotuning inside it would
+        # dominate); the last pass is the measurement
         sub_s = [0.0] * SUBMITTERS
-        for rep in range(2):
+        sat_passes, caps_in_pass = 0, 0
+        for rep in range(SAT_MAX_PASSES):
             srv.stats(reset=True)
+            caps0 = srv.stats()["graph_captures"]
             sat = serving_requests(rng, Q, backlog_n, P, prec)
             done = [None] * len(sat)
 
@@ -693,6 +698,10 @@ def serving_modes(w, dev, secs, fractions=SERVE_FRACTIONS, warm_n=400, backlog_n
             for t, _ in done:
                 t.result()
             t_sat = time.perf_counter() - t0
+            sat_passes = rep + 1
+            caps_in_pass = srv.stats()["graph_captures"] - caps0
+            if rep >= 1 and caps_in_pass == 0:
+                break
         st = srv.stats(reset=True)
         sat_qps = st["queries_done"] / t_sat
         mean_q = st["queries_done"] / max(1, st["requests_done"])
@@ -707,21 +716,23 @@ def serving_modes(w, dev, secs, fractions=SERVE_FRACTIONS, warm_n=400, backlog_n
             _, g = exact_knn_fp64(Xd, qq, 10)
             hits += recall_at_k(Xd, qq, ids, g[:, -1:]) * ids.numel()
             tot += ids.numel()
-        rates = []
-        for frac in fractions:
+        def open_loop_window(frac, dur):
+            """Poisson arrivals at frac x saturation for dur seconds; returns
+            the server's stats over the window."""
             lam = frac * sat_qps / mean_q       # requests per second, SUBMITTERS streams
             streams = []
             for c in range(SUBMITTERS):
-                reqs = serving_requests(rng, Q, int(lam / SUBMITTERS * secs * 1.2) + 10, P, prec)
+                reqs = serving_requests(rng, Q, int(lam / SUBMITTERS * dur * 1.2) + 10, P, prec)
                 arr = np.cumsum(rng.exponential(SUBMITTERS / lam, size=len(reqs)))
                 streams.append((reqs, arr))
             srv.stats(reset=True)
+            caps0 = srv.stats()["graph_captures"]
             tickets = [[] for _ in range(SUBMITTERS)]
             start = time.perf_counter()
 
             def open_loop(c):
                 for r, ta in zip(*streams[c]):
-                    if ta > secs:
+                    if ta > dur:
                         break
                     delay = start + ta - time.perf_counter()
                     if delay > 0:
@@ -737,11 +748,21 @@ def serving_modes(w, dev, secs, fractions=SERVE_FRACTIONS, warm_n=400, backlog_n
                 for t, _ in tl:
                     t.result()
             st = srv.stats(reset=True)
+            st["captures_in_window"] = st["graph_captures"] - caps0
+            return st
+
+        rates = []
+        for frac in fractions:
+            # an untimed third of the window first: the batch shapes this rate
+            # forms get their graphs (and tiles) before the timed window
+            open_loop_window(frac, secs / 3)
+            st = open_loop_window(frac, secs)
             rates.append({"offered_fraction": frac, "offered_qps": frac * sat_qps,
                           "achieved_qps": st["queries_done"] / max(1e-9, st["elapsed_s"]),
                           "requests": st["requests_done"], "p50_ms": st["latency_p50_ms"],
                           "p99_ms": st["latency_p99_ms"], "max_ms": st["latency_max_ms"],
                           "mean_batch_queries": st["mean_batch_queries"],
+                          "graph_captures_in_window": st["captures_in_window"],
                           "peak_inflight_mb": st["peak_inflight_bytes"] / 2 ** 20})
             log(f"[serving] {mname} {frac:.2f}: {rates[-1]['achieved_qps']:.0f} q/s "
                 f"p50 {st['latency_p50_ms']:.2f} ms p99 {st['latency_p99_ms']:.2f} ms")
@@ -749,6 +770,8 @@ def serving_modes(w, dev, secs, fractions=SERVE_FRACTIONS, warm_n=400, backlog_n
         srv.close()
         out[mname] = {"saturation_qps": sat_qps, "recall_at_10": hits / max(1, tot),
                       "backlog_submit_s": max(sub_s), "backlog_s": t_sat,
+                      "saturation_passes": sat_passes,
+                      "graph_captures_in_measured_pass": caps_in_pass,
                       "rates": rates, "graph_captures": info["graph_captures"],
                       "autotuned_shapes": info["autotuned_shapes"],
                       "k100_requests_in_fp32": mname != "fp32"}
@@ -763,16 +786,19 @@ def serving_summary(dev, secs=3.0, fractions=(0.5, 0.95)):
     q/s, the served recall@10, and p50/p99 request latency per rate."""
     t0 = time.perf_counter()
     out, P, rec, launches, _, _ = serving_modes(WORKLOADS["serving"], dev, secs, fractions,
-                                                warm_n=200, backlog_n=1000)
+                                                warm_n=200, backlog_n=2000)
     summ = {"workload": WORKLOADS["serving"]["desc"], "probes_P": P,
             "recall_at_10_calibration": rec, "seconds_per_rate": secs,
             "gpu_launches": int(launches)}
     for m, r in out.items():
         summ[m] = {"saturation_qps": r["saturation_qps"], "recall_at_10": r["recall_at_10"],
-                   "autotuned_shapes": r["autotuned_shapes"]}
+                   "autotuned_shapes": r["autotuned_shapes"],
+                   "saturation_passes": r["saturation_passes"],
+                   "graph_captures_in_measured_pass": r["graph_captures_in_measured_pass"]}
         for x in r["rates"]:
             summ[m][f"at_{x['offered_fraction']}"] = {
-                k: x[k] for k in ("achieved_qps", "p50_ms", "p99_ms", "mean_batch_queries")}
+                k: x[k] for k in ("achieved_qps", "p50_ms", "p99_ms", "mean_batch_queries",
+                                  "graph_captures_in_window")}
     summ["wall_s"] = time.perf_counter() - t0
     return summ
 

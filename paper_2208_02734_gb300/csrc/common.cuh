@@ -380,14 +380,12 @@ void cm_merge(const unsigned long long *pair_out, int64_t nq, int P, int K, int6
 void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, int dp,
                const float *Qp, int64_t nq, const int32_t *sel, int P, int K, float *seed_d,
                cudaStream_t s);
-// xn [rows] = ||row of Xs||^2 (FP32); the scan evaluates a row exactly only
-// where its expanded-form distance can reach the query's current K-th
 // Work-item shape of the cluster-major scans, chosen by the serving loop's
-// autotuner: queries per item (<= kCmItemQueries), the kernel (the
-// tensor-core scan where it applies, or the mma.sync scan), and for the
-// latter blocks per SM (0: as many as fit).
+// autotuner: queries per item (0: the kernel's widest, cm_item_queries), the
+// kernel (the tensor-core scan where it applies, or the mma.sync scan), and
+// for the latter blocks per SM (0: as many as fit).
 struct CmTile {
-    int qpi = 16;
+    int qpi = 0;
     int bps = 0;
     bool legacy = false;
 };
@@ -397,11 +395,16 @@ struct CmTile {
 // error word; cm_tc_check (synchronising) reports it as MASK_ETIMEOUT and
 // clears it, cm_tc_error_word gives its device address.
 bool cm_tc_supported(int dp, int K);
+// widest work item of the tensor-core scan: 32 queries for K <= 16, else 16
+int cm_tc_item_queries(int K);
+// qs: queries per item slot of meta / pid / qid (16 or 32; the kernel's MMA
+// N); qbound [nq]: per query, an upper bound of its K-th distance (FP32 bits,
+// preset large), lowered as the scan goes
 void cm_tc_scan(const float *Xs, int64_t n, const float *xn, int dp, const int32_t *xids,
                 const float *Qp, const float *qn, const float *seed_d, float mcoef,
                 const int4 *meta, const int32_t *pid, const int32_t *qid, const int64_t *item_off,
-                int k0, int K, unsigned long long *pair_out, unsigned long long *bytes_ctr,
-                cudaStream_t s);
+                int k0, int K, int qs, unsigned long long *pair_out, unsigned *qbound,
+                unsigned long long *bytes_ctr, cudaStream_t s);
 int *cm_tc_error_word();
 void cm_tc_check(cudaStream_t s);
 // Whether cm_tc_scan was called on this thread since the last call (clears).
@@ -416,16 +419,18 @@ void cm_bytes_reset();
 void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
                     Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s,
                     int qpi = 16);
-// queries per work item of the cluster-major scans
+// queries per work item of the cluster-major scans (the tensor-core scan
+// also takes items of up to kCmTcItemQueries)
 constexpr int kCmItemQueries = 16;
-// per work item i of cm_group_pairs (cluster c, up to kCmItemQueries of its
+constexpr int kCmTcItemQueries = 32;
+// per work item i of cm_group_pairs (cluster c, up to qpi <= qs of its
 // pairs): meta[i] = {first row (lo, hi), rows of c, pairs in the item};
-// pid/qid[i * kCmItemQueries + q] = the item's q-th pair (-1 past the last)
-// and its query (0 past the last)
+// pid/qid[i * qs + q] = the item's q-th pair (-1 past the last) and its
+// query (0 past the last)
 void cm_item_meta(const int32_t *pairs, const int64_t *poff, const int64_t *item_off,
                   const int64_t *leaf_off, int64_t npairs, int P, int k0, Scratch<int4> &meta,
                   Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s,
-                  int qpi = 16);
+                  int qpi = kCmItemQueries, int qs = kCmItemQueries);
 
 // Asynchronous global -> shared copies (cp.async); a false `valid` writes
 // zeros (the source is then not read, but must still be a valid address).

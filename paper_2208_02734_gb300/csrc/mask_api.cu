@@ -783,7 +783,7 @@ mask_status mask_query(const mask_index *index, const float *queries, int64_t nq
                 mode = LeafMode::Cluster;
                 int qpi = 0, bps = 0;
                 if (std::sscanf(m + 7, ":%d:%d", &qpi, &bps) == 2) {
-                    MASK_REQUIRE(qpi >= 1 && qpi <= kCmItemQueries && bps >= 0,
+                    MASK_REQUIRE(qpi >= 1 && qpi <= kCmTcItemQueries && bps >= 0,
                                  "MASK_LEAF_SCAN tile out of range");
                     tile = CmTile{qpi, bps};
                 }

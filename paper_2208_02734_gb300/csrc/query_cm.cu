@@ -165,13 +165,13 @@ __global__ void __launch_bounds__(1024) item_scan_kernel(const int64_t *__restri
     if (tid == 1023) item_off[k0] = part[1023];
 }
 
-// Per work item i (cluster c, up to qpi <= CM_QB of its pairs):
+// Per work item i (cluster c, up to qpi <= qs of its pairs):
 //   meta[i] = {first row lo, first row hi, rows of c, pairs in the item}
-//   pid[i * CM_QB + q] = the item's q-th pair (-1 past the last),
-//   qid[i * CM_QB + q] = that pair's query.
+//   pid[i * qs + q] = the item's q-th pair (-1 past the last),
+//   qid[i * qs + q] = that pair's query.
 __global__ void item_meta_kernel(const int64_t *__restrict__ item_off, const int64_t *__restrict__ poff,
                                  const int64_t *__restrict__ leaf_off,
-                                 const int32_t *__restrict__ pairs, int P, int k0, int qpi,
+                                 const int32_t *__restrict__ pairs, int P, int k0, int qpi, int qs,
                                  int4 *__restrict__ meta, int32_t *__restrict__ pid,
                                  int32_t *__restrict__ qid) {
     // one warp per cluster; lanes over the cluster's (item, slot) entries
@@ -181,13 +181,13 @@ __global__ void item_meta_kernel(const int64_t *__restrict__ item_off, const int
         const int64_t rb = leaf_off[c], rows = leaf_off[c + 1] - rb;
         const int64_t i0 = item_off[c], ni = item_off[c + 1] - i0;
         const int64_t p0 = poff[c], np = poff[c + 1] - p0;
-        for (int64_t e = lane; e < ni * CM_QB; e += 32) {
-            const int64_t i = i0 + e / CM_QB;
-            const int q = (int)(e % CM_QB);
-            const int64_t pe = (e / CM_QB) * qpi + q;  // pair offset within the cluster
+        for (int64_t e = lane; e < ni * qs; e += 32) {
+            const int64_t i = i0 + e / qs;
+            const int q = (int)(e % qs);
+            const int64_t pe = (e / qs) * qpi + q;  // pair offset within the cluster
             const int32_t pp = (q < qpi && pe < np) ? pairs[p0 + pe] : -1;
-            pid[i * CM_QB + q] = pp;
-            qid[i * CM_QB + q] = pp >= 0 ? pp / P : 0;
+            pid[i * qs + q] = pp;
+            qid[i * qs + q] = pp >= 0 ? pp / P : 0;
             if (q == 0) {
                 const int nqb = (int)min((int64_t)qpi, np - pe);
                 meta[i] = make_int4((int)(rb & 0xffffffff), (int)(rb >> 32), (int)rows, nqb);
@@ -569,7 +569,7 @@ bool cm_leaf_supported(int dp, int K) { return dp <= 128 && K >= 1 && K <= 32; }
 void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32_t> &pairs,
                     Scratch<int64_t> &poff, Scratch<int64_t> &item_off, cudaStream_t s,
                     int qpi) {
-    MASK_REQUIRE(qpi >= 1 && qpi <= CM_QB, "queries per item out of range");
+    MASK_REQUIRE(qpi >= 1 && qpi <= kCmTcItemQueries, "queries per item out of range");
     const int64_t npairs = nq * P;
     ProfRegion pr("leaf_group", s, 0.0);
     Scratch<int32_t> lab(npairs, s);
@@ -585,14 +585,17 @@ void cm_group_pairs(const int32_t *sel, int64_t nq, int P, int k0, Scratch<int32
 
 void cm_item_meta(const int32_t *pairs, const int64_t *poff, const int64_t *item_off,
                   const int64_t *leaf_off, int64_t npairs, int P, int k0, Scratch<int4> &meta,
-                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s, int qpi) {
+                  Scratch<int32_t> &pid, Scratch<int32_t> &qid, cudaStream_t s, int qpi,
+                  int qs) {
+    MASK_REQUIRE(qpi >= 1 && qpi <= qs && (qs == kCmItemQueries || qs == kCmTcItemQueries),
+                 "queries per item out of range");
     // a cluster with m pairs has ceil(m / qpi) <= m / qpi + 1 items, and at most m
     const int64_t max_items = std::max<int64_t>(
         1, std::min(npairs, (npairs + qpi - 1) / qpi + (int64_t)k0));
     meta.alloc(max_items, s);
-    pid.alloc((size_t)max_items * CM_QB, s);
-    qid.alloc((size_t)max_items * CM_QB, s);
-    item_meta_kernel<<<(k0 + 7) / 8, 256, 0, s>>>(item_off, poff, leaf_off, pairs, P, k0, qpi,
+    pid.alloc((size_t)max_items * qs, s);
+    qid.alloc((size_t)max_items * qs, s);
+    item_meta_kernel<<<(k0 + 7) / 8, 256, 0, s>>>(item_off, poff, leaf_off, pairs, P, k0, qpi, qs,
                                                   meta.get(), pid.get(), qid.get());
     MASK_LAUNCHED("item_meta");
 }
@@ -665,12 +668,18 @@ void cm_leaf_scan(const float *Xs, int64_t n, const float *xn, int dp, const int
     // pairs of an absent parent (sel = -1, fewer children than probes) are in
     // no work item: their lists stay empty
     MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
-    cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s, tile.qpi);
+    // queries per work item: the tile's, at most the kernel's widest; the
+    // tensor-core scan's items of more than 16 queries use 32-query slots
+    const bool tc = !tile.legacy && cm_tc_supported(dp, K);
+    const int qmax = tc ? cm_tc_item_queries(K) : kCmItemQueries;
+    const int qpi = tile.qpi > 0 ? std::min(tile.qpi, qmax) : qmax;
+    const int qs = qpi > kCmItemQueries ? kCmTcItemQueries : kCmItemQueries;
+    cm_group_pairs(sel, nq, P, k0, pairs, poff, item_off, s, qpi);
     Scratch<int4> meta;
     Scratch<int32_t> ipid, iqid;
     cm_item_meta(pairs.get(), poff.get(), item_off.get(), leaf_off, npairs, P, k0, meta, ipid, iqid,
-                 s, tile.qpi);
-    if (!tile.legacy && cm_tc_supported(dp, K)) {
+                 s, qpi, qs);
+    if (tc) {
         // the tensor-core scan (kind::tf32): the rows are read as TF32
         // (|x - x_tf32| <= 2^-10 |x|), the queries split into an exact TF32
         // part and a remainder read as TF32 (2^-20 |q|), which leaves
@@ -679,10 +688,14 @@ void cm_leaf_scan(const float *Xs, int64_t n, const float *xn, int dp, const int
         const float mcoef_t =
             mcoef + (float)((0x1.0p-10 + 0x1.0p-20 + 0x1.0p-30 + (2.0 * ((dp + 7) / 8) + 8.0) *
                                                                     0x1.0p-22) * 1.125);
+        // each query's running bound on its K-th distance (0x7F7F7F7F: a
+        // huge finite float), lowered by the scan's merges
+        Scratch<unsigned> qbound(nq, s);
+        MASK_CUDA(cudaMemsetAsync(qbound.get(), 0x7F, sizeof(unsigned) * nq, s));
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         cm_tc_scan(Xs, n, xn, dp, xids, Qp, qn.get(), seed_d.get(), mcoef_t, meta.get(),
-                   ipid.get(), iqid.get(), item_off.get(), k0, K, pair_out.get(),
-                   cm_bytes_counter(), s);
+                   ipid.get(), iqid.get(), item_off.get(), k0, K, qs, pair_out.get(),
+                   qbound.get(), cm_bytes_counter(), s);
     } else {
         ProfRegion pr("scan_leaf_cm", s, 0.0);
         const int XS = cm_stride(dp / 4);

@@ -84,14 +84,16 @@ struct Key {
 
 // The leaf-scan configurations the autotuner times for an FP32 shape: the
 // query-major scan, and the cluster-major scan at each (queries per work
-// item, blocks per SM) pair (0 blocks per SM: as many as fit).  All give
-// bit-identical results.
+// item, blocks per SM) pair (0 queries: the kernel's widest item, 32 on the
+// tensor-core scan for K <= 16, else 16; 0 blocks per SM: as many as fit;
+// the tensor-core scan runs one block per SM).  All give bit-identical
+// results.
 struct LeafConfig {
     LeafMode mode;
     CmTile tile;
 };
 const LeafConfig kLeafConfigs[] = {
-    {LeafMode::Query, CmTile{16, 0}},  {LeafMode::Cluster, CmTile{16, 0}},
+    {LeafMode::Query, CmTile{0, 0}},    {LeafMode::Cluster, CmTile{0, 0}},
     {LeafMode::Cluster, CmTile{16, 1}}, {LeafMode::Cluster, CmTile{8, 0}},
     {LeafMode::Cluster, CmTile{8, 1}},
 };

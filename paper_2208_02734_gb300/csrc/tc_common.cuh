@@ -82,6 +82,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const CUtensorMap *map, int x,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2}], [%3];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(bar)
+        : "memory");
+}
+
 // Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16).
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
                                           uint32_t bar) {
@@ -149,6 +158,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
         : "r"(taddr));
 }
 
+// 16 consecutive fp32 columns of this thread's TMEM lane (issue only).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -208,6 +228,27 @@ inline CUtensorMap make_map_2d(const void *base, CUtensorMapDataType dtype, int 
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         fail(MASK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return m;
+}
+
+// 1-D tensor map of `n` elements (`esize` bytes each, type `dtype`), boxes of
+// `box` elements (box * esize a multiple of 16), no swizzle, zero fill out of
+// bounds.  A load's coordinate times esize must be a multiple of 16.
+inline CUtensorMap make_map_1d(const void *base, CUtensorMapDataType dtype, int esize, int64_t n,
+                               int box) {
+    auto fn = encode_fn();
+    if (fn == nullptr) fail(MASK_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    const cuuint64_t dims[1] = {(cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * (cuuint64_t)esize};   // unused at rank 1
+    const cuuint32_t boxd[1] = {(cuuint32_t)box};
+    const cuuint32_t estr[1] = {1u};
+    const CUresult r = fn(&m, dtype, 1, const_cast<void *>(base), dims, strides, boxd, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        fail(MASK_ECUDA, "cuTensorMapEncodeTiled (1-D) failed: " + std::to_string((int)r));
     return m;
 }
 

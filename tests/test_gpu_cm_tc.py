@@ -7,8 +7,9 @@ Both cluster-major scans keep every row the exact per-query scan would keep
 return the same ids and distances bit for bit; the oracle's descent over the
 same index agrees up to near-ties.  The cases cover one and several 128-row
 chunks per cluster with ragged tails, clusters kept by more than 16 queries
-(several work items), fewer queries per item, empty leaf clusters, absent
-leaf slots, K from 1 to 32, and rows of 32 and 64 floats (d = 60 padded).
+(several work items), items of 32 queries (K <= 16) and of 16 (K up to 32),
+fewer queries per item, empty leaf clusters, absent leaf slots, K from 1 to
+32, and rows of 32 and 64 floats (d = 60 padded).
 """
 
 import numpy as np
@@ -51,7 +52,8 @@ def built(request):
     idx.free()
 
 
-@pytest.mark.parametrize("k,probes", [(10, [12, 4]), (1, [3, 2]), (32, [20, 6]), (10, [60, 1])])
+@pytest.mark.parametrize("k,probes", [(10, [12, 4]), (1, [3, 2]), (16, [20, 6]), (17, [20, 6]),
+                                     (32, [20, 6]), (10, [60, 1])])
 def test_tc_scan_equals_the_other_scans(monkeypatch, built, k, probes):
     d, X, Q, idx = built
     Qd = cuda(Q)
@@ -62,7 +64,7 @@ def test_tc_scan_equals_the_other_scans(monkeypatch, built, k, probes):
     assert torch.equal(ref[0], simt[0]) and torch.equal(ref[1], simt[1])
 
 
-@pytest.mark.parametrize("tile", [":8:0", ":3:0", ":1:0"])
+@pytest.mark.parametrize("tile", [":32:0", ":20:0", ":16:0", ":8:0", ":3:0", ":1:0"])
 def test_tc_scan_with_fewer_queries_per_item(monkeypatch, built, tile):
     d, X, Q, idx = built
     Qd = cuda(Q[:700])
