@@ -16,9 +16,12 @@
 //
 // One CTA owns 128 rows of X.  Their hi/lo parts sit in tensor memory as
 // the MMAs' A operand (so shared memory feeds only the B operand) while
-// 128-centroid tiles of C stream through a TMA pipeline; the accumulator is
-// triple-buffered in TMEM so the epilogue of tile j overlaps the MMAs of the
-// next ones.
+// 192-centroid tiles of C stream through a TMA pipeline; the accumulator is
+// double-buffered in TMEM so the epilogue of tile j overlaps the MMAs of the
+// next one.  An M = 128 kind::f16 MMA takes about as long at N = 192 as at
+// N = 128 (its issue cost, not its arithmetic, bounds it below N ~ 200), so
+// the wider tile does 1.5x the work per MMA; 2 x 192 accumulator columns and
+// the rows' 64 leave room in the 512 columns of tensor memory.
 // Warp roles: warp 0 = TMA producer (C tiles and their norms), warp 1 = MMA
 // issuer, warp 2 = TMEM allocator, warps 4-11 = epilogue (one thread per row
 // and half of each tile's columns, TMEM lane = row), which keeps the four
@@ -48,7 +51,7 @@ namespace {
 using namespace tc;
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int TC_M = 128, TC_N = 128;   // MMA tile: 128 rows x 128 centroids
+constexpr int TC_M = 128, TC_N = 192;   // MMA tile: 128 rows x 192 centroids
 constexpr int TC_EPI_PARTS = 2;         // epilogue warps per TMEM lane quadrant (column parts)
 constexpr int TC_EPI_WARPS = 4 * TC_EPI_PARTS;
 constexpr int TC_THREADS = (4 + TC_EPI_WARPS) * 32;
@@ -56,13 +59,13 @@ constexpr int TC_EPI_COLS = TC_N / TC_EPI_PARTS;   // columns per epilogue threa
 constexpr int TC_EPI_LD = TC_EPI_COLS / 32;        // 32-column TMEM loads per thread per tile
 constexpr int TC_EPI_G = TC_EPI_COLS / 8;          // groups of 8 columns per thread per tile
 constexpr int TC_DK = 64;               // fp16 columns of the split copies (dp <= 64)
-constexpr int TC_BOX_BYTES = TC_M * TC_DK * 2;      // one 128-byte row per item: 16 KB
+constexpr int TC_CBOX_BYTES = TC_N * TC_DK * 2;     // one C tile part, 128-byte rows: 24 KB
 constexpr int TC_NRING = 8;             // slots of the centroid-norm ring
-constexpr int TC_NACC = 3;              // accumulator buffers in tensor memory
+constexpr int TC_NACC = 2;              // accumulator buffers in tensor memory
 constexpr uint32_t TC_ACOL = TC_NACC * TC_N;  // tensor-memory column of the rows' hi/lo parts
 static_assert(TC_ACOL + TC_DK <= 512, "accumulators and rows fit the 512 TMEM columns");
 
-// instruction descriptor: D = F32, A = B = F16, both K-major, N = 128, M = 128
+// instruction descriptor: D = F32, A = B = F16, both K-major, N = 192, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) |
                             ((uint32_t)(TC_M >> 4) << 24);
 
@@ -147,7 +150,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
     int4 *__restrict__ list3, int *__restrict__ n3, int32_t *__restrict__ listF,
     int *__restrict__ nF, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    constexpr uint32_t kStage = 2u * TC_BOX_BYTES;       // hi + lo tiles of one C tile
+    constexpr uint32_t kStage = 2u * TC_CBOX_BYTES;      // hi + lo tiles of one C tile
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;        // swizzled tiles need 1 KB alignment
     unsigned char *basep = smem_raw + (base - raw);
@@ -215,7 +218,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
         for (int j = 0; j < ntiles; ++j) {
             const int s = j % S, u = j / S;
             if (u > 0 && !mbar_wait(b_empty(s), (u - 1) & 1, err)) { ok = false; break; }
-            const uint32_t bh = B0 + s * kStage, bl = bh + TC_BOX_BYTES;
+            const uint32_t bh = B0 + s * kStage, bl = bh + TC_CBOX_BYTES;
             mbar_expect_tx(b_full(s), kStage);
             tma_load_2d(bh, &tmCh, 0, j * TC_N, b_full(s));
             tma_load_2d(bl, &tmCl, 0, j * TC_N, b_full(s));
@@ -248,7 +251,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             if (!ok) break;
             fence_after();
             const uint32_t d = tmem + (uint32_t)(a * TC_N);
-            const uint32_t bh = B0 + s * kStage, bl = bh + TC_BOX_BYTES;
+            const uint32_t bh = B0 + s * kStage, bl = bh + TC_CBOX_BYTES;
             const uint64_t dBh = sw128_desc(bh), dBl = sw128_desc(bl);
             // K-step kk covers fp16 columns 16kk..16kk+15: 32 bytes into each
             // 128-byte row, i.e. +2 in the descriptor's 16-byte address units
@@ -348,25 +351,28 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
             // keys of this thread's columns, with the minimum of each group
             // of 8; columns past k have norm +inf, so their keys never enter
             // the list
+            // (computed in place: key 8g + e lives in u's register of its column)
             const float4 *cn4 = reinterpret_cast<const float4 *>(&s_cn[q][col]);
-            float key[TC_EPI_COLS], gm[TC_EPI_G];
+            float gm[TC_EPI_G];
 #pragma unroll
             for (int g = 0; g < TC_EPI_G; ++g) {
-                const uint32_t *uu = u[g >> 2];
-                const int b = (g & 3) * 8;
+                uint32_t *uu = u[g >> 2] + (g & 3) * 8;
                 const float4 c0v = cn4[2 * g], c1v = cn4[2 * g + 1];
-                float *kk = key + 8 * g;
-                kk[0] = fmaf(mul, __uint_as_float(uu[b + 0]), c0v.x);
-                kk[1] = fmaf(mul, __uint_as_float(uu[b + 1]), c0v.y);
-                kk[2] = fmaf(mul, __uint_as_float(uu[b + 2]), c0v.z);
-                kk[3] = fmaf(mul, __uint_as_float(uu[b + 3]), c0v.w);
-                kk[4] = fmaf(mul, __uint_as_float(uu[b + 4]), c1v.x);
-                kk[5] = fmaf(mul, __uint_as_float(uu[b + 5]), c1v.y);
-                kk[6] = fmaf(mul, __uint_as_float(uu[b + 6]), c1v.z);
-                kk[7] = fmaf(mul, __uint_as_float(uu[b + 7]), c1v.w);
+                float kk[8];
+                kk[0] = fmaf(mul, __uint_as_float(uu[0]), c0v.x);
+                kk[1] = fmaf(mul, __uint_as_float(uu[1]), c0v.y);
+                kk[2] = fmaf(mul, __uint_as_float(uu[2]), c0v.z);
+                kk[3] = fmaf(mul, __uint_as_float(uu[3]), c0v.w);
+                kk[4] = fmaf(mul, __uint_as_float(uu[4]), c1v.x);
+                kk[5] = fmaf(mul, __uint_as_float(uu[5]), c1v.y);
+                kk[6] = fmaf(mul, __uint_as_float(uu[6]), c1v.z);
+                kk[7] = fmaf(mul, __uint_as_float(uu[7]), c1v.w);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) uu[e] = __float_as_uint(kk[e]);
                 gm[g] = fminf(fminf(fminf(kk[0], kk[1]), fminf(kk[2], kk[3])),
                               fminf(fminf(kk[4], kk[5]), fminf(kk[6], kk[7])));
             }
+            auto key = [&](int c) { return __uint_as_float(u[c >> 5][c & 31]); };
             // the norms are in registers: hand the ring slot back
             __syncwarp();
             if (lane == 0) mbar_arrive(n_empty(q));
@@ -394,13 +400,13 @@ __global__ __launch_bounds__(TC_THREADS, 1) void assign_tc_kernel(
                         int cnt = 0, first = 7;
 #pragma unroll
                         for (int e = 7; e >= 0; --e) {
-                            cnt += key[8 * g + e] < T ? 1 : 0;
-                            first = key[8 * g + e] == gm[g] ? e : first;
+                            cnt += key(8 * g + e) < T ? 1 : 0;
+                            first = key(8 * g + e) == gm[g] ? e : first;
                         }
                         if (__any_sync(kFull, cnt > 1)) {
 #pragma unroll
                             for (int e = 0; e < 8; ++e)
-                                if (key[8 * g + e] < T) t4.push_nb(key[8 * g + e], cb + 8 * g + e);
+                                if (key(8 * g + e) < T) t4.push_nb(key(8 * g + e), cb + 8 * g + e);
                         } else if (gm[g] < T) {
                             t4.push_nb(gm[g], cb + 8 * g + first);
                         }
@@ -564,17 +570,17 @@ __global__ void absmax_kernel(const float *__restrict__ v, int64_t count, unsign
     if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
 }
 
-// Norms of the padding columns of the last 128-centroid tile: +inf, so their
+// Norms of the padding columns of the last C tile: +inf, so their
 // keys (-2 * 0 + inf) never enter a row's list.
 __global__ void pad_inf_kernel(float *__restrict__ cn, int k, int total) {
     const int i = k + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < total) cn[i] = __int_as_float(0x7f800000);
 }
 
-// 2-D tensor map of a [rows x 64] fp16 array, boxes of 128 rows x 64 columns
+// 2-D tensor map of a [rows x 64] fp16 array, boxes of TC_N rows x 64 columns
 // (one 128-byte row each), 128-byte swizzle, zero fill out of bounds.
 CUtensorMap make_map(const __half *base, int64_t rows) {
-    return tc::make_map_2d(base, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, rows, TC_DK, TC_M, TC_DK);
+    return tc::make_map_2d(base, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, rows, TC_DK, TC_N, TC_DK);
 }
 
 int grid_cap(int64_t work) {
@@ -584,11 +590,11 @@ int grid_cap(int64_t work) {
 
 template <int S>
 size_t tc_smem_bytes() {
-    return 1024 + (size_t)S * 2u * TC_BOX_BYTES + (2 * S + 1 + 2 * TC_NACC + 2 * TC_NRING) * 8 +
+    return 1024 + (size_t)S * 2u * TC_CBOX_BYTES + (2 * S + 1 + 2 * TC_NACC + 2 * TC_NRING) * 8 +
            16;
 }
 
-constexpr int TC_STAGES = 5;   // C tiles in flight (32 KB each)
+constexpr int TC_STAGES = 4;   // C tiles in flight (48 KB each)
 
 }  // namespace
 
@@ -648,7 +654,7 @@ void tc_assign(TcAssign &p, const float *xn, const float *C, int k, int32_t *lab
                bool seeded, cudaStream_t s) {
     const int dp = p.dp;
     const int ntiles = (k + TC_N - 1) / TC_N;
-    // centroid norms padded to whole 128-centroid tiles (+inf past k)
+    // centroid norms padded to whole C tiles (+inf past k)
     Scratch<float> cn((size_t)ntiles * TC_N, s), cmax(1, s), cinv(1, s);
     Scratch<__half> Ch((size_t)k * TC_DK, s), Cl((size_t)k * TC_DK, s);
     Scratch<unsigned> cabs(1, s);
