@@ -374,7 +374,7 @@ KERNEL_KIND = {"assign_tc": "tensor", "assign_gemm": "alu", "assign_recheck": "a
                "csr_spmm_assign": "alu", "csr_scan_leaf": "hbm", "csr_scan_level": "hbm",
                "csr_scan_leaf_cm": "hbm",
                "csr_centroid_update": "hbm",
-               "scan_leaf_cm": "hbm", "leaf_group": "hbm", "leaf_merge": "hbm",
+               "scan_leaf_cm": "hbm", "leaf_exact": "hbm", "leaf_group": "hbm", "leaf_merge": "hbm",
                "scan_topk_leaf": "hbm",
                "scan_topk_level": "hbm", "centroid_update": "hbm", "label_sort": "hbm",
                "kmeanspp": "hbm"}

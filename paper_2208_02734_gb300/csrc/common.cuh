@@ -391,19 +391,23 @@ struct CmTile {
 };
 
 // The tensor-core cluster-major scan (query_cm_tc.cu): rows of 32 or 64
-// floats, K <= 32.  A bounded pipeline wait that ran out raises a device
-// error word; cm_tc_check (synchronising) reports it as MASK_ETIMEOUT and
-// clears it, cm_tc_error_word gives its device address.
+// floats, K <= 32, in two passes (a tensor-core filter against T_q that
+// appends candidates per query, then one warp per query for the exact keys
+// and the top-K, written to ids / dists).  A bounded pipeline wait that ran
+// out raises a device error word; cm_tc_check (synchronising) reports it as
+// MASK_ETIMEOUT and clears it, cm_tc_error_word gives its device address.
 bool cm_tc_supported(int dp, int K);
 // widest work item of the tensor-core scan: 32 queries for K <= 16, else 16
 int cm_tc_item_queries(int K);
-// qs: queries per item slot of meta / pid / qid (16 or 32; the kernel's MMA
-// N); qbound [nq]: per query, an upper bound of its K-th distance (FP32 bits,
-// preset large), lowered as the scan goes
+// candidates kept per query (beyond them a query is scanned in full)
+int cm_tc_cand_cap(int64_t nq);
+// qs: queries per item slot of meta / qid (16 or 32; the filter's MMA N);
+// ccount [nq] (preset 0) and cand [nq x cap]: the candidate lists
 void cm_tc_scan(const float *Xs, int64_t n, const float *xn, int dp, const int32_t *xids,
-                const float *Qp, const float *qn, const float *seed_d, float mcoef,
-                const int4 *meta, const int32_t *pid, const int32_t *qid, const int64_t *item_off,
-                int k0, int K, int qs, unsigned long long *pair_out, unsigned *qbound,
+                const int64_t *leaf_off, int k0, const float *Qp, int64_t nq, const int32_t *sel,
+                int P, const float *qn, const float *seed_d, float mcoef, const int4 *meta,
+                const int32_t *qid, const int64_t *item_off, int K, int qs, unsigned *ccount,
+                uint32_t *cand, int cap, int64_t *ids, float *dists,
                 unsigned long long *bytes_ctr, cudaStream_t s);
 int *cm_tc_error_word();
 void cm_tc_check(cudaStream_t s);

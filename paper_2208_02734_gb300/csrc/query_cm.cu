@@ -69,7 +69,8 @@ __global__ void first_col_kernel(const int32_t *__restrict__ sel, int64_t nq, in
 
 // The seed of the leaf scans, one warp per query: the K smallest exact
 // distances among the rows of the query's nearest kept cluster sel[q * P]
-// (ascending, +inf past the cluster's rows).  Rows one per lane with the
+// and, while those hold fewer than K rows, the next kept clusters of the
+// list (ascending, +inf past the rows seen).  Rows one per lane with the
 // arithmetic of the per-query leaf scan (sum over t of (x_t - q_t)^2, FMAs, t
 // ascending); each lane keeps its 32 smallest in registers (an insertion
 // network), and K rounds of warp minimum take the K smallest of all lanes.
@@ -84,35 +85,36 @@ __global__ __launch_bounds__(256) void leaf_seed_warp_kernel(
     if (q >= nq) return;   // whole warps leave together
     for (int c = lane; c < dp4; c += 32) qs[w][c] = Q[q * dp4 + c];
     __syncwarp();
-    const int32_t c0 = sel[q * P];
-    int64_t b = 0, e = 0;
-    if (c0 >= 0) {
-        b = leaf_off[c0];
-        e = leaf_off[c0 + 1];
-    }
     const float inf = __int_as_float(0x7f800000);
     float t[kSeedK];
 #pragma unroll
     for (int j = 0; j < kSeedK; ++j) t[j] = inf;
-    for (int64_t row = b + lane; row < e; row += 32) {
-        const float4 *r = Xs + row * dp4;
-        float acc = 0.f;
+    int64_t seen = 0;   // warp-uniform
+    for (int p = 0; p < P && seen < K; ++p) {
+        const int32_t c0 = sel[q * P + p];
+        if (c0 < 0) continue;
+        const int64_t b = leaf_off[c0], e = leaf_off[c0 + 1];
+        seen += e - b;
+        for (int64_t row = b + lane; row < e; row += 32) {
+            const float4 *r = Xs + row * dp4;
+            float acc = 0.f;
 #pragma unroll 4
-        for (int c = 0; c < dp4; ++c) {
-            const float4 v = r[c], x = qs[w][c];
-            float d = v.x - x.x;
-            acc = fmaf(d, d, acc);
-            d = v.y - x.y;
-            acc = fmaf(d, d, acc);
-            d = v.z - x.z;
-            acc = fmaf(d, d, acc);
-            d = v.w - x.w;
-            acc = fmaf(d, d, acc);
-        }
+            for (int c = 0; c < dp4; ++c) {
+                const float4 v = r[c], x = qs[w][c];
+                float d = v.x - x.x;
+                acc = fmaf(d, d, acc);
+                d = v.y - x.y;
+                acc = fmaf(d, d, acc);
+                d = v.z - x.z;
+                acc = fmaf(d, d, acc);
+                d = v.w - x.w;
+                acc = fmaf(d, d, acc);
+            }
 #pragma unroll
-        for (int j = kSeedK - 1; j > 0; --j)
-            t[j] = t[j - 1] > acc ? t[j - 1] : (t[j] > acc ? acc : t[j]);
-        t[0] = fminf(t[0], acc);
+            for (int j = kSeedK - 1; j > 0; --j)
+                t[j] = t[j - 1] > acc ? t[j - 1] : (t[j] > acc ? acc : t[j]);
+            t[0] = fminf(t[0], acc);
+        }
     }
     for (int rd = 0; rd < K; ++rd) {
         float m = t[0];
@@ -664,10 +666,6 @@ void cm_leaf_scan(const float *Xs, int64_t n, const float *xn, int dp, const int
         mcoef + (float)((2.5 * 0x1.0p-21 + (3.0 * ((dp + 7) / 8) + 8.0) * 0x1.0p-22) * 1.125);
     Scratch<int32_t> pairs;
     Scratch<int64_t> poff, item_off;
-    Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
-    // pairs of an absent parent (sel = -1, fewer children than probes) are in
-    // no work item: their lists stay empty
-    MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
     // queries per work item: the tile's, at most the kernel's widest; the
     // tensor-core scan's items of more than 16 queries use 32-query slots
     const bool tc = !tile.legacy && cm_tc_supported(dp, K);
@@ -688,35 +686,43 @@ void cm_leaf_scan(const float *Xs, int64_t n, const float *xn, int dp, const int
         const float mcoef_t =
             mcoef + (float)((0x1.0p-10 + 0x1.0p-20 + 0x1.0p-30 + (2.0 * ((dp + 7) / 8) + 8.0) *
                                                                     0x1.0p-22) * 1.125);
-        // each query's running bound on its K-th distance (0x7F7F7F7F: a
-        // huge finite float), lowered by the scan's merges
-        Scratch<unsigned> qbound(nq, s);
-        MASK_CUDA(cudaMemsetAsync(qbound.get(), 0x7F, sizeof(unsigned) * nq, s));
-        ProfRegion pr("scan_leaf_cm", s, 0.0);
-        cm_tc_scan(Xs, n, xn, dp, xids, Qp, qn.get(), seed_d.get(), mcoef_t, meta.get(),
-                   ipid.get(), iqid.get(), item_off.get(), k0, K, qs, pair_out.get(),
-                   qbound.get(), cm_bytes_counter(), s);
-    } else {
-        ProfRegion pr("scan_leaf_cm", s, 0.0);
-        const int XS = cm_stride(dp / 4);
-        const size_t smem = ((size_t)2 * CM_R * XS + (size_t)2 * CM_QB * XS + 2 * CM_R) * 4 +
-                            (size_t)CM_QB * K * 8 + (size_t)CM_QB * CM_R * 8 + 16;
-        MASK_CUDA(cudaFuncSetAttribute(cm_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-        int per_sm = 0;
-        MASK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cm_scan_kernel,
-                                                                CM_THREADS, smem));
-        int dev = 0, sms = 0;
-        MASK_CUDA(cudaGetDevice(&dev));
-        MASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        if (tile.bps > 0) per_sm = std::min(per_sm, tile.bps);
-        cm_scan_kernel<<<std::max(1, per_sm) * sms, CM_THREADS, smem, s>>>(
-            reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids,
-            reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef_tc, meta.get(),
-            ipid.get(), iqid.get(), item_off.get(), k0, K, pair_out.get(), cm_bytes_counter());
-        MASK_LAUNCHED("cm_scan");
+        // candidate lists of the filter pass; the exact pass writes ids / dists
+        const int cap = cm_tc_cand_cap(nq);
+        Scratch<unsigned> ccount(nq, s);
+        Scratch<uint32_t> cand((size_t)nq * cap, s);
+        MASK_CUDA(cudaMemsetAsync(ccount.get(), 0, sizeof(unsigned) * nq, s));
+        cm_tc_scan(Xs, n, xn, dp, xids, leaf_off, k0, Qp, nq, sel, P, qn.get(), seed_d.get(),
+                   mcoef_t, meta.get(), iqid.get(), item_off.get(), K, qs, ccount.get(),
+                   cand.get(), cap, ids, dists, cm_bytes_counter(), s);
+        return;
     }
-    cm_merge(pair_out.get(), nq, P, K, ids, dists, s);
+    {
+        // pairs of an absent parent (sel = -1, fewer children than probes) are in
+        // no work item: their lists stay empty
+        Scratch<unsigned long long> pair_out((size_t)npairs * K, s);
+        MASK_CUDA(cudaMemsetAsync(pair_out.get(), 0xFF, sizeof(unsigned long long) * npairs * K, s));
+        {
+            ProfRegion pr("scan_leaf_cm", s, 0.0);
+            const int XS = cm_stride(dp / 4);
+            const size_t smem = ((size_t)2 * CM_R * XS + (size_t)2 * CM_QB * XS + 2 * CM_R) * 4 +
+                                (size_t)CM_QB * K * 8 + (size_t)CM_QB * CM_R * 8 + 16;
+            MASK_CUDA(cudaFuncSetAttribute(cm_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+            int per_sm = 0;
+            MASK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cm_scan_kernel,
+                                                                    CM_THREADS, smem));
+            int dev = 0, sms = 0;
+            MASK_CUDA(cudaGetDevice(&dev));
+            MASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            if (tile.bps > 0) per_sm = std::min(per_sm, tile.bps);
+            cm_scan_kernel<<<std::max(1, per_sm) * sms, CM_THREADS, smem, s>>>(
+                reinterpret_cast<const float4 *>(Xs), xn, dp / 4, xids,
+                reinterpret_cast<const float4 *>(Qp), qn.get(), seed_d.get(), mcoef_tc, meta.get(),
+                ipid.get(), iqid.get(), item_off.get(), k0, K, pair_out.get(), cm_bytes_counter());
+            MASK_LAUNCHED("cm_scan");
+        }
+        cm_merge(pair_out.get(), nq, P, K, ids, dists, s);
+    }
 }
 
 double cm_bytes() {

@@ -3,13 +3,14 @@ floats) against the per-query scan, the mma.sync cluster-major scan and the
 oracle.
 
 Both cluster-major scans keep every row the exact per-query scan would keep
-(their expanded-form filters carry proven rounding bounds), so all three
-return the same ids and distances bit for bit; the oracle's descent over the
-same index agrees up to near-ties.  The cases cover one and several 128-row
+(their expanded-form filters carry proven rounding bounds) and key it with
+the same arithmetic, so all three return the same ids and distances bit for
+bit; the oracle's descent over the same index agrees up to near-ties.  The cases cover one and several 128-row
 chunks per cluster with ragged tails, clusters kept by more than 16 queries
 (several work items), items of 32 queries (K <= 16) and of 16 (K up to 32),
-fewer queries per item, empty leaf clusters, absent leaf slots, K from 1 to
-32, and rows of 32 and 64 floats (d = 60 padded).
+fewer queries per item, empty leaf clusters, absent leaf slots, candidate
+lists that overflow (those queries are scanned in full), K from 1 to 32, and
+rows of 32 and 64 floats (d = 60 padded).
 """
 
 import numpy as np
@@ -109,6 +110,19 @@ def test_tc_scan_with_empty_leaf_clusters(monkeypatch):
         assert torch.equal(ref[0], tc[0]) and torch.equal(ref[1], tc[1])
     finally:
         idx.free()
+
+
+@pytest.mark.parametrize("cap", ["1", "7", "40"])
+def test_tc_scan_candidate_overflow(monkeypatch, built, cap):
+    # queries with more filter passes than their candidate list holds are
+    # answered from every row of their kept clusters: same answers
+    d, X, Q, idx = built
+    Qd = cuda(Q[:600])
+    ref = run(monkeypatch, idx, Qd, 10, [12, 4], "query")
+    monkeypatch.setenv("MASK_CM_CAND_CAP", cap)
+    tc = run(monkeypatch, idx, Qd, 10, [12, 4], "cluster")
+    monkeypatch.delenv("MASK_CM_CAND_CAP")
+    assert torch.equal(ref[0], tc[0]) and torch.equal(ref[1], tc[1])
 
 
 def test_tc_scan_batch_independence(monkeypatch, built):
