@@ -204,7 +204,12 @@ size_t batch_bytes(const mask_index &idx, const Key &key, int64_t B, int K) {
     for (int p : key.probes) sp += (size_t)p;
     size_t per = dp * 4 + (size_t)K * 12 + sp * 4;
     if (key.prec == MASK_FP32) {
-        per += p0 * (12 + (size_t)K * 8);  // cluster-major pairs and per-pair lists
+        // cluster-major pairs, and per-pair lists (mma.sync scan) or the
+        // candidate list (tensor-core scan), whichever is larger
+        size_t lists = p0 * (size_t)K * 8;
+        if (cm_tc_supported(idx.dp, K))
+            lists = std::max(lists, (size_t)cm_tc_cand_cap(B) * 4 + 4);
+        per += p0 * 12 + lists;
     } else {
         const size_t dpl = (size_t)lp_padded_dim(idx.dp);
         const size_t Kp = (size_t)lp_shortlist(K);
