@@ -436,6 +436,23 @@ int64_t mask_test_alloc_count(void);
  */
 mask_status mask_test_bounded_wait(int32_t flag_set, int32_t limit_us, mask_stream stream);
 
+/*
+ * Timing probe of the 5th-generation tensor-core MMA behind the tensor-core
+ * assignment's tile width (the paper has no counterpart: this measures the
+ * hardware).  One CTA on the current device issues rounds x 12
+ * tcgen05.mma.cta_group::1.kind::f16 instructions (M = 128, N = n, K = 16,
+ * zero operands: 4 K-steps x 3 products, the assignment's pattern) into
+ * n_acc accumulators used round-robin, with A in tensor memory (a_in_tmem
+ * nonzero) or shared memory and B in shared memory.  cycles_out[0] = SM
+ * cycles spent issuing them, cycles_out[1] = cycles until the last one
+ * completed.  n: a multiple of 16 in [16, 256]; n_acc * n <= 448 with A in
+ * tensor memory, else 512; rounds in [1, 65536].  MASK_EINVAL outside these,
+ * MASK_ETIMEOUT if completion does not arrive within the library's wait
+ * limit.  Synchronous.
+ */
+mask_status mask_test_tc_mma_cycles(int32_t n, int32_t a_in_tmem, int32_t n_acc, int32_t rounds,
+                                    int64_t *cycles_out);
+
 /* ---- serving: continuous batching over a resident index ----------------
  *
  * The paper answers queries one at a time (§3.3); a service takes a stream

@@ -380,6 +380,10 @@ void cm_merge(const unsigned long long *pair_out, int64_t nq, int P, int K, int6
 void leaf_seed(const float *Xs, const int32_t *xids, const int64_t *leaf_off, int dp,
                const float *Qp, int64_t nq, const int32_t *sel, int P, int K, float *seed_d,
                cudaStream_t s);
+// probe_tc.cu: cycles to issue (cycles[0]) and to complete (cycles[1])
+// rounds x 12 tcgen05 kind::f16 MMAs of M = 128, K = 16 and the given N
+void probe_tc_mma(int n, int a_in_tmem, int n_acc, int rounds, int64_t *cycles_out);
+
 // Work-item shape of the cluster-major scans, chosen by the serving loop's
 // autotuner: queries per item (0: the kernel's widest, cm_item_queries), the
 // kernel (the tensor-core scan where it applies, or the mma.sync scan), and

@@ -973,6 +973,11 @@ mask_status mask_test_bounded_wait(int32_t flag_set, int32_t limit_us, mask_stre
     });
 }
 
+mask_status mask_test_tc_mma_cycles(int32_t n, int32_t a_in_tmem, int32_t n_acc, int32_t rounds,
+                                    int64_t *cycles_out) {
+    return guard([&] { probe_tc_mma(n, a_in_tmem, n_acc, rounds, cycles_out); });
+}
+
 mask_status mask_kmeans_update(const float *X, int64_t n, int32_t d, const int32_t *labels,
                                int32_t k, const float *C_prev, float *C_out,
                                int64_t *counts_out, mask_stream stream) {

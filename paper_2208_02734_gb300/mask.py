@@ -34,6 +34,7 @@ EXPORTED = [
     "mask_kmeans_assign_noalloc", "mask_kmeanspp_csr", "mask_kmeans_assign_csr",
     "mask_kmeans_update_csr", "mask_server_open", "mask_server_submit", "mask_server_poll",
     "mask_server_wait", "mask_server_stats", "mask_server_close", "mask_test_bounded_wait",
+    "mask_test_tc_mma_cycles",
     "mask_test_alloc_count", "mask_grouped_levels", "mask_build_grouped", "mask_descend",
     "mask_relocate", "mask_range_query", "mask_insert", "mask_merge_topk",
 ]
@@ -114,6 +115,7 @@ def load(build_if_stale: bool = True):
             "mask_insert": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
             "mask_merge_topk": (C.c_int, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _vp, _vp]),
             "mask_test_bounded_wait": (C.c_int, [_i32, _i32, _vp]),
+            "mask_test_tc_mma_cycles": (C.c_int, [_i32, _i32, _i32, _i32, _vp]),
             "mask_kmeans_assign_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, _i32, _vp, _vp, _vp]),
             "mask_kmeanspp_csr": (C.c_int, [_vp, _vp, _vp, _i64, _i32, _i32, _u64, _i32, _vp,
                                             _vp, _vp]),
@@ -641,6 +643,15 @@ def mask_launch_count() -> int:
 
 def mask_test_alloc_count() -> int:
     return int(load().mask_test_alloc_count())
+
+
+def mask_test_tc_mma_cycles(n: int, a_in_tmem: bool, n_acc: int, rounds: int):
+    """(issue cycles, completion cycles) of rounds x 12 tcgen05 kind::f16 MMAs
+    of M = 128, N = n, K = 16 on one SM (see include/mask.h)."""
+    out = (C.c_int64 * 2)()
+    _check(load().mask_test_tc_mma_cycles(int(n), 1 if a_in_tmem else 0, int(n_acc), int(rounds),
+                                          C.cast(out, C.c_void_p)), "mask_test_tc_mma_cycles")
+    return int(out[0]), int(out[1])
 
 
 def mask_test_bounded_wait(flag_set: bool, limit_us: int, stream=None) -> str:

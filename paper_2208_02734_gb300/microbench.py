@@ -31,7 +31,8 @@ import numpy as np
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("step", choices=["assign", "update", "kmeanspp", "query", "build",
-                                     "csr_assign", "csr_kmeanspp", "csr_query", "csr_build"])
+                                     "csr_assign", "csr_kmeanspp", "csr_query", "csr_build",
+                                     "mma_probe"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--d", type=int, default=64)
     ap.add_argument("--k", type=int, default=4096)
@@ -54,6 +55,24 @@ def main(argv=None) -> None:
     from . import synth
 
     dev = torch.device("cuda:0")
+    if a.step == "mma_probe":
+        # cycles per tcgen05 kind::f16 MMA (M = 128, K = 16) by N, operand A's
+        # memory and the number of accumulators used round-robin
+        torch.cuda.init()
+        rounds = 256
+        for n in (64, 128, 192, 256):
+            for a_tmem in (False, True):
+                for n_acc in (1, 2):
+                    if n_acc * n > (448 if a_tmem else 512):
+                        continue
+                    issue, done = M.mask_test_tc_mma_cycles(n, a_tmem, n_acc, rounds)
+                    mmas = 12 * rounds
+                    print(json.dumps({"step": "mma_probe", "n": n, "a": "tmem" if a_tmem else "smem",
+                                      "n_acc": n_acc, "cycles_per_mma": round(done / mmas, 1),
+                                      "issue_cycles_per_mma": round(issue / mmas, 1),
+                                      "f16_mac_per_cycle": round(128 * n * 16 * mmas / done)}),
+                          flush=True)
+        return
     levels = [int(v) for v in a.levels.split(",")] if a.levels else [a.k]
     probes = [int(v) for v in a.probes.split(",")] if a.probes else [8] * len(levels)
     rng = np.random.default_rng(1)
