@@ -8,6 +8,8 @@
 // rows are read once per group of up to 16 of its queries, and all distances
 // of the group are computed from shared memory.  Each pair leaves its K best
 // keys; a merge pass then keeps every query's K best over its kept clusters.
+// (Rows of 32 or 64 floats go to the tensor-core scan of query_cm_tc.cu,
+// which shares this file's pair grouping, work items and seed pass.)
 //
 // Every key that can enter a result is computed with the arithmetic of
 // query.cu (one thread per (row, query) pair, sum_t (r_t - q_t)^2 in
@@ -17,7 +19,8 @@
 // tensor cores, 3xTF32) and evaluates a row exactly only where that value,
 // less its rounding bound, can reach the smaller of the pair's current K-th
 // distance and T_q -- the K-th exact distance within the query's nearest kept
-// cluster (a seed pass), which bounds the query's final K-th from above.  Rows
+// cluster, extended over the next kept clusters while those hold fewer than
+// K rows (a seed pass), which bounds the query's final K-th from above.  Rows
 // the test drops cannot be among the query's K nearest, so the result equals
 // the full exact scan's.
 #include <algorithm>
